@@ -1,0 +1,195 @@
+/*
+ * icm.h -- C ABI of the GB300 (sm_103a) library for one time step of the
+ * incompressible Inertial Coupling Method (ICM):
+ *
+ *   F. Balboa Usabiaga, R. Delgado-Buscalioni, B. E. Griffith, A. Donev,
+ *   "Inertial coupling method for particles in an incompressible fluctuating
+ *   fluid", arXiv:1212.6427.
+ *
+ * Blob particles (positions q, velocities u, excess masses m_e, external forces F)
+ * are coupled by a no-slip constraint to a periodic, incompressible, thermally
+ * fluctuating fluid discretised on a staggered (MAC) grid.  One call of
+ * icm_step advances the nine-step scheme of Sec. III.C ("Summary of Algorithm")
+ * once per step entirely on the GPU.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Grid: Nx x Ny x Nz cells of side h, periodic in every direction.  Cell
+ *    (i,j,k) is centred at ((i+1/2)h, (j+1/2)h, (k+1/2)h).  Component v_x of a
+ *    face field sits at (ih, (j+1/2)h, (k+1/2)h), v_y and v_z likewise.
+ *  - A "face field" on the host is a double array of 3*Nx*Ny*Nz values, the three
+ *    components one after the other, each with flat index i + Nx*(j + Ny*k).
+ *  - Blob arrays on the host are double, row-major: pos[n][3], vel[n][3],
+ *    force[n][3], excess_mass[n].
+ *  - All pointers named in a signature are HOST pointers unless the name ends
+ *    in _dev.  The caller owns every host buffer; the library copies what it
+ *    needs before returning and never keeps a host pointer.  The library owns all
+ *    device memory of a simulation (allocated through the allocator set with
+ *    icm_set_default_allocator, else cudaMalloc) and frees it in icm_destroy.
+ *  - Every call is issued on the simulation's CUDA stream.  Calls that return
+ *    host data synchronise that stream; icm_step only enqueues work.
+ *  - Every function returns an icm_status; on failure icm_last_error() gives a
+ *    one-line reason.  A failed call leaves the simulation as it was, except
+ *    ICM_ECUDA, after which the simulation should be destroyed.
+ *  - Not thread safe per simulation: one host thread at a time per icm_sim.
+ */
+#ifndef ICM_H_
+#define ICM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct icm_sim icm_sim;   /* opaque */
+
+typedef enum {
+  ICM_OK = 0,
+  ICM_EINVAL = -1,       /* invalid argument (value, size, NULL where required)      */
+  ICM_ENOMEM = -2,       /* device allocation failed or over the memory budget       */
+  ICM_ECUDA = -3,        /* a CUDA call failed (message in icm_last_error)            */
+  ICM_ECFL = -4,         /* a blob moved more than one cell in a step: |u| dt / h > 1  */
+  ICM_ENONFINITE = -5,   /* a NaN or Inf appeared in the blob state                   */
+  ICM_ETIMEOUT = -6,     /* a bounded device-side wait gave up                        */
+  ICM_EBUSY = -7         /* the request cannot be taken now (e.g. batch slots full)   */
+} icm_status;
+
+/* Flags of icm_create. */
+#define ICM_FLAG_NO_ADVECTION 0x1   /* drop the advective flux (Sec. II.B: no measurable effect) */
+#define ICM_FLAG_SLIP_VISC    0x0   /* slip correction Eq. delta_u_nph_visc (paper's default)   */
+#define ICM_FLAG_SLIP_ZERO    0x2   /* delta u = 0: first-order variant (Sec. III.C)            */
+#define ICM_FLAG_SLIP_FULL    0x4   /* Eq. delta_u_nph: viscous + centring correction           */
+
+/* Allocator used for the device memory of simulations created afterwards.
+ * alloc(ctx, bytes, stream) returns a device pointer aligned to >= 256 bytes or
+ * NULL; free(ctx, ptr, stream) releases it.  Passing NULL for both restores
+ * cudaMalloc/cudaFree.  Process-wide; not thread safe against icm_create. */
+typedef void* (*icm_alloc_fn)(void* ctx, size_t bytes, void* cuda_stream);
+typedef void (*icm_free_fn)(void* ctx, void* ptr, void* cuda_stream);
+icm_status icm_set_default_allocator(icm_alloc_fn alloc, icm_free_fn release, void* ctx);
+
+/* Create a simulation (Sec. III: MAC grid, Peskin kernel, parameters of the
+ * fluid equation Eq. LLNS_incomp_v).
+ *   grid[3]   : Nx, Ny, Nz.  Each side 2^a 3^b, at least 2*kernel and at most 512.
+ *   h         : grid spacing (> 0).        rho : fluid density (> 0).
+ *   eta       : shear viscosity (> 0).     kT  : temperature (>= 0; 0 = deterministic).
+ *   dt        : time step (> 0).
+ *   kernel    : 3 or 4 (Peskin 3-point or 4-point function, Sec. III.A.1).
+ *   seed      : key of the Philox4x32-10 stream of the stochastic stress.
+ *   precision : 32 (FP32 fields, FP64 blob state and momentum bookkeeping) or 64.
+ *   flags     : ICM_FLAG_* above.
+ *   cuda_stream : cudaStream_t to work on, or NULL for a stream the library creates.
+ *   out       : receives the handle.
+ * Errors: ICM_EINVAL for any value outside the ranges above or a non-finite
+ * value; ICM_ENOMEM if the device state cannot be allocated. */
+icm_status icm_create(const int32_t grid[3], double h, double rho, double eta, double kT,
+                      double dt, int32_t kernel, uint64_t seed, int32_t precision,
+                      int32_t flags, void* cuda_stream, icm_sim** out);
+
+/* Release all device memory of the simulation (synchronises its stream). */
+void icm_destroy(icm_sim* sim);
+
+/* One-line description of the last error of this thread (never NULL). */
+const char* icm_last_error(void);
+
+/* Append n blobs (Sec. II.A: position q, velocity u, excess mass m_e = m - rho dV).
+ *   pos  : n*3 positions; wrapped into [0, N h) per axis.
+ *   vel  : n*3 velocities, or NULL for zero.
+ *   excess_mass : n values, each > -m~_f = -(3/2) rho dV with dV = h^3/(sum phi^2)^3
+ *                 (8 h^3 for the 3-point kernel), so that m~ = m_e + m~_f > 0
+ *                 (Appendix A, Eq. rho_eff_inv_incomp).
+ * New blobs get F = 0 and a zero lagged slip term (q^{-1/2} = q^0).
+ * Errors: ICM_EINVAL (n < 0, NULL pos, non-finite input, excess mass out of range). */
+icm_status icm_add_blobs(icm_sim* sim, int64_t n, const double* pos, const double* vel,
+                         const double* excess_mass);
+
+/* Set the external force of every blob (Sec. III.C step 1: F^{n+1/2}), held until
+ * the next call: force[n_total*3].  Errors: ICM_EINVAL (NULL, non-finite). */
+icm_status icm_set_blob_forces(icm_sim* sim, const double* force);
+
+/* Enqueue nsteps ICM steps (Sec. III.C steps 1-9) on the simulation's stream.
+ * Asynchronous: errors detected on the device (ICM_ECFL, ICM_ENONFINITE) are
+ * reported by the next icm_sync / icm_read_state.  Errors: ICM_EINVAL (nsteps<0). */
+icm_status icm_step(icm_sim* sim, int64_t nsteps);
+
+/* Wait for the simulation's stream; report device-side errors raised since the
+ * last report (ICM_ECFL: some blob had |u| dt/h > 1, Sec. III.D; ICM_ENONFINITE). */
+icm_status icm_sync(icm_sim* sim);
+
+/* Read the state at the current time level (synchronises).  Any pointer may be
+ * NULL to skip that output.
+ *   pos[n*3], vel[n*3] : blob positions (in [0, N h)) and velocities.
+ *   fluid_v[3*N]       : face velocities, layout as in the header comment.
+ *   momentum[3]        : total momentum P = rho dV_f sum_k v_k + sum_i m_e,i u_i
+ *                        (Sec. II, after Eq. no_slip), from the FP64 bookkeeping.
+ *   step               : number of steps taken (time level n). */
+icm_status icm_read_state(icm_sim* sim, double* pos, double* vel, double* fluid_v,
+                          double momentum[3], int64_t* step);
+
+/* Overwrite the full state (checkpoint restore).  pos, vel: n_total*3 (required);
+ * fluid_v: 3*N (required); adv_prev: 3*N advective flux div(rho v v^T)^{n-1} of the
+ * previous step (Eq. Adams_Bashforth), or NULL for "no history" (A^{n-1} := A^n);
+ * slip_g: n_total*3 lagged term J^{n-1/2} L dv^{n-1/2} (Eq. delta_u_nph_visc), or
+ * NULL for zero; step: time level n (the Philox counter).  The total fluid
+ * momentum bookkeeping is recomputed from fluid_v in FP64. */
+icm_status icm_write_state(icm_sim* sim, const double* pos, const double* vel,
+                           const double* fluid_v, const double* adv_prev,
+                           const double* slip_g, int64_t step);
+
+/* Read the rest of the state needed to resume bit-for-bit: adv_prev (3*N, or NULL),
+ * slip_g (n_total*3, or NULL), has_history (0 if no step was taken since the last
+ * icm_write_state with adv_prev = NULL). */
+icm_status icm_read_aux(icm_sim* sim, double* adv_prev, double* slip_g, int32_t* has_history);
+
+/* Number of blobs and bytes of device memory the simulation holds. */
+int64_t icm_num_blobs(const icm_sim* sim);
+int64_t icm_device_bytes(const icm_sim* sim);
+
+/* ------------------------------------------------------------------------
+ * Operator-level entry points.  Each runs one operator of the step on the GPU
+ * with the simulation's grid, kernel and parameters, using its scratch buffers
+ * (the simulation's state is not touched), and synchronises.  Inputs and
+ * outputs are host arrays in the layouts above.
+ * ------------------------------------------------------------------------ */
+
+/* J (Sec. III.A.1): out[nb*3] = sum_k phi(q_i - r_k) v_k per component. */
+icm_status icm_op_interpolate(icm_sim* sim, int64_t nb, const double* pos,
+                              const double* fluid_v, double* out);
+
+/* J L (the lagged slip term of Eq. delta_u_nph_visc): out = J (L v), L the
+ * 7-point Laplacian of each component, evaluated as one gather. */
+icm_status icm_op_interpolate_laplacian(icm_sim* sim, int64_t nb, const double* pos,
+                                        const double* fluid_v, double* out);
+
+/* S (Sec. III.A.1): out[3*N] = sum_i dV_f^-1 phi(q_i - r_k) F_i. */
+icm_status icm_op_spread(icm_sim* sim, int64_t nb, const double* pos, const double* force,
+                         double* out);
+
+/* Helmholtz solve + projection by 3D FFT (Sec. III.D): solves
+ * (a I - b L) x + G pi = rhs, D x = 0, i.e. x^ = P^ rhs^ / (a + b |d|^2) with P = I on
+ * the mean.  (a, b) = (rho/dt, eta/2) is Eq. provisional_step-1, (1, 0) the
+ * projection of step 5, (rho, dt eta/2) Eq. dv_eq_modified-1.  a > 0, b >= 0. */
+icm_status icm_op_spectral_solve(icm_sim* sim, double a, double b, const double* rhs,
+                                 double* out);
+
+/* Dense explicit right-hand side of Eq. provisional_step-1 at time level `step`:
+ * r = (rho/dt) v + (eta/2) L v + div Sigma^n - (3/2 A^n - 1/2 A^{n-1}), and A^n.
+ * adv_prev may be NULL (no history).  out_adv may be NULL. */
+icm_status icm_op_explicit_rhs(icm_sim* sim, const double* fluid_v, const double* adv_prev,
+                               int64_t step, double* out_rhs, double* out_adv);
+
+/* The 6 unit normals per cell of step `step` (Sec. III.B.2: W^n), ordered
+ * (xx, yy, zz, xy, xz, yz), out[6*N]. */
+icm_status icm_op_stress_normals(icm_sim* sim, int64_t step, double* out);
+
+/* Raw Philox4x32-10 words: for i < n, counter (ctr0 + i, ctr1, ctr2, ctr3) and
+ * key (key0, key1); out[4*n].  No simulation needed. */
+icm_status icm_op_philox(int64_t n, uint32_t ctr0, uint32_t ctr1, uint32_t ctr2,
+                         uint32_t ctr3, uint32_t key0, uint32_t key1, uint32_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ICM_H_ */

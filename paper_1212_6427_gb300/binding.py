@@ -1,0 +1,322 @@
+"""Thin ctypes binding of libicm (include/icm.h): same names, argument marshalling only.
+
+Every step of the method runs in the CUDA library.  There is no CPU fallback:
+if libicm.so is missing or cannot be loaded, every call raises.
+
+PyTorch provides the device memory (its caching allocator, installed as the
+library's allocator by `use_torch_allocator`) and the CUDA stream of each
+simulation (`Simulation` creates a torch.cuda.Stream unless given one).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libicm.so")
+
+ICM_OK, ICM_EINVAL, ICM_ENOMEM, ICM_ECUDA, ICM_ECFL, ICM_ENONFINITE, ICM_ETIMEOUT, ICM_EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
+STATUS_NAMES = {0: "ICM_OK", -1: "ICM_EINVAL", -2: "ICM_ENOMEM", -3: "ICM_ECUDA", -4: "ICM_ECFL",
+                -5: "ICM_ENONFINITE", -6: "ICM_ETIMEOUT", -7: "ICM_EBUSY"}
+FLAG_NO_ADVECTION, FLAG_SLIP_VISC, FLAG_SLIP_ZERO, FLAG_SLIP_FULL = 0x1, 0x0, 0x2, 0x4
+
+# name -> (restype, argtypes)
+_c_d = ctypes.c_double
+_c_i32 = ctypes.c_int32
+_c_i64 = ctypes.c_int64
+_c_u32 = ctypes.c_uint32
+_c_u64 = ctypes.c_uint64
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+SIGNATURES = {
+    "icm_set_default_allocator": (_c_i32, [_ALLOC_T, _FREE_T, _vp]),
+    "icm_create": (_c_i32, [ctypes.POINTER(_c_i32), _c_d, _c_d, _c_d, _c_d, _c_d, _c_i32, _c_u64, _c_i32, _c_i32,
+                            _vp, ctypes.POINTER(_vp)]),
+    "icm_destroy": (None, [_vp]),
+    "icm_last_error": (ctypes.c_char_p, []),
+    "icm_add_blobs": (_c_i32, [_vp, _c_i64, _dp, _dp, _dp]),
+    "icm_set_blob_forces": (_c_i32, [_vp, _dp]),
+    "icm_step": (_c_i32, [_vp, _c_i64]),
+    "icm_sync": (_c_i32, [_vp]),
+    "icm_read_state": (_c_i32, [_vp, _dp, _dp, _dp, _dp, ctypes.POINTER(_c_i64)]),
+    "icm_write_state": (_c_i32, [_vp, _dp, _dp, _dp, _dp, _dp, _c_i64]),
+    "icm_read_aux": (_c_i32, [_vp, _dp, _dp, ctypes.POINTER(_c_i32)]),
+    "icm_num_blobs": (_c_i64, [_vp]),
+    "icm_device_bytes": (_c_i64, [_vp]),
+    "icm_op_interpolate": (_c_i32, [_vp, _c_i64, _dp, _dp, _dp]),
+    "icm_op_interpolate_laplacian": (_c_i32, [_vp, _c_i64, _dp, _dp, _dp]),
+    "icm_op_spread": (_c_i32, [_vp, _c_i64, _dp, _dp, _dp]),
+    "icm_op_spectral_solve": (_c_i32, [_vp, _c_d, _c_d, _dp, _dp]),
+    "icm_op_explicit_rhs": (_c_i32, [_vp, _dp, _dp, _c_i64, _dp, _dp]),
+    "icm_op_stress_normals": (_c_i32, [_vp, _c_i64, _dp]),
+    "icm_op_philox": (_c_i32, [_c_i64, _c_u32, _c_u32, _c_u32, _c_u32, _c_u32, _c_u32, ctypes.POINTER(_c_u32)]),
+}
+
+_lib = None
+_keep = []
+
+
+class IcmError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, str(status)), message))
+        self.status = status
+
+
+def lib():
+    """Load libicm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libicm.so is not built; run paper_1212_6427_gb300.build.build_library()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != ICM_OK:
+        raise IcmError(status, lib().icm_last_error().decode())
+
+
+def _f64(a, n=None):
+    if a is None:
+        return None, None
+    arr = np.ascontiguousarray(a, dtype=np.float64)
+    if n is not None and arr.size != n:
+        raise ValueError("expected %d values, got %d" % (n, arr.size))
+    return arr, arr.ctypes.data_as(_dp)
+
+
+def _out(n):
+    arr = np.empty(n, dtype=np.float64)
+    return arr, arr.ctypes.data_as(_dp)
+
+
+# ---------------------------------------------------------------------------
+# Allocator: torch's caching allocator provides the library's device memory.
+# ---------------------------------------------------------------------------
+def use_torch_allocator():
+    import torch
+
+    def _alloc(ctx, nbytes, stream):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:  # out of memory -> the library reports ICM_ENOMEM
+            return None
+
+    def _free(ctx, ptr, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    fa, ff = _ALLOC_T(_alloc), _FREE_T(_free)
+    _keep[:] = [fa, ff]
+    _check(lib().icm_set_default_allocator(fa, ff, None))
+
+
+def use_cuda_malloc():
+    _check(lib().icm_set_default_allocator(_ALLOC_T(), _FREE_T(), None))
+
+
+# ---------------------------------------------------------------------------
+# C-ABI functions, same names
+# ---------------------------------------------------------------------------
+def icm_create(grid, h, rho, eta, kT, dt, kernel, seed, precision=32, flags=0, cuda_stream=None):
+    g = (_c_i32 * 3)(*[int(x) for x in grid])
+    out = _vp()
+    _check(lib().icm_create(g, h, rho, eta, kT, dt, int(kernel), int(seed) & 0xFFFFFFFFFFFFFFFF, int(precision),
+                            int(flags), cuda_stream, ctypes.byref(out)))
+    return out
+
+
+def icm_destroy(sim):
+    lib().icm_destroy(sim)
+
+
+def icm_last_error():
+    return lib().icm_last_error().decode()
+
+
+def icm_add_blobs(sim, pos, vel, excess_mass):
+    p, pp = _f64(pos)
+    n = p.size // 3
+    _, vp = _f64(vel, 3 * n)
+    _, mp = _f64(excess_mass, n)
+    _check(lib().icm_add_blobs(sim, n, pp, vp, mp))
+
+
+def icm_set_blob_forces(sim, force):
+    f, fp = _f64(force)
+    _check(lib().icm_set_blob_forces(sim, fp))
+
+
+def icm_step(sim, nsteps=1):
+    _check(lib().icm_step(sim, int(nsteps)))
+
+
+def icm_sync(sim):
+    _check(lib().icm_sync(sim))
+
+
+def icm_num_blobs(sim):
+    return int(lib().icm_num_blobs(sim))
+
+
+def icm_device_bytes(sim):
+    return int(lib().icm_device_bytes(sim))
+
+
+def icm_read_state(sim, ncell, fluid=False, check=True):
+    """Returns (pos (n,3), vel (n,3), fluid_v (3N,) or None, momentum (3,), step, status)."""
+    nb = icm_num_blobs(sim)
+    pos, pp = _out(3 * nb)
+    vel, vp = _out(3 * nb)
+    mom, mp = _out(3)
+    if fluid:
+        fv, fp = _out(3 * ncell)
+    else:
+        fv, fp = None, None
+    step = _c_i64()
+    st = lib().icm_read_state(sim, pp, vp, fp, mp, ctypes.byref(step))
+    if check:
+        _check(st)
+    return pos.reshape(nb, 3), vel.reshape(nb, 3), fv, mom, int(step.value), st
+
+
+def icm_write_state(sim, pos, vel, fluid_v, adv_prev=None, slip_g=None, step=0):
+    nb = icm_num_blobs(sim)
+    _, pp = _f64(pos, 3 * nb)
+    _, vp = _f64(vel, 3 * nb)
+    fv, fp = _f64(fluid_v)
+    _, ap = _f64(adv_prev, fv.size)
+    _, gp = _f64(slip_g, 3 * nb)
+    _check(lib().icm_write_state(sim, pp, vp, fp, ap, gp, int(step)))
+
+
+def icm_read_aux(sim, ncell):
+    nb = icm_num_blobs(sim)
+    adv, ap = _out(3 * ncell)
+    g, gp = _out(3 * nb)
+    hist = _c_i32()
+    _check(lib().icm_read_aux(sim, ap, gp, ctypes.byref(hist)))
+    return adv, g.reshape(nb, 3), int(hist.value)
+
+
+def icm_op_interpolate(sim, pos, fluid_v):
+    p, pp = _f64(pos)
+    n = p.size // 3
+    _, fp = _f64(fluid_v)
+    out, op = _out(3 * n)
+    _check(lib().icm_op_interpolate(sim, n, pp, fp, op))
+    return out.reshape(n, 3)
+
+
+def icm_op_interpolate_laplacian(sim, pos, fluid_v):
+    p, pp = _f64(pos)
+    n = p.size // 3
+    _, fp = _f64(fluid_v)
+    out, op = _out(3 * n)
+    _check(lib().icm_op_interpolate_laplacian(sim, n, pp, fp, op))
+    return out.reshape(n, 3)
+
+
+def icm_op_spread(sim, ncell, pos, force):
+    p, pp = _f64(pos)
+    n = p.size // 3
+    _, fp = _f64(force, 3 * n)
+    out, op = _out(3 * ncell)
+    _check(lib().icm_op_spread(sim, n, pp, fp, op))
+    return out
+
+
+def icm_op_spectral_solve(sim, a, b, rhs):
+    r, rp = _f64(rhs)
+    out, op = _out(r.size)
+    _check(lib().icm_op_spectral_solve(sim, float(a), float(b), rp, op))
+    return out
+
+
+def icm_op_explicit_rhs(sim, fluid_v, adv_prev, step):
+    fv, fp = _f64(fluid_v)
+    _, ap = _f64(adv_prev, fv.size)
+    r, rp = _out(fv.size)
+    a, aq = _out(fv.size)
+    _check(lib().icm_op_explicit_rhs(sim, fp, ap, int(step), rp, aq))
+    return r, a
+
+
+def icm_op_stress_normals(sim, ncell, step):
+    out, op = _out(6 * ncell)
+    _check(lib().icm_op_stress_normals(sim, int(step), op))
+    return out.reshape(6, ncell)
+
+
+def icm_op_philox(n, ctr, key):
+    out = np.empty(4 * max(int(n), 0), dtype=np.uint32)
+    _check(lib().icm_op_philox(int(n), *[int(c) & 0xFFFFFFFF for c in ctr], *[int(k) & 0xFFFFFFFF for k in key],
+                               out.ctypes.data_as(ctypes.POINTER(_c_u32))))
+    return out.reshape(-1, 4)
+
+
+# ---------------------------------------------------------------------------
+# Convenience owner of one simulation (still only marshalling)
+# ---------------------------------------------------------------------------
+class Simulation:
+    """One ICM simulation on the GPU: device memory from torch's caching allocator,
+    work on a dedicated torch.cuda.Stream."""
+
+    def __init__(self, grid, h=1.0, rho=1.0, eta=1.0, kT=0.0, dt=0.05, kernel=4, seed=1, precision=32, flags=0,
+                 stream=None):
+        import torch
+        use_torch_allocator()
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.grid = tuple(int(x) for x in grid)
+        self.ncell = int(np.prod(self.grid))
+        self.precision = precision
+        self.handle = icm_create(self.grid, h, rho, eta, kT, dt, kernel, seed, precision, flags,
+                                 ctypes.c_void_p(self.stream.cuda_stream))
+
+    def close(self):
+        if self.handle is not None:
+            icm_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_blobs(self, pos, vel=None, excess_mass=None):
+        n = np.asarray(pos).size // 3
+        icm_add_blobs(self.handle, pos, vel, np.zeros(n) if excess_mass is None else excess_mass)
+
+    def set_forces(self, force):
+        icm_set_blob_forces(self.handle, force)
+
+    def step(self, n=1):
+        icm_step(self.handle, n)
+
+    def sync(self):
+        icm_sync(self.handle)
+
+    def read(self, fluid=False):
+        pos, vel, fv, mom, step, _ = icm_read_state(self.handle, self.ncell, fluid)
+        return dict(pos=pos, vel=vel, fluid=fv, momentum=mom, step=step)
+
+    def write(self, pos, vel, fluid_v, adv_prev=None, slip_g=None, step=0):
+        icm_write_state(self.handle, pos, vel, fluid_v, adv_prev, slip_g, step)
+
+    def read_aux(self):
+        return icm_read_aux(self.handle, self.ncell)

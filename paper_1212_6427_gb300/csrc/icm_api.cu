@@ -1,0 +1,858 @@
+// Host side of libicm: the C ABI declared in include/icm.h.
+//
+// Owns the device state of a simulation (face fields, Adams-Bashforth history,
+// spectrum scratch, FFT tables, blob arrays, FP64 scalars) and enqueues one ICM
+// step (arXiv:1212.6427, Sec. III.C, steps 1-9) as a fixed sequence of kernels on
+// the simulation's stream.  The sequence is captured once into a CUDA graph; the
+// time level lives in device memory, so the same graph replays every step.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/icm.h"
+#include "icm_internal.h"
+
+using namespace icm;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+icm_alloc_fn g_alloc = nullptr;
+icm_free_fn g_free = nullptr;
+void* g_actx = nullptr;
+
+icm_status fail(icm_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define ICM_CK(call)                                                                                 \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess) return fail(ICM_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+bool side_ok(int n) {
+  if (n < 1) return false;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  return n == 1;
+}
+
+std::vector<int> factor_radices(int n) {
+  std::vector<int> r;
+  int m = n;
+  while (m % 16 == 0) { r.push_back(16); m /= 16; }
+  if (m % 8 == 0) { r.push_back(8); m /= 8; }
+  if (m % 4 == 0) { r.push_back(4); m /= 4; }
+  if (m % 2 == 0) { r.push_back(2); m /= 2; }
+  while (m % 3 == 0) { r.push_back(3); m /= 3; }
+  return r;
+}
+
+double kernel_sum_sq(int kernel) { return kernel == 3 ? 0.5 : 0.375; }
+
+}  // namespace
+
+struct icm_sim {
+  int nx = 0, ny = 0, nz = 0;
+  long long ncell = 0;
+  double h = 1, rho = 1, eta = 1, kT = 0, dt = 1;
+  int kernel = 4, prec = 32, flags = 0, slip = 0;
+  uint64_t seed = 0;
+  bool advection = true;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  icm_alloc_fn alloc = nullptr;
+  icm_free_fn release = nullptr;
+  void* actx = nullptr;
+  std::vector<std::pair<void*, size_t>> allocs;
+  long long bytes = 0;
+
+  // grid state (precision R = float or double)
+  void* v = nullptr;     // face velocities
+  void* adv = nullptr;   // A^{n-1}, overwritten by A^n
+  void* work = nullptr;  // right-hand side / spread sources / dv~ / dv
+  void* spec = nullptr;  // spectrum scratch
+  // FFT plans and symbol tables
+  AxisPlan px, py, pz;
+  void *dx = nullptr, *ddx = nullptr, *dy = nullptr, *ddy = nullptr, *dz = nullptr, *ddz = nullptr;
+  int kx = 0, kxp = 0;
+  // blobs
+  long long nb = 0, cap = 0;
+  double* blob = nullptr;
+  double *q = nullptr, *qh = nullptr, *u = nullptr, *me = nullptr, *f = nullptr, *g = nullptr, *w0 = nullptr,
+         *w1 = nullptr, *jvt = nullptr, *du = nullptr, *dp = nullptr, *cdp = nullptr, *src = nullptr;
+  std::vector<double> me_host, f_host;
+  bool any_me = false, any_force = false;
+  // scalars
+  double* scal = nullptr;
+  long long* step_dev = nullptr;
+  int* hist_dev = nullptr;
+  int* err_dev = nullptr;
+  double* partial = nullptr;
+  static constexpr int kPartials = 1024;
+  // graph of one step
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_ok = false;
+
+  size_t rsize() const { return prec == 32 ? sizeof(float) : sizeof(double); }
+};
+
+namespace {
+
+void* dalloc(icm_sim* s, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 256;
+  if (s->alloc) {
+    p = s->alloc(s->actx, bytes, (void*)s->stream);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) {
+    s->allocs.push_back({p, bytes});
+    s->bytes += (long long)bytes;
+  }
+  return p;
+}
+
+void dfree(icm_sim* s, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < s->allocs.size(); ++i) {
+    if (s->allocs[i].first == p) {
+      s->bytes -= (long long)s->allocs[i].second;
+      s->allocs.erase(s->allocs.begin() + i);
+      break;
+    }
+  }
+  if (s->release)
+    s->release(s->actx, p, (void*)s->stream);
+  else
+    cudaFree(p);
+}
+
+// Scoped temporary device buffer for the operator entry points.
+struct Tmp {
+  icm_sim* s;
+  void* p;
+  Tmp(icm_sim* s_, size_t bytes) : s(s_), p(dalloc(s_, bytes)) {}
+  ~Tmp() {
+    if (p) {
+      cudaStreamSynchronize(s->stream);
+      dfree(s, p);
+    }
+  }
+};
+
+template <typename R>
+FftCtx<R> fft_ctx(const icm_sim* s) {
+  FftCtx<R> f;
+  f.nx = s->nx; f.ny = s->ny; f.nz = s->nz;
+  f.kx = s->kx; f.kxp = s->kxp;
+  f.ncell = s->ncell;
+  f.px = s->px; f.py = s->py; f.pz = s->pz;
+  f.dx = (const cplx_t<R>*)s->dx; f.ddx = (const R*)s->ddx;
+  f.dy = (const cplx_t<R>*)s->dy; f.ddy = (const R*)s->ddy;
+  f.dz = (const cplx_t<R>*)s->dz; f.ddz = (const R*)s->ddz;
+  f.spec = (cplx_t<R>*)s->spec;
+  return f;
+}
+
+GridParams grid_params(const icm_sim* s) {
+  GridParams g;
+  g.nx = s->nx; g.ny = s->ny; g.nz = s->nz;
+  g.ncell = s->ncell;
+  g.h = s->h; g.rho = s->rho; g.eta = s->eta; g.kT = s->kT; g.dt = s->dt;
+  g.key0 = (uint32_t)(s->seed & 0xffffffffu);
+  g.key1 = (uint32_t)(s->seed >> 32);
+  g.advection = s->advection ? 1 : 0;
+  return g;
+}
+
+double blob_volume(const icm_sim* s) {
+  const double q = kernel_sum_sq(s->kernel);
+  return s->h * s->h * s->h / (q * q * q);
+}
+
+BlobParams blob_params(const icm_sim* s) {
+  BlobParams p;
+  p.nx = s->nx; p.ny = s->ny; p.nz = s->nz;
+  p.ncell = s->ncell;
+  p.h = s->h; p.rho = s->rho; p.eta = s->eta; p.dt = s->dt;
+  p.kernel = s->kernel;
+  p.slip = s->slip;
+  p.mtf = 1.5 * s->rho * blob_volume(s);
+  return p;
+}
+
+BlobState blob_state(const icm_sim* s) {
+  BlobState b;
+  b.nb = s->nb;
+  b.q = s->q; b.qh = s->qh; b.u = s->u; b.me = s->me; b.f = s->f; b.g = s->g;
+  b.w0 = s->w0; b.w1 = s->w1; b.jvt = s->jvt; b.du = s->du; b.dp = s->dp; b.cdp = s->cdp; b.src = s->src;
+  b.scal = s->scal;
+  b.err = s->err_dev;
+  return b;
+}
+
+// Build one axis plan: radices, twiddles (long double), digit-reversed order, and
+// the symbol d = (exp(i theta) - 1)/h, |d|^2 = 4 sin^2(theta/2)/h^2 by storage position
+// (x: by natural wavenumber, only nx/2+1 of them).
+icm_status build_axis(icm_sim* s, int n, bool natural, int count, AxisPlan& P, void*& dtab, void*& ddtab) {
+  const std::vector<int> rad = factor_radices(n);
+  P.n = n;
+  P.nstages = (int)rad.size();
+  for (size_t i = 0; i < rad.size(); ++i) P.radix[i] = rad[i];
+  const long double pi = 3.141592653589793238462643383279502884L;
+  std::vector<int> pof(n), fop(n);
+  for (int k = 0; k < n; ++k) {
+    int pos = 0, M = n, rem = k;
+    for (int r : rad) {
+      pos += (M / r) * (rem % r);
+      rem /= r;
+      M /= r;
+    }
+    pof[k] = pos;
+    fop[pos] = k;
+  }
+  const size_t rs = s->rsize();
+  std::vector<unsigned char> tw(2 * rs * n), dt(2 * rs * count), dd(rs * count);
+  auto put = [&](std::vector<unsigned char>& buf, size_t idx, long double val) {
+    if (rs == 4) {
+      float x = (float)val;
+      memcpy(&buf[idx * 4], &x, 4);
+    } else {
+      double x = (double)val;
+      memcpy(&buf[idx * 8], &x, 8);
+    }
+  };
+  for (int m = 0; m < n; ++m) {
+    const long double th = 2.0L * pi * (long double)m / (long double)n;
+    put(tw, 2 * m, cosl(th));
+    put(tw, 2 * m + 1, -sinl(th));
+  }
+  for (int i = 0; i < count; ++i) {
+    const int k = natural ? i : fop[i];
+    const long double th = 2.0L * pi * (long double)k / (long double)n;
+    const long double h = s->h;
+    put(dt, 2 * i, (cosl(th) - 1.0L) / h);
+    put(dt, 2 * i + 1, sinl(th) / h);
+    const long double sn = sinl(0.5L * th);
+    put(dd, i, 4.0L * sn * sn / (h * h));
+  }
+  void* dtw = dalloc(s, tw.size());
+  void* dpof = dalloc(s, sizeof(int) * n);
+  dtab = dalloc(s, dt.size());
+  ddtab = dalloc(s, dd.size());
+  if (!dtw || !dpof || !dtab || !ddtab) return fail(ICM_ENOMEM, "device allocation of FFT tables failed");
+  ICM_CK(cudaMemcpyAsync(dtw, tw.data(), tw.size(), cudaMemcpyHostToDevice, s->stream));
+  ICM_CK(cudaMemcpyAsync(dpof, pof.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s->stream));
+  ICM_CK(cudaMemcpyAsync(dtab, dt.data(), dt.size(), cudaMemcpyHostToDevice, s->stream));
+  ICM_CK(cudaMemcpyAsync(ddtab, dd.data(), dd.size(), cudaMemcpyHostToDevice, s->stream));
+  ICM_CK(cudaStreamSynchronize(s->stream));
+  P.tw = dtw;
+  P.pos_of_freq = (const int*)dpof;
+  return ICM_OK;
+}
+
+bool finite_all(const double* a, long long n) {
+  for (long long i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+void invalidate_graph(icm_sim* s) {
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  s->gexec = nullptr;
+  s->graph_ok = false;
+}
+
+// The nine steps of Sec. III.C for one time level, enqueued on s->stream.
+template <typename R>
+void enqueue_step(icm_sim* s) {
+  cudaStream_t st = s->stream;
+  const FftCtx<R> fc = fft_ctx<R>(s);
+  const GridParams gp = grid_params(s);
+  const BlobParams bp = blob_params(s);
+  const BlobState bs = blob_state(s);
+  R* v = (R*)s->v;
+  R* adv = (R*)s->adv;
+  R* work = (R*)s->work;
+  const double dvf = s->h * s->h * s->h;
+  const double k0scale = 1.0 / (s->rho * dvf);
+  const size_t fbytes = 3 * (size_t)s->ncell * sizeof(R);
+
+  scalars_before_step(s->scal, s->dt, s->rho, dvf, st);
+  // step 1: midpoint predictor (Eq. particle_pred)
+  blob_predict<R>(bp, bs, v, st);
+  // step 2: unperturbed fluid solve (Eq. provisional_step-1)
+  explicit_rhs<R>(gp, v, adv, work, s->step_dev, s->hist_dev, st);
+  if (s->any_force) blob_spread<R>(bp, s->nb, s->qh, s->f, work, st);
+  spectral_solve<R>(fc, work, v, nullptr, OUT_STORE, s->rho / s->dt, 0.5 * s->eta, s->scal + SC_K0, k0scale, st);
+  if (s->any_me) {
+    // step 4: slip correction and momentum change (Eq. delta_u_nph_visc)
+    blob_momentum_change<R>(bp, bs, v, st);
+    // step 5: dv~ = m~_f / (rho (m~_f + m_e)) P S dp
+    cudaMemsetAsync(work, 0, fbytes, st);
+    blob_spread<R>(bp, s->nb, s->qh, s->cdp, work, st);
+    spectral_solve<R>(fc, work, work, nullptr, OUT_STORE, 1.0, 0.0, nullptr, 0.0, st);
+    // steps 6 and 8 (blob side): J dv~, source dp - m_e J dv~, u^{n+1}
+    blob_inertial<R>(bp, bs, work, st);
+    // step 6: (rho - dt/2 eta L) dv + dt grad dpi = S (dp - m_e J dv~); step 7: v = v~ + dv
+    cudaMemsetAsync(work, 0, fbytes, st);
+    blob_spread<R>(bp, s->nb, s->qh, s->src, work, st);
+    spectral_solve<R>(fc, work, v, work, OUT_ADD_AND_STORE2, s->rho, 0.5 * s->dt * s->eta, s->scal + SC_SUMSRC,
+                      k0scale, st);
+    // step 9 and the lagged slip term
+    blob_finish<R>(bp, bs, v, work, true, st);
+  } else {
+    blob_finish<R>(bp, bs, v, nullptr, false, st);
+  }
+  scalars_after_step(s->scal, s->dt, s->rho, dvf, s->any_me, s->step_dev, s->hist_dev, st);
+}
+
+icm_status capture_graph(icm_sim* s) {
+  invalidate_graph(s);
+  cudaGraph_t graph = nullptr;
+  ICM_CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+  if (s->prec == 32)
+    enqueue_step<float>(s);
+  else
+    enqueue_step<double>(s);
+  const cudaError_t e = cudaStreamEndCapture(s->stream, &graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ICM_ECUDA, "graph capture of the step failed: %s", cudaGetErrorString(e));
+  }
+  const cudaError_t e2 = cudaGraphInstantiate(&s->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e2 != cudaSuccess) return fail(ICM_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e2));
+  s->graph_ok = true;
+  return ICM_OK;
+}
+
+icm_status grow_blobs(icm_sim* s, long long need) {
+  if (need <= s->cap) return ICM_OK;
+  long long cap = s->cap > 0 ? s->cap : 64;
+  while (cap < need) cap *= 2;
+  const long long per = 12 * 3 + 1;  // 12 vector arrays + masses
+  double* nbuf = (double*)dalloc(s, sizeof(double) * per * cap);
+  if (!nbuf) return fail(ICM_ENOMEM, "device allocation of %lld blob slots failed", cap);
+  ICM_CK(cudaMemsetAsync(nbuf, 0, sizeof(double) * per * cap, s->stream));
+  double* arrs[12];
+  for (int i = 0; i < 12; ++i) arrs[i] = nbuf + (size_t)i * 3 * cap;
+  double* me = nbuf + (size_t)36 * cap;
+  if (s->nb > 0) {
+    double* old[12] = {s->q, s->qh, s->u, s->f, s->g, s->w0, s->w1, s->jvt, s->du, s->dp, s->cdp, s->src};
+    for (int i = 0; i < 12; ++i)
+      ICM_CK(cudaMemcpyAsync(arrs[i], old[i], sizeof(double) * 3 * s->nb, cudaMemcpyDeviceToDevice, s->stream));
+    ICM_CK(cudaMemcpyAsync(me, s->me, sizeof(double) * s->nb, cudaMemcpyDeviceToDevice, s->stream));
+  }
+  ICM_CK(cudaStreamSynchronize(s->stream));
+  if (s->blob) dfree(s, s->blob);
+  s->blob = nbuf;
+  s->cap = cap;
+  s->q = arrs[0]; s->qh = arrs[1]; s->u = arrs[2]; s->f = arrs[3]; s->g = arrs[4]; s->w0 = arrs[5];
+  s->w1 = arrs[6]; s->jvt = arrs[7]; s->du = arrs[8]; s->dp = arrs[9]; s->cdp = arrs[10]; s->src = arrs[11];
+  s->me = me;
+  return ICM_OK;
+}
+
+void wrap_host(double* p, long long n, const icm_sim* s) {
+  const double L[3] = {s->nx * s->h, s->ny * s->h, s->nz * s->h};
+  for (long long i = 0; i < n; ++i)
+    for (int a = 0; a < 3; ++a) {
+      double x = p[3 * i + a];
+      x -= L[a] * std::floor(x / L[a]);
+      if (x >= L[a]) x -= L[a];
+      if (x < 0) x += L[a];
+      p[3 * i + a] = x;
+    }
+}
+
+// host double[3N] -> device field of precision R (via a temporary double buffer)
+icm_status upload_field(icm_sim* s, const double* host, void* dst) {
+  const long long n = 3 * s->ncell;
+  if (s->prec == 64) {
+    ICM_CK(cudaMemcpyAsync(dst, host, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
+    return ICM_OK;
+  }
+  Tmp t(s, sizeof(double) * n);
+  if (!t.p) return fail(ICM_ENOMEM, "staging allocation failed");
+  ICM_CK(cudaMemcpyAsync(t.p, host, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
+  convert_from_double<float>((const double*)t.p, (float*)dst, n, s->stream);
+  ICM_CK(cudaGetLastError());
+  return ICM_OK;
+}
+
+icm_status download_field(icm_sim* s, const void* src, double* host) {
+  const long long n = 3 * s->ncell;
+  if (s->prec == 64) {
+    ICM_CK(cudaMemcpyAsync(host, src, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream));
+    ICM_CK(cudaStreamSynchronize(s->stream));
+    return ICM_OK;
+  }
+  Tmp t(s, sizeof(double) * n);
+  if (!t.p) return fail(ICM_ENOMEM, "staging allocation failed");
+  convert_to_double<float>((const float*)src, (double*)t.p, n, s->stream);
+  ICM_CK(cudaGetLastError());
+  ICM_CK(cudaMemcpyAsync(host, t.p, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream));
+  ICM_CK(cudaStreamSynchronize(s->stream));
+  return ICM_OK;
+}
+
+icm_status recompute_pbar(icm_sim* s) {
+  if (s->prec == 32)
+    field_sums<float>((const float*)s->v, s->ncell, s->scal + SC_PBAR, s->partial, icm_sim::kPartials, s->stream);
+  else
+    field_sums<double>((const double*)s->v, s->ncell, s->scal + SC_PBAR, s->partial, icm_sim::kPartials, s->stream);
+  ICM_CK(cudaGetLastError());
+  double sums[3];
+  ICM_CK(cudaMemcpyAsync(sums, s->scal + SC_PBAR, sizeof(sums), cudaMemcpyDeviceToHost, s->stream));
+  ICM_CK(cudaStreamSynchronize(s->stream));
+  const double m = s->rho * s->h * s->h * s->h;
+  for (int a = 0; a < 3; ++a) sums[a] *= m;
+  ICM_CK(cudaMemcpyAsync(s->scal + SC_PBAR, sums, sizeof(sums), cudaMemcpyHostToDevice, s->stream));
+  ICM_CK(cudaStreamSynchronize(s->stream));
+  return ICM_OK;
+}
+
+icm_status check_device_errors(icm_sim* s) {
+  int err = 0;
+  ICM_CK(cudaMemcpyAsync(&err, s->err_dev, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  ICM_CK(cudaStreamSynchronize(s->stream));
+  if (err) {
+    ICM_CK(cudaMemsetAsync(s->err_dev, 0, sizeof(int), s->stream));
+    ICM_CK(cudaStreamSynchronize(s->stream));
+    if (err & DEV_ERR_NONFINITE) return fail(ICM_ENONFINITE, "a non-finite blob position or velocity appeared");
+    return fail(ICM_ECFL, "a blob moved more than one cell in a step (|u| dt / h > 1)");
+  }
+  return ICM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+icm_status icm_set_default_allocator(icm_alloc_fn alloc, icm_free_fn release, void* ctx) {
+  if ((alloc == nullptr) != (release == nullptr)) return fail(ICM_EINVAL, "allocator needs both alloc and free");
+  g_alloc = alloc;
+  g_free = release;
+  g_actx = ctx;
+  return ICM_OK;
+}
+
+const char* icm_last_error(void) { return g_err.c_str(); }
+
+icm_status icm_create(const int32_t grid[3], double h, double rho, double eta, double kT, double dt, int32_t kernel,
+                      uint64_t seed, int32_t precision, int32_t flags, void* cuda_stream, icm_sim** out) {
+  if (!grid || !out) return fail(ICM_EINVAL, "grid and out must not be NULL");
+  *out = nullptr;
+  if (kernel != 3 && kernel != 4) return fail(ICM_EINVAL, "kernel must be 3 or 4, got %d", kernel);
+  for (int a = 0; a < 3; ++a) {
+    if (!side_ok(grid[a]) || grid[a] < 2 * kernel || grid[a] > kMaxSide)
+      return fail(ICM_EINVAL, "grid side %d must be 2^a 3^b in [%d, %d]", grid[a], 2 * kernel, kMaxSide);
+  }
+  const double vals[5] = {h, rho, eta, kT, dt};
+  for (double x : vals)
+    if (!std::isfinite(x)) return fail(ICM_EINVAL, "non-finite parameter");
+  if (h <= 0 || rho <= 0 || eta <= 0 || dt <= 0) return fail(ICM_EINVAL, "h, rho, eta and dt must be > 0");
+  if (kT < 0) return fail(ICM_EINVAL, "kT must be >= 0");
+  if (precision != 32 && precision != 64) return fail(ICM_EINVAL, "precision must be 32 or 64");
+  if (flags & ~(ICM_FLAG_NO_ADVECTION | ICM_FLAG_SLIP_ZERO | ICM_FLAG_SLIP_FULL))
+    return fail(ICM_EINVAL, "unknown flag bits 0x%x", flags);
+  if ((flags & ICM_FLAG_SLIP_ZERO) && (flags & ICM_FLAG_SLIP_FULL))
+    return fail(ICM_EINVAL, "choose one slip correction");
+
+  icm_sim* s = new icm_sim();
+  s->nx = grid[0]; s->ny = grid[1]; s->nz = grid[2];
+  s->ncell = (long long)s->nx * s->ny * s->nz;
+  s->h = h; s->rho = rho; s->eta = eta; s->kT = kT; s->dt = dt;
+  s->kernel = kernel; s->seed = seed; s->prec = precision; s->flags = flags;
+  s->advection = !(flags & ICM_FLAG_NO_ADVECTION);
+  s->slip = (flags & ICM_FLAG_SLIP_ZERO) ? 1 : ((flags & ICM_FLAG_SLIP_FULL) ? 2 : 0);
+  s->alloc = g_alloc; s->release = g_free; s->actx = g_actx;
+  if (cuda_stream) {
+    s->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete s;
+      return fail(ICM_ECUDA, "cudaStreamCreate failed");
+    }
+    s->own_stream = true;
+  }
+  fft_prepare();
+  grid_prepare();
+  s->kx = s->nx / 2 + 1;
+  s->kxp = (s->kx + 15) / 16 * 16;
+  const size_t rs = s->rsize();
+  const size_t fbytes = 3 * (size_t)s->ncell * rs;
+  s->v = dalloc(s, fbytes);
+  s->adv = dalloc(s, fbytes);
+  s->work = dalloc(s, fbytes);
+  s->spec = dalloc(s, 3 * (size_t)s->nz * s->ny * s->kxp * 2 * rs);
+  s->scal = (double*)dalloc(s, sizeof(double) * SC_COUNT);
+  s->step_dev = (long long*)dalloc(s, 256);
+  s->hist_dev = (int*)dalloc(s, 256);
+  s->err_dev = (int*)dalloc(s, 256);
+  s->partial = (double*)dalloc(s, sizeof(double) * 3 * icm_sim::kPartials);
+  if (!s->v || !s->adv || !s->work || !s->spec || !s->scal || !s->step_dev || !s->hist_dev || !s->err_dev ||
+      !s->partial) {
+    icm_destroy(s);
+    return fail(ICM_ENOMEM, "device allocation of %.1f MB of grid state failed", (4.0 * fbytes) / 1e6);
+  }
+  icm_status st = ICM_OK;
+  if ((st = build_axis(s, s->nx, true, s->kx, s->px, s->dx, s->ddx)) != ICM_OK ||
+      (st = build_axis(s, s->ny, false, s->ny, s->py, s->dy, s->ddy)) != ICM_OK ||
+      (st = build_axis(s, s->nz, false, s->nz, s->pz, s->dz, s->ddz)) != ICM_OK) {
+    const std::string msg = g_err;
+    icm_destroy(s);
+    return fail(st, "%s", msg.c_str());
+  }
+  cudaMemsetAsync(s->v, 0, fbytes, s->stream);
+  cudaMemsetAsync(s->adv, 0, fbytes, s->stream);
+  cudaMemsetAsync(s->work, 0, fbytes, s->stream);
+  cudaMemsetAsync(s->scal, 0, sizeof(double) * SC_COUNT, s->stream);
+  cudaMemsetAsync(s->step_dev, 0, 256, s->stream);
+  cudaMemsetAsync(s->hist_dev, 0, 256, s->stream);
+  cudaMemsetAsync(s->err_dev, 0, 256, s->stream);
+  const cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) {
+    icm_destroy(s);
+    return fail(ICM_ECUDA, "initialisation failed: %s", cudaGetErrorString(e));
+  }
+  *out = s;
+  return ICM_OK;
+}
+
+void icm_destroy(icm_sim* s) {
+  if (!s) return;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  invalidate_graph(s);
+  while (!s->allocs.empty()) dfree(s, s->allocs.back().first);
+  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+  delete s;
+}
+
+icm_status icm_add_blobs(icm_sim* s, int64_t n, const double* pos, const double* vel, const double* excess_mass) {
+  if (!s) return fail(ICM_EINVAL, "NULL simulation");
+  if (n < 0) return fail(ICM_EINVAL, "n must be >= 0");
+  if (n == 0) return ICM_OK;
+  if (!pos || !excess_mass) return fail(ICM_EINVAL, "pos and excess_mass are required");
+  if (!finite_all(pos, 3 * n) || !finite_all(excess_mass, n) || (vel && !finite_all(vel, 3 * n)))
+    return fail(ICM_EINVAL, "non-finite blob input");
+  const double mtf = 1.5 * s->rho * blob_volume(s);
+  for (int64_t i = 0; i < n; ++i)
+    if (!(excess_mass[i] > -mtf)) return fail(ICM_EINVAL, "excess mass %g <= -m~_f = %g", excess_mass[i], -mtf);
+  if (vel)
+    for (int64_t i = 0; i < 3 * n; ++i)
+      if (std::fabs(vel[i]) * s->dt > s->h) return fail(ICM_ECFL, "blob velocity %g gives |u| dt / h > 1", vel[i]);
+  icm_status st = grow_blobs(s, s->nb + n);
+  if (st != ICM_OK) return st;
+  std::vector<double> p(pos, pos + 3 * n);
+  wrap_host(p.data(), n, s);
+  ICM_CK(cudaMemcpyAsync(s->q + 3 * s->nb, p.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s->stream));
+  ICM_CK(cudaMemcpyAsync(s->qh + 3 * s->nb, p.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s->stream));
+  if (vel)
+    ICM_CK(cudaMemcpyAsync(s->u + 3 * s->nb, vel, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s->stream));
+  else
+    ICM_CK(cudaMemsetAsync(s->u + 3 * s->nb, 0, sizeof(double) * 3 * n, s->stream));
+  ICM_CK(cudaMemsetAsync(s->f + 3 * s->nb, 0, sizeof(double) * 3 * n, s->stream));
+  ICM_CK(cudaMemsetAsync(s->g + 3 * s->nb, 0, sizeof(double) * 3 * n, s->stream));
+  ICM_CK(cudaMemcpyAsync(s->me + s->nb, excess_mass, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
+  ICM_CK(cudaStreamSynchronize(s->stream));
+  s->me_host.insert(s->me_host.end(), excess_mass, excess_mass + n);
+  s->f_host.resize(3 * (s->nb + n), 0.0);
+  s->nb += n;
+  bool any = false;
+  for (double m : s->me_host) any |= (m != 0.0);
+  s->any_me = any;
+  invalidate_graph(s);
+  return ICM_OK;
+}
+
+icm_status icm_set_blob_forces(icm_sim* s, const double* force) {
+  if (!s) return fail(ICM_EINVAL, "NULL simulation");
+  if (s->nb == 0) return ICM_OK;
+  if (!force) return fail(ICM_EINVAL, "force must not be NULL");
+  if (!finite_all(force, 3 * s->nb)) return fail(ICM_EINVAL, "non-finite force");
+  // FP64 compensated total force for the momentum bookkeeping
+  double sum[3] = {0, 0, 0}, c[3] = {0, 0, 0};
+  bool any = false;
+  for (long long i = 0; i < s->nb; ++i)
+    for (int a = 0; a < 3; ++a) {
+      const double y = force[3 * i + a] - c[a];
+      const double t = sum[a] + y;
+      c[a] = (t - sum[a]) - y;
+      sum[a] = t;
+      any |= force[3 * i + a] != 0.0;
+    }
+  ICM_CK(cudaMemcpyAsync(s->f, force, sizeof(double) * 3 * s->nb, cudaMemcpyHostToDevice, s->stream));
+  ICM_CK(cudaMemcpyAsync(s->scal + SC_SUMF, sum, sizeof(sum), cudaMemcpyHostToDevice, s->stream));
+  if (any != s->any_force) {
+    s->any_force = any;
+    invalidate_graph(s);
+  }
+  // the copies read pageable host memory: they have completed when this returns
+  return ICM_OK;
+}
+
+icm_status icm_step(icm_sim* s, int64_t nsteps) {
+  if (!s) return fail(ICM_EINVAL, "NULL simulation");
+  if (nsteps < 0) return fail(ICM_EINVAL, "nsteps must be >= 0");
+  if (nsteps == 0) return ICM_OK;
+  if (!s->graph_ok) {
+    icm_status st = capture_graph(s);
+    if (st != ICM_OK) return st;
+  }
+  for (int64_t i = 0; i < nsteps; ++i) ICM_CK(cudaGraphLaunch(s->gexec, s->stream));
+  return ICM_OK;
+}
+
+icm_status icm_sync(icm_sim* s) {
+  if (!s) return fail(ICM_EINVAL, "NULL simulation");
+  ICM_CK(cudaStreamSynchronize(s->stream));
+  return check_device_errors(s);
+}
+
+icm_status icm_read_state(icm_sim* s, double* pos, double* vel, double* fluid_v, double momentum[3], int64_t* step) {
+  if (!s) return fail(ICM_EINVAL, "NULL simulation");
+  ICM_CK(cudaStreamSynchronize(s->stream));
+  const icm_status dev = check_device_errors(s);
+  std::vector<double> u(3 * s->nb);
+  if (pos && s->nb) ICM_CK(cudaMemcpyAsync(pos, s->q, sizeof(double) * 3 * s->nb, cudaMemcpyDeviceToHost, s->stream));
+  if (s->nb) ICM_CK(cudaMemcpyAsync(u.data(), s->u, sizeof(double) * 3 * s->nb, cudaMemcpyDeviceToHost, s->stream));
+  double pbar[3];
+  long long stp = 0;
+  ICM_CK(cudaMemcpyAsync(pbar, s->scal + SC_PBAR, sizeof(pbar), cudaMemcpyDeviceToHost, s->stream));
+  ICM_CK(cudaMemcpyAsync(&stp, s->step_dev, sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
+  ICM_CK(cudaStreamSynchronize(s->stream));
+  if (fluid_v) {
+    const icm_status st = download_field(s, s->v, fluid_v);
+    if (st != ICM_OK) return st;
+  }
+  if (vel && s->nb) memcpy(vel, u.data(), sizeof(double) * 3 * s->nb);
+  if (momentum) {
+    for (int a = 0; a < 3; ++a) {
+      double sum = pbar[a], c = 0.0;
+      for (long long i = 0; i < s->nb; ++i) {
+        const double y = s->me_host[i] * u[3 * i + a] - c;
+        const double t = sum + y;
+        c = (t - sum) - y;
+        sum = t;
+      }
+      momentum[a] = sum;
+    }
+  }
+  if (step) *step = stp;
+  return dev;
+}
+
+icm_status icm_write_state(icm_sim* s, const double* pos, const double* vel, const double* fluid_v,
+                           const double* adv_prev, const double* slip_g, int64_t step) {
+  if (!s) return fail(ICM_EINVAL, "NULL simulation");
+  if (!fluid_v || (s->nb > 0 && (!pos || !vel))) return fail(ICM_EINVAL, "pos, vel and fluid_v are required");
+  if (step < 0) return fail(ICM_EINVAL, "step must be >= 0");
+  const long long n3 = 3 * s->ncell;
+  if (!finite_all(fluid_v, n3) || (adv_prev && !finite_all(adv_prev, n3)) ||
+      (s->nb && (!finite_all(pos, 3 * s->nb) || !finite_all(vel, 3 * s->nb))) ||
+      (slip_g && !finite_all(slip_g, 3 * s->nb)))
+    return fail(ICM_EINVAL, "non-finite state");
+  icm_status st = upload_field(s, fluid_v, s->v);
+  if (st != ICM_OK) return st;
+  if (adv_prev) {
+    if ((st = upload_field(s, adv_prev, s->adv)) != ICM_OK) return st;
+  }
+  const int hist = adv_prev ? 1 : 0;
+  ICM_CK(cudaMemcpyAsync(s->hist_dev, &hist, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+  const long long stp = step;
+  ICM_CK(cudaMemcpyAsync(s->step_dev, &stp, sizeof(long long), cudaMemcpyHostToDevice, s->stream));
+  if (s->nb) {
+    std::vector<double> p(pos, pos + 3 * s->nb);
+    wrap_host(p.data(), s->nb, s);
+    ICM_CK(cudaMemcpyAsync(s->q, p.data(), sizeof(double) * 3 * s->nb, cudaMemcpyHostToDevice, s->stream));
+    ICM_CK(cudaMemcpyAsync(s->u, vel, sizeof(double) * 3 * s->nb, cudaMemcpyHostToDevice, s->stream));
+    if (slip_g)
+      ICM_CK(cudaMemcpyAsync(s->g, slip_g, sizeof(double) * 3 * s->nb, cudaMemcpyHostToDevice, s->stream));
+    else
+      ICM_CK(cudaMemsetAsync(s->g, 0, sizeof(double) * 3 * s->nb, s->stream));
+  }
+  ICM_CK(cudaMemsetAsync(s->err_dev, 0, sizeof(int), s->stream));
+  ICM_CK(cudaStreamSynchronize(s->stream));
+  return recompute_pbar(s);
+}
+
+icm_status icm_read_aux(icm_sim* s, double* adv_prev, double* slip_g, int32_t* has_history) {
+  if (!s) return fail(ICM_EINVAL, "NULL simulation");
+  ICM_CK(cudaStreamSynchronize(s->stream));
+  if (adv_prev) {
+    const icm_status st = download_field(s, s->adv, adv_prev);
+    if (st != ICM_OK) return st;
+  }
+  if (slip_g && s->nb)
+    ICM_CK(cudaMemcpyAsync(slip_g, s->g, sizeof(double) * 3 * s->nb, cudaMemcpyDeviceToHost, s->stream));
+  int hist = 0;
+  ICM_CK(cudaMemcpyAsync(&hist, s->hist_dev, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  ICM_CK(cudaStreamSynchronize(s->stream));
+  if (has_history) *has_history = hist;
+  return ICM_OK;
+}
+
+int64_t icm_num_blobs(const icm_sim* s) { return s ? s->nb : -1; }
+int64_t icm_device_bytes(const icm_sim* s) { return s ? s->bytes : -1; }
+
+// ---------------------------------------------------------------------------
+// Operator-level entry points
+// ---------------------------------------------------------------------------
+
+icm_status icm_op_interpolate(icm_sim* s, int64_t nb, const double* pos, const double* fluid_v, double* out) {
+  if (!s || nb < 0 || (nb > 0 && (!pos || !fluid_v || !out))) return fail(ICM_EINVAL, "bad arguments");
+  if (nb == 0) return ICM_OK;
+  std::vector<double> p(pos, pos + 3 * nb);
+  wrap_host(p.data(), nb, s);
+  Tmp dq(s, sizeof(double) * 3 * nb), dout(s, sizeof(double) * 3 * nb);
+  if (!dq.p || !dout.p) return fail(ICM_ENOMEM, "allocation failed");
+  icm_status st = upload_field(s, fluid_v, s->work);
+  if (st != ICM_OK) return st;
+  ICM_CK(cudaMemcpyAsync(dq.p, p.data(), sizeof(double) * 3 * nb, cudaMemcpyHostToDevice, s->stream));
+  const BlobParams bp = blob_params(s);
+  if (s->prec == 32)
+    blob_interp<float>(bp, nb, (const double*)dq.p, (const float*)s->work, false, (double*)dout.p, s->stream);
+  else
+    blob_interp<double>(bp, nb, (const double*)dq.p, (const double*)s->work, false, (double*)dout.p, s->stream);
+  ICM_CK(cudaGetLastError());
+  ICM_CK(cudaMemcpyAsync(out, dout.p, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost, s->stream));
+  ICM_CK(cudaStreamSynchronize(s->stream));
+  return ICM_OK;
+}
+
+icm_status icm_op_interpolate_laplacian(icm_sim* s, int64_t nb, const double* pos, const double* fluid_v,
+                                        double* out) {
+  if (!s || nb < 0 || (nb > 0 && (!pos || !fluid_v || !out))) return fail(ICM_EINVAL, "bad arguments");
+  if (nb == 0) return ICM_OK;
+  std::vector<double> p(pos, pos + 3 * nb);
+  wrap_host(p.data(), nb, s);
+  Tmp dq(s, sizeof(double) * 3 * nb), dout(s, sizeof(double) * 3 * nb);
+  if (!dq.p || !dout.p) return fail(ICM_ENOMEM, "allocation failed");
+  icm_status st = upload_field(s, fluid_v, s->work);
+  if (st != ICM_OK) return st;
+  ICM_CK(cudaMemcpyAsync(dq.p, p.data(), sizeof(double) * 3 * nb, cudaMemcpyHostToDevice, s->stream));
+  const BlobParams bp = blob_params(s);
+  if (s->prec == 32)
+    blob_interp<float>(bp, nb, (const double*)dq.p, (const float*)s->work, true, (double*)dout.p, s->stream);
+  else
+    blob_interp<double>(bp, nb, (const double*)dq.p, (const double*)s->work, true, (double*)dout.p, s->stream);
+  ICM_CK(cudaGetLastError());
+  ICM_CK(cudaMemcpyAsync(out, dout.p, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost, s->stream));
+  ICM_CK(cudaStreamSynchronize(s->stream));
+  return ICM_OK;
+}
+
+icm_status icm_op_spread(icm_sim* s, int64_t nb, const double* pos, const double* force, double* out) {
+  if (!s || nb < 0 || !out || (nb > 0 && (!pos || !force))) return fail(ICM_EINVAL, "bad arguments");
+  std::vector<double> p(pos ? pos : (const double*)nullptr, pos ? pos + 3 * nb : (const double*)nullptr);
+  wrap_host(p.data(), nb, s);
+  Tmp dq(s, sizeof(double) * 3 * (nb + 1)), df(s, sizeof(double) * 3 * (nb + 1));
+  if (!dq.p || !df.p) return fail(ICM_ENOMEM, "allocation failed");
+  ICM_CK(cudaMemsetAsync(s->work, 0, 3 * (size_t)s->ncell * s->rsize(), s->stream));
+  if (nb > 0) {
+    ICM_CK(cudaMemcpyAsync(dq.p, p.data(), sizeof(double) * 3 * nb, cudaMemcpyHostToDevice, s->stream));
+    ICM_CK(cudaMemcpyAsync(df.p, force, sizeof(double) * 3 * nb, cudaMemcpyHostToDevice, s->stream));
+    const BlobParams bp = blob_params(s);
+    if (s->prec == 32)
+      blob_spread<float>(bp, nb, (const double*)dq.p, (const double*)df.p, (float*)s->work, s->stream);
+    else
+      blob_spread<double>(bp, nb, (const double*)dq.p, (const double*)df.p, (double*)s->work, s->stream);
+    ICM_CK(cudaGetLastError());
+  }
+  return download_field(s, s->work, out);
+}
+
+icm_status icm_op_spectral_solve(icm_sim* s, double a, double b, const double* rhs, double* out) {
+  if (!s || !rhs || !out) return fail(ICM_EINVAL, "bad arguments");
+  if (!(a > 0) || !(b >= 0) || !std::isfinite(a) || !std::isfinite(b)) return fail(ICM_EINVAL, "need a > 0, b >= 0");
+  icm_status st = upload_field(s, rhs, s->work);
+  if (st != ICM_OK) return st;
+  if (s->prec == 32)
+    spectral_solve<float>(fft_ctx<float>(s), (const float*)s->work, (float*)s->work, nullptr, OUT_STORE, a, b, nullptr,
+                          0.0, s->stream);
+  else
+    spectral_solve<double>(fft_ctx<double>(s), (const double*)s->work, (double*)s->work, nullptr, OUT_STORE, a, b,
+                           nullptr, 0.0, s->stream);
+  ICM_CK(cudaGetLastError());
+  return download_field(s, s->work, out);
+}
+
+icm_status icm_op_explicit_rhs(icm_sim* s, const double* fluid_v, const double* adv_prev, int64_t step,
+                               double* out_rhs, double* out_adv) {
+  if (!s || !fluid_v || !out_rhs || step < 0) return fail(ICM_EINVAL, "bad arguments");
+  const size_t fb = 3 * (size_t)s->ncell * s->rsize();
+  Tmp tv(s, fb), ta(s, fb), tc(s, 256);
+  if (!tv.p || !ta.p || !tc.p) return fail(ICM_ENOMEM, "allocation failed");
+  icm_status st = upload_field(s, fluid_v, tv.p);
+  if (st != ICM_OK) return st;
+  if (adv_prev) {
+    if ((st = upload_field(s, adv_prev, ta.p)) != ICM_OK) return st;
+  } else {
+    ICM_CK(cudaMemsetAsync(ta.p, 0, fb, s->stream));
+  }
+  long long hdr[2] = {step, adv_prev ? 1 : 0};
+  int hist = adv_prev ? 1 : 0;
+  ICM_CK(cudaMemcpyAsync(tc.p, &hdr[0], sizeof(long long), cudaMemcpyHostToDevice, s->stream));
+  ICM_CK(cudaMemcpyAsync((char*)tc.p + 64, &hist, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+  const GridParams gp = grid_params(s);
+  if (s->prec == 32)
+    explicit_rhs<float>(gp, (const float*)tv.p, (float*)ta.p, (float*)s->work, (const long long*)tc.p,
+                        (const int*)((char*)tc.p + 64), s->stream);
+  else
+    explicit_rhs<double>(gp, (const double*)tv.p, (double*)ta.p, (double*)s->work, (const long long*)tc.p,
+                         (const int*)((char*)tc.p + 64), s->stream);
+  ICM_CK(cudaGetLastError());
+  if ((st = download_field(s, s->work, out_rhs)) != ICM_OK) return st;
+  if (out_adv) return download_field(s, ta.p, out_adv);
+  return ICM_OK;
+}
+
+icm_status icm_op_stress_normals(icm_sim* s, int64_t step, double* out) {
+  if (!s || !out || step < 0) return fail(ICM_EINVAL, "bad arguments");
+  const size_t n6 = 6 * (size_t)s->ncell;
+  Tmp t(s, n6 * s->rsize()), td(s, n6 * sizeof(double));
+  if (!t.p || !td.p) return fail(ICM_ENOMEM, "allocation failed");
+  const GridParams gp = grid_params(s);
+  if (s->prec == 32) {
+    stress_normals<float>(gp, step, (float*)t.p, s->stream);
+    convert_to_double<float>((const float*)t.p, (double*)td.p, (long long)n6, s->stream);
+  } else {
+    stress_normals<double>(gp, step, (double*)td.p, s->stream);
+  }
+  ICM_CK(cudaGetLastError());
+  ICM_CK(cudaMemcpyAsync(out, td.p, n6 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  ICM_CK(cudaStreamSynchronize(s->stream));
+  return ICM_OK;
+}
+
+icm_status icm_op_philox(int64_t n, uint32_t ctr0, uint32_t ctr1, uint32_t ctr2, uint32_t ctr3, uint32_t key0,
+                         uint32_t key1, uint32_t* out) {
+  if (n < 0 || (n > 0 && !out)) return fail(ICM_EINVAL, "bad arguments");
+  if (n == 0) return ICM_OK;
+  uint32_t* d = nullptr;
+  ICM_CK(cudaMalloc(&d, sizeof(uint32_t) * 4 * n));
+  philox_words(n, ctr0, ctr1, ctr2, ctr3, key0, key1, d, nullptr);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpy(out, d, sizeof(uint32_t) * 4 * n, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(ICM_ECUDA, "philox kernel: %s", cudaGetErrorString(e));
+  return ICM_OK;
+}
+
+}  // extern "C"

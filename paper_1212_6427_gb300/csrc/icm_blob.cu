@@ -1,0 +1,386 @@
+// Blob kernels of the ICM step (arXiv:1212.6427, Sec. III.A.1 and III.C).
+//
+// One warp per blob.  Lanes 0-8 build the 1-D Peskin stencils of the three
+// staggered velocity components (first node and weights per axis, from the FP64
+// position); the warp then walks the 3 x w^3 nodes with the x index fastest so
+// that a group of lanes reads consecutive addresses, and reduces with shuffles.
+//   interpolation (J v)_i = sum_k phi(q_i - r_k) v_k            (gather)
+//   spreading     (S F)_k = dV_f^-1 sum_i phi(q_i - r_k) F_i    (atomicAdd scatter)
+// Blob state (positions, velocities, masses, lagged slip terms) is FP64 in both
+// precision modes; only the grid values are R.
+#include "icm_internal.h"
+
+namespace icm {
+namespace {
+
+constexpr int kWarps = 8;
+
+template <typename R, int K>
+struct WarpStencil {
+  int first[3][3];       // [component][axis] first node, wrapped into [0, n)
+  R w[3][3][K + 2];      // weights; the Laplacian form uses indices 0..K+1 (zero padded)
+  R d2[3][3][K + 2];     // second differences of the zero-padded weights
+};
+
+__device__ __forceinline__ double wrap_pos(double x, double L) {
+  double y = x - L * floor(x / L);
+  if (y >= L) y -= L;
+  if (y < 0.0) y += L;
+  return y;
+}
+
+// Lanes 0..8 fill the stencil of blob position q; `ext` adds the padded form.
+template <typename R, int K>
+__device__ __forceinline__ void build_stencil(WarpStencil<R, K>& S, const double q[3], const BlobParams& p, bool ext,
+                                              int lane) {
+  if (lane < 9) {
+    const int comp = lane / 3, ax = lane % 3;
+    const int n = ax == 0 ? p.nx : (ax == 1 ? p.ny : p.nz);
+    const double off = (ax == comp) ? 0.0 : 0.5;
+    const double s = q[ax] / p.h - off;
+    const long long f = Peskin<R, K>::first(s);
+    R w[K];
+#pragma unroll
+    for (int a = 0; a < K; ++a) w[a] = Peskin<R, K>::phi((R)(s - (double)(f + a)));
+    if (!ext) {
+      long long fw = f % n;
+      if (fw < 0) fw += n;
+      S.first[comp][ax] = (int)fw;
+#pragma unroll
+      for (int a = 0; a < K; ++a) S.w[comp][ax][a] = w[a];
+    } else {
+      long long fw = (f - 1) % n;
+      if (fw < 0) fw += n;
+      S.first[comp][ax] = (int)fw;
+      R we[K + 2];
+      we[0] = R(0);
+      we[K + 1] = R(0);
+#pragma unroll
+      for (int a = 0; a < K; ++a) we[a + 1] = w[a];
+#pragma unroll
+      for (int a = 0; a < K + 2; ++a) {
+        const R lo = a > 0 ? we[a - 1] : R(0);
+        const R hi = a < K + 1 ? we[a + 1] : R(0);
+        S.w[comp][ax][a] = we[a];
+        S.d2[comp][ax][a] = lo - R(2) * we[a] + hi;
+      }
+    }
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ int wrap_add(int a, int b, int n) {
+  const int t = a + b;
+  return t >= n ? t - n : t;
+}
+
+template <typename R>
+__device__ __forceinline__ R warp_sum(R x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// (J field) for the three components; result valid in every lane.
+template <typename R, int K>
+__device__ __forceinline__ void gather(const WarpStencil<R, K>& S, const R* __restrict__ field, const BlobParams& p,
+                                       int lane, double out[3]) {
+  constexpr int W3 = K * K * K;
+  R acc[3] = {R(0), R(0), R(0)};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const R* f = field + c * p.ncell;
+    for (int it = lane; it < W3; it += 32) {
+      const int a = it % K, b = (it / K) % K, cz = it / (K * K);
+      const int ix = wrap_add(S.first[c][0], a, p.nx);
+      const int iy = wrap_add(S.first[c][1], b, p.ny);
+      const int iz = wrap_add(S.first[c][2], cz, p.nz);
+      const R wgt = S.w[c][0][a] * S.w[c][1][b] * S.w[c][2][cz];
+      acc[c] += wgt * f[ix + (long long)p.nx * (iy + (long long)p.ny * iz)];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) out[c] = (double)warp_sum(acc[c]);
+}
+
+// J (L field): gather with the discrete Laplacian of the weights (L is symmetric).
+template <typename R, int K>
+__device__ __forceinline__ void gather_lap(const WarpStencil<R, K>& S, const R* __restrict__ field,
+                                           const BlobParams& p, int lane, double out[3]) {
+  constexpr int E = K + 2, E3 = E * E * E;
+  const R inv_h2 = (R)(1.0 / (p.h * p.h));
+  R acc[3] = {R(0), R(0), R(0)};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const R* f = field + c * p.ncell;
+    for (int it = lane; it < E3; it += 32) {
+      const int a = it % E, b = (it / E) % E, cz = it / (E * E);
+      const int ix = wrap_add(S.first[c][0], a, p.nx);
+      const int iy = wrap_add(S.first[c][1], b, p.ny);
+      const int iz = wrap_add(S.first[c][2], cz, p.nz);
+      const R wx = S.w[c][0][a], wy = S.w[c][1][b], wz = S.w[c][2][cz];
+      const R wgt = S.d2[c][0][a] * wy * wz + wx * S.d2[c][1][b] * wz + wx * wy * S.d2[c][2][cz];
+      acc[c] += wgt * f[ix + (long long)p.nx * (iy + (long long)p.ny * iz)];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) out[c] = (double)warp_sum(acc[c]) * (double)inv_h2;
+}
+
+template <typename R, int K>
+__device__ __forceinline__ void scatter(const WarpStencil<R, K>& S, R* __restrict__ field, const BlobParams& p,
+                                        int lane, const double vec[3]) {
+  constexpr int W3 = K * K * K;
+  const double inv_dvf = 1.0 / (p.h * p.h * p.h);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const R amp = (R)(vec[c] * inv_dvf);
+    R* f = field + c * p.ncell;
+    for (int it = lane; it < W3; it += 32) {
+      const int a = it % K, b = (it / K) % K, cz = it / (K * K);
+      const int ix = wrap_add(S.first[c][0], a, p.nx);
+      const int iy = wrap_add(S.first[c][1], b, p.ny);
+      const int iz = wrap_add(S.first[c][2], cz, p.nz);
+      const R wgt = S.w[c][0][a] * S.w[c][1][b] * S.w[c][2][cz];
+      atomicAdd(f + ix + (long long)p.nx * (iy + (long long)p.ny * iz), wgt * amp);
+    }
+  }
+}
+
+__device__ __forceinline__ void load3(const double* a, long long b, double out[3]) {
+  out[0] = a[3 * b];
+  out[1] = a[3 * b + 1];
+  out[2] = a[3 * b + 2];
+}
+__device__ __forceinline__ void store3(double* a, long long b, const double v[3]) {
+  a[3 * b] = v[0];
+  a[3 * b + 1] = v[1];
+  a[3 * b + 2] = v[2];
+}
+
+#define ICM_WARP_SETUP                                                  \
+  __shared__ WarpStencil<R, K> sten[kWarps];                            \
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;            \
+  const long long b = (long long)blockIdx.x * kWarps + wid;             \
+  if (b >= s.nb) return;                                                \
+  WarpStencil<R, K>& S = sten[wid];
+
+// Step 1 (Eq. particle_pred): w0 = J^n v^n, q^{n+1/2} = q^n + dt/2 w0; also
+// w1 = J^{n+1/2} v^n, needed by the position update (Eq. update_q) and the full slip.
+template <typename R, int K>
+__global__ void __launch_bounds__(32 * kWarps) k_predict(BlobParams p, BlobState s, const R* __restrict__ v) {
+  ICM_WARP_SETUP
+  double q[3], w0[3], qh[3], w1[3];
+  load3(s.q, b, q);
+  build_stencil<R, K>(S, q, p, false, lane);
+  gather<R, K>(S, v, p, lane, w0);
+  const double L[3] = {p.nx * p.h, p.ny * p.h, p.nz * p.h};
+  for (int a = 0; a < 3; ++a) qh[a] = wrap_pos(q[a] + 0.5 * p.dt * w0[a], L[a]);
+  __syncwarp();
+  build_stencil<R, K>(S, qh, p, false, lane);
+  gather<R, K>(S, v, p, lane, w1);
+  if (lane == 0) {
+    store3(s.w0, b, w0);
+    store3(s.qh, b, qh);
+    store3(s.w1, b, w1);
+  }
+}
+
+// Step 4 (Eq. delta_u_nph[_visc]): slip correction du and momentum change
+// dp = m_e (u^n - J v~ - du); cdp = m~_f / (rho (m~_f + m_e)) dp for step 5.
+template <typename R, int K>
+__global__ void __launch_bounds__(32 * kWarps) k_dp(BlobParams p, BlobState s, const R* __restrict__ vt) {
+  ICM_WARP_SETUP
+  double qh[3], jvt[3];
+  load3(s.qh, b, qh);
+  build_stencil<R, K>(S, qh, p, false, lane);
+  gather<R, K>(S, vt, p, lane, jvt);
+  if (lane == 0) {
+    double u[3], g[3], du[3], dp[3], cdp[3];
+    load3(s.u, b, u);
+    load3(s.g, b, g);
+    const double me = s.me[b];
+    const double visc = 0.5 * (p.eta / p.rho) * p.dt;
+    const double coef = p.mtf / (p.rho * (p.mtf + me));
+    for (int a = 0; a < 3; ++a) {
+      du[a] = p.slip == 1 ? 0.0 : visc * g[a];
+      if (p.slip == 2) du[a] += s.w1[3 * b + a] - s.w0[3 * b + a];
+      dp[a] = me * (u[a] - jvt[a] - du[a]);
+      cdp[a] = coef * dp[a];
+    }
+    store3(s.jvt, b, jvt);
+    store3(s.du, b, du);
+    store3(s.dp, b, dp);
+    store3(s.cdp, b, cdp);
+  }
+}
+
+// Steps 6-8: J dv~, the source dp - m_e J dv~ of the viscous correction, and the
+// momentum-conserving velocity u^{n+1} = J (v~ + dv~) + du (Eq. update_u).  The
+// grid sum of the source feeds the FP64 momentum bookkeeping.
+template <typename R, int K>
+__global__ void __launch_bounds__(32 * kWarps) k_inertial(BlobParams p, BlobState s, const R* __restrict__ dvt) {
+  __shared__ double red[kWarps][3];
+  __shared__ WarpStencil<R, K> sten[kWarps];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long b = (long long)blockIdx.x * kWarps + wid;
+  double src[3] = {0.0, 0.0, 0.0};
+  if (b < s.nb) {
+    WarpStencil<R, K>& S = sten[wid];
+    double qh[3], jd[3];
+    load3(s.qh, b, qh);
+    build_stencil<R, K>(S, qh, p, false, lane);
+    gather<R, K>(S, dvt, p, lane, jd);
+    const double me = s.me[b];
+    double un[3];
+    for (int a = 0; a < 3; ++a) {
+      src[a] = s.dp[3 * b + a] - me * jd[a];
+      un[a] = s.jvt[3 * b + a] + jd[a] + s.du[3 * b + a];
+    }
+    if (lane == 0) {
+      store3(s.src, b, src);
+      store3(s.u, b, un);
+    }
+  }
+  if (lane == 0)
+    for (int a = 0; a < 3; ++a) red[wid][a] = src[a];
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int w = 0; w < kWarps; ++w) t += red[w][threadIdx.x];
+    atomicAdd(&s.scal[SC_SUMSRC + threadIdx.x], t);
+  }
+}
+
+// Step 9 (Eq. update_q): q^{n+1} = q^n + dt/2 (J^{n+1/2} v^{n+1} + J^{n+1/2} v^n).
+// Inertial path: store the lagged slip term g = J^{n+1/2} L dv.  Neutral path:
+// u^{n+1} = J^{n+1/2} v^{n+1}, g = 0.  Raises CFL / non-finite flags.
+template <typename R, int K>
+__global__ void __launch_bounds__(32 * kWarps) k_finish(BlobParams p, BlobState s, const R* __restrict__ vn,
+                                                        const R* __restrict__ dv, int inertial) {
+  ICM_WARP_SETUP
+  double q[3], qh[3], jv[3], g[3] = {0.0, 0.0, 0.0};
+  load3(s.qh, b, qh);
+  build_stencil<R, K>(S, qh, p, false, lane);
+  gather<R, K>(S, vn, p, lane, jv);
+  if (inertial) {
+    __syncwarp();
+    build_stencil<R, K>(S, qh, p, true, lane);
+    gather_lap<R, K>(S, dv, p, lane, g);
+  }
+  if (lane == 0) {
+    load3(s.q, b, q);
+    const double L[3] = {p.nx * p.h, p.ny * p.h, p.nz * p.h};
+    double qn[3], u[3];
+    if (inertial)
+      load3(s.u, b, u);
+    else
+      for (int a = 0; a < 3; ++a) u[a] = jv[a];
+    bool bad = false, cfl = false;
+    for (int a = 0; a < 3; ++a) {
+      qn[a] = wrap_pos(q[a] + 0.5 * p.dt * (jv[a] + s.w1[3 * b + a]), L[a]);
+      bad |= !isfinite(qn[a]) || !isfinite(u[a]);
+      cfl |= fabs(u[a]) * p.dt > p.h;
+    }
+    store3(s.q, b, qn);
+    store3(s.u, b, u);
+    store3(s.g, b, g);
+    if (bad) atomicOr(s.err, DEV_ERR_NONFINITE);
+    if (cfl) atomicOr(s.err, DEV_ERR_CFL);
+  }
+}
+
+template <typename R, int K>
+__global__ void __launch_bounds__(32 * kWarps) k_spread(BlobParams p, long long nb, const double* __restrict__ qv,
+                                                        const double* __restrict__ vec, R* __restrict__ field) {
+  __shared__ WarpStencil<R, K> sten[kWarps];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long b = (long long)blockIdx.x * kWarps + wid;
+  if (b >= nb) return;
+  WarpStencil<R, K>& S = sten[wid];
+  double q[3], f[3];
+  load3(qv, b, q);
+  load3(vec, b, f);
+  build_stencil<R, K>(S, q, p, false, lane);
+  scatter<R, K>(S, field, p, lane, f);
+}
+
+template <typename R, int K>
+__global__ void __launch_bounds__(32 * kWarps) k_interp(BlobParams p, long long nb, const double* __restrict__ qv,
+                                                        const R* __restrict__ field, int lap, double* __restrict__ out) {
+  __shared__ WarpStencil<R, K> sten[kWarps];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long b = (long long)blockIdx.x * kWarps + wid;
+  if (b >= nb) return;
+  WarpStencil<R, K>& S = sten[wid];
+  double q[3], r[3];
+  load3(qv, b, q);
+  build_stencil<R, K>(S, q, p, lap != 0, lane);
+  if (lap)
+    gather_lap<R, K>(S, field, p, lane, r);
+  else
+    gather<R, K>(S, field, p, lane, r);
+  if (lane == 0) store3(out, b, r);
+}
+
+inline unsigned nblocks(long long nb) { return (unsigned)((nb + kWarps - 1) / kWarps); }
+
+}  // namespace
+
+#define ICM_KSWITCH(call3, call4) \
+  if (p.kernel == 3) {            \
+    call3;                        \
+  } else {                        \
+    call4;                        \
+  }
+
+template <typename R>
+void blob_predict(const BlobParams& p, BlobState s, const R* v, cudaStream_t st) {
+  if (s.nb <= 0) return;
+  ICM_KSWITCH((k_predict<R, 3><<<nblocks(s.nb), 32 * kWarps, 0, st>>>(p, s, v)),
+              (k_predict<R, 4><<<nblocks(s.nb), 32 * kWarps, 0, st>>>(p, s, v)))
+}
+template <typename R>
+void blob_spread(const BlobParams& p, long long nb, const double* q, const double* vec, R* field, cudaStream_t st) {
+  if (nb <= 0) return;
+  ICM_KSWITCH((k_spread<R, 3><<<nblocks(nb), 32 * kWarps, 0, st>>>(p, nb, q, vec, field)),
+              (k_spread<R, 4><<<nblocks(nb), 32 * kWarps, 0, st>>>(p, nb, q, vec, field)))
+}
+template <typename R>
+void blob_momentum_change(const BlobParams& p, BlobState s, const R* vt, cudaStream_t st) {
+  if (s.nb <= 0) return;
+  ICM_KSWITCH((k_dp<R, 3><<<nblocks(s.nb), 32 * kWarps, 0, st>>>(p, s, vt)),
+              (k_dp<R, 4><<<nblocks(s.nb), 32 * kWarps, 0, st>>>(p, s, vt)))
+}
+template <typename R>
+void blob_inertial(const BlobParams& p, BlobState s, const R* dvt, cudaStream_t st) {
+  if (s.nb <= 0) return;
+  ICM_KSWITCH((k_inertial<R, 3><<<nblocks(s.nb), 32 * kWarps, 0, st>>>(p, s, dvt)),
+              (k_inertial<R, 4><<<nblocks(s.nb), 32 * kWarps, 0, st>>>(p, s, dvt)))
+}
+template <typename R>
+void blob_finish(const BlobParams& p, BlobState s, const R* v_new, const R* dv, bool inertial, cudaStream_t st) {
+  if (s.nb <= 0) return;
+  ICM_KSWITCH((k_finish<R, 3><<<nblocks(s.nb), 32 * kWarps, 0, st>>>(p, s, v_new, dv, inertial ? 1 : 0)),
+              (k_finish<R, 4><<<nblocks(s.nb), 32 * kWarps, 0, st>>>(p, s, v_new, dv, inertial ? 1 : 0)))
+}
+template <typename R>
+void blob_interp(const BlobParams& p, long long nb, const double* q, const R* field, bool laplacian, double* out,
+                 cudaStream_t st) {
+  if (nb <= 0) return;
+  ICM_KSWITCH((k_interp<R, 3><<<nblocks(nb), 32 * kWarps, 0, st>>>(p, nb, q, field, laplacian ? 1 : 0, out)),
+              (k_interp<R, 4><<<nblocks(nb), 32 * kWarps, 0, st>>>(p, nb, q, field, laplacian ? 1 : 0, out)))
+}
+
+#define ICM_INST(R)                                                                                            \
+  template void blob_predict<R>(const BlobParams&, BlobState, const R*, cudaStream_t);                        \
+  template void blob_spread<R>(const BlobParams&, long long, const double*, const double*, R*, cudaStream_t); \
+  template void blob_momentum_change<R>(const BlobParams&, BlobState, const R*, cudaStream_t);                \
+  template void blob_inertial<R>(const BlobParams&, BlobState, const R*, cudaStream_t);                       \
+  template void blob_finish<R>(const BlobParams&, BlobState, const R*, const R*, bool, cudaStream_t);          \
+  template void blob_interp<R>(const BlobParams&, long long, const double*, const R*, bool, double*, cudaStream_t);
+ICM_INST(float)
+ICM_INST(double)
+#undef ICM_INST
+
+}  // namespace icm

@@ -1,0 +1,447 @@
+// 3D real-to-complex FFT Helmholtz solve and discrete projection on the MAC grid
+// (arXiv:1212.6427, Sec. III.D and Appendix C: the periodic velocity and pressure
+// systems are diagonalised by Fourier transforms).
+//
+// Layout.  A real face field is 3 components x [Nz][Ny][Nx] (x fastest).  The
+// spectrum is 3 x [Nz][Ny][kxp] complex with kx = Nx/2+1 stored x wavenumbers.
+//
+// Passes (each one read + one write of the spectrum, tiles staged in shared
+// memory, every global access a contiguous 128-byte row segment):
+//   x forward : two real rows packed as one complex row, Nx-point FFT, split into
+//               two half spectra (Hermitian symmetry).
+//   y forward : in-place decimation-in-frequency stages; leaves ky in digit-reversed
+//               storage order (the symbol tables are indexed by storage position).
+//   z         : forward DIF, symbol P^/(a + b|d|^2) on all three components at once,
+//               inverse DIT back to natural z order.
+//   y inverse : DIT, digit-reversed -> natural order.
+//   x inverse : Hermitian extension, Nx-point inverse FFT, two real rows out.
+// Each stage of a pass is a radix-2/3/4/8/16 butterfly done in registers with the
+// operands read from and written back to the same shared-memory positions.
+#include <cstdio>
+
+#include "icm_internal.h"
+
+namespace icm {
+namespace {
+
+// ---------------------------------------------------------------------------
+// Small DFTs in registers (forward, W = exp(-2 pi i / R)).
+// ---------------------------------------------------------------------------
+template <typename C> __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
+  const C s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3), d13 = csub(a1, a3);
+  a0 = cadd(s02, s13);
+  a2 = csub(s02, s13);
+  a1 = cadd(d02, cmul_mi(d13));
+  a3 = cadd(d02, cmul_pi(d13));
+}
+
+// multiply by exp(-2 pi i m / 16); m is a compile-time constant after unrolling
+template <typename R> __device__ __forceinline__ cplx_t<R> w16mul(cplx_t<R> a, int m) {
+  const R c1 = R(0.92387953251128675613), s1 = R(0.38268343236508977173), r2 = R(0.70710678118654752440);
+  R c, s;  // exp(-i t) = c - i s
+  switch (m & 15) {
+    case 0: return a;
+    case 1: c = c1; s = s1; break;
+    case 2: c = r2; s = r2; break;
+    case 3: c = s1; s = c1; break;
+    case 4: return cmul_mi(a);
+    case 5: c = -s1; s = c1; break;
+    case 6: c = -r2; s = r2; break;
+    case 7: c = -c1; s = s1; break;
+    case 8: return mk(-a.x, -a.y);
+    case 9: c = -c1; s = -s1; break;
+    case 10: c = -r2; s = -r2; break;
+    case 11: c = -s1; s = -c1; break;
+    case 12: return cmul_pi(a);
+    case 13: c = s1; s = -c1; break;
+    case 14: c = r2; s = -r2; break;
+    default: c = c1; s = -s1; break;
+  }
+  return mk(a.x * c + a.y * s, a.y * c - a.x * s);
+}
+
+template <typename R, int RAD> struct Dft;
+template <typename R> struct Dft<R, 2> {
+  __device__ __forceinline__ static void run(cplx_t<R>* a) {
+    const cplx_t<R> t = a[0];
+    a[0] = cadd(t, a[1]);
+    a[1] = csub(t, a[1]);
+  }
+};
+template <typename R> struct Dft<R, 3> {
+  __device__ __forceinline__ static void run(cplx_t<R>* a) {
+    const R s = R(0.86602540378443864676);
+    const cplx_t<R> t1 = cadd(a[1], a[2]);
+    const cplx_t<R> t2 = mk(a[0].x - R(0.5) * t1.x, a[0].y - R(0.5) * t1.y);
+    const cplx_t<R> d = csub(a[1], a[2]);
+    const cplx_t<R> t3 = mk(s * d.x, s * d.y);
+    a[0] = cadd(a[0], t1);
+    a[1] = cadd(t2, cmul_mi(t3));
+    a[2] = cadd(t2, cmul_pi(t3));
+  }
+};
+template <typename R> struct Dft<R, 4> {
+  __device__ __forceinline__ static void run(cplx_t<R>* a) { dft4(a[0], a[1], a[2], a[3]); }
+};
+template <typename R> struct Dft<R, 8> {
+  // 8 = 2 x 4: b_k2[n1] = W8^(n1 k2) sum_n2 x[n1 + 4 n2] W2^(n2 k2); X[2 k1 + k2] = DFT4(b_k2)[k1]
+  __device__ __forceinline__ static void run(cplx_t<R>* a) {
+    cplx_t<R> b0[4], b1[4];
+#pragma unroll
+    for (int n1 = 0; n1 < 4; ++n1) {
+      b0[n1] = cadd(a[n1], a[n1 + 4]);
+      b1[n1] = w16mul<R>(csub(a[n1], a[n1 + 4]), 2 * n1);
+    }
+    dft4(b0[0], b0[1], b0[2], b0[3]);
+    dft4(b1[0], b1[1], b1[2], b1[3]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      a[2 * k1] = b0[k1];
+      a[2 * k1 + 1] = b1[k1];
+    }
+  }
+};
+template <typename R> struct Dft<R, 16> {
+  // 16 = 4 x 4: t[n1][k2] = W16^(n1 k2) DFT4_n2(x[n1 + 4 n2])[k2]; X[4 k1 + k2] = DFT4_n1(t[.][k2])[k1]
+  __device__ __forceinline__ static void run(cplx_t<R>* a) {
+    cplx_t<R> t[16];
+#pragma unroll
+    for (int n1 = 0; n1 < 4; ++n1) {
+      cplx_t<R> y0 = a[n1], y1 = a[n1 + 4], y2 = a[n1 + 8], y3 = a[n1 + 12];
+      dft4(y0, y1, y2, y3);
+      t[n1 * 4 + 0] = y0;
+      t[n1 * 4 + 1] = w16mul<R>(y1, n1);
+      t[n1 * 4 + 2] = w16mul<R>(y2, 2 * n1);
+      t[n1 * 4 + 3] = w16mul<R>(y3, 3 * n1);
+    }
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) {
+      cplx_t<R> z0 = t[k2], z1 = t[4 + k2], z2 = t[8 + k2], z3 = t[12 + k2];
+      dft4(z0, z1, z2, z3);
+      a[k2] = z0;
+      a[4 + k2] = z1;
+      a[8 + k2] = z2;
+      a[12 + k2] = z3;
+    }
+  }
+};
+
+// One in-place stage over ncomp groups of NL interleaved lines: element (pos, line)
+// of group c is s[c*cs + pos*LS + line].  Sub-transform length M, radix RAD.
+// Forward (DIF): y[n1 + (M/R) k2] = W_M^(n1 k2) sum_n2 x[n1 + (M/R) n2] W_R^(n2 k2).
+// Inverse: the exact (unnormalised) inverse of that map, via conj o DFT o conj.
+template <typename R, int RAD, bool INV, int NL>
+__device__ __forceinline__ void fft_stage(cplx_t<R>* s, int N, int M, int LS, int ncomp, int cs,
+                                          const cplx_t<R>* tw, int tid, int nthr) {
+  using C = cplx_t<R>;
+  const int Mr = M / RAD;
+  const int nbf = N / RAD;
+  const int tws = N / M;
+  const int total = nbf * NL * ncomp;
+  const int str = Mr * LS;
+  for (int it = tid; it < total; it += nthr) {
+    const int line = it % NL;
+    const int rest = it / NL;
+    const int comp = rest / nbf;
+    const int bf = rest - comp * nbf;
+    const int blk = bf / Mr;
+    const int n1 = bf - blk * Mr;
+    C* p = s + comp * cs + (blk * M + n1) * LS + line;
+    C a[RAD];
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) a[r] = p[r * str];
+    if (INV) {
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) {
+        a[r] = cconj(a[r]);
+        if (r > 0) a[r] = cmul(a[r], tw[n1 * r * tws]);
+      }
+      Dft<R, RAD>::run(a);
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) a[r] = cconj(a[r]);
+    } else {
+      Dft<R, RAD>::run(a);
+#pragma unroll
+      for (int r = 1; r < RAD; ++r) a[r] = cmul(a[r], tw[n1 * r * tws]);
+    }
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) p[r * str] = a[r];
+  }
+}
+
+template <typename R, bool INV, int NL>
+__device__ void run_fft(cplx_t<R>* s, const AxisPlan& P, int LS, int ncomp, int cs, const cplx_t<R>* tw,
+                        int tid, int nthr) {
+  int Ms[kMaxStages];
+  int M = P.n;
+  for (int k = 0; k < P.nstages; ++k) {
+    Ms[k] = M;
+    M /= P.radix[k];
+  }
+  for (int k = 0; k < P.nstages; ++k) {
+    const int si = INV ? P.nstages - 1 - k : k;
+    const int m = Ms[si];
+    switch (P.radix[si]) {
+      case 2: fft_stage<R, 2, INV, NL>(s, P.n, m, LS, ncomp, cs, tw, tid, nthr); break;
+      case 3: fft_stage<R, 3, INV, NL>(s, P.n, m, LS, ncomp, cs, tw, tid, nthr); break;
+      case 4: fft_stage<R, 4, INV, NL>(s, P.n, m, LS, ncomp, cs, tw, tid, nthr); break;
+      case 8: fft_stage<R, 8, INV, NL>(s, P.n, m, LS, ncomp, cs, tw, tid, nthr); break;
+      default: fft_stage<R, 16, INV, NL>(s, P.n, m, LS, ncomp, cs, tw, tid, nthr); break;
+    }
+    __syncthreads();
+  }
+}
+
+constexpr int kThreads = 256;
+constexpr int kXLines = 16;   // complex lines (= 32 real rows) per x-pass block
+constexpr int kXLS = 17;      // padded line stride of the x pass (transposing loads)
+
+template <typename R> constexpr int seg_lines() { return 128 / (int)sizeof(cplx_t<R>); }
+
+template <typename R>
+__device__ __forceinline__ void load_tables(cplx_t<R>* tw, int* pof, const AxisPlan& P, int tid) {
+  const cplx_t<R>* g = (const cplx_t<R>*)P.tw;
+  for (int i = tid; i < P.n; i += kThreads) {
+    tw[i] = g[i];
+    if (pof) pof[i] = P.pos_of_freq[i];
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_xfwd(const R* __restrict__ src, cplx_t<R>* __restrict__ spec,
+                                                   AxisPlan P, int nrows, long long ncell, int kx, int kxp) {
+  using C = cplx_t<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = P.n;
+  C* lines = reinterpret_cast<C*>(smem_raw);
+  C* tw = lines + N * kXLS;
+  int* pof = reinterpret_cast<int*>(tw + N);
+  const int tid = threadIdx.x;
+  load_tables<R>(tw, pof, P, tid);
+  const int comp = blockIdx.y;
+  const long long row0 = (long long)blockIdx.x * (2 * kXLines);
+  const R* s = src + comp * ncell;
+  for (int idx = tid; idx < 2 * kXLines * N; idx += kThreads) {
+    const int rr = idx / N, x = idx - rr * N;
+    const long long row = row0 + rr;
+    const R val = row < nrows ? s[row * N + x] : R(0);
+    reinterpret_cast<R*>(&lines[x * kXLS + (rr >> 1)])[rr & 1] = val;
+  }
+  __syncthreads();
+  run_fft<R, false, kXLines>(lines, P, kXLS, 1, 0, tw, tid, kThreads);
+  C* out = spec + (size_t)comp * nrows * kxp;
+  for (int idx = tid; idx < kXLines * kx; idx += kThreads) {
+    const int l = idx / kx, k = idx - l * kx;
+    const C zk = lines[pof[k] * kXLS + l];
+    const C zm = lines[pof[k == 0 ? 0 : N - k] * kXLS + l];
+    const C x1 = mk((zk.x + zm.x) * R(0.5), (zk.y - zm.y) * R(0.5));
+    const C x2 = cmul_mi(mk((zk.x - zm.x) * R(0.5), (zk.y + zm.y) * R(0.5)));
+    const long long r1 = row0 + 2 * l;
+    if (r1 < nrows) out[r1 * kxp + k] = x1;
+    if (r1 + 1 < nrows) out[(r1 + 1) * kxp + k] = x2;
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_xinv(const cplx_t<R>* __restrict__ spec, R* __restrict__ dst,
+                                                   R* __restrict__ dst2, int mode, AxisPlan P, int nrows,
+                                                   long long ncell, int kxp) {
+  using C = cplx_t<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = P.n;
+  C* lines = reinterpret_cast<C*>(smem_raw);
+  C* tw = lines + N * kXLS;
+  int* pof = reinterpret_cast<int*>(tw + N);
+  const int tid = threadIdx.x;
+  load_tables<R>(tw, pof, P, tid);
+  __syncthreads();
+  const int comp = blockIdx.y;
+  const long long row0 = (long long)blockIdx.x * (2 * kXLines);
+  const C* in = spec + (size_t)comp * nrows * kxp;
+  const C zero = mk(R(0), R(0));
+  for (int idx = tid; idx < kXLines * N; idx += kThreads) {
+    const int l = idx / N, k = idx - l * N;
+    const long long r1 = row0 + 2 * l;
+    const bool direct = 2 * k <= N;
+    const int kk = direct ? k : N - k;
+    C a = r1 < nrows ? in[r1 * kxp + kk] : zero;
+    C b = r1 + 1 < nrows ? in[(r1 + 1) * kxp + kk] : zero;
+    if (!direct) {
+      a = cconj(a);
+      b = cconj(b);
+    }
+    if (k == 0 || 2 * k == N) {  // real by Hermitian symmetry: drop round-off imaginary parts
+      a.y = R(0);
+      b.y = R(0);
+    }
+    lines[pof[k] * kXLS + l] = mk(a.x - b.y, a.y + b.x);
+  }
+  __syncthreads();
+  run_fft<R, true, kXLines>(lines, P, kXLS, 1, 0, tw, tid, kThreads);
+  const size_t base = (size_t)comp * ncell;
+  for (int idx = tid; idx < 2 * kXLines * N; idx += kThreads) {
+    const int rr = idx / N, x = idx - rr * N;
+    const long long row = row0 + rr;
+    if (row >= nrows) continue;
+    const R val = reinterpret_cast<const R*>(&lines[x * kXLS + (rr >> 1)])[rr & 1];
+    const size_t o = base + (size_t)row * N + x;
+    if (mode == OUT_STORE) {
+      dst[o] = val;
+    } else {
+      dst[o] += val;
+      dst2[o] = val;
+    }
+  }
+}
+
+template <typename R, bool INV>
+__global__ void __launch_bounds__(kThreads) k_ypass(cplx_t<R>* __restrict__ spec, AxisPlan P, int nz, int kx,
+                                                    int kxp) {
+  using C = cplx_t<R>;
+  constexpr int NL = seg_lines<R>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = P.n;
+  C* lines = reinterpret_cast<C*>(smem_raw);
+  C* tw = lines + N * NL;
+  const int tid = threadIdx.x;
+  load_tables<R>(tw, nullptr, P, tid);
+  const int kx0 = blockIdx.x * NL;
+  const int z = blockIdx.y, comp = blockIdx.z;
+  C* base = spec + ((size_t)(comp * nz + z) * N) * kxp + kx0;
+  const C zero = mk(R(0), R(0));
+  for (int idx = tid; idx < N * NL; idx += kThreads) {
+    const int t = idx % NL, y = idx / NL;
+    lines[idx] = (kx0 + t < kx) ? base[(size_t)y * kxp + t] : zero;
+  }
+  __syncthreads();
+  run_fft<R, INV, NL>(lines, P, NL, 1, 0, tw, tid, kThreads);
+  for (int idx = tid; idx < N * NL; idx += kThreads) {
+    const int t = idx % NL, y = idx / NL;
+    if (kx0 + t < kx) base[(size_t)y * kxp + t] = lines[idx];
+  }
+}
+
+template <typename R>
+struct SymParams {
+  R a, b, inv_ntot;
+  const cplx_t<R>* dx; const R* ddx;
+  const cplx_t<R>* dy; const R* ddy;
+  const cplx_t<R>* dz; const R* ddz;
+  const double* k0sum;
+  double k0mul;   // k0scale / ncell
+};
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_zsym(cplx_t<R>* __restrict__ spec, AxisPlan P, int ny, int kx,
+                                                   int kxp, SymParams<R> sp) {
+  using C = cplx_t<R>;
+  constexpr int NL = seg_lines<R>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = P.n;  // nz
+  C* lines = reinterpret_cast<C*>(smem_raw);
+  const int cs = N * NL;
+  C* tw = lines + 3 * cs;
+  const int tid = threadIdx.x;
+  load_tables<R>(tw, nullptr, P, tid);
+  const int kx0 = blockIdx.x * NL;
+  const int py = blockIdx.y;
+  const size_t zstride = (size_t)ny * kxp;
+  const size_t cstride = (size_t)N * zstride;
+  C* base = spec + (size_t)py * kxp + kx0;
+  const C zero = mk(R(0), R(0));
+  for (int idx = tid; idx < 3 * cs; idx += kThreads) {
+    const int c = idx / cs, rem = idx - c * cs;
+    const int t = rem % NL, z = rem / NL;
+    lines[idx] = (kx0 + t < kx) ? base[c * cstride + z * zstride + t] : zero;
+  }
+  __syncthreads();
+  run_fft<R, false, NL>(lines, P, NL, 3, cs, tw, tid, kThreads);
+  const C dyv = sp.dy[py];
+  const R ddy = sp.ddy[py];
+  for (int idx = tid; idx < cs; idx += kThreads) {
+    const int t = idx % NL, pz = idx / NL;
+    const int k = kx0 + t;
+    if (k >= kx) continue;
+    const C d0 = sp.dx[k], d2 = sp.dz[pz];
+    const R dd = sp.ddx[k] + ddy + sp.ddz[pz];
+    C c0 = lines[idx], c1 = lines[cs + idx], c2 = lines[2 * cs + idx];
+    if (dd > R(0)) {
+      const C div = cadd(cadd(cmul(d0, c0), cmul(dyv, c1)), cmul(d2, c2));
+      const C q = mk(div.x / dd, div.y / dd);
+      c0 = csub(c0, cmul(cconj(d0), q));
+      c1 = csub(c1, cmul(cconj(dyv), q));
+      c2 = csub(c2, cmul(cconj(d2), q));
+    }
+    const R scale = sp.inv_ntot / (sp.a + sp.b * dd);
+    c0 = cscale(c0, scale);
+    c1 = cscale(c1, scale);
+    c2 = cscale(c2, scale);
+    if (sp.k0sum != nullptr && k == 0 && py == 0 && pz == 0) {
+      c0 = mk((R)(sp.k0sum[0] * sp.k0mul), R(0));
+      c1 = mk((R)(sp.k0sum[1] * sp.k0mul), R(0));
+      c2 = mk((R)(sp.k0sum[2] * sp.k0mul), R(0));
+    }
+    lines[idx] = c0;
+    lines[cs + idx] = c1;
+    lines[2 * cs + idx] = c2;
+  }
+  __syncthreads();
+  run_fft<R, true, NL>(lines, P, NL, 3, cs, tw, tid, kThreads);
+  for (int idx = tid; idx < 3 * cs; idx += kThreads) {
+    const int c = idx / cs, rem = idx - c * cs;
+    const int t = rem % NL, z = rem / NL;
+    if (kx0 + t < kx) base[c * cstride + z * zstride + t] = lines[idx];
+  }
+}
+
+template <typename R> size_t smem_x(int n) { return (size_t)n * kXLS * sizeof(cplx_t<R>) + n * sizeof(cplx_t<R>) + n * sizeof(int); }
+template <typename R> size_t smem_y(int n) { return (size_t)n * seg_lines<R>() * sizeof(cplx_t<R>) + n * sizeof(cplx_t<R>); }
+template <typename R> size_t smem_z(int n) { return 3 * (size_t)n * seg_lines<R>() * sizeof(cplx_t<R>) + n * sizeof(cplx_t<R>); }
+
+template <typename R>
+void set_smem_attributes() {
+  const int big = 227 * 1024;
+  cudaFuncSetAttribute(k_xfwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_xinv<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_ypass<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_ypass<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_zsym<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+}
+
+}  // namespace
+
+template <typename R>
+void spectral_solve(const FftCtx<R>& f, const R* src, R* dst, R* dst2, int mode, double a, double b,
+                    const double* k0sum, double k0scale, cudaStream_t st) {
+  constexpr int NL = seg_lines<R>();
+  const int nrows = f.ny * f.nz;
+  const int xblocks = (nrows + 2 * kXLines - 1) / (2 * kXLines);
+  const int kxt = (f.kx + NL - 1) / NL;
+  k_xfwd<R><<<dim3(xblocks, 3), kThreads, smem_x<R>(f.nx), st>>>(src, f.spec, f.px, nrows, f.ncell, f.kx, f.kxp);
+  k_ypass<R, false><<<dim3(kxt, f.nz, 3), kThreads, smem_y<R>(f.ny), st>>>(f.spec, f.py, f.nz, f.kx, f.kxp);
+  SymParams<R> sp;
+  sp.a = (R)a;
+  sp.b = (R)b;
+  sp.inv_ntot = (R)(1.0 / (double)f.ncell);
+  sp.k0mul = k0scale / (double)f.ncell;
+  sp.dx = f.dx; sp.ddx = f.ddx;
+  sp.dy = f.dy; sp.ddy = f.ddy;
+  sp.dz = f.dz; sp.ddz = f.ddz;
+  sp.k0sum = k0sum;
+  k_zsym<R><<<dim3(kxt, f.ny), kThreads, smem_z<R>(f.nz), st>>>(f.spec, f.pz, f.ny, f.kx, f.kxp, sp);
+  k_ypass<R, true><<<dim3(kxt, f.nz, 3), kThreads, smem_y<R>(f.ny), st>>>(f.spec, f.py, f.nz, f.kx, f.kxp);
+  k_xinv<R><<<dim3(xblocks, 3), kThreads, smem_x<R>(f.nx), st>>>(f.spec, dst, dst2, mode, f.px, nrows, f.ncell,
+                                                                 f.kxp);
+}
+
+void fft_prepare() {
+  set_smem_attributes<float>();
+  set_smem_attributes<double>();
+}
+
+template void spectral_solve<float>(const FftCtx<float>&, const float*, float*, float*, int, double, double,
+                                    const double*, double, cudaStream_t);
+template void spectral_solve<double>(const FftCtx<double>&, const double*, double*, double*, int, double, double,
+                                     const double*, double, cudaStream_t);
+
+}  // namespace icm

@@ -1,0 +1,145 @@
+// Internal (non-ABI) declarations shared by the translation units of libicm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "icm_common.cuh"
+
+namespace icm {
+
+constexpr int kMaxSide = 512;
+constexpr int kMaxStages = 12;
+
+// One axis of the 3D FFT: a mixed-radix factorisation N = prod radix[s] with
+// in-place decimation-in-frequency stages.  The forward pass leaves frequency k
+// at storage position pos_of_freq[k]; the inverse pass takes that order back to
+// natural order, so the spectrum is never reordered.
+struct AxisPlan {
+  int n = 0;
+  int nstages = 0;
+  int radix[kMaxStages] = {0};
+  const void* tw = nullptr;          // device: n complex, tw[m] = exp(-2 pi i m / n)
+  const int* pos_of_freq = nullptr;  // device: n ints
+};
+
+// Everything the FFT passes need for one grid.
+template <typename R>
+struct FftCtx {
+  int nx, ny, nz;
+  int kx;        // nx/2 + 1 stored x wavenumbers
+  int kxp;       // padded row length of the spectrum (multiple of 16)
+  long long ncell;
+  AxisPlan px, py, pz;
+  // Discrete symbols d_a = (exp(i theta_a) - 1)/h and |d_a|^2: x by natural kx,
+  // y and z by storage position of the forward pass.
+  const cplx_t<R>* dx; const R* ddx;
+  const cplx_t<R>* dy; const R* ddy;
+  const cplx_t<R>* dz; const R* ddz;
+  cplx_t<R>* spec;   // 3 * nz * ny * kxp complex scratch
+};
+
+enum OutMode : int { OUT_STORE = 0, OUT_ADD_AND_STORE2 = 1 };
+
+// x^ = P^ r^ / (a + b |d|^2) for the three components of src (real face field,
+// 3*ncell values).  OUT_STORE: dst = x.  OUT_ADD_AND_STORE2: dst += x, dst2 = x.
+// k0sum (device, 3 doubles, may be null): prescribed sum over the grid of each
+// output component (the FP64 momentum bookkeeping of the mean mode).
+// k0sum * k0scale is the prescribed grid sum (k0scale folds rho dV_f).
+template <typename R>
+void spectral_solve(const FftCtx<R>& f, const R* src, R* dst, R* dst2, int mode, double a, double b,
+                    const double* k0sum, double k0scale, cudaStream_t st);
+
+// Raise the dynamic shared-memory limits of the kernels (call once, outside capture).
+void fft_prepare();
+void grid_prepare();
+
+// ---------------------------------------------------------------------------
+// Grid kernels (icm_grid.cu)
+// ---------------------------------------------------------------------------
+struct GridParams {
+  int nx, ny, nz;
+  long long ncell;
+  double h, rho, eta, kT, dt;
+  uint32_t key0, key1;
+  int advection;
+};
+
+// r = (rho/dt) v + (eta/2) L v + div Sigma^n - (3/2 A^n - 1/2 A^{n-1}); adv <- A^n.
+// step_dev: device int64 time level (Philox counter word 1).  has_hist_dev: device
+// int, 0 = no history (A^{n-1} := A^n); set to 1 by the kernel launch sequence.
+template <typename R>
+void explicit_rhs(const GridParams& g, const R* v, R* adv, R* rhs, const long long* step_dev,
+                  const int* has_hist_dev, cudaStream_t st);
+
+template <typename R>
+void stress_normals(const GridParams& g, long long step, R* out, cudaStream_t st);
+
+void philox_words(long long n, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
+                  uint32_t* out, cudaStream_t st);
+
+// out[c] = sum over the grid of component c (FP64, compensated), 3 doubles.
+template <typename R>
+void field_sums(const R* v, long long ncell, double* out_dev, double* partial_dev, int npartial, cudaStream_t st);
+
+template <typename R>
+void convert_to_double(const R* src, double* dst, long long n, cudaStream_t st);
+template <typename R>
+void convert_from_double(const double* src, R* dst, long long n, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Blob kernels (icm_blob.cu)
+// ---------------------------------------------------------------------------
+struct BlobParams {
+  int nx, ny, nz;
+  long long ncell;
+  double h, rho, eta, dt;
+  int kernel;
+  int slip;        // 0 visc, 1 zero, 2 full
+  double mtf;      // m~_f = 3 rho dV / 2
+};
+
+struct BlobState {
+  long long nb;
+  double* q;        // positions q^n (n,3)
+  double* qh;       // midpoint q^{n+1/2}
+  double* u;        // velocities
+  const double* me; // excess masses
+  const double* f;  // external forces
+  double* g;        // lagged J L dv (slip term)
+  double* w0;       // J^n v^n at q^n
+  double* w1;       // J^{n+1/2} v^n
+  double* jvt;      // J v~
+  double* du;       // slip correction
+  double* dp;       // momentum change
+  double* cdp;      // m~_f/(rho(m~_f+m_e)) dp
+  double* src;      // dp - m_e J dv~
+  double* scal;     // device scalars (see ScalarSlot)
+  int* err;         // device error bits
+};
+
+enum ScalarSlot : int {
+  SC_PBAR = 0,      // [3] total fluid momentum rho dV_f sum v (FP64 bookkeeping)
+  SC_SUMF = 3,      // [3] sum of external forces
+  SC_SUMSRC = 6,    // [3] sum_i (dp_i - m_e,i J dv~_i) of this step
+  SC_K0 = 9,        // [3] prescribed grid sum of the provisional solve output
+  SC_K0B = 12,      // [3] prescribed grid sum of the viscous correction output
+  SC_COUNT = 16
+};
+
+template <typename R> void blob_predict(const BlobParams& p, BlobState s, const R* v, cudaStream_t st);
+template <typename R> void blob_spread(const BlobParams& p, long long nb, const double* q, const double* vec,
+                                       R* field, cudaStream_t st);
+template <typename R> void blob_momentum_change(const BlobParams& p, BlobState s, const R* vt, cudaStream_t st);
+template <typename R> void blob_inertial(const BlobParams& p, BlobState s, const R* dvt, cudaStream_t st);
+template <typename R> void blob_finish(const BlobParams& p, BlobState s, const R* v_new, const R* dv,
+                                       bool inertial, cudaStream_t st);
+template <typename R> void blob_interp(const BlobParams& p, long long nb, const double* q, const R* field,
+                                       bool laplacian, double* out, cudaStream_t st);
+
+// Scalar bookkeeping kernels.
+void scalars_before_step(double* scal, double dt, double rho, double dvf, cudaStream_t st);
+void scalars_after_step(double* scal, double dt, double rho, double dvf, bool inertial, long long* step_dev,
+                        int* has_hist_dev, cudaStream_t st);
+
+}  // namespace icm

@@ -1,0 +1,111 @@
+"""GPU parity of each operator of the step against the FP64 oracle, through the C ABI.
+
+Sizes span several shared-memory tiles and ragged tails (odd and radix-3 sides,
+non-cubic boxes, blobs on the periodic seam)."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import icm as oracle
+from oracle import philox
+
+from _gpu_helpers import TOL, rel
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+GRIDS = [(16, 16, 16), (32, 12, 24), (9, 18, 8), (48, 32, 27), (96, 8, 16)]
+
+
+@pytest.fixture(scope="module")
+def icm():
+    import paper_1212_6427_gb300 as m
+    from paper_1212_6427_gb300 import build
+    build.build_library()
+    return m
+
+
+def _sim(icm, grid, precision, kernel=4, kT=1e-3, dt=0.05, h=1.0, seed=7, flags=0):
+    return icm.Simulation(grid, h, 1.3, 0.7, kT, dt, kernel, seed, precision, flags)
+
+
+def test_philox_bitwise_against_oracle_and_known_answers(icm):
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as fh:
+        rows = [[int(x, 16) for x in ln.split()] for ln in fh if ln.strip() and not ln.startswith("#")]
+    for r in rows:
+        got = icm.icm_op_philox(1, r[0:4], r[4:6])
+        assert [int(x) for x in got[0]] == r[6:10]
+    n = 100_000
+    got = icm.icm_op_philox(n, (5, 77, 1, 0), (0xDEADBEEF, 0x12345678))
+    want = philox.philox4x32((np.arange(5, 5 + n), 77, 1, 0), (0xDEADBEEF, 0x12345678))
+    for w in range(4):
+        assert np.array_equal(got[:, w], want[w])
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_stress_normals(icm, precision):
+    grid = (16, 12, 9)
+    sim = _sim(icm, grid, precision, seed=(1 << 40) + 3)
+    n = int(np.prod(grid))
+    got = icm.icm_op_stress_normals(sim.handle, n, 11)
+    want = philox.stress_normals((1 << 40) + 3, 11, n)
+    tol = 1e-14 if precision == 64 else 2e-6
+    assert rel(got, want) < tol
+    sim.close()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("grid", GRIDS)
+@pytest.mark.parametrize("ab", [(26.0, 0.35), (1.0, 0.0), (1.3, 0.0175)])
+def test_spectral_solve(icm, precision, grid, ab):
+    sim = _sim(icm, grid, precision, h=0.8)
+    nx, ny, nz = grid
+    rng = np.random.default_rng(1)
+    r = rng.standard_normal((3, nz, ny, nx))
+    got = icm.icm_op_spectral_solve(sim.handle, ab[0], ab[1], r.ravel())
+    want = oracle.spectral_solve(r, ab[0], ab[1], 0.8)
+    assert rel(got, want) < TOL[precision] / 2
+    sim.close()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("kernel", [3, 4])
+@pytest.mark.parametrize("grid", [(16, 16, 16), (9, 18, 8), (48, 32, 27)])
+def test_interpolate_spread_and_laplacian_gather(icm, precision, kernel, grid):
+    h = 0.9
+    sim = _sim(icm, grid, precision, kernel=kernel, h=h)
+    nx, ny, nz = grid
+    box = np.array(grid) * h
+    rng = np.random.default_rng(2)
+    q = rng.uniform(0, 1, size=(300, 3)) * box
+    q[:4] = [[0.0, 0.0, 0.0], [box[0] - 1e-12, 0.5 * h, 0.25 * h], [0.5 * h, box[1] - 0.5 * h, 1e-9],
+             [h * 3.5, h * 4.5, h * 2.0]]
+    v = rng.standard_normal((3, nz, ny, nx))
+    F = rng.standard_normal((300, 3))
+    tol = TOL[precision] / 2
+    assert rel(icm.icm_op_interpolate(sim.handle, q, v.ravel()), oracle.interpolate(v, q, kernel, h)) < tol
+    want_l = oracle.interpolate(oracle.vector_laplacian(v, h), q, kernel, h)
+    assert rel(icm.icm_op_interpolate_laplacian(sim.handle, q, v.ravel()), want_l) < tol
+    got_s = icm.icm_op_spread(sim.handle, sim.ncell, q, F)
+    assert rel(got_s, oracle.spread(F, q, kernel, h, (nz, ny, nx))) < tol
+    sim.close()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("grid", [(16, 16, 16), (48, 24, 36), (9, 18, 8)])
+@pytest.mark.parametrize("kT,hist,adv", [(1e-3, True, True), (0.0, False, True), (2e-3, True, False)])
+def test_explicit_rhs(icm, precision, grid, kT, hist, adv):
+    sim = _sim(icm, grid, precision, kT=kT, flags=0 if adv else 0x1, seed=99)
+    nx, ny, nz = grid
+    rng = np.random.default_rng(3)
+    v = 0.3 * rng.standard_normal((3, nz, ny, nx))
+    a_prev = rng.standard_normal((3, nz, ny, nx)) if hist else None
+    step = 17
+    r, a = icm.icm_op_explicit_rhs(sim.handle, v.ravel(), None if a_prev is None else a_prev.ravel(), step)
+    prm = oracle.Params(grid, h=1.0, rho=1.3, eta=0.7, kT=kT, dt=0.05, kernel=4, seed=99, advection=adv)
+    rw, aw = oracle.explicit_rhs(v, a_prev, step, prm)
+    assert rel(r, rw) < TOL[precision] / 2
+    if adv:
+        assert rel(a, aw) < TOL[precision] / 2
+    sim.close()
