@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Throughput of the ICM time step (arXiv:1212.6427, Sec. III.C) on GB300.
+
+One "step" is one pass of the whole hot path: midpoint predictor, fused
+noise/viscous/advection right-hand side, spreading, three FFT Helmholtz/projection
+round trips (two of them for the inertial correction), gathers and the blob
+updates, for one synthetic simulation resident in HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload large|bulk|plain]
+                  [--precision 32|64] [--impl ours|reference]
+
+Default workload "large": 256^3 MAC grid, 20000 blobs (min spacing 2h), Peskin
+4-point kernel, excess masses U[-0.5, 2] rho h^3, F = (1e-4, 0, 0), kT = 1e-3,
+dt = 0.01, FP32 fields with FP64 blob state and momentum bookkeeping.  Every face
+field (201 MB) is larger than the 126 MB L2, so no L2 flush is needed between steps.
+
+Under torchrun (N > 1) every rank advances an independent replica (seed offset by
+rank): the method does not shard within one simulation, so scaling is weak and no
+collective is on the data path; the max over ranks of the timed region is used.
+
+--impl reference times the FP64 numpy oracle (the CPU statement of the method) on
+the host cores on the same workload and prints the same JSON line.
+"""
+import argparse
+import faulthandler
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import icm_workloads as wl  # noqa: E402
+
+METRIC = "cell-updates/s"
+faulthandler.enable()
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="large", choices=["large", "bulk", "plain"])
+    ap.add_argument("--precision", type=int, default=None, choices=[32, 64])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64, cuFFT and CPU comparison legs")
+    ap.add_argument("--cpu-budget", type=float, default=150.0, help="seconds of oracle time for the CPU legs")
+    return ap.parse_args()
+
+
+def workload_config(w, precision, world):
+    nx, ny, nz = w["grid"]
+    return {"workload": "icm-%s-%dx%dx%d-%dblobs-k%d-fp%d" % (w["name"], nx, ny, nz, len(w["q"]), w["kernel"], precision),
+            "grid": [nx, ny, nz], "blobs": int(len(w["q"])), "kernel": w["kernel"], "kT": w["kT"], "dt": w["dt"],
+            "excess_mass": "U[-0.5,2] rho h^3" if w["me_range"] else "0",
+            "force": [float(x) for x in np.asarray(w["force"]).reshape(-1, 3)[0]] if len(w["q"]) else [0.0, 0.0, 0.0], "replicas": world, "parallelism": "replicas only (independent per rank)",
+            "l2": "inputs larger than L2 (one face field %.0f MB > 126 MB)" % (3 * nx * ny * nz * precision / 8 / 1e6)
+            if 3 * nx * ny * nz * precision / 8 > 126e6 else "inputs smaller than L2 (no flush)"}
+
+
+def load_workload(name, rank=0):
+    w = wl.workload(name)
+    if rank:
+        w = wl.workload(name, seed=w["seed"] + rank, place_seed=w["place_seed"] + rank)
+    w["name"] = name
+    return w
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1212_6427_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            m = json.load(fh)
+        return float(m["hbm_gbs"]), "of measured"
+    except Exception:
+        return 6800.0, "of fallback"
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it is current."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as fh:
+            t = json.load(fh)
+        if t.get("source_sha") != source_hash():
+            return None
+        return t["kernels"].get(kernel)
+    except Exception:
+        return None
+
+
+def kernel_of(stage):
+    return stage.split(".", 1)[1] if "." in stage else stage
+
+
+def oracle_step_rate(w, budget_s, max_steps):
+    """Time the FP64 numpy oracle on the workload: (seconds per step, steps timed)."""
+    from oracle import icm as oracle
+    prm = oracle.Params(w["grid"], h=w["h"], rho=w["rho"], eta=w["eta"], kT=w["kT"], dt=w["dt"],
+                        kernel=w["kernel"], seed=w["seed"])
+    st = oracle.State(np.zeros((3,) + prm.shape), w["q"], w["u"], w["me"], w["force"])
+    times = []
+    t_all = time.perf_counter()
+    while len(times) < max(1, max_steps):
+        t0 = time.perf_counter()
+        st = oracle.icm_step(st, prm)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_all > budget_s:
+            break
+    return float(np.mean(times)), len(times)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = load_workload(args.workload)
+    prec = args.precision or w["precision"]
+    ncell = int(np.prod(w["grid"]))
+    sec, n = oracle_step_rate(w, args.cpu_budget, args.steps)
+    val = ncell / sec
+    cfg = workload_config(w, prec, 1)
+    line = {"metric": METRIC, "value": val, "unit": "cell-updates/s", "n_gpus": world, "steps": n,
+            "warmup": 0, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg, "impl": "reference",
+            "blob_steps_per_s": len(w["q"]) / sec,
+            "cpu_baseline": {"value": val, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d full oracle step(s) of the %s workload (numpy FP64, single thread)"
+                                       % (n, args.workload)},
+            "e2e": {"value": val, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+    import paper_1212_6427_gb300 as icm
+    from paper_1212_6427_gb300 import build
+    if rank == 0:
+        build.build_library()
+    if dist is not None:
+        dist.barrier()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    log("[bench] rank %d: generating workload %s" % (rank, args.workload))
+    w = load_workload(args.workload, rank)
+    prec = args.precision or w["precision"]
+    grid = w["grid"]
+    ncell = int(np.prod(grid))
+    nb = len(w["q"])
+    sim = icm.Simulation(grid, w["h"], w["rho"], w["eta"], w["kT"], w["dt"], w["kernel"], w["seed"], prec)
+    sim.add_blobs(w["q"], w["u"], w["me"])
+    sim.set_forces(w["force"])
+    stream = sim.stream
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    log("[bench] simulation created (%.0f MB on device); warming up" % (icm.icm_device_bytes(sim.handle) / 1e6))
+    # warm-up (graph capture happens on the first step)
+    sim.step(max(args.warmup, 3))
+    sim.sync()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        sim.step(1)
+    ev1.record(stream)
+    ev1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    sim.sync()   # raises on a CFL / non-finite error raised during the timed steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = ncell * args.steps * world / (ms / 1e3)
+
+    log("[bench] timed region: %.3f ms/step" % (ms / args.steps))
+    # end to end through the public API: host forces in (pinned), blob state out (pinned)
+    f_host = torch.empty((nb, 3), dtype=torch.float64, pin_memory=True).numpy()
+    f_host[:] = w["force"]
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.set_forces(f_host)
+        sim.step(1)
+        sim.read()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": ncell * args.steps * world / e2e_s, "unit": "cell-updates/s",
+           "h2d_bytes_per_step": nb * 3 * 8, "d2h_bytes_per_step": nb * 6 * 8 + 3 * 8 + 8,
+           "calls_per_step": "icm_set_blob_forces + icm_step(1) + icm_read_state(pos, vel, momentum)"}
+
+    log("[bench] e2e done; profiling launches")
+    # per-kernel durations: every launch bracketed by CUDA events on the simulation stream
+    nprof = min(args.steps, 10)
+    prof = sim.profile(nprof)
+    launches_per_step = sum(1 for name, _, _ in prof if kernel_of(name) != "zero")   # memsets are not kernels
+    per_kernel = {}
+    for name, ms_tot, by in prof:
+        k = kernel_of(name)
+        d = per_kernel.setdefault(k, {"ms": 0.0, "bytes": 0.0, "launches": 0})
+        d["ms"] += ms_tot / nprof
+        d["bytes"] += by
+        d["launches"] += 1
+    total = sum(d["ms"] for d in per_kernel.values())
+    dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
+    d = per_kernel[dom]
+    peak, peak_kind = measured_peaks()
+    achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+    traffic = ncu_traffic(dom)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind,
+                "traffic": traffic, "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
+                "avg_launch_ms": d["ms"] / d["launches"], "launches_per_step": d["launches"],
+                "share_of_step": d["ms"] / total}
+    step_bytes = sum(by for _, _, by in prof)
+    kernels = {k: {"ms_per_step": round(v["ms"], 4), "launches": v["launches"],
+                   "GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 else None,
+                   "share": round(v["ms"] / total, 4)} for k, v in sorted(per_kernel.items(), key=lambda kv: -kv[1]["ms"])}
+
+    line = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == 32 else "f64", "data": "synthetic",
+            "config": workload_config(w, prec, world),
+            "blob_steps_per_s": nb * args.steps * world / (ms / 1e3),
+            "step_hbm": {"algorithmic_bytes_per_step": step_bytes,
+                         "achieved_GBps": step_bytes / (ms_step / 1e3) / 1e9,
+                         "frac": step_bytes / (ms_step / 1e3) / 1e9 / peak, "peak_kind": peak_kind},
+            "roofline": roofline, "kernels": kernels, "clocks": clk, "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps, "launches_per_step": launches_per_step}
+
+    if rank == 0 and world == 1 and not args.no_extras:
+        extras(args, w, prec, sim, line, torch, icm, per_kernel)
+    sim.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def extras(args, w, prec, sim, line, torch, icm, per_kernel):
+    grid = w["grid"]
+    ncell = int(np.prod(grid))
+    # the plain FP64 GPU path on the same workload
+    log("[bench] extras: FP64 GPU path")
+    if prec == 32:
+        s64 = icm.Simulation(grid, w["h"], w["rho"], w["eta"], w["kT"], w["dt"], w["kernel"], w["seed"], 64)
+        s64.add_blobs(w["q"], w["u"], w["me"])
+        s64.set_forces(w["force"])
+        s64.step(3)
+        s64.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        n64 = max(3, min(args.steps, 10))
+        e0.record(s64.stream)
+        s64.step(n64)
+        e1.record(s64.stream)
+        e1.synchronize()
+        ms64 = e0.elapsed_time(e1) / n64
+        s64.close()
+        line["fp64_gpu"] = {"ms_per_step": ms64, "value": ncell / (ms64 / 1e3), "unit": "cell-updates/s",
+                            "speedup_fp32_over_fp64": ms64 / line["ms_per_step"]}
+    log("[bench] extras: cuFFT round trip")
+    # cuFFT (through torch.fft) R2C + C2R round trip of the three components, against ours
+    x = torch.randn((3,) + tuple(reversed(grid)), device="cuda",
+                    dtype=torch.float32 if prec == 32 else torch.float64)
+    for _ in range(3):
+        y = torch.fft.irfftn(torch.fft.rfftn(x, dim=(1, 2, 3)), s=x.shape[1:], dim=(1, 2, 3))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        y = torch.fft.irfftn(torch.fft.rfftn(x, dim=(1, 2, 3)), s=x.shape[1:], dim=(1, 2, 3))
+    e1.record()
+    e1.synchronize()
+    del y
+    cufft_ms = e0.elapsed_time(e1) / 10
+    ours_rt = sum(per_kernel[k]["ms"] for k in ("x_fwd", "y_fwd", "z_sym", "y_inv", "x_inv")) / \
+        max(1, per_kernel["z_sym"]["launches"])
+    line["fft_roundtrip"] = {"ours_ms": ours_rt, "cufft_ms": cufft_ms,
+                             "note": "ours includes the fused Helmholtz/projection symbol; cuFFT is R2C+C2R only"}
+    log("[bench] extras: oracle on the host")
+    # the FP64 numpy oracle on the host cores, one bounded sample of the same workload
+    sec, n = oracle_step_rate(w, min(args.cpu_budget, 60.0), 1)
+    line["cpu_baseline"] = {"value": ncell / sec, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                            "sample": "%d full oracle step(s) of this workload (numpy FP64, single thread), %.1f s"
+                                      % (n, sec * n)}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if (args.impl == "ours" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group(backend)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, dist)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

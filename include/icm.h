@@ -143,6 +143,16 @@ icm_status icm_write_state(icm_sim* sim, const double* pos, const double* vel,
  * icm_write_state with adv_prev = NULL). */
 icm_status icm_read_aux(icm_sim* sim, double* adv_prev, double* slip_g, int32_t* has_history);
 
+/* Advance nsteps steps like icm_step, but with every kernel launched eagerly and
+ * bracketed by CUDA events on the simulation's stream (for measurement; slower
+ * than the graph).  For each launch of one step, in order (at most max_stages):
+ * names[i*32 .. i*32+31] a NUL-terminated stage name ("rhs", "rt1.z_sym", ...),
+ * ms[i] the milliseconds summed over the nsteps steps, bytes[i] the algorithmic
+ * bytes one launch must move (reads + writes of its operands, no re-reads).
+ * Synchronises.  Errors: ICM_EINVAL (NULL, nsteps < 1), device errors as icm_sync. */
+icm_status icm_profile_steps(icm_sim* sim, int64_t nsteps, int32_t max_stages, int32_t* nstages, char* names,
+                             double* ms, double* bytes);
+
 /* Number of blobs and bytes of device memory the simulation holds. */
 int64_t icm_num_blobs(const icm_sim* sim);
 int64_t icm_device_bytes(const icm_sim* sim);

@@ -44,6 +44,7 @@ SIGNATURES = {
     "icm_read_state": (_c_i32, [_vp, _dp, _dp, _dp, _dp, ctypes.POINTER(_c_i64)]),
     "icm_write_state": (_c_i32, [_vp, _dp, _dp, _dp, _dp, _dp, _c_i64]),
     "icm_read_aux": (_c_i32, [_vp, _dp, _dp, ctypes.POINTER(_c_i32)]),
+    "icm_profile_steps": (_c_i32, [_vp, _c_i64, _c_i32, ctypes.POINTER(_c_i32), ctypes.c_char_p, _dp, _dp]),
     "icm_num_blobs": (_c_i64, [_vp]),
     "icm_device_bytes": (_c_i64, [_vp]),
     "icm_op_interpolate": (_c_i32, [_vp, _c_i64, _dp, _dp, _dp]),
@@ -161,6 +162,21 @@ def icm_step(sim, nsteps=1):
 
 def icm_sync(sim):
     _check(lib().icm_sync(sim))
+
+
+def icm_profile_steps(sim, nsteps, max_stages=128):
+    """[(stage name, total ms over nsteps, algorithmic bytes per launch)] of one step's launches."""
+    n = _c_i32()
+    names = ctypes.create_string_buffer(32 * max_stages)
+    ms, mp = _out(max_stages)
+    by, bp = _out(max_stages)
+    _check(lib().icm_profile_steps(sim, int(nsteps), max_stages, ctypes.byref(n), names, mp, bp))
+    raw = names.raw
+    out = []
+    for i in range(n.value):
+        nm = raw[32 * i:32 * (i + 1)].split(b"\0", 1)[0].decode()
+        out.append((nm, float(ms[i]), float(by[i])))
+    return out
 
 
 def icm_num_blobs(sim):
@@ -320,3 +336,6 @@ class Simulation:
 
     def read_aux(self):
         return icm_read_aux(self.handle, self.ncell)
+
+    def profile(self, nsteps):
+        return icm_profile_steps(self.handle, nsteps)

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -277,9 +278,54 @@ void invalidate_graph(icm_sim* s) {
   s->graph_ok = false;
 }
 
+// Per-launch CUDA events of an instrumented (eager) step: stage name, algorithmic
+// bytes of one launch, accumulated milliseconds.
+struct Prof {
+  struct Entry {
+    std::string name;
+    double bytes = 0, ms = 0;
+    cudaEvent_t a = nullptr, b = nullptr;
+  };
+  std::vector<Entry> e;
+  size_t idx = 0;
+  void begin(cudaStream_t st, const char* name, double bytes) {
+    if (idx == e.size()) {
+      Entry x;
+      x.name = name;
+      x.bytes = bytes;
+      cudaEventCreate(&x.a);
+      cudaEventCreate(&x.b);
+      e.push_back(x);
+    }
+    cudaEventRecord(e[idx].a, st);
+  }
+  void end(cudaStream_t st) { cudaEventRecord(e[idx++].b, st); }
+  void collect() {
+    for (auto& x : e) {
+      float t = 0;
+      cudaEventElapsedTime(&t, x.a, x.b);
+      x.ms += t;
+    }
+    idx = 0;
+  }
+  ~Prof() {
+    for (auto& x : e) {
+      cudaEventDestroy(x.a);
+      cudaEventDestroy(x.b);
+    }
+  }
+};
+
+#define ICM_STAGE(name, bytes, ...)            \
+  do {                                         \
+    if (prof) prof->begin(st, name, (bytes));  \
+    __VA_ARGS__;                               \
+    if (prof) prof->end(st);                   \
+  } while (0)
+
 // The nine steps of Sec. III.C for one time level, enqueued on s->stream.
 template <typename R>
-void enqueue_step(icm_sim* s) {
+void enqueue_step(icm_sim* s, Prof* prof) {
   cudaStream_t st = s->stream;
   const FftCtx<R> fc = fft_ctx<R>(s);
   const GridParams gp = grid_params(s);
@@ -291,44 +337,59 @@ void enqueue_step(icm_sim* s) {
   const double dvf = s->h * s->h * s->h;
   const double k0scale = 1.0 / (s->rho * dvf);
   const size_t fbytes = 3 * (size_t)s->ncell * sizeof(R);
+  // algorithmic bytes per launch
+  const double F = (double)fbytes;
+  const double S = 3.0 * s->ny * s->nz * s->kx * 2.0 * sizeof(R);
+  const double w3 = (double)s->kernel * s->kernel * s->kernel;
+  const double w3l = (double)(s->kernel + 2) * (s->kernel + 2) * (s->kernel + 2);
+  const double nb = (double)s->nb;
+  const double gath = nb * 3.0 * w3 * sizeof(R);
+  auto solve = [&](const char* tag, const R* src, R* dst, R* dst2, int mode, double a, double b, const double* k0) {
+    std::string t(tag);
+    ICM_STAGE((t + ".x_fwd").c_str(), F + S, fft_x_forward<R>(fc, src, st));
+    ICM_STAGE((t + ".y_fwd").c_str(), 2 * S, fft_y<R>(fc, false, st));
+    ICM_STAGE((t + ".z_sym").c_str(), 2 * S, fft_z_symbol<R>(fc, a, b, k0, k0 ? k0scale : 0.0, st));
+    ICM_STAGE((t + ".y_inv").c_str(), 2 * S, fft_y<R>(fc, true, st));
+    ICM_STAGE((t + ".x_inv").c_str(), S + (mode == OUT_STORE ? F : 3 * F), fft_x_inverse<R>(fc, dst, dst2, mode, st));
+  };
 
-  scalars_before_step(s->scal, s->dt, s->rho, dvf, st);
+  ICM_STAGE("scalars", 0, scalars_before_step(s->scal, s->dt, s->rho, dvf, st));
   // step 1: midpoint predictor (Eq. particle_pred)
-  blob_predict<R>(bp, bs, v, st);
+  ICM_STAGE("predict", 2 * gath + nb * 72, blob_predict<R>(bp, bs, v, st));
   // step 2: unperturbed fluid solve (Eq. provisional_step-1)
-  explicit_rhs<R>(gp, v, adv, work, s->step_dev, s->hist_dev, st);
-  if (s->any_force) blob_spread<R>(bp, s->nb, s->qh, s->f, work, st);
-  spectral_solve<R>(fc, work, v, nullptr, OUT_STORE, s->rho / s->dt, 0.5 * s->eta, s->scal + SC_K0, k0scale, st);
+  ICM_STAGE("rhs", 4 * F, explicit_rhs<R>(gp, v, adv, work, s->step_dev, s->hist_dev, st));
+  if (s->any_force) ICM_STAGE("spread", 2 * gath + nb * 48, blob_spread<R>(bp, s->nb, s->qh, s->f, work, st));
+  solve("rt1", work, v, nullptr, OUT_STORE, s->rho / s->dt, 0.5 * s->eta, s->scal + SC_K0);
   if (s->any_me) {
     // step 4: slip correction and momentum change (Eq. delta_u_nph_visc)
-    blob_momentum_change<R>(bp, bs, v, st);
+    ICM_STAGE("dp", gath + nb * 136, blob_momentum_change<R>(bp, bs, v, st));
     // step 5: dv~ = m~_f / (rho (m~_f + m_e)) P S dp
-    cudaMemsetAsync(work, 0, fbytes, st);
-    blob_spread<R>(bp, s->nb, s->qh, s->cdp, work, st);
-    spectral_solve<R>(fc, work, work, nullptr, OUT_STORE, 1.0, 0.0, nullptr, 0.0, st);
+    ICM_STAGE("zero", F, cudaMemsetAsync(work, 0, fbytes, st));
+    ICM_STAGE("spread", 2 * gath + nb * 48, blob_spread<R>(bp, s->nb, s->qh, s->cdp, work, st));
+    solve("rt2", work, work, nullptr, OUT_STORE, 1.0, 0.0, nullptr);
     // steps 6 and 8 (blob side): J dv~, source dp - m_e J dv~, u^{n+1}
-    blob_inertial<R>(bp, bs, work, st);
+    ICM_STAGE("inertial", gath + nb * 160, blob_inertial<R>(bp, bs, work, st));
     // step 6: (rho - dt/2 eta L) dv + dt grad dpi = S (dp - m_e J dv~); step 7: v = v~ + dv
-    cudaMemsetAsync(work, 0, fbytes, st);
-    blob_spread<R>(bp, s->nb, s->qh, s->src, work, st);
-    spectral_solve<R>(fc, work, v, work, OUT_ADD_AND_STORE2, s->rho, 0.5 * s->dt * s->eta, s->scal + SC_SUMSRC,
-                      k0scale, st);
+    ICM_STAGE("zero", F, cudaMemsetAsync(work, 0, fbytes, st));
+    ICM_STAGE("spread", 2 * gath + nb * 48, blob_spread<R>(bp, s->nb, s->qh, s->src, work, st));
+    solve("rt3", work, v, work, OUT_ADD_AND_STORE2, s->rho, 0.5 * s->dt * s->eta, s->scal + SC_SUMSRC);
     // step 9 and the lagged slip term
-    blob_finish<R>(bp, bs, v, work, true, st);
+    ICM_STAGE("finish", gath + nb * 3.0 * w3l * sizeof(R) + nb * 144, blob_finish<R>(bp, bs, v, work, true, st));
   } else {
-    blob_finish<R>(bp, bs, v, nullptr, false, st);
+    ICM_STAGE("finish", gath + nb * 144, blob_finish<R>(bp, bs, v, nullptr, false, st));
   }
-  scalars_after_step(s->scal, s->dt, s->rho, dvf, s->any_me, s->step_dev, s->hist_dev, st);
+  ICM_STAGE("scalars", 0, scalars_after_step(s->scal, s->dt, s->rho, dvf, s->any_me, s->step_dev, s->hist_dev, st));
 }
+#undef ICM_STAGE
 
 icm_status capture_graph(icm_sim* s) {
   invalidate_graph(s);
   cudaGraph_t graph = nullptr;
   ICM_CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
   if (s->prec == 32)
-    enqueue_step<float>(s);
+    enqueue_step<float>(s, nullptr);
   else
-    enqueue_step<double>(s);
+    enqueue_step<double>(s, nullptr);
   const cudaError_t e = cudaStreamEndCapture(s->stream, &graph);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -706,6 +767,32 @@ icm_status icm_read_aux(icm_sim* s, double* adv_prev, double* slip_g, int32_t* h
   ICM_CK(cudaStreamSynchronize(s->stream));
   if (has_history) *has_history = hist;
   return ICM_OK;
+}
+
+icm_status icm_profile_steps(icm_sim* s, int64_t nsteps, int32_t max_stages, int32_t* nstages, char* names,
+                             double* ms, double* bytes) {
+  if (!s || nsteps < 1 || max_stages < 1 || !nstages || !names || !ms || !bytes)
+    return fail(ICM_EINVAL, "bad arguments");
+  ICM_CK(cudaStreamSynchronize(s->stream));
+  Prof prof;
+  for (int64_t i = 0; i < nsteps; ++i) {
+    if (s->prec == 32)
+      enqueue_step<float>(s, &prof);
+    else
+      enqueue_step<double>(s, &prof);
+    ICM_CK(cudaGetLastError());
+    ICM_CK(cudaStreamSynchronize(s->stream));
+    prof.collect();
+  }
+  const int n = (int)std::min<size_t>(prof.e.size(), (size_t)max_stages);
+  for (int i = 0; i < n; ++i) {
+    memset(names + 32 * i, 0, 32);
+    strncpy(names + 32 * i, prof.e[i].name.c_str(), 31);
+    ms[i] = prof.e[i].ms;
+    bytes[i] = prof.e[i].bytes;
+  }
+  *nstages = n;
+  return check_device_errors(s);
 }
 
 int64_t icm_num_blobs(const icm_sim* s) { return s ? s->nb : -1; }

@@ -411,27 +411,54 @@ void set_smem_attributes() {
 }  // namespace
 
 template <typename R>
-void spectral_solve(const FftCtx<R>& f, const R* src, R* dst, R* dst2, int mode, double a, double b,
-                    const double* k0sum, double k0scale, cudaStream_t st) {
-  constexpr int NL = seg_lines<R>();
+void fft_x_forward(const FftCtx<R>& f, const R* src, cudaStream_t st) {
   const int nrows = f.ny * f.nz;
   const int xblocks = (nrows + 2 * kXLines - 1) / (2 * kXLines);
-  const int kxt = (f.kx + NL - 1) / NL;
   k_xfwd<R><<<dim3(xblocks, 3), kThreads, smem_x<R>(f.nx), st>>>(src, f.spec, f.px, nrows, f.ncell, f.kx, f.kxp);
-  k_ypass<R, false><<<dim3(kxt, f.nz, 3), kThreads, smem_y<R>(f.ny), st>>>(f.spec, f.py, f.nz, f.kx, f.kxp);
+}
+
+template <typename R>
+void fft_y(const FftCtx<R>& f, bool inverse, cudaStream_t st) {
+  constexpr int NL = seg_lines<R>();
+  const int kxt = (f.kx + NL - 1) / NL;
+  if (inverse)
+    k_ypass<R, true><<<dim3(kxt, f.nz, 3), kThreads, smem_y<R>(f.ny), st>>>(f.spec, f.py, f.nz, f.kx, f.kxp);
+  else
+    k_ypass<R, false><<<dim3(kxt, f.nz, 3), kThreads, smem_y<R>(f.ny), st>>>(f.spec, f.py, f.nz, f.kx, f.kxp);
+}
+
+template <typename R>
+void fft_z_symbol(const FftCtx<R>& f, double a, double b, const double* k0sum, double k0scale, cudaStream_t st) {
+  constexpr int NL = seg_lines<R>();
+  const int kxt = (f.kx + NL - 1) / NL;
   SymParams<R> sp;
   sp.a = (R)a;
   sp.b = (R)b;
   sp.inv_ntot = (R)(1.0 / (double)f.ncell);
-  sp.k0mul = k0scale / (double)f.ncell;
   sp.dx = f.dx; sp.ddx = f.ddx;
   sp.dy = f.dy; sp.ddy = f.ddy;
   sp.dz = f.dz; sp.ddz = f.ddz;
   sp.k0sum = k0sum;
+  sp.k0mul = k0scale / (double)f.ncell;
   k_zsym<R><<<dim3(kxt, f.ny), kThreads, smem_z<R>(f.nz), st>>>(f.spec, f.pz, f.ny, f.kx, f.kxp, sp);
-  k_ypass<R, true><<<dim3(kxt, f.nz, 3), kThreads, smem_y<R>(f.ny), st>>>(f.spec, f.py, f.nz, f.kx, f.kxp);
+}
+
+template <typename R>
+void fft_x_inverse(const FftCtx<R>& f, R* dst, R* dst2, int mode, cudaStream_t st) {
+  const int nrows = f.ny * f.nz;
+  const int xblocks = (nrows + 2 * kXLines - 1) / (2 * kXLines);
   k_xinv<R><<<dim3(xblocks, 3), kThreads, smem_x<R>(f.nx), st>>>(f.spec, dst, dst2, mode, f.px, nrows, f.ncell,
                                                                  f.kxp);
+}
+
+template <typename R>
+void spectral_solve(const FftCtx<R>& f, const R* src, R* dst, R* dst2, int mode, double a, double b,
+                    const double* k0sum, double k0scale, cudaStream_t st) {
+  fft_x_forward<R>(f, src, st);
+  fft_y<R>(f, false, st);
+  fft_z_symbol<R>(f, a, b, k0sum, k0scale, st);
+  fft_y<R>(f, true, st);
+  fft_x_inverse<R>(f, dst, dst2, mode, st);
 }
 
 void fft_prepare() {
@@ -439,9 +466,15 @@ void fft_prepare() {
   set_smem_attributes<double>();
 }
 
-template void spectral_solve<float>(const FftCtx<float>&, const float*, float*, float*, int, double, double,
-                                    const double*, double, cudaStream_t);
-template void spectral_solve<double>(const FftCtx<double>&, const double*, double*, double*, int, double, double,
-                                     const double*, double, cudaStream_t);
+#define ICM_INST(R)                                                                                    \
+  template void spectral_solve<R>(const FftCtx<R>&, const R*, R*, R*, int, double, double, const double*, double, \
+                                  cudaStream_t);                                                        \
+  template void fft_x_forward<R>(const FftCtx<R>&, const R*, cudaStream_t);                             \
+  template void fft_y<R>(const FftCtx<R>&, bool, cudaStream_t);                                         \
+  template void fft_z_symbol<R>(const FftCtx<R>&, double, double, const double*, double, cudaStream_t); \
+  template void fft_x_inverse<R>(const FftCtx<R>&, R*, R*, int, cudaStream_t);
+ICM_INST(float)
+ICM_INST(double)
+#undef ICM_INST
 
 }  // namespace icm

@@ -50,6 +50,13 @@ template <typename R>
 void spectral_solve(const FftCtx<R>& f, const R* src, R* dst, R* dst2, int mode, double a, double b,
                     const double* k0sum, double k0scale, cudaStream_t st);
 
+// The five passes of spectral_solve, for callers that time them one by one.
+template <typename R> void fft_x_forward(const FftCtx<R>& f, const R* src, cudaStream_t st);
+template <typename R> void fft_y(const FftCtx<R>& f, bool inverse, cudaStream_t st);
+template <typename R>
+void fft_z_symbol(const FftCtx<R>& f, double a, double b, const double* k0sum, double k0scale, cudaStream_t st);
+template <typename R> void fft_x_inverse(const FftCtx<R>& f, R* dst, R* dst2, int mode, cudaStream_t st);
+
 // Raise the dynamic shared-memory limits of the kernels (call once, outside capture).
 void fft_prepare();
 void grid_prepare();

@@ -55,5 +55,5 @@ def compare_states(got, want, prm, q_prev):
     if want.q.shape[0]:
         err["u"] = rel(got.u, want.u)
         err["dq"] = rel(min_image(got.q - q_prev, box), min_image(want.q - q_prev, box))
-        err["q"] = rel(min_image(got.q - want.q, box), want.q)
+        err["q"] = float(np.linalg.norm(min_image(got.q - want.q, box)) / np.linalg.norm(want.q))
     return err

@@ -41,7 +41,9 @@ def _run_parity(prm, st0, precision, nsteps):
         sim.step(1)
         got, mom = read_oracle_state(sim, prm, state.me, state.force)
         err = compare_states(got, want, prm, q_prev)
-        err["P"] = rel(mom, oracle.total_momentum(want, prm)) if np.abs(oracle.total_momentum(want, prm)).max() > 0 else 0.0
+        # momentum against its natural scale rho dV_f sum|v| + sum|m_e u| (P itself may be ~0)
+        scale = prm.rho * prm.h ** 3 * np.abs(want.v).sum() + np.abs(want.me[:, None] * want.u).sum()
+        err["P"] = float(np.abs(mom - oracle.total_momentum(want, prm)).max() / scale)
         for k, e in err.items():
             worst[k] = max(worst.get(k, 0.0), e)
         assert got.step == want.step
