@@ -104,6 +104,13 @@ def _out(n):
 # Allocator: torch's caching allocator provides the library's device memory.
 # ---------------------------------------------------------------------------
 def use_torch_allocator():
+    """Install torch's caching allocator as the library's allocator, once per process.
+
+    Simulations keep the function pointers they were created with, so the ctypes
+    thunks must live as long as the process: they are created once and never replaced."""
+    if _keep:
+        _check(lib().icm_set_default_allocator(_keep[0], _keep[1], None))
+        return
     import torch
 
     def _alloc(ctx, nbytes, stream):
@@ -121,6 +128,7 @@ def use_torch_allocator():
 
 
 def use_cuda_malloc():
+    """Simulations created afterwards use cudaMalloc/cudaFree (existing ones keep theirs)."""
     _check(lib().icm_set_default_allocator(_ALLOC_T(), _FREE_T(), None))
 
 

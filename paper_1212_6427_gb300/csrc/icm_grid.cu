@@ -11,18 +11,30 @@
 namespace icm {
 namespace {
 
-constexpr int TX = 32, TY = 16;     // cells per block in x and y
+constexpr int TX = 32, TY = 16;     // cells per block in x and y (one thread each)
 constexpr int KZ = 16;              // z planes marched per block
 constexpr int HX = TX + 2, HY = TY + 2;
+constexpr int HALO = HX * HY;       // cells of one plane with a one-cell halo
+constexpr int NT = TX * TY;         // threads per block
+constexpr int PER = (HALO + NT - 1) / NT;   // halo cells loaded per thread
 
 __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
-// One (TX+2) x (TY+2) plane of stress normals (halo of one cell) into ring slot s.
+// Shared-memory rings of the marching block: three velocity planes (k-1, k, k+1) of
+// the three components and three planes of the six stress normals, each with a
+// one-cell halo in x and y.
 template <typename R>
-__device__ __forceinline__ void gen_plane(R (*ring)[6][HY][HX], int slot, int i0, int j0, int k, const GridParams& g,
-                                          uint32_t step, int tid, int nthr) {
+struct RhsSmem {
+  R v[3][3][HY][HX];
+  R z[3][6][HY][HX];
+};
+
+// One plane of stress normals (with halo) into ring slot `slot`.
+template <typename R>
+__device__ __forceinline__ void gen_plane(RhsSmem<R>& sm, int slot, int i0, int j0, int k, const GridParams& g,
+                                          uint32_t step, int tid) {
   const int kk = wrapi(k, g.nz);
-  for (int idx = tid; idx < HX * HY; idx += nthr) {
+  for (int idx = tid; idx < HALO; idx += NT) {
     const int hx = idx % HX, hy = idx / HX;
     const int gi = wrapi(i0 - 1 + hx, g.nx);
     const int gj = wrapi(j0 - 1 + hy, g.ny);
@@ -30,68 +42,113 @@ __device__ __forceinline__ void gen_plane(R (*ring)[6][HY][HX], int slot, int i0
     R z[6];
     cell_normals<R>(cell, step, g.key0, g.key1, z);
 #pragma unroll
-    for (int c = 0; c < 6; ++c) ring[slot][c][hy][hx] = z[c];
+    for (int c = 0; c < 6; ++c) sm.z[slot][c][hy][hx] = z[c];
   }
 }
 
+// Global loads of one velocity plane (with halo) into registers: thread tid takes
+// halo cells tid, tid + NT, ...
+template <typename R>
+__device__ __forceinline__ void load_plane(R (&r)[PER][3], const R* __restrict__ v, int i0, int j0, int k,
+                                           const GridParams& g, int tid) {
+  const int kk = wrapi(k, g.nz);
+#pragma unroll
+  for (int t = 0; t < PER; ++t) {
+    const int idx = tid + t * NT;
+    if (idx < HALO) {
+      const int hx = idx % HX, hy = idx / HX;
+      const long long o = wrapi(i0 - 1 + hx, g.nx) + (long long)g.nx * (wrapi(j0 - 1 + hy, g.ny) + (long long)g.ny * kk);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) r[t][c] = v[c * g.ncell + o];
+    }
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void store_plane(RhsSmem<R>& sm, int slot, const R (&r)[PER][3], int tid) {
+#pragma unroll
+  for (int t = 0; t < PER; ++t) {
+    const int idx = tid + t * NT;
+    if (idx < HALO) {
+      const int hx = idx % HX, hy = idx / HX;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) sm.v[slot][c][hy][hx] = r[t][c];
+    }
+  }
+}
+
+// Marching block: TX x TY cells per plane, KZ planes.  Per plane: the loads of the
+// plane after next are issued first, the stress normals of the next plane are
+// generated while they are in flight, then the current plane is computed entirely
+// from shared memory.
 template <typename R, bool NOISE>
-__global__ void __launch_bounds__(TX* TY) k_rhs(const R* __restrict__ v, R* __restrict__ adv, R* __restrict__ rhs,
-                                               GridParams g, const long long* __restrict__ step_dev,
-                                               const int* __restrict__ hist_dev) {
+__global__ void __launch_bounds__(NT) k_rhs(const R* __restrict__ v, R* __restrict__ adv, R* __restrict__ rhs,
+                                            GridParams g, const long long* __restrict__ step_dev,
+                                            const int* __restrict__ hist_dev) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R(*ring)[6][HY][HX] = reinterpret_cast<R(*)[6][HY][HX]>(smem_raw);
+  RhsSmem<R>& sm = *reinterpret_cast<RhsSmem<R>*>(smem_raw);
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int tid = tx + TX * ty, nthr = TX * TY;
+  const int tid = tx + TX * ty;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * KZ;
   const int i = i0 + tx, j = j0 + ty;
   const bool active = i < g.nx && j < g.ny;
   const uint32_t step = (uint32_t)(*step_dev);
   const bool hist = *hist_dev != 0;
-  const int nx = g.nx, ny = g.ny, nz = g.nz;
   const long long nc = g.ncell;
   const R rho = (R)g.rho, inv_h = (R)(1.0 / g.h), inv_h2 = (R)(1.0 / (g.h * g.h));
   const R rho_dt = (R)(g.rho / g.dt), half_eta = (R)(0.5 * g.eta);
-  const R s_amp = (R)sqrt(g.kT * g.eta / (g.h * g.h * g.h * g.dt));
-  const R sd = R(2) * s_amp, so = (R)(1.4142135623730951 * sqrt(g.kT * g.eta / (g.h * g.h * g.h * g.dt)));
+  const double s_amp = sqrt(g.kT * g.eta / (g.h * g.h * g.h * g.dt));
+  const R sd = (R)(2.0 * s_amp * (1.0 / g.h)), so = (R)(1.4142135623730951 * s_amp * (1.0 / g.h));
   const R adv_on = g.advection ? R(1) : R(0);
+  const R h2 = R(0.5);
+  const int lx = tx + 1, ly = ty + 1;
 
+  R pre[PER][3];
+  load_plane<R>(pre, v, i0, j0, k0 - 1, g, tid);
+  store_plane<R>(sm, 0, pre, tid);
+  load_plane<R>(pre, v, i0, j0, k0, g, tid);
+  store_plane<R>(sm, 1, pre, tid);
+  load_plane<R>(pre, v, i0, j0, k0 + 1, g, tid);
   if (NOISE) {
-    gen_plane<R>(ring, 0, i0, j0, k0 - 1, g, step, tid, nthr);
-    gen_plane<R>(ring, 1, i0, j0, k0, g, step, tid, nthr);
+    gen_plane<R>(sm, 0, i0, j0, k0 - 1, g, step, tid);
+    gen_plane<R>(sm, 1, i0, j0, k0, g, step, tid);
   }
-  const int kend = min(k0 + KZ, nz);
+  const int kend = min(k0 + KZ, g.nz);
   for (int k = k0; k < kend; ++k) {
     const int kk = k - k0;
     const int sp = kk % 3, sc = (kk + 1) % 3, sn = (kk + 2) % 3;
-    if (NOISE) gen_plane<R>(ring, sn, i0, j0, k + 1, g, step, tid, nthr);
+    store_plane<R>(sm, sn, pre, tid);                       // plane k+1
+    long long o = 0;
+    R ao[3] = {R(0), R(0), R(0)};
+    if (active) {
+      o = i + (long long)g.nx * (j + (long long)g.ny * k);
+      if (hist) {
+        ao[0] = adv[o];
+        ao[1] = adv[nc + o];
+        ao[2] = adv[2 * nc + o];
+      }
+    }
+    if (k + 1 < kend) load_plane<R>(pre, v, i0, j0, k + 2, g, tid);   // in flight during the noise
+    if (NOISE) gen_plane<R>(sm, sn, i0, j0, k + 1, g, step, tid);
     __syncthreads();
     if (active) {
-      const int im = wrapi(i - 1, nx), ip = wrapi(i + 1, nx);
-      const int jm = wrapi(j - 1, ny), jp = wrapi(j + 1, ny);
-      const int km = wrapi(k - 1, nz), kp = wrapi(k + 1, nz);
-      const long long rc = (long long)nx * (j + (long long)ny * k);
-      const long long rym = (long long)nx * (jm + (long long)ny * k), ryp = (long long)nx * (jp + (long long)ny * k);
-      const long long rzm = (long long)nx * (j + (long long)ny * km), rzp = (long long)nx * (j + (long long)ny * kp);
-      const long long rypzm = (long long)nx * (jp + (long long)ny * km);
-      const long long rymzp = (long long)nx * (jm + (long long)ny * kp);
-      const R* vx = v;
-      const R* vy = v + nc;
-      const R* vz = v + 2 * nc;
+      const auto P = sm.v[sp];
+      const auto C = sm.v[sc];
+      const auto N = sm.v[sn];
       // component x
-      const R x_c = vx[rc + i], x_xp = vx[rc + ip], x_xm = vx[rc + im];
-      const R x_yp = vx[ryp + i], x_ym = vx[rym + i], x_zp = vx[rzp + i], x_zm = vx[rzm + i];
-      const R x_xpym = vx[rym + ip], x_xpzm = vx[rzm + ip];
+      const R x_c = C[0][ly][lx], x_xp = C[0][ly][lx + 1], x_xm = C[0][ly][lx - 1];
+      const R x_yp = C[0][ly + 1][lx], x_ym = C[0][ly - 1][lx], x_zp = N[0][ly][lx], x_zm = P[0][ly][lx];
+      const R x_xpym = C[0][ly - 1][lx + 1], x_xpzm = P[0][ly][lx + 1];
       // component y
-      const R y_c = vy[rc + i], y_xp = vy[rc + ip], y_xm = vy[rc + im];
-      const R y_yp = vy[ryp + i], y_ym = vy[rym + i], y_zp = vy[rzp + i], y_zm = vy[rzm + i];
-      const R y_ypxm = vy[ryp + im], y_ypzm = vy[rypzm + i];
+      const R y_c = C[1][ly][lx], y_xp = C[1][ly][lx + 1], y_xm = C[1][ly][lx - 1];
+      const R y_yp = C[1][ly + 1][lx], y_ym = C[1][ly - 1][lx], y_zp = N[1][ly][lx], y_zm = P[1][ly][lx];
+      const R y_ypxm = C[1][ly + 1][lx - 1], y_ypzm = P[1][ly + 1][lx];
       // component z
-      const R z_c = vz[rc + i], z_xp = vz[rc + ip], z_xm = vz[rc + im];
-      const R z_yp = vz[ryp + i], z_ym = vz[rym + i], z_zp = vz[rzp + i], z_zm = vz[rzm + i];
-      const R z_zpxm = vz[rzp + im], z_zpym = vz[rymzp + i];
+      const R z_c = C[2][ly][lx], z_xp = C[2][ly][lx + 1], z_xm = C[2][ly][lx - 1];
+      const R z_yp = C[2][ly + 1][lx], z_ym = C[2][ly - 1][lx], z_zp = N[2][ly][lx], z_zm = P[2][ly][lx];
+      const R z_zpxm = N[2][ly][lx - 1], z_zpym = N[2][ly - 1][lx];
 
-      const R h2 = R(0.5);
-      // edge products ut_a ut_b, edge index e: ut_a = (v_a[e] + v_a[e-e_b])/2, ut_b = (v_b[e] + v_b[e-e_a])/2
+      // edge products ut_a ut_b at edge index e: ut_a = (v_a[e] + v_a[e-e_b])/2, ut_b = (v_b[e] + v_b[e-e_a])/2
       const R exy_c = (x_c + x_ym) * h2 * ((y_c + y_xm) * h2);
       const R exy_yp = (x_yp + x_c) * h2 * ((y_yp + y_ypxm) * h2);
       const R exy_xp = (x_xp + x_xpym) * h2 * ((y_xp + y_c) * h2);
@@ -101,44 +158,39 @@ __global__ void __launch_bounds__(TX* TY) k_rhs(const R* __restrict__ v, R* __re
       const R eyz_c = (y_c + y_zm) * h2 * ((z_c + z_ym) * h2);
       const R eyz_zp = (y_zp + y_c) * h2 * ((z_zp + z_zpym) * h2);
       const R eyz_yp = (y_yp + y_ypzm) * h2 * ((z_yp + z_c) * h2);
-
       const R ubx_c = (x_xp + x_c) * h2, ubx_m = (x_c + x_xm) * h2;
       const R uby_c = (y_yp + y_c) * h2, uby_m = (y_c + y_ym) * h2;
       const R ubz_c = (z_zp + z_c) * h2, ubz_m = (z_c + z_zm) * h2;
       const R ax = adv_on * rho * inv_h * (ubx_c * ubx_c - ubx_m * ubx_m + exy_yp - exy_c + exz_zp - exz_c);
       const R ay = adv_on * rho * inv_h * (uby_c * uby_c - uby_m * uby_m + exy_xp - exy_c + eyz_zp - eyz_c);
       const R az = adv_on * rho * inv_h * (ubz_c * ubz_c - ubz_m * ubz_m + exz_xp - exz_c + eyz_yp - eyz_c);
-
-      const R lx = (x_xp + x_xm + x_yp + x_ym + x_zp + x_zm - R(6) * x_c) * inv_h2;
-      const R ly = (y_xp + y_xm + y_yp + y_ym + y_zp + y_zm - R(6) * y_c) * inv_h2;
-      const R lz = (z_xp + z_xm + z_yp + z_ym + z_zp + z_zm - R(6) * z_c) * inv_h2;
-
+      const R lapx = (x_xp + x_xm + x_yp + x_ym + x_zp + x_zm - R(6) * x_c) * inv_h2;
+      const R lapy = (y_xp + y_xm + y_yp + y_ym + y_zp + y_zm - R(6) * y_c) * inv_h2;
+      const R lapz = (z_xp + z_xm + z_yp + z_ym + z_zp + z_zm - R(6) * z_c) * inv_h2;
       R fx = R(0), fy = R(0), fz = R(0);
       if (NOISE) {
-        const int lx_ = tx + 1, ly_ = ty + 1;
-        auto cur = ring[sc];
-        auto prv = ring[sp];
-        auto nxt = ring[sn];
-        fx = sd * (cur[0][ly_][lx_] - cur[0][ly_][lx_ - 1]) + so * (cur[3][ly_ + 1][lx_] - cur[3][ly_][lx_]) +
-             so * (nxt[4][ly_][lx_] - cur[4][ly_][lx_]);
-        fy = sd * (cur[1][ly_][lx_] - cur[1][ly_ - 1][lx_]) + so * (cur[3][ly_][lx_ + 1] - cur[3][ly_][lx_]) +
-             so * (nxt[5][ly_][lx_] - cur[5][ly_][lx_]);
-        fz = sd * (cur[2][ly_][lx_] - prv[2][ly_][lx_]) + so * (cur[4][ly_][lx_ + 1] - cur[4][ly_][lx_]) +
-             so * (cur[5][ly_ + 1][lx_] - cur[5][ly_][lx_]);
-        fx *= inv_h;
-        fy *= inv_h;
-        fz *= inv_h;
+        const auto ZC = sm.z[sc];
+        const auto ZP = sm.z[sp];
+        const auto ZN = sm.z[sn];
+        // divergence of the stress at the faces: Sigma_aa at cells, Sigma_ab on edges
+        fx = sd * (ZC[0][ly][lx] - ZC[0][ly][lx - 1]) + so * (ZC[3][ly + 1][lx] - ZC[3][ly][lx]) +
+             so * (ZN[4][ly][lx] - ZC[4][ly][lx]);
+        fy = sd * (ZC[1][ly][lx] - ZC[1][ly - 1][lx]) + so * (ZC[3][ly][lx + 1] - ZC[3][ly][lx]) +
+             so * (ZN[5][ly][lx] - ZC[5][ly][lx]);
+        fz = sd * (ZC[2][ly][lx] - ZP[2][ly][lx]) + so * (ZC[4][ly][lx + 1] - ZC[4][ly][lx]) +
+             so * (ZC[5][ly + 1][lx] - ZC[5][ly][lx]);
       }
-      const long long o = rc + i;
-      const R ox = hist ? adv[o] : ax;
-      const R oy = hist ? adv[nc + o] : ay;
-      const R oz = hist ? adv[2 * nc + o] : az;
+      if (!hist) {
+        ao[0] = ax;
+        ao[1] = ay;
+        ao[2] = az;
+      }
       adv[o] = ax;
       adv[nc + o] = ay;
       adv[2 * nc + o] = az;
-      rhs[o] = rho_dt * x_c + half_eta * lx + fx - (R(1.5) * ax - R(0.5) * ox);
-      rhs[nc + o] = rho_dt * y_c + half_eta * ly + fy - (R(1.5) * ay - R(0.5) * oy);
-      rhs[2 * nc + o] = rho_dt * z_c + half_eta * lz + fz - (R(1.5) * az - R(0.5) * oz);
+      rhs[o] = rho_dt * x_c + half_eta * lapx + fx - (R(1.5) * ax - R(0.5) * ao[0]);
+      rhs[nc + o] = rho_dt * y_c + half_eta * lapy + fy - (R(1.5) * ay - R(0.5) * ao[1]);
+      rhs[2 * nc + o] = rho_dt * z_c + half_eta * lapz + fz - (R(1.5) * az - R(0.5) * ao[2]);
     }
     __syncthreads();
   }
@@ -230,7 +282,7 @@ __global__ void k_scal_after(double* scal, int inertial, long long* step_dev, in
 }
 
 template <typename R>
-size_t rhs_smem() { return (size_t)3 * 6 * HY * HX * sizeof(R); }
+size_t rhs_smem() { return sizeof(RhsSmem<R>); }
 
 }  // namespace
 
@@ -242,7 +294,7 @@ void explicit_rhs(const GridParams& g, const R* v, R* adv, R* rhs, const long lo
   if (g.kT > 0.0)
     k_rhs<R, true><<<grid, block, rhs_smem<R>(), st>>>(v, adv, rhs, g, step_dev, hist_dev);
   else
-    k_rhs<R, false><<<grid, block, 0, st>>>(v, adv, rhs, g, step_dev, hist_dev);
+    k_rhs<R, false><<<grid, block, rhs_smem<R>(), st>>>(v, adv, rhs, g, step_dev, hist_dev);
 }
 
 template <typename R>
@@ -276,6 +328,8 @@ void convert_from_double(const double* src, R* dst, long long n, cudaStream_t st
 void grid_prepare() {
   cudaFuncSetAttribute(k_rhs<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_smem<float>());
   cudaFuncSetAttribute(k_rhs<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_smem<double>());
+  cudaFuncSetAttribute(k_rhs<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_smem<float>());
+  cudaFuncSetAttribute(k_rhs<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_smem<double>());
 }
 
 void scalars_before_step(double* scal, double dt, double, double, cudaStream_t st) {
