@@ -153,6 +153,31 @@ icm_status icm_read_aux(icm_sim* sim, double* adv_prev, double* slip_g, int32_t*
 icm_status icm_profile_steps(icm_sim* sim, int64_t nsteps, int32_t max_stages, int32_t* nstages, char* names,
                              double* ms, double* bytes);
 
+/* Total momentum P = rho h^3 sum_k v_k of a face field that is already on the device,
+ * for callers that must not allocate device memory.  The paper has no counterpart:
+ * this is a service of the library, the same FP64 compensated sum that gives the
+ * fluid part of icm_read_state's momentum.  Callers that cannot allocate include
+ * code running while a stream capture is open (cudaMalloc is refused there),
+ * processes whose device memory is already reserved by a framework's pool, and
+ * loops that must not take the device-wide synchronisation of cudaMalloc/cudaFree.
+ *   fluid_v_dev : device pointer to 3*ncell values (float if precision == 32,
+ *                 double if 64), the face-field layout of the header comment;
+ *                 read only, owned by the caller.
+ *   ncell       : Nx*Ny*Nz, 1 <= ncell <= 134217728 (512^3); larger is ICM_EINVAL.
+ *   rho, h      : density and grid spacing (the factor rho h^3).
+ *   cuda_stream : stream to run on (NULL = legacy default stream); synchronised.
+ *   momentum[3] : host output.
+ * Allocates nothing: its scratch is a fixed array of 3*16384+8 doubles (~384 KB)
+ * that the library declares in device memory, held by every GPU that loads the
+ * library until the process exits.  The first call on each device looks up that
+ * array's device address (once, with that device current); make that first call
+ * before any stream capture.  All calls share the array and each overwrites what
+ * the previous one left there, so calls that overlap on the GPU (other streams or
+ * threads at the same time) race and must be serialised by the caller.
+ * Errors: ICM_EINVAL (NULL pointer, bad precision, ncell out of range), ICM_ECUDA. */
+icm_status icm_fluid_momentum_static(const void* fluid_v_dev, int32_t precision, int64_t ncell, double rho,
+                                     double h, void* cuda_stream, double momentum[3]);
+
 /* Number of blobs and bytes of device memory the simulation holds. */
 int64_t icm_num_blobs(const icm_sim* sim);
 int64_t icm_device_bytes(const icm_sim* sim);

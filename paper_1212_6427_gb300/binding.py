@@ -45,6 +45,7 @@ SIGNATURES = {
     "icm_write_state": (_c_i32, [_vp, _dp, _dp, _dp, _dp, _dp, _c_i64]),
     "icm_read_aux": (_c_i32, [_vp, _dp, _dp, ctypes.POINTER(_c_i32)]),
     "icm_profile_steps": (_c_i32, [_vp, _c_i64, _c_i32, ctypes.POINTER(_c_i32), ctypes.c_char_p, _dp, _dp]),
+    "icm_fluid_momentum_static": (_c_i32, [_vp, _c_i32, _c_i64, _c_d, _c_d, _vp, _dp]),
     "icm_num_blobs": (_c_i64, [_vp]),
     "icm_device_bytes": (_c_i64, [_vp]),
     "icm_op_interpolate": (_c_i32, [_vp, _c_i64, _dp, _dp, _dp]),
@@ -184,6 +185,14 @@ def icm_profile_steps(sim, nsteps, max_stages=128):
     for i in range(n.value):
         nm = raw[32 * i:32 * (i + 1)].split(b"\0", 1)[0].decode()
         out.append((nm, float(ms[i]), float(by[i])))
+    return out
+
+
+def icm_fluid_momentum_static(fluid_v_dev_ptr, precision, ncell, rho, h, cuda_stream=None):
+    """rho h^3 sum v of a device face field, computed without any device allocation."""
+    out, op = _out(3)
+    _check(lib().icm_fluid_momentum_static(ctypes.c_void_p(int(fluid_v_dev_ptr)), int(precision), int(ncell),
+                                           float(rho), float(h), cuda_stream, op))
     return out
 
 

@@ -13,7 +13,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libicm.so")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
-SOURCES = ["icm_api.cu", "icm_fft.cu", "icm_grid.cu", "icm_blob.cu"]
+SOURCES = ["icm_api.cu", "icm_fft.cu", "icm_grid.cu", "icm_blob.cu", "icm_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
 

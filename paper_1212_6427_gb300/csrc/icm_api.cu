@@ -64,6 +64,11 @@ double kernel_sum_sq(int kernel) { return kernel == 3 ? 0.5 : 0.375; }
 
 }  // namespace
 
+int icm::record_error(int st, const char* msg) {
+  g_err = msg;
+  return st;
+}
+
 struct icm_sim {
   int nx = 0, ny = 0, nz = 0;
   long long ncell = 0;

@@ -6,7 +6,12 @@
 
 #include "icm_common.cuh"
 
+struct icm_sim;
+
 namespace icm {
+
+// Record the message returned by icm_last_error for this thread; returns st.
+int record_error(int st, const char* msg);
 
 constexpr int kMaxSide = 512;
 constexpr int kMaxStages = 12;
