@@ -215,7 +215,8 @@ BlobState blob_state(const icm_sim* s) {
 // the symbol d = (exp(i theta) - 1)/h, |d|^2 = 4 sin^2(theta/2)/h^2 by storage position
 // (x: by natural wavenumber, only nx/2+1 of them).
 icm_status build_axis(icm_sim* s, int n, bool natural, int count, AxisPlan& P, void*& dtab, void*& ddtab) {
-  const std::vector<int> rad = factor_radices(n);
+  int r1 = 0, r2 = 0;
+  const std::vector<int> rad = fft_split(n, r1, r2) ? std::vector<int>{r1, r2} : factor_radices(n);
   P.n = n;
   P.nstages = (int)rad.size();
   for (size_t i = 0; i < rad.size(); ++i) P.radix[i] = rad[i];

@@ -20,6 +20,7 @@
 #include <cstdio>
 
 #include "icm_internal.h"
+#include "icm_fft_reg.cuh"
 
 namespace icm {
 namespace {
@@ -331,6 +332,30 @@ struct SymParams {
   double k0mul;   // k0scale / ncell
 };
 
+// P^ w / (a + b|d|^2) / ncell on one wave vector: (P^ w)_a = w_a - conj(d_a)(d . w)/|d|^2,
+// identity on the mean mode, whose value is replaced by the FP64 bookkeeping if given.
+template <typename R>
+__device__ __forceinline__ void apply_symbol(cplx_t<R>& c0, cplx_t<R>& c1, cplx_t<R>& c2, cplx_t<R> d0,
+                                             cplx_t<R> d1, cplx_t<R> d2, R dd, const SymParams<R>& sp,
+                                             bool mean_mode) {
+  if (dd > R(0)) {
+    const cplx_t<R> div = cadd(cadd(cmul(d0, c0), cmul(d1, c1)), cmul(d2, c2));
+    const cplx_t<R> q = mk(div.x / dd, div.y / dd);
+    c0 = csub(c0, cmul(cconj(d0), q));
+    c1 = csub(c1, cmul(cconj(d1), q));
+    c2 = csub(c2, cmul(cconj(d2), q));
+  }
+  const R scale = sp.inv_ntot / (sp.a + sp.b * dd);
+  c0 = cscale(c0, scale);
+  c1 = cscale(c1, scale);
+  c2 = cscale(c2, scale);
+  if (mean_mode && sp.k0sum != nullptr) {
+    c0 = mk((R)(sp.k0sum[0] * sp.k0mul), R(0));
+    c1 = mk((R)(sp.k0sum[1] * sp.k0mul), R(0));
+    c2 = mk((R)(sp.k0sum[2] * sp.k0mul), R(0));
+  }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_zsym(cplx_t<R>* __restrict__ spec, AxisPlan P, int ny, int kx,
                                                    int kxp, SymParams<R> sp) {
@@ -365,22 +390,7 @@ __global__ void __launch_bounds__(kThreads) k_zsym(cplx_t<R>* __restrict__ spec,
     const C d0 = sp.dx[k], d2 = sp.dz[pz];
     const R dd = sp.ddx[k] + ddy + sp.ddz[pz];
     C c0 = lines[idx], c1 = lines[cs + idx], c2 = lines[2 * cs + idx];
-    if (dd > R(0)) {
-      const C div = cadd(cadd(cmul(d0, c0), cmul(dyv, c1)), cmul(d2, c2));
-      const C q = mk(div.x / dd, div.y / dd);
-      c0 = csub(c0, cmul(cconj(d0), q));
-      c1 = csub(c1, cmul(cconj(dyv), q));
-      c2 = csub(c2, cmul(cconj(d2), q));
-    }
-    const R scale = sp.inv_ntot / (sp.a + sp.b * dd);
-    c0 = cscale(c0, scale);
-    c1 = cscale(c1, scale);
-    c2 = cscale(c2, scale);
-    if (sp.k0sum != nullptr && k == 0 && py == 0 && pz == 0) {
-      c0 = mk((R)(sp.k0sum[0] * sp.k0mul), R(0));
-      c1 = mk((R)(sp.k0sum[1] * sp.k0mul), R(0));
-      c2 = mk((R)(sp.k0sum[2] * sp.k0mul), R(0));
-    }
+    apply_symbol<R>(c0, c1, c2, d0, dyv, d2, dd, sp, k == 0 && py == 0 && pz == 0);
     lines[idx] = c0;
     lines[cs + idx] = c1;
     lines[2 * cs + idx] = c2;
@@ -394,6 +404,320 @@ __global__ void __launch_bounds__(kThreads) k_zsym(cplx_t<R>* __restrict__ spec,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Two-stage register passes (sides listed in fft_split).
+// ---------------------------------------------------------------------------
+constexpr int kXPad = 16;   // x pass: one padding slot every 16 positions (bank spread)
+__host__ __device__ constexpr int xrow(int n) { return n + n / kXPad; }
+__device__ __forceinline__ int xaddr(int l, int p, int N) { return l * xrow(N) + p + p / kXPad; }
+
+template <typename R, int N, int R1, int R2>
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_zsym2(cplx_t<R>* __restrict__ spec, const cplx_t<R>* __restrict__ gtw,
+                                                    int ny, int kx, int kxp, SymParams<R> sp) {
+  using C = cplx_t<R>;
+  constexpr int NL = seg_lines<R>();
+  constexpr bool HOLD3 = sizeof(R) == 4 && R2 <= 12;   // 3 x R2 complex in registers
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);   // [3][N][NL]
+  C* tw = buf + 3 * N * NL;                  // [N]
+  const int tid = threadIdx.x;
+  for (int i = tid; i < N; i += kThreads) tw[i] = gtw[i];
+  const int kx0 = blockIdx.x * NL, py = blockIdx.y;
+  const size_t zs = (size_t)ny * kxp, cs = (size_t)N * zs;
+  C* base = spec + (size_t)py * kxp + kx0;
+  const C zero = mk(R(0), R(0));
+  __syncthreads();
+  for (int it = tid; it < 3 * R2 * NL; it += kThreads) {
+    const int line = it % NL, rest = it / NL, n1 = rest % R2, c = rest / R2;
+    const bool ok = kx0 + line < kx;
+    C a[R1];
+#pragma unroll
+    for (int r = 0; r < R1; ++r) a[r] = ok ? base[c * cs + (size_t)(n1 + R2 * r) * zs + line] : zero;
+    stage_a_fwd<R, R1>(a, n1, tw);
+#pragma unroll
+    for (int k2 = 0; k2 < R1; ++k2) buf[(c * N + n1 + R2 * k2) * NL + line] = a[k2];
+  }
+  __syncthreads();
+  const C dyv = sp.dy[py];
+  const R ddy = sp.ddy[py];
+  if (HOLD3) {
+    for (int it = tid; it < R1 * NL; it += kThreads) {
+      const int line = it % NL, blk = it / NL, k = kx0 + line;
+      if (k >= kx) continue;
+      C b[3][R2];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+#pragma unroll
+        for (int n = 0; n < R2; ++n) b[c][n] = buf[(c * N + R2 * blk + n) * NL + line];
+        SDft<R, R2>::run(b[c]);
+      }
+      const C d0 = sp.dx[k];
+      const R ddx = sp.ddx[k];
+#pragma unroll
+      for (int k1 = 0; k1 < R2; ++k1) {
+        const int pz = R2 * blk + k1;
+        apply_symbol<R>(b[0][k1], b[1][k1], b[2][k1], d0, dyv, sp.dz[pz], ddx + ddy + sp.ddz[pz], sp,
+                        k == 0 && py == 0 && pz == 0);
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        sdft_inv<R, R2>(b[c]);
+#pragma unroll
+        for (int n = 0; n < R2; ++n) buf[(c * N + R2 * blk + n) * NL + line] = b[c][n];
+      }
+    }
+  } else {
+    for (int it = tid; it < 3 * R1 * NL; it += kThreads) {
+      const int line = it % NL, rest = it / NL, blk = rest % R1, c = rest / R1;
+      C b[R2];
+#pragma unroll
+      for (int n = 0; n < R2; ++n) b[n] = buf[(c * N + R2 * blk + n) * NL + line];
+      SDft<R, R2>::run(b);
+#pragma unroll
+      for (int n = 0; n < R2; ++n) buf[(c * N + R2 * blk + n) * NL + line] = b[n];
+    }
+    __syncthreads();
+    for (int it = tid; it < N * NL; it += kThreads) {
+      const int line = it % NL, pz = it / NL, k = kx0 + line;
+      if (k >= kx) continue;
+      C& c0 = buf[it];
+      C& c1 = buf[N * NL + it];
+      C& c2 = buf[2 * N * NL + it];
+      apply_symbol<R>(c0, c1, c2, sp.dx[k], dyv, sp.dz[pz], sp.ddx[k] + ddy + sp.ddz[pz], sp,
+                      k == 0 && py == 0 && pz == 0);
+    }
+    __syncthreads();
+    for (int it = tid; it < 3 * R1 * NL; it += kThreads) {
+      const int line = it % NL, rest = it / NL, blk = rest % R1, c = rest / R1;
+      C b[R2];
+#pragma unroll
+      for (int n = 0; n < R2; ++n) b[n] = buf[(c * N + R2 * blk + n) * NL + line];
+      sdft_inv<R, R2>(b);
+#pragma unroll
+      for (int n = 0; n < R2; ++n) buf[(c * N + R2 * blk + n) * NL + line] = b[n];
+    }
+  }
+  __syncthreads();
+  for (int it = tid; it < 3 * R2 * NL; it += kThreads) {
+    const int line = it % NL, rest = it / NL, n1 = rest % R2, c = rest / R2;
+    if (kx0 + line >= kx) continue;
+    C a[R1];
+#pragma unroll
+    for (int k2 = 0; k2 < R1; ++k2) a[k2] = buf[(c * N + n1 + R2 * k2) * NL + line];
+    stage_a_inv<R, R1>(a, n1, tw);
+#pragma unroll
+    for (int n2 = 0; n2 < R1; ++n2) base[c * cs + (size_t)(n1 + R2 * n2) * zs + line] = a[n2];
+  }
+}
+
+template <typename R, int N, int R1, int R2, bool INV>
+__global__ void __launch_bounds__(kThreads) k_ypass2(cplx_t<R>* __restrict__ spec, const cplx_t<R>* __restrict__ gtw,
+                                                     int nz, int kx, int kxp) {
+  using C = cplx_t<R>;
+  constexpr int NL = seg_lines<R>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);   // [N][NL]
+  C* tw = buf + N * NL;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < N; i += kThreads) tw[i] = gtw[i];
+  const int kx0 = blockIdx.x * NL, z = blockIdx.y, comp = blockIdx.z;
+  C* base = spec + ((size_t)(comp * nz + z) * N) * kxp + kx0;
+  const C zero = mk(R(0), R(0));
+  __syncthreads();
+  if (!INV) {
+    for (int it = tid; it < R2 * NL; it += kThreads) {
+      const int line = it % NL, n1 = it / NL;
+      const bool ok = kx0 + line < kx;
+      C a[R1];
+#pragma unroll
+      for (int r = 0; r < R1; ++r) a[r] = ok ? base[(size_t)(n1 + R2 * r) * kxp + line] : zero;
+      stage_a_fwd<R, R1>(a, n1, tw);
+#pragma unroll
+      for (int k2 = 0; k2 < R1; ++k2) buf[(n1 + R2 * k2) * NL + line] = a[k2];
+    }
+    __syncthreads();
+    for (int it = tid; it < R1 * NL; it += kThreads) {
+      const int line = it % NL, blk = it / NL;
+      if (kx0 + line >= kx) continue;
+      C b[R2];
+#pragma unroll
+      for (int n = 0; n < R2; ++n) b[n] = buf[(R2 * blk + n) * NL + line];
+      SDft<R, R2>::run(b);
+#pragma unroll
+      for (int k1 = 0; k1 < R2; ++k1) base[(size_t)(R2 * blk + k1) * kxp + line] = b[k1];
+    }
+  } else {
+    for (int it = tid; it < R1 * NL; it += kThreads) {
+      const int line = it % NL, blk = it / NL;
+      const bool ok = kx0 + line < kx;
+      C b[R2];
+#pragma unroll
+      for (int k1 = 0; k1 < R2; ++k1) b[k1] = ok ? base[(size_t)(R2 * blk + k1) * kxp + line] : zero;
+      sdft_inv<R, R2>(b);
+#pragma unroll
+      for (int n = 0; n < R2; ++n) buf[(R2 * blk + n) * NL + line] = b[n];
+    }
+    __syncthreads();
+    for (int it = tid; it < R2 * NL; it += kThreads) {
+      const int line = it % NL, n1 = it / NL;
+      if (kx0 + line >= kx) continue;
+      C a[R1];
+#pragma unroll
+      for (int k2 = 0; k2 < R1; ++k2) a[k2] = buf[(n1 + R2 * k2) * NL + line];
+      stage_a_inv<R, R1>(a, n1, tw);
+#pragma unroll
+      for (int n2 = 0; n2 < R1; ++n2) base[(size_t)(n1 + R2 * n2) * kxp + line] = a[n2];
+    }
+  }
+}
+
+// x forward, two real rows per complex line; frequency k ends at position
+// R2 (k mod R1) + k div R1 of its line.
+template <typename R, int N, int R1, int R2>
+__global__ void __launch_bounds__(kThreads) k_xfwd2(const R* __restrict__ src, cplx_t<R>* __restrict__ spec,
+                                                    const cplx_t<R>* __restrict__ gtw, int nrows, long long ncell,
+                                                    int kx, int kxp) {
+  using C = cplx_t<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);   // [kXLines][xrow(N)]
+  C* tw = buf + kXLines * xrow(N);
+  const int tid = threadIdx.x;
+  for (int i = tid; i < N; i += kThreads) tw[i] = gtw[i];
+  const int comp = blockIdx.y;
+  const long long row0 = (long long)blockIdx.x * (2 * kXLines);
+  const R* s = src + comp * ncell;
+  __syncthreads();
+  for (int it = tid; it < kXLines * R2; it += kThreads) {
+    const int n1 = it % R2, l = it / R2;
+    const long long r0 = row0 + 2 * l;
+    const R* p0 = s + r0 * N;
+    const bool ok0 = r0 < nrows, ok1 = r0 + 1 < nrows;
+    C a[R1];
+#pragma unroll
+    for (int r = 0; r < R1; ++r) {
+      const int x = n1 + R2 * r;
+      a[r] = mk(ok0 ? p0[x] : R(0), ok1 ? p0[N + x] : R(0));
+    }
+    stage_a_fwd<R, R1>(a, n1, tw);
+#pragma unroll
+    for (int k2 = 0; k2 < R1; ++k2) buf[xaddr(l, n1 + R2 * k2, N)] = a[k2];
+  }
+  __syncthreads();
+  for (int it = tid; it < kXLines * R1; it += kThreads) {
+    const int blk = it % R1, l = it / R1;
+    C b[R2];
+#pragma unroll
+    for (int n = 0; n < R2; ++n) b[n] = buf[xaddr(l, R2 * blk + n, N)];
+    SDft<R, R2>::run(b);
+#pragma unroll
+    for (int k1 = 0; k1 < R2; ++k1) buf[xaddr(l, R2 * blk + k1, N)] = b[k1];
+  }
+  __syncthreads();
+  C* out = spec + (size_t)comp * nrows * kxp;
+  for (int it = tid; it < kXLines * kx; it += kThreads) {
+    const int k = it % kx, l = it / kx;
+    const int km = k == 0 ? 0 : N - k;
+    const C zk = buf[xaddr(l, R2 * (k % R1) + k / R1, N)];
+    const C zm = buf[xaddr(l, R2 * (km % R1) + km / R1, N)];
+    const C x1 = mk((zk.x + zm.x) * R(0.5), (zk.y - zm.y) * R(0.5));
+    const C x2 = cmul_mi(mk((zk.x - zm.x) * R(0.5), (zk.y + zm.y) * R(0.5)));
+    const long long r1 = row0 + 2 * l;
+    if (r1 < nrows) out[r1 * kxp + k] = x1;
+    if (r1 + 1 < nrows) out[(r1 + 1) * kxp + k] = x2;
+  }
+}
+
+template <typename R, int N, int R1, int R2>
+__global__ void __launch_bounds__(kThreads) k_xinv2(const cplx_t<R>* __restrict__ spec, R* __restrict__ dst,
+                                                    R* __restrict__ dst2, int mode, const cplx_t<R>* __restrict__ gtw,
+                                                    int nrows, long long ncell, int kxp) {
+  using C = cplx_t<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* tw = buf + kXLines * xrow(N);
+  const int tid = threadIdx.x;
+  for (int i = tid; i < N; i += kThreads) tw[i] = gtw[i];
+  const int comp = blockIdx.y;
+  const long long row0 = (long long)blockIdx.x * (2 * kXLines);
+  const C* in = spec + (size_t)comp * nrows * kxp;
+  const C zero = mk(R(0), R(0));
+  for (int it = tid; it < kXLines * N; it += kThreads) {
+    const int k = it % N, l = it / N;
+    const long long r1 = row0 + 2 * l;
+    const bool direct = 2 * k <= N;
+    const int kk = direct ? k : N - k;
+    C a = r1 < nrows ? in[r1 * kxp + kk] : zero;
+    C b = r1 + 1 < nrows ? in[(r1 + 1) * kxp + kk] : zero;
+    if (!direct) {
+      a = cconj(a);
+      b = cconj(b);
+    }
+    if (k == 0 || 2 * k == N) {
+      a.y = R(0);
+      b.y = R(0);
+    }
+    buf[xaddr(l, R2 * (k % R1) + k / R1, N)] = mk(a.x - b.y, a.y + b.x);
+  }
+  __syncthreads();
+  for (int it = tid; it < kXLines * R1; it += kThreads) {
+    const int blk = it % R1, l = it / R1;
+    C b[R2];
+#pragma unroll
+    for (int k1 = 0; k1 < R2; ++k1) b[k1] = buf[xaddr(l, R2 * blk + k1, N)];
+    sdft_inv<R, R2>(b);
+#pragma unroll
+    for (int n = 0; n < R2; ++n) buf[xaddr(l, R2 * blk + n, N)] = b[n];
+  }
+  __syncthreads();
+  const size_t cb = (size_t)comp * ncell;
+  for (int it = tid; it < kXLines * R2; it += kThreads) {
+    const int n1 = it % R2, l = it / R2;
+    C a[R1];
+#pragma unroll
+    for (int k2 = 0; k2 < R1; ++k2) a[k2] = buf[xaddr(l, n1 + R2 * k2, N)];
+    stage_a_inv<R, R1>(a, n1, tw);
+    const long long r0 = row0 + 2 * l;
+#pragma unroll
+    for (int n2 = 0; n2 < R1; ++n2) {
+      const int x = n1 + R2 * n2;
+      if (r0 < nrows) {
+        const size_t o = cb + (size_t)r0 * N + x;
+        if (mode == OUT_STORE) {
+          dst[o] = a[n2].x;
+        } else {
+          dst[o] += a[n2].x;
+          dst2[o] = a[n2].x;
+        }
+      }
+      if (r0 + 1 < nrows) {
+        const size_t o = cb + (size_t)(r0 + 1) * N + x;
+        if (mode == OUT_STORE) {
+          dst[o] = a[n2].y;
+        } else {
+          dst[o] += a[n2].y;
+          dst2[o] = a[n2].y;
+        }
+      }
+    }
+  }
+}
+
+template <typename R, int N> size_t smem_z2() { return 3 * (size_t)N * seg_lines<R>() * sizeof(cplx_t<R>) + N * sizeof(cplx_t<R>); }
+template <typename R, int N> size_t smem_y2() { return (size_t)N * seg_lines<R>() * sizeof(cplx_t<R>) + N * sizeof(cplx_t<R>); }
+template <typename R, int N> size_t smem_x2() { return (size_t)kXLines * xrow(N) * sizeof(cplx_t<R>) + N * sizeof(cplx_t<R>); }
+
+// Every side with register kernels, as (N, R1, R2); must agree with fft_split.
+#define ICM_FFT_SIDES(X) \
+  X(32, 8, 4)            \
+  X(48, 16, 3)           \
+  X(64, 8, 8)            \
+  X(96, 16, 6)           \
+  X(128, 16, 8)          \
+  X(192, 16, 12)         \
+  X(256, 16, 16)         \
+  X(384, 32, 12)         \
+  X(512, 32, 16)
+
 template <typename R> size_t smem_x(int n) { return (size_t)n * kXLS * sizeof(cplx_t<R>) + n * sizeof(cplx_t<R>) + n * sizeof(int); }
 template <typename R> size_t smem_y(int n) { return (size_t)n * seg_lines<R>() * sizeof(cplx_t<R>) + n * sizeof(cplx_t<R>); }
 template <typename R> size_t smem_z(int n) { return 3 * (size_t)n * seg_lines<R>() * sizeof(cplx_t<R>) + n * sizeof(cplx_t<R>); }
@@ -401,6 +725,14 @@ template <typename R> size_t smem_z(int n) { return 3 * (size_t)n * seg_lines<R>
 template <typename R>
 void set_smem_attributes() {
   const int big = 227 * 1024;
+#define ICM_ATTR(N, R1, R2)                                                                               \
+  cudaFuncSetAttribute(k_zsym2<R, N, R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);         \
+  cudaFuncSetAttribute(k_ypass2<R, N, R1, R2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big); \
+  cudaFuncSetAttribute(k_ypass2<R, N, R1, R2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);  \
+  cudaFuncSetAttribute(k_xfwd2<R, N, R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);         \
+  cudaFuncSetAttribute(k_xinv2<R, N, R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  ICM_FFT_SIDES(ICM_ATTR)
+#undef ICM_ATTR
   cudaFuncSetAttribute(k_xfwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_xinv<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_ypass<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
@@ -414,6 +746,14 @@ template <typename R>
 void fft_x_forward(const FftCtx<R>& f, const R* src, cudaStream_t st) {
   const int nrows = f.ny * f.nz;
   const int xblocks = (nrows + 2 * kXLines - 1) / (2 * kXLines);
+  const cplx_t<R>* tw = (const cplx_t<R>*)f.px.tw;
+  switch (f.nx) {
+#define ICM_CASE(N, R1, R2) \
+  case N: k_xfwd2<R, N, R1, R2><<<dim3(xblocks, 3), kThreads, smem_x2<R, N>(), st>>>(src, f.spec, tw, nrows, f.ncell, f.kx, f.kxp); return;
+    ICM_FFT_SIDES(ICM_CASE)
+#undef ICM_CASE
+    default: break;
+  }
   k_xfwd<R><<<dim3(xblocks, 3), kThreads, smem_x<R>(f.nx), st>>>(src, f.spec, f.px, nrows, f.ncell, f.kx, f.kxp);
 }
 
@@ -421,6 +761,20 @@ template <typename R>
 void fft_y(const FftCtx<R>& f, bool inverse, cudaStream_t st) {
   constexpr int NL = seg_lines<R>();
   const int kxt = (f.kx + NL - 1) / NL;
+  const cplx_t<R>* tw = (const cplx_t<R>*)f.py.tw;
+  const dim3 grid(kxt, f.nz, 3);
+  switch (f.ny) {
+#define ICM_CASE(N, R1, R2)                                                                                   \
+  case N:                                                                                                     \
+    if (inverse)                                                                                              \
+      k_ypass2<R, N, R1, R2, true><<<grid, kThreads, smem_y2<R, N>(), st>>>(f.spec, tw, f.nz, f.kx, f.kxp);  \
+    else                                                                                                      \
+      k_ypass2<R, N, R1, R2, false><<<grid, kThreads, smem_y2<R, N>(), st>>>(f.spec, tw, f.nz, f.kx, f.kxp); \
+    return;
+    ICM_FFT_SIDES(ICM_CASE)
+#undef ICM_CASE
+    default: break;
+  }
   if (inverse)
     k_ypass<R, true><<<dim3(kxt, f.nz, 3), kThreads, smem_y<R>(f.ny), st>>>(f.spec, f.py, f.nz, f.kx, f.kxp);
   else
@@ -440,6 +794,14 @@ void fft_z_symbol(const FftCtx<R>& f, double a, double b, const double* k0sum, d
   sp.dz = f.dz; sp.ddz = f.ddz;
   sp.k0sum = k0sum;
   sp.k0mul = k0scale / (double)f.ncell;
+  const cplx_t<R>* tw = (const cplx_t<R>*)f.pz.tw;
+  switch (f.nz) {
+#define ICM_CASE(N, R1, R2) \
+  case N: k_zsym2<R, N, R1, R2><<<dim3(kxt, f.ny), kThreads, smem_z2<R, N>(), st>>>(f.spec, tw, f.ny, f.kx, f.kxp, sp); return;
+    ICM_FFT_SIDES(ICM_CASE)
+#undef ICM_CASE
+    default: break;
+  }
   k_zsym<R><<<dim3(kxt, f.ny), kThreads, smem_z<R>(f.nz), st>>>(f.spec, f.pz, f.ny, f.kx, f.kxp, sp);
 }
 
@@ -447,6 +809,14 @@ template <typename R>
 void fft_x_inverse(const FftCtx<R>& f, R* dst, R* dst2, int mode, cudaStream_t st) {
   const int nrows = f.ny * f.nz;
   const int xblocks = (nrows + 2 * kXLines - 1) / (2 * kXLines);
+  const cplx_t<R>* tw = (const cplx_t<R>*)f.px.tw;
+  switch (f.nx) {
+#define ICM_CASE(N, R1, R2) \
+  case N: k_xinv2<R, N, R1, R2><<<dim3(xblocks, 3), kThreads, smem_x2<R, N>(), st>>>(f.spec, dst, dst2, mode, tw, nrows, f.ncell, f.kxp); return;
+    ICM_FFT_SIDES(ICM_CASE)
+#undef ICM_CASE
+    default: break;
+  }
   k_xinv<R><<<dim3(xblocks, 3), kThreads, smem_x<R>(f.nx), st>>>(f.spec, dst, dst2, mode, f.px, nrows, f.ncell,
                                                                  f.kxp);
 }

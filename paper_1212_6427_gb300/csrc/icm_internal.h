@@ -16,6 +16,23 @@ int record_error(int st, const char* msg);
 constexpr int kMaxSide = 512;
 constexpr int kMaxStages = 12;
 
+// Sides with two-stage register FFT kernels: N = r1 * r2 (first stage radix r1).
+// The host plan of such an axis uses exactly these two radices, in this order.
+inline bool fft_split(int n, int& r1, int& r2) {
+  switch (n) {
+    case 32: r1 = 8; r2 = 4; return true;
+    case 48: r1 = 16; r2 = 3; return true;
+    case 64: r1 = 8; r2 = 8; return true;
+    case 96: r1 = 16; r2 = 6; return true;
+    case 128: r1 = 16; r2 = 8; return true;
+    case 192: r1 = 16; r2 = 12; return true;
+    case 256: r1 = 16; r2 = 16; return true;
+    case 384: r1 = 32; r2 = 12; return true;
+    case 512: r1 = 32; r2 = 16; return true;
+    default: return false;
+  }
+}
+
 // One axis of the 3D FFT: a mixed-radix factorisation N = prod radix[s] with
 // in-place decimation-in-frequency stages.  The forward pass leaves frequency k
 // at storage position pos_of_freq[k]; the inverse pass takes that order back to

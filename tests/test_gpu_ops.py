@@ -15,7 +15,8 @@ from _gpu_helpers import TOL, rel
 pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-GRIDS = [(16, 16, 16), (32, 12, 24), (9, 18, 8), (48, 32, 27), (96, 8, 16)]
+GRIDS = [(16, 16, 16), (32, 12, 24), (9, 18, 8), (48, 32, 27), (96, 8, 16), (64, 128, 96), (256, 24, 192),
+         (128, 64, 48), (384, 8, 12)]
 
 
 @pytest.fixture(scope="module")
