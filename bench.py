@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="large", choices=["large", "bulk", "plain"])
+    ap.add_argument("--workload", default="large", choices=["large", "bulk", "plain", "batch", "served"])
+    ap.add_argument("--jobs", type=int, default=120, help="served workload: number of Poisson-arriving jobs")
     ap.add_argument("--precision", type=int, default=None, choices=[32, 64])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64, cuFFT and CPU comparison legs")
@@ -180,7 +181,12 @@ def oracle_step_rate(w, budget_s, max_steps):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    w = load_workload(args.workload)
+    if args.workload in ("batch", "served"):
+        # the oracle on the first replica / job of the set: one bounded sample of the same workload
+        w = (wl.batch_replicas(1) if args.workload == "batch" else wl.served_jobs(1))[0]
+        w["name"] = args.workload
+    else:
+        w = load_workload(args.workload)
     prec = args.precision or w["precision"]
     ncell = int(np.prod(w["grid"]))
     sec, n = oracle_step_rate(w, args.cpu_budget, args.steps)
@@ -307,7 +313,8 @@ def run_ours(args, rank, world, dist):
                          "achieved_GBps": step_bytes / (ms_step / 1e3) / 1e9,
                          "frac": step_bytes / (ms_step / 1e3) / 1e9 / peak, "peak_kind": peak_kind},
             "roofline": roofline, "kernels": kernels, "clocks": clk, "e2e": e2e,
-            "gpu_launches": launches_per_step * args.steps, "launches_per_step": launches_per_step}
+            "gpu_launches": launches_per_step * args.steps, "launches_per_step": launches_per_step,
+            "stage_ms": {"%02d.%s" % (i, name): round(ms_tot / nprof, 4) for i, (name, ms_tot, _) in enumerate(prof)}}
 
     if rank == 0 and world == 1 and not args.no_extras:
         extras(args, w, prec, sim, line, torch, icm, per_kernel)
@@ -366,6 +373,142 @@ def extras(args, w, prec, sim, line, torch, icm, per_kernel):
                                       % (n, sec * n)}
 
 
+def run_batch(args, rank, world, dist):
+    """64 replicas (sides {32,48,64,96}, 1-500 blobs, kernel 3 or 4, FP32), one graph launch per step."""
+    import torch
+    import paper_1212_6427_gb300 as icm
+    from paper_1212_6427_gb300 import build
+    if rank == 0:
+        build.build_library()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    icm.use_torch_allocator()
+    reps = wl.batch_replicas(64, seed0=1 + 64 * rank)
+    sims = []
+    for r in reps:
+        s = icm.Simulation(r["grid"], r["h"], r["rho"], r["eta"], r["kT"], r["dt"], r["kernel"], r["seed"], 32)
+        s.add_blobs(r["q"], r["u"], r["me"])
+        sims.append(s)
+    cells = sum(int(np.prod(r["grid"])) for r in reps)
+    blobs = sum(len(r["q"]) for r in reps)
+    step_bytes = 0.0
+    launches = 0
+    for s in sims:
+        prof = s.profile(1)
+        step_bytes += sum(by for _, _, by in prof)
+        launches += sum(1 for n, _, _ in prof if kernel_of(n) != "zero")
+    b = icm.icm_batch_create()
+    icm.icm_batch_set(b, [s.handle for s in sims])
+    icm.icm_batch_step(b, max(args.warmup, 3))
+    icm.icm_batch_sync(b)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    time.sleep(0.3)
+    t0 = time.perf_counter()
+    icm.icm_batch_step(b, args.steps)
+    icm.icm_batch_sync(b)
+    sec = time.perf_counter() - t0
+    clk = clocks.stop()
+    # the same replicas stepped one after another without batching
+    t1 = time.perf_counter()
+    for _ in range(max(3, args.steps // 10)):
+        for s in sims:
+            s.step(1)
+    for s in sims:
+        s.sync()
+    seq = (time.perf_counter() - t1) / max(3, args.steps // 10)
+    if dist is not None:
+        t = torch.tensor([sec], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        sec = float(t.item())
+    ms_step = sec / args.steps * 1e3
+    peak, peak_kind = measured_peaks()
+    achieved = step_bytes / (ms_step / 1e3) / 1e9
+    line = {"metric": METRIC, "value": cells * args.steps * world / sec, "unit": "cell-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "icm-batch-64-replicas-sides-32-48-64-96-fp32", "replicas": 64 * world,
+                       "cells_per_replica_set": cells, "blobs": blobs, "parallelism": "replicas only",
+                       "l2": "replica set of %.0f MB per field: timed on host clock around whole batch steps"
+                             % (3 * cells * 4 / 1e6)},
+            "blob_steps_per_s": blobs * args.steps * world / sec,
+            "roofline": {"bound": "hbm", "kernel": "whole batched step", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None},
+            "unbatched_ms_per_step": seq * 1e3, "speedup_over_unbatched": seq * 1e3 / ms_step,
+            "clocks": clk, "gpu_launches": launches * args.steps,
+            "e2e": {"value": cells * args.steps * world / sec, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0, "note": "device-resident batch; no per-step host I/O"}}
+    icm.icm_batch_destroy(b)
+    for s in sims:
+        s.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_served(args, rank, world, dist):
+    """Poisson-arriving jobs (mean 50/s) admitted by a 150 GB HBM budget, continuously batched."""
+    import torch
+    import paper_1212_6427_gb300 as icm
+    from paper_1212_6427_gb300 import build
+    if rank == 0:
+        build.build_library()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    icm.use_torch_allocator()
+    jobs = wl.served_jobs(args.jobs, rate=50.0, seed=5 + rank)
+    sv = icm.icm_server_create(150 * 10 ** 9, 256)
+    ids = {}
+    pending = list(jobs)
+    done = 0
+    peak_bytes = 0
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    t0 = time.perf_counter()
+    while done < len(jobs):
+        now = time.perf_counter() - t0
+        while pending and pending[0]["arrival"] <= now:
+            j = pending.pop(0)
+            ids[icm.icm_server_submit(sv, j["grid"], j["h"], j["rho"], j["eta"], j["kT"], j["dt"], j["kernel"],
+                                      j["seed"], 32, 0, j["q"], j["u"], j["me"], None, j["steps"])] = j
+        a, w, f = icm.icm_server_pump(sv, 4)
+        done += f
+        peak_bytes = max(peak_bytes, icm.icm_server_bytes_in_use(sv))
+        if a == 0 and w == 0 and pending:
+            time.sleep(max(0.0, pending[0]["arrival"] - (time.perf_counter() - t0)))
+        else:
+            time.sleep(0.0005)   # let the enqueued steps run; polling, not waiting on the GPU
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    lat = []
+    cell_steps = 0
+    blob_steps = 0
+    for jid, j in ids.items():
+        r = icm.icm_server_result(sv, jid, len(j["q"]))
+        assert r["state"] == 2, r["state"]
+        lat.append(r["latency_s"])
+        cell_steps += int(np.prod(j["grid"])) * j["steps"]
+        blob_steps += len(j["q"]) * j["steps"]
+    icm.icm_server_destroy(sv)
+    lat = np.array(lat)
+    line = {"metric": METRIC, "value": cell_steps / wall, "unit": "cell-updates/s", "n_gpus": world,
+            "steps": int(sum(j["steps"] for j in jobs)), "warmup": 0, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "icm-served-poisson-50ps-%djobs-sides-32-128-fp32" % len(jobs),
+                       "hbm_budget_bytes": 150 * 10 ** 9, "max_active": 256, "steps_per_pump": 4,
+                       "parallelism": "replicas only"},
+            "blob_steps_per_s": blob_steps / wall, "jobs_per_s": len(jobs) / wall,
+            "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+            "latency_mean_s": float(lat.mean()), "peak_device_bytes": peak_bytes, "wall_s": wall, "clocks": clk,
+            "e2e": {"value": cell_steps / wall, "unit": "cell-updates/s", "note": "host submit to host result"}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -380,6 +523,10 @@ def main():
         dist.init_process_group(backend)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "batch":
+        run_batch(args, rank, world, dist)
+    elif args.workload == "served":
+        run_served(args, rank, world, dist)
     else:
         run_ours(args, rank, world, dist)
     if dist is not None:

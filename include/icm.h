@@ -224,6 +224,73 @@ icm_status icm_op_stress_normals(icm_sim* sim, int64_t step, double* out);
 icm_status icm_op_philox(int64_t n, uint32_t ctr0, uint32_t ctr1, uint32_t ctr2,
                          uint32_t ctr3, uint32_t key0, uint32_t key1, uint32_t* out);
 
+/* ------------------------------------------------------------------------
+ * Batched replicas.  A batch advances several independent simulations with one
+ * CUDA graph launch per step: the step of every member (Sec. III.C) is captured as
+ * an independent branch, so the GPU runs the members' kernels side by side.  The
+ * paper runs one simulation at a time; this layer has no counterpart there.
+ * ------------------------------------------------------------------------ */
+typedef struct icm_batch icm_batch;
+
+/* Create an empty batch working on cuda_stream (NULL: a stream of its own). */
+icm_status icm_batch_create(void* cuda_stream, icm_batch** out);
+
+/* Set the members (n distinct simulations; the caller keeps ownership and must
+ * not destroy a member while it belongs to a batch).  Synchronises the batch. */
+icm_status icm_batch_set(icm_batch* batch, int32_t n, icm_sim* const* sims);
+
+/* Advance every member nsteps steps (one graph launch per step; recaptured when
+ * membership or a member's step sequence changed).  Asynchronous; later work on a
+ * member's own stream is ordered after these steps. */
+icm_status icm_batch_step(icm_batch* batch, int64_t nsteps);
+
+/* Wait for the batch; returns the first device-side error of any member. */
+icm_status icm_batch_sync(icm_batch* batch);
+void icm_batch_destroy(icm_batch* batch);
+
+/* Device bytes a simulation of this grid, precision and blob count will hold
+ * (-1 for invalid arguments); what the server admits jobs by. */
+int64_t icm_estimate_device_bytes(const int32_t grid[3], int32_t precision, int64_t nblobs);
+
+/* ------------------------------------------------------------------------
+ * Serving.  Jobs (one simulation each, advanced a given number of steps) queue on
+ * the host and are admitted first come first served while their device footprint
+ * fits the HBM budget and an active slot is free.  Every active job replays its own
+ * step graph on its own stream, so the jobs' kernels overlap on the GPU; a job
+ * leaves with its final blob state once its last step has completed, freeing its
+ * memory for the next.  No counterpart in the paper.
+ * ------------------------------------------------------------------------ */
+typedef struct icm_server icm_server;
+typedef struct {
+  int32_t grid[3];
+  double h, rho, eta, kT, dt;
+  int32_t kernel;
+  uint64_t seed;
+  int32_t precision, flags;
+  int64_t nblobs;
+  const double* pos;          /* nblobs*3 (copied at submit) */
+  const double* vel;          /* nblobs*3 or NULL */
+  const double* excess_mass;  /* nblobs */
+  const double* force;        /* nblobs*3 or NULL (constant external force) */
+  int64_t nsteps;             /* >= 1 */
+} icm_job_desc;
+
+icm_status icm_server_create(int64_t hbm_budget_bytes, int32_t max_active, icm_server** out);
+/* Queue a job; its arrays are copied.  ICM_ENOMEM if it can never fit the budget. */
+icm_status icm_server_submit(icm_server* server, const icm_job_desc* job, int64_t* job_id);
+/* Retire jobs whose last step has completed, admit waiting jobs that fit, and
+ * enqueue up to steps_per_pump more steps of every active job.  Does not wait for
+ * the GPU (reading a finished job's results is the only synchronisation).  Any
+ * output pointer may be NULL; n_finished counts jobs retired by this call. */
+icm_status icm_server_pump(icm_server* server, int32_t steps_per_pump, int32_t* n_active, int32_t* n_waiting,
+                           int32_t* n_finished);
+/* state: 0 waiting, 1 active, 2 done, 3 failed.  When done: pos, vel (nblobs*3),
+ * momentum[3] and latency_s (submit to completion, seconds), each may be NULL. */
+icm_status icm_server_result(icm_server* server, int64_t job_id, int32_t* state, double* pos, double* vel,
+                             double momentum[3], double* latency_s);
+int64_t icm_server_bytes_in_use(const icm_server* server);
+void icm_server_destroy(icm_server* server);
+
 #ifdef __cplusplus
 }
 #endif

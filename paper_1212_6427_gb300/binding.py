@@ -31,6 +31,14 @@ _dp = ctypes.POINTER(ctypes.c_double)
 _ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
 
+class JobDesc(ctypes.Structure):
+    """icm_job_desc of include/icm.h."""
+    _fields_ = [("grid", _c_i32 * 3), ("h", _c_d), ("rho", _c_d), ("eta", _c_d), ("kT", _c_d), ("dt", _c_d),
+                ("kernel", _c_i32), ("seed", _c_u64), ("precision", _c_i32), ("flags", _c_i32),
+                ("nblobs", _c_i64), ("pos", _dp), ("vel", _dp), ("excess_mass", _dp), ("force", _dp),
+                ("nsteps", _c_i64)]
+
+
 SIGNATURES = {
     "icm_set_default_allocator": (_c_i32, [_ALLOC_T, _FREE_T, _vp]),
     "icm_create": (_c_i32, [ctypes.POINTER(_c_i32), _c_d, _c_d, _c_d, _c_d, _c_d, _c_i32, _c_u64, _c_i32, _c_i32,
@@ -47,6 +55,18 @@ SIGNATURES = {
     "icm_profile_steps": (_c_i32, [_vp, _c_i64, _c_i32, ctypes.POINTER(_c_i32), ctypes.c_char_p, _dp, _dp]),
     "icm_fluid_momentum_static": (_c_i32, [_vp, _c_i32, _c_i64, _c_d, _c_d, _vp, _dp]),
     "icm_num_blobs": (_c_i64, [_vp]),
+    "icm_batch_create": (_c_i32, [_vp, ctypes.POINTER(_vp)]),
+    "icm_batch_set": (_c_i32, [_vp, _c_i32, ctypes.POINTER(_vp)]),
+    "icm_batch_step": (_c_i32, [_vp, _c_i64]),
+    "icm_batch_sync": (_c_i32, [_vp]),
+    "icm_batch_destroy": (None, [_vp]),
+    "icm_estimate_device_bytes": (_c_i64, [ctypes.POINTER(_c_i32), _c_i32, _c_i64]),
+    "icm_server_create": (_c_i32, [_c_i64, _c_i32, ctypes.POINTER(_vp)]),
+    "icm_server_submit": (_c_i32, [_vp, ctypes.POINTER(JobDesc), ctypes.POINTER(_c_i64)]),
+    "icm_server_pump": (_c_i32, [_vp, _c_i32, ctypes.POINTER(_c_i32), ctypes.POINTER(_c_i32), ctypes.POINTER(_c_i32)]),
+    "icm_server_result": (_c_i32, [_vp, _c_i64, ctypes.POINTER(_c_i32), _dp, _dp, _dp, _dp]),
+    "icm_server_bytes_in_use": (_c_i64, [_vp]),
+    "icm_server_destroy": (None, [_vp]),
     "icm_device_bytes": (_c_i64, [_vp]),
     "icm_op_interpolate": (_c_i32, [_vp, _c_i64, _dp, _dp, _dp]),
     "icm_op_interpolate_laplacian": (_c_i32, [_vp, _c_i64, _dp, _dp, _dp]),
@@ -294,6 +314,79 @@ def icm_op_philox(n, ctr, key):
     _check(lib().icm_op_philox(int(n), *[int(c) & 0xFFFFFFFF for c in ctr], *[int(k) & 0xFFFFFFFF for k in key],
                                out.ctypes.data_as(ctypes.POINTER(_c_u32))))
     return out.reshape(-1, 4)
+
+
+def icm_batch_create(cuda_stream=None):
+    out = _vp()
+    _check(lib().icm_batch_create(cuda_stream, ctypes.byref(out)))
+    return out
+
+
+def icm_batch_set(batch, sims):
+    arr = (_vp * max(1, len(sims)))(*[s.value if isinstance(s, _vp) else s for s in sims])
+    _check(lib().icm_batch_set(batch, len(sims), arr))
+
+
+def icm_batch_step(batch, nsteps=1):
+    _check(lib().icm_batch_step(batch, int(nsteps)))
+
+
+def icm_batch_sync(batch):
+    _check(lib().icm_batch_sync(batch))
+
+
+def icm_batch_destroy(batch):
+    lib().icm_batch_destroy(batch)
+
+
+def icm_estimate_device_bytes(grid, precision, nblobs):
+    g = (_c_i32 * 3)(*[int(x) for x in grid])
+    return int(lib().icm_estimate_device_bytes(g, int(precision), int(nblobs)))
+
+
+def icm_server_create(hbm_budget_bytes, max_active):
+    out = _vp()
+    _check(lib().icm_server_create(int(hbm_budget_bytes), int(max_active), ctypes.byref(out)))
+    return out
+
+
+def icm_server_submit(server, grid, h, rho, eta, kT, dt, kernel, seed, precision, flags, pos, vel, excess_mass,
+                      force, nsteps):
+    p, pp = _f64(pos)
+    n = p.size // 3
+    _, vp = _f64(vel, 3 * n)
+    m, mp = _f64(excess_mass, n)
+    _, fp = _f64(force, 3 * n)
+    d = JobDesc((_c_i32 * 3)(*[int(x) for x in grid]), h, rho, eta, kT, dt, int(kernel),
+                int(seed) & 0xFFFFFFFFFFFFFFFF, int(precision), int(flags), n, pp, vp, mp, fp, int(nsteps))
+    jid = _c_i64()
+    _check(lib().icm_server_submit(server, ctypes.byref(d), ctypes.byref(jid)))
+    return int(jid.value)
+
+
+def icm_server_pump(server, steps_per_pump=1):
+    a, w, f = _c_i32(), _c_i32(), _c_i32()
+    _check(lib().icm_server_pump(server, int(steps_per_pump), ctypes.byref(a), ctypes.byref(w), ctypes.byref(f)))
+    return int(a.value), int(w.value), int(f.value)
+
+
+def icm_server_result(server, job_id, nblobs):
+    st = _c_i32()
+    pos, pp = _out(3 * nblobs)
+    vel, vp = _out(3 * nblobs)
+    mom, mp = _out(3)
+    lat, lp = _out(1)
+    _check(lib().icm_server_result(server, int(job_id), ctypes.byref(st), pp, vp, mp, lp))
+    return dict(state=int(st.value), pos=pos.reshape(nblobs, 3), vel=vel.reshape(nblobs, 3), momentum=mom,
+                latency_s=float(lat[0]))
+
+
+def icm_server_bytes_in_use(server):
+    return int(lib().icm_server_bytes_in_use(server))
+
+
+def icm_server_destroy(server):
+    lib().icm_server_destroy(server)
 
 
 # ---------------------------------------------------------------------------

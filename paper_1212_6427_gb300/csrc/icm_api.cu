@@ -9,7 +9,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <algorithm>
+#include <chrono>
 #include <cstring>
+#include <deque>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -110,6 +113,7 @@ struct icm_sim {
   // graph of one step
   cudaGraphExec_t gexec = nullptr;
   bool graph_ok = false;
+  long long version = 0;     // bumped whenever the step sequence changes (batch graphs recapture)
 
   size_t rsize() const { return prec == 32 ? sizeof(float) : sizeof(double); }
 };
@@ -198,6 +202,12 @@ BlobParams blob_params(const icm_sim* s) {
   p.kernel = s->kernel;
   p.slip = s->slip;
   p.mtf = 1.5 * s->rho * blob_volume(s);
+  p.inv_h = 1.0 / s->h;
+  const int n[3] = {s->nx, s->ny, s->nz};
+  for (int a = 0; a < 3; ++a) {
+    p.box[a] = n[a] * s->h;
+    p.inv_box[a] = 1.0 / p.box[a];
+  }
   return p;
 }
 
@@ -282,6 +292,7 @@ void invalidate_graph(icm_sim* s) {
   if (s->gexec) cudaGraphExecDestroy(s->gexec);
   s->gexec = nullptr;
   s->graph_ok = false;
+  s->version++;
 }
 
 // Per-launch CUDA events of an instrumented (eager) step: stage name, algorithmic
@@ -946,6 +957,318 @@ icm_status icm_op_philox(int64_t n, uint32_t ctr0, uint32_t ctr1, uint32_t ctr2,
   cudaFree(d);
   if (e != cudaSuccess) return fail(ICM_ECUDA, "philox kernel: %s", cudaGetErrorString(e));
   return ICM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched replicas: the steps of every member simulation captured into one graph
+// as independent branches (fork on the batch stream, one chain per member stream,
+// join back), so one graph launch advances all of them and the GPU runs the
+// members' kernels side by side.
+// ---------------------------------------------------------------------------
+struct icm_batch {
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<icm_sim*> sims;
+  std::vector<long long> versions;
+  std::vector<cudaEvent_t> events;  // fork, joins, done
+  cudaGraphExec_t gexec = nullptr;
+  bool ok = false;
+};
+
+namespace {
+
+void batch_clear_graph(icm_batch* b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  b->gexec = nullptr;
+  b->ok = false;
+  for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+  b->events.clear();
+}
+
+icm_status batch_capture(icm_batch* b) {
+  batch_clear_graph(b);
+  const size_t n = b->sims.size();
+  b->events.resize(n + 2);
+  for (auto& e : b->events) ICM_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  cudaGraph_t graph = nullptr;
+  ICM_CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  cudaEventRecord(b->events[0], b->stream);
+  for (size_t i = 0; i < n; ++i) {
+    icm_sim* s = b->sims[i];
+    cudaStreamWaitEvent(s->stream, b->events[0], 0);
+    if (s->prec == 32)
+      enqueue_step<float>(s, nullptr);
+    else
+      enqueue_step<double>(s, nullptr);
+    cudaEventRecord(b->events[1 + i], s->stream);
+    cudaStreamWaitEvent(b->stream, b->events[1 + i], 0);
+  }
+  const cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ICM_ECUDA, "batch graph capture failed: %s", cudaGetErrorString(e));
+  }
+  const cudaError_t e2 = cudaGraphInstantiate(&b->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e2 != cudaSuccess) return fail(ICM_ECUDA, "batch graph instantiation failed: %s", cudaGetErrorString(e2));
+  b->versions.clear();
+  for (icm_sim* s : b->sims) b->versions.push_back(s->version);
+  b->ok = true;
+  return ICM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Serving: jobs queue on the host and are admitted first come first served while
+// their device footprint fits the HBM budget and a slot is free.  Each active job
+// replays its own step graph on its own stream, so the jobs' kernels overlap on the
+// device; a pump enqueues a few steps per active job without waiting, and a job is
+// retired (results read, memory freed) once the event recorded after its last step
+// has completed.  Nothing blocks except reading a finished job's results.
+// ---------------------------------------------------------------------------
+struct icm_server {
+  struct Job {
+    int64_t id = 0;
+    int32_t grid[3];
+    double h, rho, eta, kT, dt;
+    int32_t kernel, precision, flags;
+    uint64_t seed;
+    std::vector<double> pos, vel, me, force;
+    int64_t nsteps = 0, enqueued = 0;
+    int32_t state = 0;  // 0 waiting, 1 active, 2 done, 3 failed
+    icm_sim* sim = nullptr;
+    cudaEvent_t done = nullptr;
+    int64_t bytes = 0;
+    std::chrono::steady_clock::time_point t_submit, t_done;
+    std::vector<double> out_pos, out_vel;
+    double out_mom[3] = {0, 0, 0};
+  };
+  int64_t budget = 0, used = 0;
+  int32_t max_active = 0;
+  int64_t next_id = 1;
+  std::deque<Job*> waiting;
+  std::vector<Job*> active;
+  std::map<int64_t, Job*> jobs;
+};
+
+extern "C" {
+
+int64_t icm_estimate_device_bytes(const int32_t grid[3], int32_t precision, int64_t nblobs) {
+  if (!grid || grid[0] < 1 || grid[1] < 1 || grid[2] < 1 || (precision != 32 && precision != 64) || nblobs < 0)
+    return -1;
+  const int64_t rs = precision == 32 ? 4 : 8;
+  const int64_t ncell = (int64_t)grid[0] * grid[1] * grid[2];
+  const int64_t kxp = (grid[0] / 2 + 1 + 15) / 16 * 16;
+  int64_t cap = 64;
+  while (cap < nblobs) cap *= 2;
+  const int64_t fields = 3 * (3 * ncell * rs);
+  const int64_t spec = 3 * (int64_t)grid[2] * grid[1] * kxp * 2 * rs;
+  const int64_t tables = 3 * (int64_t)kMaxSide * (3 * 2 * rs + 4) + 16 * 256;
+  const int64_t blobs = nblobs > 0 ? 37 * cap * 8 : 0;
+  return fields + spec + tables + blobs + 8 * 3 * 1024 + 4096;
+}
+
+icm_status icm_batch_create(void* cuda_stream, icm_batch** out) {
+  if (!out) return fail(ICM_EINVAL, "out must not be NULL");
+  icm_batch* b = new icm_batch();
+  if (cuda_stream) {
+    b->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete b;
+      return fail(ICM_ECUDA, "cudaStreamCreate failed");
+    }
+    b->own_stream = true;
+  }
+  *out = b;
+  return ICM_OK;
+}
+
+icm_status icm_batch_set(icm_batch* b, int32_t n, icm_sim* const* sims) {
+  if (!b || n < 0 || (n > 0 && !sims)) return fail(ICM_EINVAL, "bad arguments");
+  std::vector<icm_sim*> v(sims, sims + n);
+  for (size_t i = 0; i < v.size(); ++i) {
+    if (!v[i]) return fail(ICM_EINVAL, "NULL simulation in batch");
+    for (size_t j = 0; j < i; ++j)
+      if (v[j] == v[i]) return fail(ICM_EINVAL, "a simulation appears twice in the batch");
+  }
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  b->sims = v;
+  batch_clear_graph(b);
+  return ICM_OK;
+}
+
+icm_status icm_batch_step(icm_batch* b, int64_t nsteps) {
+  if (!b || nsteps < 0) return fail(ICM_EINVAL, "bad arguments");
+  if (nsteps == 0 || b->sims.empty()) return ICM_OK;
+  bool stale = !b->ok;
+  for (size_t i = 0; !stale && i < b->sims.size(); ++i) stale = b->versions[i] != b->sims[i]->version;
+  if (stale) {
+    // work already queued on the members' own streams must precede the batch
+    for (icm_sim* s : b->sims) cudaStreamSynchronize(s->stream);
+    const icm_status st = batch_capture(b);
+    if (st != ICM_OK) return st;
+  }
+  for (int64_t i = 0; i < nsteps; ++i) ICM_CK(cudaGraphLaunch(b->gexec, b->stream));
+  // later work on a member's own stream waits for the batch
+  cudaEvent_t done = b->events.back();
+  ICM_CK(cudaEventRecord(done, b->stream));
+  for (icm_sim* s : b->sims) ICM_CK(cudaStreamWaitEvent(s->stream, done, 0));
+  return ICM_OK;
+}
+
+icm_status icm_batch_sync(icm_batch* b) {
+  if (!b) return fail(ICM_EINVAL, "NULL batch");
+  ICM_CK(cudaStreamSynchronize(b->stream));
+  icm_status worst = ICM_OK;
+  for (icm_sim* s : b->sims) {
+    const icm_status st = check_device_errors(s);
+    if (st != ICM_OK) worst = st;
+  }
+  return worst;
+}
+
+void icm_batch_destroy(icm_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  batch_clear_graph(b);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+icm_status icm_server_create(int64_t hbm_budget_bytes, int32_t max_active, icm_server** out) {
+  if (!out || hbm_budget_bytes <= 0 || max_active < 1) return fail(ICM_EINVAL, "bad arguments");
+  icm_server* sv = new icm_server();
+  sv->budget = hbm_budget_bytes;
+  sv->max_active = max_active;
+  *out = sv;
+  return ICM_OK;
+}
+
+icm_status icm_server_submit(icm_server* sv, const icm_job_desc* d, int64_t* job_id) {
+  if (!sv || !d || !job_id) return fail(ICM_EINVAL, "bad arguments");
+  if (d->nsteps < 1 || d->nblobs < 0 || (d->nblobs > 0 && (!d->pos || !d->excess_mass)))
+    return fail(ICM_EINVAL, "a job needs nsteps >= 1 and, with blobs, positions and masses");
+  const int64_t est = icm_estimate_device_bytes(d->grid, d->precision, d->nblobs);
+  if (est < 0) return fail(ICM_EINVAL, "invalid grid or precision");
+  if (est > sv->budget) return fail(ICM_ENOMEM, "the job needs %lld bytes, more than the whole budget", (long long)est);
+  auto* j = new icm_server::Job();
+  j->id = sv->next_id++;
+  memcpy(j->grid, d->grid, sizeof(j->grid));
+  j->h = d->h; j->rho = d->rho; j->eta = d->eta; j->kT = d->kT; j->dt = d->dt;
+  j->kernel = d->kernel; j->precision = d->precision; j->flags = d->flags; j->seed = d->seed;
+  const int64_t n = d->nblobs;
+  j->pos.assign(d->pos, d->pos + 3 * n);
+  if (d->vel) j->vel.assign(d->vel, d->vel + 3 * n);
+  j->me.assign(d->excess_mass, d->excess_mass + n);
+  if (d->force) j->force.assign(d->force, d->force + 3 * n);
+  j->nsteps = d->nsteps;
+  j->bytes = est;
+  j->t_submit = std::chrono::steady_clock::now();
+  sv->waiting.push_back(j);
+  sv->jobs[j->id] = j;
+  *job_id = j->id;
+  return ICM_OK;
+}
+
+icm_status icm_server_pump(icm_server* sv, int32_t steps_per_pump, int32_t* n_active, int32_t* n_waiting,
+                           int32_t* n_finished) {
+  if (!sv || steps_per_pump < 1) return fail(ICM_EINVAL, "bad arguments");
+  int32_t finished = 0;
+  // 1. retire jobs whose last step has completed on the device
+  std::vector<icm_server::Job*> still;
+  for (auto* j : sv->active) {
+    if (j->enqueued < j->nsteps || cudaEventQuery(j->done) != cudaSuccess) {
+      still.push_back(j);
+      continue;
+    }
+    const int64_t nb = (int64_t)j->me.size();
+    j->out_pos.resize(3 * nb);
+    j->out_vel.resize(3 * nb);
+    const icm_status rs = icm_read_state(j->sim, nb ? j->out_pos.data() : nullptr, nb ? j->out_vel.data() : nullptr,
+                                         nullptr, j->out_mom, nullptr);
+    j->state = rs == ICM_OK ? 2 : 3;
+    j->t_done = std::chrono::steady_clock::now();
+    sv->used -= j->bytes;
+    cudaEventDestroy(j->done);
+    j->done = nullptr;
+    icm_destroy(j->sim);
+    j->sim = nullptr;
+    ++finished;
+  }
+  sv->active.swap(still);
+  // 2. admission, first come first served, while the footprint fits
+  while (!sv->waiting.empty() && (int32_t)sv->active.size() < sv->max_active) {
+    icm_server::Job* j = sv->waiting.front();
+    if (sv->used + j->bytes > sv->budget) break;
+    icm_sim* s = nullptr;
+    icm_status st = icm_create(j->grid, j->h, j->rho, j->eta, j->kT, j->dt, j->kernel, j->seed, j->precision, j->flags,
+                               nullptr, &s);
+    if (st == ICM_ENOMEM) break;
+    const int64_t nb = (int64_t)j->me.size();
+    if (st == ICM_OK && nb > 0)
+      st = icm_add_blobs(s, nb, j->pos.data(), j->vel.empty() ? nullptr : j->vel.data(), j->me.data());
+    if (st == ICM_OK && nb > 0 && !j->force.empty()) st = icm_set_blob_forces(s, j->force.data());
+    if (st == ICM_OK && cudaEventCreateWithFlags(&j->done, cudaEventDisableTiming) != cudaSuccess) st = ICM_ECUDA;
+    sv->waiting.pop_front();
+    if (st != ICM_OK) {
+      if (s) icm_destroy(s);
+      j->state = 3;
+      j->t_done = std::chrono::steady_clock::now();
+      ++finished;
+      continue;
+    }
+    j->sim = s;
+    j->bytes = icm_device_bytes(s);
+    sv->used += j->bytes;
+    j->state = 1;
+    sv->active.push_back(j);
+  }
+  // 3. enqueue the next steps of every active job on its own stream (no waiting)
+  for (auto* j : sv->active) {
+    const int64_t k = std::min<int64_t>(steps_per_pump, j->nsteps - j->enqueued);
+    if (k <= 0) continue;
+    const icm_status st = icm_step(j->sim, k);
+    if (st != ICM_OK) return st;
+    j->enqueued += k;
+    if (j->enqueued == j->nsteps) ICM_CK(cudaEventRecord(j->done, j->sim->stream));
+  }
+  if (n_active) *n_active = (int32_t)sv->active.size();
+  if (n_waiting) *n_waiting = (int32_t)sv->waiting.size();
+  if (n_finished) *n_finished = finished;
+  return ICM_OK;
+}
+
+icm_status icm_server_result(icm_server* sv, int64_t job_id, int32_t* state, double* pos, double* vel,
+                             double momentum[3], double* latency_s) {
+  if (!sv) return fail(ICM_EINVAL, "NULL server");
+  auto it = sv->jobs.find(job_id);
+  if (it == sv->jobs.end()) return fail(ICM_EINVAL, "unknown job id %lld", (long long)job_id);
+  icm_server::Job* j = it->second;
+  if (state) *state = j->state;
+  if (j->state >= 2) {
+    const size_t n = j->out_pos.size();
+    if (pos && n) memcpy(pos, j->out_pos.data(), sizeof(double) * n);
+    if (vel && n) memcpy(vel, j->out_vel.data(), sizeof(double) * n);
+    if (momentum) memcpy(momentum, j->out_mom, sizeof(j->out_mom));
+    if (latency_s) latency_s[0] = std::chrono::duration<double>(j->t_done - j->t_submit).count();
+  }
+  return ICM_OK;
+}
+
+int64_t icm_server_bytes_in_use(const icm_server* sv) { return sv ? sv->used : -1; }
+
+void icm_server_destroy(icm_server* sv) {
+  if (!sv) return;
+  for (auto& kv : sv->jobs) {
+    if (kv.second->sim) icm_destroy(kv.second->sim);
+    if (kv.second->done) cudaEventDestroy(kv.second->done);
+    delete kv.second;
+  }
+  delete sv;
 }
 
 }  // extern "C"

@@ -22,8 +22,10 @@ struct WarpStencil {
   R d2[3][3][K + 2];     // second differences of the zero-padded weights
 };
 
-__device__ __forceinline__ double wrap_pos(double x, double L) {
-  double y = x - L * floor(x / L);
+// Periodic image in [0, L), with 1/L precomputed (GB300 has little FP64 throughput,
+// so the blob kernels keep their double-precision operations few).
+__device__ __forceinline__ double wrap_pos(double x, double L, double inv_L) {
+  double y = fma(-L, floor(x * inv_L), x);
   if (y >= L) y -= L;
   if (y < 0.0) y += L;
   return y;
@@ -37,11 +39,14 @@ __device__ __forceinline__ void build_stencil(WarpStencil<R, K>& S, const double
     const int comp = lane / 3, ax = lane % 3;
     const int n = ax == 0 ? p.nx : (ax == 1 ? p.ny : p.nz);
     const double off = (ax == comp) ? 0.0 : 0.5;
-    const double s = q[ax] / p.h - off;
-    const long long f = Peskin<R, K>::first(s);
+    const double s = fma(q[ax], p.inv_h, -off);
+    // node 'first' + 1 is the anchor cell; offsets from it are exact small numbers in R
+    const double anc = Peskin<R, K>::anchor(s);
+    const long long f = (long long)anc - 1;
+    const R frac = (R)(s - anc);
     R w[K];
 #pragma unroll
-    for (int a = 0; a < K; ++a) w[a] = Peskin<R, K>::phi((R)(s - (double)(f + a)));
+    for (int a = 0; a < K; ++a) w[a] = Peskin<R, K>::phi(frac + R(1 - a));
     if (!ext) {
       long long fw = f % n;
       if (fw < 0) fw += n;
@@ -81,23 +86,38 @@ __device__ __forceinline__ R warp_sum(R x) {
   return x;
 }
 
-// (J field) for the three components; result valid in every lane.
+// (J field) for the three components; result valid in every lane.  Each lane takes
+// items lane, lane + 32, ... of the 3 w^3 nodes (x index fastest); the trip count is a
+// compile-time constant so every load of a lane is issued before the first use.
 template <typename R, int K>
 __device__ __forceinline__ void gather(const WarpStencil<R, K>& S, const R* __restrict__ field, const BlobParams& p,
                                        int lane, double out[3]) {
-  constexpr int W3 = K * K * K;
-  R acc[3] = {R(0), R(0), R(0)};
+  constexpr int W3 = K * K * K, ITEMS = 3 * W3, ROUNDS = (ITEMS + 31) / 32;
+  R val[ROUNDS], wgt[ROUNDS];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const R* f = field + c * p.ncell;
-    for (int it = lane; it < W3; it += 32) {
-      const int a = it % K, b = (it / K) % K, cz = it / (K * K);
+  for (int j = 0; j < ROUNDS; ++j) {
+    const int it = lane + 32 * j;
+    val[j] = R(0);
+    wgt[j] = R(0);
+    if (it < ITEMS) {
+      const int c = it / W3, r = it - c * W3;
+      const int a = r % K, b = (r / K) % K, cz = r / (K * K);
       const int ix = wrap_add(S.first[c][0], a, p.nx);
       const int iy = wrap_add(S.first[c][1], b, p.ny);
       const int iz = wrap_add(S.first[c][2], cz, p.nz);
-      const R wgt = S.w[c][0][a] * S.w[c][1][b] * S.w[c][2][cz];
-      acc[c] += wgt * f[ix + (long long)p.nx * (iy + (long long)p.ny * iz)];
+      wgt[j] = S.w[c][0][a] * S.w[c][1][b] * S.w[c][2][cz];
+      val[j] = __ldg(field + c * p.ncell + ix + (long long)p.nx * (iy + (long long)p.ny * iz));
     }
+  }
+  R acc[3] = {R(0), R(0), R(0)};
+#pragma unroll
+  for (int j = 0; j < ROUNDS; ++j) {
+    const int it = lane + 32 * j;
+    const int c = it / W3;
+    const R t = wgt[j] * val[j];
+    acc[0] += c == 0 ? t : R(0);
+    acc[1] += c == 1 ? t : R(0);
+    acc[2] += c == 2 ? t : R(0);
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c) out[c] = (double)warp_sum(acc[c]);
@@ -107,42 +127,47 @@ __device__ __forceinline__ void gather(const WarpStencil<R, K>& S, const R* __re
 template <typename R, int K>
 __device__ __forceinline__ void gather_lap(const WarpStencil<R, K>& S, const R* __restrict__ field,
                                            const BlobParams& p, int lane, double out[3]) {
-  constexpr int E = K + 2, E3 = E * E * E;
-  const R inv_h2 = (R)(1.0 / (p.h * p.h));
+  constexpr int E = K + 2, E3 = E * E * E, ITEMS = 3 * E3, ROUNDS = (ITEMS + 31) / 32;
   R acc[3] = {R(0), R(0), R(0)};
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const R* f = field + c * p.ncell;
-    for (int it = lane; it < E3; it += 32) {
-      const int a = it % E, b = (it / E) % E, cz = it / (E * E);
+  for (int j = 0; j < ROUNDS; ++j) {
+    const int it = lane + 32 * j;
+    if (it < ITEMS) {
+      const int c = it / E3, r = it - c * E3;
+      const int a = r % E, b = (r / E) % E, cz = r / (E * E);
       const int ix = wrap_add(S.first[c][0], a, p.nx);
       const int iy = wrap_add(S.first[c][1], b, p.ny);
       const int iz = wrap_add(S.first[c][2], cz, p.nz);
       const R wx = S.w[c][0][a], wy = S.w[c][1][b], wz = S.w[c][2][cz];
       const R wgt = S.d2[c][0][a] * wy * wz + wx * S.d2[c][1][b] * wz + wx * wy * S.d2[c][2][cz];
-      acc[c] += wgt * f[ix + (long long)p.nx * (iy + (long long)p.ny * iz)];
+      const R t = wgt * __ldg(field + c * p.ncell + ix + (long long)p.nx * (iy + (long long)p.ny * iz));
+      acc[0] += c == 0 ? t : R(0);
+      acc[1] += c == 1 ? t : R(0);
+      acc[2] += c == 2 ? t : R(0);
     }
   }
+  const double inv_h2 = 1.0 / (p.h * p.h);
 #pragma unroll
-  for (int c = 0; c < 3; ++c) out[c] = (double)warp_sum(acc[c]) * (double)inv_h2;
+  for (int c = 0; c < 3; ++c) out[c] = (double)warp_sum(acc[c]) * inv_h2;
 }
 
 template <typename R, int K>
 __device__ __forceinline__ void scatter(const WarpStencil<R, K>& S, R* __restrict__ field, const BlobParams& p,
                                         int lane, const double vec[3]) {
-  constexpr int W3 = K * K * K;
+  constexpr int W3 = K * K * K, ITEMS = 3 * W3, ROUNDS = (ITEMS + 31) / 32;
   const double inv_dvf = 1.0 / (p.h * p.h * p.h);
+  const R amp[3] = {(R)(vec[0] * inv_dvf), (R)(vec[1] * inv_dvf), (R)(vec[2] * inv_dvf)};
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const R amp = (R)(vec[c] * inv_dvf);
-    R* f = field + c * p.ncell;
-    for (int it = lane; it < W3; it += 32) {
-      const int a = it % K, b = (it / K) % K, cz = it / (K * K);
+  for (int j = 0; j < ROUNDS; ++j) {
+    const int it = lane + 32 * j;
+    if (it < ITEMS) {
+      const int c = it / W3, r = it - c * W3;
+      const int a = r % K, b = (r / K) % K, cz = r / (K * K);
       const int ix = wrap_add(S.first[c][0], a, p.nx);
       const int iy = wrap_add(S.first[c][1], b, p.ny);
       const int iz = wrap_add(S.first[c][2], cz, p.nz);
       const R wgt = S.w[c][0][a] * S.w[c][1][b] * S.w[c][2][cz];
-      atomicAdd(f + ix + (long long)p.nx * (iy + (long long)p.ny * iz), wgt * amp);
+      atomicAdd(field + c * p.ncell + ix + (long long)p.nx * (iy + (long long)p.ny * iz), wgt * amp[c]);
     }
   }
 }
@@ -174,8 +199,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_predict(BlobParams p, BlobState
   load3(s.q, b, q);
   build_stencil<R, K>(S, q, p, false, lane);
   gather<R, K>(S, v, p, lane, w0);
-  const double L[3] = {p.nx * p.h, p.ny * p.h, p.nz * p.h};
-  for (int a = 0; a < 3; ++a) qh[a] = wrap_pos(q[a] + 0.5 * p.dt * w0[a], L[a]);
+  for (int a = 0; a < 3; ++a) qh[a] = wrap_pos(fma(0.5 * p.dt, w0[a], q[a]), p.box[a], p.inv_box[a]);
   __syncwarp();
   build_stencil<R, K>(S, qh, p, false, lane);
   gather<R, K>(S, v, p, lane, w1);
@@ -270,7 +294,6 @@ __global__ void __launch_bounds__(32 * kWarps) k_finish(BlobParams p, BlobState 
   }
   if (lane == 0) {
     load3(s.q, b, q);
-    const double L[3] = {p.nx * p.h, p.ny * p.h, p.nz * p.h};
     double qn[3], u[3];
     if (inertial)
       load3(s.u, b, u);
@@ -278,7 +301,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_finish(BlobParams p, BlobState 
       for (int a = 0; a < 3; ++a) u[a] = jv[a];
     bool bad = false, cfl = false;
     for (int a = 0; a < 3; ++a) {
-      qn[a] = wrap_pos(q[a] + 0.5 * p.dt * (jv[a] + s.w1[3 * b + a]), L[a]);
+      qn[a] = wrap_pos(fma(0.5 * p.dt, jv[a] + s.w1[3 * b + a], q[a]), p.box[a], p.inv_box[a]);
       bad |= !isfinite(qn[a]) || !isfinite(u[a]);
       cfl |= fabs(u[a]) * p.dt > p.h;
     }

@@ -74,7 +74,9 @@ template <> struct BoxMuller<float> {
     // full 32-bit resolution near 0 (where the tail of the normal lives).
     const float u1 = fmaf((float)(a >> 8), 5.9604644775390625e-08f, ((float)(a & 0xffu) + 0.5f) * 2.3283064365386963e-10f);
     const float u2 = fmaf((float)(b >> 8), 5.9604644775390625e-08f, ((float)(b & 0xffu) + 0.5f) * 2.3283064365386963e-10f);
-    const float rad = sqrtf(-2.0f * logf(u1));
+    // -2 ln u1 = -2 ln(2) log2(u1); the hardware log2 is accurate to ~2^-22 absolute,
+    // far inside the FP32 path's tolerance (the uniforms themselves carry 2^-24)
+    const float rad = sqrtf(-1.38629436111989061f * __log2f(u1));
     float s, c;
     __sincosf(6.28318530717958648f * u2, &s, &c);
     z0 = rad * c;
@@ -92,6 +94,22 @@ __device__ __forceinline__ void cell_normals(uint32_t cell, uint32_t step, uint3
   BoxMuller<R>::apply(a.x, a.y, z[0], z[1]);
   BoxMuller<R>::apply(a.z, a.w, z[2], z[3]);
   BoxMuller<R>::apply(b.x, b.y, z[4], z[5]);
+}
+
+// The same normals, computing only the Box-Muller pairs flagged: p00 -> (xx, yy),
+// p01 -> (zz, xy), p10 -> (xz, yz).  Entries of pairs not flagged are left unset.
+template <typename R>
+__device__ __forceinline__ void cell_normals_masked(uint32_t cell, uint32_t step, uint32_t k0, uint32_t k1, R z[6],
+                                                    bool p00, bool p01, bool p10) {
+  if (p00 || p01) {
+    const u32x4 a = philox4x32_10(u32x4{cell, step, 0u, 0u}, k0, k1);
+    if (p00) BoxMuller<R>::apply(a.x, a.y, z[0], z[1]);
+    if (p01) BoxMuller<R>::apply(a.z, a.w, z[2], z[3]);
+  }
+  if (p10) {
+    const u32x4 b = philox4x32_10(u32x4{cell, step, 1u, 0u}, k0, k1);
+    BoxMuller<R>::apply(b.x, b.y, z[4], z[5]);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -116,6 +134,8 @@ template <typename R> struct Peskin<R, 3> {
   }
   // first node of the support: round-half-up(s) - 1
   __device__ __forceinline__ static long long first(double s) { return (long long)floor(s + 0.5) - 1; }
+  // the cell that fixes the support (its node 'first' + 1), as a double: round-half-up(s)
+  __device__ __forceinline__ static double anchor(double s) { return floor(s + 0.5); }
 };
 template <typename R> struct Peskin<R, 4> {
   static constexpr int W = 4;
@@ -126,6 +146,7 @@ template <typename R> struct Peskin<R, 4> {
     return R(0);
   }
   __device__ __forceinline__ static long long first(double s) { return (long long)floor(s) - 1; }
+  __device__ __forceinline__ static double anchor(double s) { return floor(s); }
 };
 
 // Status bits the device raises (read back by icm_sync).

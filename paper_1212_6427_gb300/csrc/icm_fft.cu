@@ -411,29 +411,36 @@ constexpr int kXPad = 16;   // x pass: one padding slot every 16 positions (bank
 __host__ __device__ constexpr int xrow(int n) { return n + n / kXPad; }
 __device__ __forceinline__ int xaddr(int l, int p, int N) { return l * xrow(N) + p + p / kXPad; }
 
+// One thread per first-stage item (3 components x R2 x NL), so the loads of all three
+// components are in flight together.
 template <typename R, int N, int R1, int R2>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_zsym2(cplx_t<R>* __restrict__ spec, const cplx_t<R>* __restrict__ gtw,
-                                                    int ny, int kx, int kxp, SymParams<R> sp) {
+constexpr int zsym2_threads() { return 3 * R2 * seg_lines<R>() > 1024 ? 1024 : 3 * R2 * seg_lines<R>(); }
+
+template <typename R, int N, int R1, int R2>
+__global__ void __launch_bounds__(zsym2_threads<R, N, R1, R2>()) k_zsym2(cplx_t<R>* __restrict__ spec,
+                                                                        const cplx_t<R>* __restrict__ gtw,
+                                                                        int ny, int kx, int kxp, SymParams<R> sp) {
   using C = cplx_t<R>;
   constexpr int NL = seg_lines<R>();
+  constexpr int NT = zsym2_threads<R, N, R1, R2>();
   constexpr bool HOLD3 = sizeof(R) == 4 && R2 <= 12;   // 3 x R2 complex in registers
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);   // [3][N][NL]
-  C* tw = buf + 3 * N * NL;                  // [N]
+  C* tw = buf + 3 * N * NL;                  // [N] first-stage twiddles, [k2][n1]
   const int tid = threadIdx.x;
-  for (int i = tid; i < N; i += kThreads) tw[i] = gtw[i];
+  load_stage_twiddles<R, R1, R2>(tw, gtw, tid, NT);
   const int kx0 = blockIdx.x * NL, py = blockIdx.y;
   const size_t zs = (size_t)ny * kxp, cs = (size_t)N * zs;
   C* base = spec + (size_t)py * kxp + kx0;
   const C zero = mk(R(0), R(0));
   __syncthreads();
-  for (int it = tid; it < 3 * R2 * NL; it += kThreads) {
+  for (int it = tid; it < 3 * R2 * NL; it += NT) {
     const int line = it % NL, rest = it / NL, n1 = rest % R2, c = rest / R2;
     const bool ok = kx0 + line < kx;
     C a[R1];
 #pragma unroll
     for (int r = 0; r < R1; ++r) a[r] = ok ? base[c * cs + (size_t)(n1 + R2 * r) * zs + line] : zero;
-    stage_a_fwd<R, R1>(a, n1, tw);
+    stage_a_fwd<R, R1, R2>(a, tw + n1);
 #pragma unroll
     for (int k2 = 0; k2 < R1; ++k2) buf[(c * N + n1 + R2 * k2) * NL + line] = a[k2];
   }
@@ -441,7 +448,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_zsym2(cplx
   const C dyv = sp.dy[py];
   const R ddy = sp.ddy[py];
   if (HOLD3) {
-    for (int it = tid; it < R1 * NL; it += kThreads) {
+    for (int it = tid; it < R1 * NL; it += NT) {
       const int line = it % NL, blk = it / NL, k = kx0 + line;
       if (k >= kx) continue;
       C b[3][R2];
@@ -467,7 +474,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_zsym2(cplx
       }
     }
   } else {
-    for (int it = tid; it < 3 * R1 * NL; it += kThreads) {
+    for (int it = tid; it < 3 * R1 * NL; it += NT) {
       const int line = it % NL, rest = it / NL, blk = rest % R1, c = rest / R1;
       C b[R2];
 #pragma unroll
@@ -477,7 +484,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_zsym2(cplx
       for (int n = 0; n < R2; ++n) buf[(c * N + R2 * blk + n) * NL + line] = b[n];
     }
     __syncthreads();
-    for (int it = tid; it < N * NL; it += kThreads) {
+    for (int it = tid; it < N * NL; it += NT) {
       const int line = it % NL, pz = it / NL, k = kx0 + line;
       if (k >= kx) continue;
       C& c0 = buf[it];
@@ -487,7 +494,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_zsym2(cplx
                       k == 0 && py == 0 && pz == 0);
     }
     __syncthreads();
-    for (int it = tid; it < 3 * R1 * NL; it += kThreads) {
+    for (int it = tid; it < 3 * R1 * NL; it += NT) {
       const int line = it % NL, rest = it / NL, blk = rest % R1, c = rest / R1;
       C b[R2];
 #pragma unroll
@@ -498,13 +505,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_zsym2(cplx
     }
   }
   __syncthreads();
-  for (int it = tid; it < 3 * R2 * NL; it += kThreads) {
+  for (int it = tid; it < 3 * R2 * NL; it += NT) {
     const int line = it % NL, rest = it / NL, n1 = rest % R2, c = rest / R2;
     if (kx0 + line >= kx) continue;
     C a[R1];
 #pragma unroll
     for (int k2 = 0; k2 < R1; ++k2) a[k2] = buf[(c * N + n1 + R2 * k2) * NL + line];
-    stage_a_inv<R, R1>(a, n1, tw);
+    stage_a_inv<R, R1, R2>(a, tw + n1);
 #pragma unroll
     for (int n2 = 0; n2 < R1; ++n2) base[c * cs + (size_t)(n1 + R2 * n2) * zs + line] = a[n2];
   }
@@ -519,7 +526,7 @@ __global__ void __launch_bounds__(kThreads) k_ypass2(cplx_t<R>* __restrict__ spe
   C* buf = reinterpret_cast<C*>(smem_raw);   // [N][NL]
   C* tw = buf + N * NL;
   const int tid = threadIdx.x;
-  for (int i = tid; i < N; i += kThreads) tw[i] = gtw[i];
+  load_stage_twiddles<R, R1, R2>(tw, gtw, tid, kThreads);
   const int kx0 = blockIdx.x * NL, z = blockIdx.y, comp = blockIdx.z;
   C* base = spec + ((size_t)(comp * nz + z) * N) * kxp + kx0;
   const C zero = mk(R(0), R(0));
@@ -531,7 +538,7 @@ __global__ void __launch_bounds__(kThreads) k_ypass2(cplx_t<R>* __restrict__ spe
       C a[R1];
 #pragma unroll
       for (int r = 0; r < R1; ++r) a[r] = ok ? base[(size_t)(n1 + R2 * r) * kxp + line] : zero;
-      stage_a_fwd<R, R1>(a, n1, tw);
+      stage_a_fwd<R, R1, R2>(a, tw + n1);
 #pragma unroll
       for (int k2 = 0; k2 < R1; ++k2) buf[(n1 + R2 * k2) * NL + line] = a[k2];
     }
@@ -564,7 +571,7 @@ __global__ void __launch_bounds__(kThreads) k_ypass2(cplx_t<R>* __restrict__ spe
       C a[R1];
 #pragma unroll
       for (int k2 = 0; k2 < R1; ++k2) a[k2] = buf[(n1 + R2 * k2) * NL + line];
-      stage_a_inv<R, R1>(a, n1, tw);
+      stage_a_inv<R, R1, R2>(a, tw + n1);
 #pragma unroll
       for (int n2 = 0; n2 < R1; ++n2) base[(size_t)(n1 + R2 * n2) * kxp + line] = a[n2];
     }
@@ -582,7 +589,7 @@ __global__ void __launch_bounds__(kThreads) k_xfwd2(const R* __restrict__ src, c
   C* buf = reinterpret_cast<C*>(smem_raw);   // [kXLines][xrow(N)]
   C* tw = buf + kXLines * xrow(N);
   const int tid = threadIdx.x;
-  for (int i = tid; i < N; i += kThreads) tw[i] = gtw[i];
+  load_stage_twiddles<R, R1, R2>(tw, gtw, tid, kThreads);
   const int comp = blockIdx.y;
   const long long row0 = (long long)blockIdx.x * (2 * kXLines);
   const R* s = src + comp * ncell;
@@ -598,7 +605,7 @@ __global__ void __launch_bounds__(kThreads) k_xfwd2(const R* __restrict__ src, c
       const int x = n1 + R2 * r;
       a[r] = mk(ok0 ? p0[x] : R(0), ok1 ? p0[N + x] : R(0));
     }
-    stage_a_fwd<R, R1>(a, n1, tw);
+    stage_a_fwd<R, R1, R2>(a, tw + n1);
 #pragma unroll
     for (int k2 = 0; k2 < R1; ++k2) buf[xaddr(l, n1 + R2 * k2, N)] = a[k2];
   }
@@ -627,28 +634,58 @@ __global__ void __launch_bounds__(kThreads) k_xfwd2(const R* __restrict__ src, c
   }
 }
 
-template <typename R, int N, int R1, int R2>
+// MODE OUT_STORE: dst = x.  MODE OUT_ADD_AND_STORE2: dst += x, dst2 = x, with the old
+// dst values loaded at kernel start so that they are in flight during the FFT.
+template <typename R, int N, int R1, int R2, int MODE>
 __global__ void __launch_bounds__(kThreads) k_xinv2(const cplx_t<R>* __restrict__ spec, R* __restrict__ dst,
-                                                    R* __restrict__ dst2, int mode, const cplx_t<R>* __restrict__ gtw,
+                                                    R* __restrict__ dst2, const cplx_t<R>* __restrict__ gtw,
                                                     int nrows, long long ncell, int kxp) {
   using C = cplx_t<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* tw = buf + kXLines * xrow(N);
   const int tid = threadIdx.x;
-  for (int i = tid; i < N; i += kThreads) tw[i] = gtw[i];
+  load_stage_twiddles<R, R1, R2>(tw, gtw, tid, kThreads);
   const int comp = blockIdx.y;
   const long long row0 = (long long)blockIdx.x * (2 * kXLines);
   const C* in = spec + (size_t)comp * nrows * kxp;
   const C zero = mk(R(0), R(0));
-  for (int it = tid; it < kXLines * N; it += kThreads) {
+  const size_t cb = (size_t)comp * ncell;
+  // this thread's output positions: line l = tid / R2, x = n1 + R2 n2, rows r0 and r0 + 1
+  constexpr int OUTS = (kXLines * R2 + kThreads - 1) / kThreads;
+  R old0[MODE == OUT_ADD_AND_STORE2 ? OUTS * R1 : 1], old1[MODE == OUT_ADD_AND_STORE2 ? OUTS * R1 : 1];
+  if (MODE == OUT_ADD_AND_STORE2) {
+#pragma unroll
+    for (int o = 0; o < OUTS; ++o) {
+      const int it = tid + o * kThreads;
+      const int n1 = it % R2, l = it / R2;
+      const long long r0 = row0 + 2 * l;
+#pragma unroll
+      for (int n2 = 0; n2 < R1; ++n2) {
+        const int x = n1 + R2 * n2;
+        old0[o * R1 + n2] = (it < kXLines * R2 && r0 < nrows) ? dst[cb + (size_t)r0 * N + x] : R(0);
+        old1[o * R1 + n2] = (it < kXLines * R2 && r0 + 1 < nrows) ? dst[cb + (size_t)(r0 + 1) * N + x] : R(0);
+      }
+    }
+  }
+  constexpr int LOADS = (kXLines * N + kThreads - 1) / kThreads;   // compile-time: all loads in flight
+  C av[LOADS], bv[LOADS];
+#pragma unroll
+  for (int j = 0; j < LOADS; ++j) {
+    const int it = tid + j * kThreads;
     const int k = it % N, l = it / N;
     const long long r1 = row0 + 2 * l;
-    const bool direct = 2 * k <= N;
-    const int kk = direct ? k : N - k;
-    C a = r1 < nrows ? in[r1 * kxp + kk] : zero;
-    C b = r1 + 1 < nrows ? in[(r1 + 1) * kxp + kk] : zero;
-    if (!direct) {
+    const int kk = 2 * k <= N ? k : N - k;
+    av[j] = (it < kXLines * N && r1 < nrows) ? in[r1 * kxp + kk] : zero;
+    bv[j] = (it < kXLines * N && r1 + 1 < nrows) ? in[(r1 + 1) * kxp + kk] : zero;
+  }
+#pragma unroll
+  for (int j = 0; j < LOADS; ++j) {
+    const int it = tid + j * kThreads;
+    if (it >= kXLines * N) break;
+    const int k = it % N, l = it / N;
+    C a = av[j], b = bv[j];
+    if (2 * k > N) {
       a = cconj(a);
       b = cconj(b);
     }
@@ -669,33 +706,35 @@ __global__ void __launch_bounds__(kThreads) k_xinv2(const cplx_t<R>* __restrict_
     for (int n = 0; n < R2; ++n) buf[xaddr(l, R2 * blk + n, N)] = b[n];
   }
   __syncthreads();
-  const size_t cb = (size_t)comp * ncell;
-  for (int it = tid; it < kXLines * R2; it += kThreads) {
+#pragma unroll
+  for (int o = 0; o < OUTS; ++o) {
+    const int it = tid + o * kThreads;
+    if (it >= kXLines * R2) break;
     const int n1 = it % R2, l = it / R2;
     C a[R1];
 #pragma unroll
     for (int k2 = 0; k2 < R1; ++k2) a[k2] = buf[xaddr(l, n1 + R2 * k2, N)];
-    stage_a_inv<R, R1>(a, n1, tw);
+    stage_a_inv<R, R1, R2>(a, tw + n1);
     const long long r0 = row0 + 2 * l;
 #pragma unroll
     for (int n2 = 0; n2 < R1; ++n2) {
       const int x = n1 + R2 * n2;
       if (r0 < nrows) {
-        const size_t o = cb + (size_t)r0 * N + x;
-        if (mode == OUT_STORE) {
-          dst[o] = a[n2].x;
+        const size_t ox = cb + (size_t)r0 * N + x;
+        if (MODE == OUT_STORE) {
+          dst[ox] = a[n2].x;
         } else {
-          dst[o] += a[n2].x;
-          dst2[o] = a[n2].x;
+          dst[ox] = old0[o * R1 + n2] + a[n2].x;
+          dst2[ox] = a[n2].x;
         }
       }
       if (r0 + 1 < nrows) {
-        const size_t o = cb + (size_t)(r0 + 1) * N + x;
-        if (mode == OUT_STORE) {
-          dst[o] = a[n2].y;
+        const size_t ox = cb + (size_t)(r0 + 1) * N + x;
+        if (MODE == OUT_STORE) {
+          dst[ox] = a[n2].y;
         } else {
-          dst[o] += a[n2].y;
-          dst2[o] = a[n2].y;
+          dst[ox] = old1[o * R1 + n2] + a[n2].y;
+          dst2[ox] = a[n2].y;
         }
       }
     }
@@ -730,7 +769,8 @@ void set_smem_attributes() {
   cudaFuncSetAttribute(k_ypass2<R, N, R1, R2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big); \
   cudaFuncSetAttribute(k_ypass2<R, N, R1, R2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);  \
   cudaFuncSetAttribute(k_xfwd2<R, N, R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);         \
-  cudaFuncSetAttribute(k_xinv2<R, N, R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_xinv2<R, N, R1, R2, OUT_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);        \
+  cudaFuncSetAttribute(k_xinv2<R, N, R1, R2, OUT_ADD_AND_STORE2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   ICM_FFT_SIDES(ICM_ATTR)
 #undef ICM_ATTR
   cudaFuncSetAttribute(k_xfwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
@@ -797,7 +837,7 @@ void fft_z_symbol(const FftCtx<R>& f, double a, double b, const double* k0sum, d
   const cplx_t<R>* tw = (const cplx_t<R>*)f.pz.tw;
   switch (f.nz) {
 #define ICM_CASE(N, R1, R2) \
-  case N: k_zsym2<R, N, R1, R2><<<dim3(kxt, f.ny), kThreads, smem_z2<R, N>(), st>>>(f.spec, tw, f.ny, f.kx, f.kxp, sp); return;
+  case N: k_zsym2<R, N, R1, R2><<<dim3(kxt, f.ny), zsym2_threads<R, N, R1, R2>(), smem_z2<R, N>(), st>>>(f.spec, tw, f.ny, f.kx, f.kxp, sp); return;
     ICM_FFT_SIDES(ICM_CASE)
 #undef ICM_CASE
     default: break;
@@ -812,7 +852,12 @@ void fft_x_inverse(const FftCtx<R>& f, R* dst, R* dst2, int mode, cudaStream_t s
   const cplx_t<R>* tw = (const cplx_t<R>*)f.px.tw;
   switch (f.nx) {
 #define ICM_CASE(N, R1, R2) \
-  case N: k_xinv2<R, N, R1, R2><<<dim3(xblocks, 3), kThreads, smem_x2<R, N>(), st>>>(f.spec, dst, dst2, mode, tw, nrows, f.ncell, f.kxp); return;
+  case N:                                                                                                              \
+    if (mode == OUT_STORE)                                                                                             \
+      k_xinv2<R, N, R1, R2, OUT_STORE><<<dim3(xblocks, 3), kThreads, smem_x2<R, N>(), st>>>(f.spec, dst, dst2, tw, nrows, f.ncell, f.kxp); \
+    else                                                                                                               \
+      k_xinv2<R, N, R1, R2, OUT_ADD_AND_STORE2><<<dim3(xblocks, 3), kThreads, smem_x2<R, N>(), st>>>(f.spec, dst, dst2, tw, nrows, f.ncell, f.kxp); \
+    return;
     ICM_FFT_SIDES(ICM_CASE)
 #undef ICM_CASE
     default: break;

@@ -29,18 +29,45 @@ struct RhsSmem {
   R z[3][6][HY][HX];
 };
 
-// One plane of stress normals (with halo) into ring slot `slot`.
+// One plane of stress normals (with halo) into ring slot `slot`.  Each thread first
+// draws the normals of its own cell (no divergence), then the first HALO - NT threads
+// draw the halo cells, computing only what their neighbours read: x-1 needs Z_xx,
+// y-1 Z_yy, x+1 Z_xy and Z_xz, y+1 Z_xy and Z_yz; the corners nothing.
+constexpr int NHALO = 2 * HX + 2 * TY;   // ring of halo cells around the TX x TY tile
+
 template <typename R>
 __device__ __forceinline__ void gen_plane(RhsSmem<R>& sm, int slot, int i0, int j0, int k, const GridParams& g,
                                           uint32_t step, int tid) {
   const int kk = wrapi(k, g.nz);
-  for (int idx = tid; idx < HALO; idx += NT) {
-    const int hx = idx % HX, hy = idx / HX;
-    const int gi = wrapi(i0 - 1 + hx, g.nx);
-    const int gj = wrapi(j0 - 1 + hy, g.ny);
-    const uint32_t cell = (uint32_t)(gi + g.nx * (gj + g.ny * kk));
+  {
+    const int tx = tid % TX, ty = tid / TX;
+    const int gi = wrapi(i0 + tx, g.nx), gj = wrapi(j0 + ty, g.ny);
     R z[6];
-    cell_normals<R>(cell, step, g.key0, g.key1, z);
+    cell_normals<R>((uint32_t)(gi + g.nx * (gj + g.ny * kk)), step, g.key0, g.key1, z);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) sm.z[slot][c][ty + 1][tx + 1] = z[c];
+  }
+  for (int h = tid; h < NHALO; h += NT) {
+    int hx, hy;
+    if (h < HX) {                 // bottom row y = -1
+      hx = h;
+      hy = 0;
+    } else if (h < 2 * HX) {      // top row y = TY
+      hx = h - HX;
+      hy = HY - 1;
+    } else if (h < 2 * HX + TY) { // left column x = -1
+      hx = 0;
+      hy = 1 + (h - 2 * HX);
+    } else {                      // right column x = TX
+      hx = HX - 1;
+      hy = 1 + (h - 2 * HX - TY);
+    }
+    const bool xl = hx == 0, xr = hx == HX - 1, yl = hy == 0, yr = hy == HY - 1;
+    if ((xl || xr) && (yl || yr)) continue;
+    const int gi = wrapi(i0 - 1 + hx, g.nx), gj = wrapi(j0 - 1 + hy, g.ny);
+    R z[6];
+    cell_normals_masked<R>((uint32_t)(gi + g.nx * (gj + g.ny * kk)), step, g.key0, g.key1, z, xl || yl, xr || yr,
+                           xr || yr);
 #pragma unroll
     for (int c = 0; c < 6; ++c) sm.z[slot][c][hy][hx] = z[c];
   }
@@ -82,7 +109,7 @@ __device__ __forceinline__ void store_plane(RhsSmem<R>& sm, int slot, const R (&
 // generated while they are in flight, then the current plane is computed entirely
 // from shared memory.
 template <typename R, bool NOISE>
-__global__ void __launch_bounds__(NT) k_rhs(const R* __restrict__ v, R* __restrict__ adv, R* __restrict__ rhs,
+__global__ void __launch_bounds__(NT, 2) k_rhs(const R* __restrict__ v, R* __restrict__ adv, R* __restrict__ rhs,
                                             GridParams g, const long long* __restrict__ step_dev,
                                             const int* __restrict__ hist_dev) {
   extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -126,6 +126,9 @@ struct BlobParams {
   int kernel;
   int slip;        // 0 visc, 1 zero, 2 full
   double mtf;      // m~_f = 3 rho dV / 2
+  double inv_h;    // 1/h
+  double box[3];   // periodic box lengths N h
+  double inv_box[3];
 };
 
 struct BlobState {

@@ -1,0 +1,112 @@
+"""Batched replicas and the serving loop: every simulation gives the same result
+whether it runs alone or together with others (one graph launch advancing many),
+within the parity tolerance, and the server never holds more device memory than
+its budget."""
+import time
+
+import numpy as np
+import pytest
+
+import icm_workloads as wl
+
+from _gpu_helpers import TOL, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def icm():
+    from paper_1212_6427_gb300 import build
+    build.build_library()
+    import paper_1212_6427_gb300 as m
+    m.use_torch_allocator()
+    return m
+
+
+def _jobs(precision, count=5, seed0=40):
+    out = []
+    for r, (side, kernel, nb) in enumerate([(32, 4, 7), (48, 3, 12), (24, 4, 1), (32, 3, 20), (16, 4, 3)][:count]):
+        cfg = dict(grid=(side, side, side), h=1.0, rho=1.0, eta=1.0, kT=2e-3, dt=0.05, kernel=kernel,
+                   seed=seed0 + r, precision=precision, steps=4 + r, nblobs=nb, me_range=(-0.5, 2.0),
+                   force=(1e-3, 0.0, -2e-3), place_seed=seed0 + 100 + r, min_spacing=2.0)
+        out.append(wl._materialise(cfg))
+    return out
+
+
+def _alone(icm, j):
+    sim = icm.Simulation(j["grid"], j["h"], j["rho"], j["eta"], j["kT"], j["dt"], j["kernel"], j["seed"],
+                         j["precision"])
+    sim.add_blobs(j["q"], j["u"], j["me"])
+    sim.set_forces(j["force"])
+    sim.step(j["steps"])
+    r = sim.read()
+    sim.close()
+    return r
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_batch_matches_individual_runs(icm, precision):
+    jobs = _jobs(precision, 4)
+    sims = []
+    for j in jobs:
+        s = icm.Simulation(j["grid"], j["h"], j["rho"], j["eta"], j["kT"], j["dt"], j["kernel"], j["seed"], precision)
+        s.add_blobs(j["q"], j["u"], j["me"])
+        s.set_forces(j["force"])
+        sims.append(s)
+    b = icm.icm_batch_create()
+    icm.icm_batch_set(b, [s.handle for s in sims])
+    icm.icm_batch_step(b, 5)
+    icm.icm_batch_sync(b)
+    for j, s in zip(jobs, sims):
+        got = s.read()
+        assert got["step"] == 5
+        j5 = dict(j, steps=5)
+        want = _alone(icm, j5)
+        assert rel(got["vel"], want["vel"]) < TOL[precision]
+        assert rel(got["pos"], want["pos"]) < TOL[precision] * 1e-2
+    icm.icm_batch_destroy(b)
+    for s in sims:
+        s.close()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_server_results_same_alone_and_in_the_mix(icm, precision):
+    jobs = _jobs(precision)
+    est = [icm.icm_estimate_device_bytes(j["grid"], precision, len(j["q"])) for j in jobs]
+    budget = int(sum(sorted(est)[-2:]) * 1.05)           # about two jobs at a time
+    sv = icm.icm_server_create(budget, 8)
+    ids = []
+    peak = 0
+    pending = list(jobs)
+    done = 0
+    pumps = 0
+    while done < len(jobs):
+        if pending and pumps % 2 == 0:                     # staggered arrivals
+            j = pending.pop(0)
+            ids.append(icm.icm_server_submit(sv, j["grid"], j["h"], j["rho"], j["eta"], j["kT"], j["dt"],
+                                             j["kernel"], j["seed"], precision, 0, j["q"], j["u"], j["me"],
+                                             j["force"], j["steps"]))
+        a, w, f = icm.icm_server_pump(sv, 2)
+        peak = max(peak, icm.icm_server_bytes_in_use(sv))
+        done += f
+        pumps += 1
+        time.sleep(0.0002)                               # pumps do not wait for the GPU
+        assert pumps < 100000
+    assert peak <= budget
+    for jid, j in zip(ids, jobs):
+        r = icm.icm_server_result(sv, jid, len(j["q"]))
+        assert r["state"] == 2 and r["latency_s"] > 0
+        want = _alone(icm, j)
+        assert rel(r["vel"], want["vel"]) < TOL[precision]
+        assert rel(r["pos"], want["pos"]) < TOL[precision] * 1e-2
+        np.testing.assert_allclose(r["momentum"], want["momentum"], rtol=1e-9, atol=1e-12)
+    icm.icm_server_destroy(sv)
+
+
+def test_server_rejects_job_larger_than_budget(icm):
+    sv = icm.icm_server_create(1 << 20, 4)
+    with pytest.raises(icm.IcmError) as ei:
+        icm.icm_server_submit(sv, (64, 64, 64), 1.0, 1.0, 1.0, 0.0, 0.05, 4, 1, 32, 0, np.zeros((1, 3)), None,
+                              np.zeros(1), None, 3)
+    assert ei.value.status == icm.ICM_ENOMEM
+    icm.icm_server_destroy(sv)
