@@ -183,6 +183,11 @@ __device__ __forceinline__ void store3(double* a, long long b, const double v[3]
   a[3 * b + 2] = v[2];
 }
 
+// The per-component FP64 arithmetic of a blob runs on lanes 0-2 (one component each):
+// on GB300 every FP64 warp instruction is expensive, so three lanes doing one
+// component beat one lane doing three.
+__device__ __forceinline__ double pick3(const double v[3], int a) { return a == 0 ? v[0] : (a == 1 ? v[1] : v[2]); }
+
 #define ICM_WARP_SETUP                                                  \
   __shared__ WarpStencil<R, K> sten[kWarps];                            \
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;            \
@@ -199,7 +204,10 @@ __global__ void __launch_bounds__(32 * kWarps) k_predict(BlobParams p, BlobState
   load3(s.q, b, q);
   build_stencil<R, K>(S, q, p, false, lane);
   gather<R, K>(S, v, p, lane, w0);
-  for (int a = 0; a < 3; ++a) qh[a] = wrap_pos(fma(0.5 * p.dt, w0[a], q[a]), p.box[a], p.inv_box[a]);
+  // every lane needs q^{n+1/2} for the second stencil; lanes 0-2 compute one axis each
+  const int ax = lane < 3 ? lane : 0;
+  const double mine = wrap_pos(fma(0.5 * p.dt, pick3(w0, ax), pick3(q, ax)), p.box[ax], p.inv_box[ax]);
+  for (int a = 0; a < 3; ++a) qh[a] = __shfl_sync(0xffffffffu, mine, a);
   __syncwarp();
   build_stencil<R, K>(S, qh, p, false, lane);
   gather<R, K>(S, v, p, lane, w1);
@@ -219,23 +227,20 @@ __global__ void __launch_bounds__(32 * kWarps) k_dp(BlobParams p, BlobState s, c
   load3(s.qh, b, qh);
   build_stencil<R, K>(S, qh, p, false, lane);
   gather<R, K>(S, vt, p, lane, jvt);
-  if (lane == 0) {
-    double u[3], g[3], du[3], dp[3], cdp[3];
-    load3(s.u, b, u);
-    load3(s.g, b, g);
+  if (lane < 3) {
+    const int a = lane;
+    const long long i = 3 * b + a;
     const double me = s.me[b];
     const double visc = 0.5 * (p.eta / p.rho) * p.dt;
     const double coef = p.mtf / (p.rho * (p.mtf + me));
-    for (int a = 0; a < 3; ++a) {
-      du[a] = p.slip == 1 ? 0.0 : visc * g[a];
-      if (p.slip == 2) du[a] += s.w1[3 * b + a] - s.w0[3 * b + a];
-      dp[a] = me * (u[a] - jvt[a] - du[a]);
-      cdp[a] = coef * dp[a];
-    }
-    store3(s.jvt, b, jvt);
-    store3(s.du, b, du);
-    store3(s.dp, b, dp);
-    store3(s.cdp, b, cdp);
+    const double jv = pick3(jvt, a);
+    double du = p.slip == 1 ? 0.0 : visc * s.g[i];
+    if (p.slip == 2) du += s.w1[i] - s.w0[i];
+    const double dp = me * (s.u[i] - jv - du);
+    s.jvt[i] = jv;
+    s.du[i] = du;
+    s.dp[i] = dp;
+    s.cdp[i] = coef * dp;
   }
 }
 
@@ -255,19 +260,17 @@ __global__ void __launch_bounds__(32 * kWarps) k_inertial(BlobParams p, BlobStat
     load3(s.qh, b, qh);
     build_stencil<R, K>(S, qh, p, false, lane);
     gather<R, K>(S, dvt, p, lane, jd);
-    const double me = s.me[b];
-    double un[3];
-    for (int a = 0; a < 3; ++a) {
-      src[a] = s.dp[3 * b + a] - me * jd[a];
-      un[a] = s.jvt[3 * b + a] + jd[a] + s.du[3 * b + a];
-    }
-    if (lane == 0) {
-      store3(s.src, b, src);
-      store3(s.u, b, un);
+    if (lane < 3) {
+      const int a = lane;
+      const long long i = 3 * b + a;
+      const double jv = pick3(jd, a);
+      const double sr = s.dp[i] - s.me[b] * jv;
+      s.src[i] = sr;
+      s.u[i] = s.jvt[i] + jv + s.du[i];
+      src[a] = sr;
     }
   }
-  if (lane == 0)
-    for (int a = 0; a < 3; ++a) red[wid][a] = src[a];
+  if (lane < 3) red[wid][lane] = src[lane];
   __syncthreads();
   if (threadIdx.x < 3) {
     double t = 0.0;
@@ -283,7 +286,7 @@ template <typename R, int K>
 __global__ void __launch_bounds__(32 * kWarps) k_finish(BlobParams p, BlobState s, const R* __restrict__ vn,
                                                         const R* __restrict__ dv, int inertial) {
   ICM_WARP_SETUP
-  double q[3], qh[3], jv[3], g[3] = {0.0, 0.0, 0.0};
+  double qh[3], jv[3], g[3] = {0.0, 0.0, 0.0};
   load3(s.qh, b, qh);
   build_stencil<R, K>(S, qh, p, false, lane);
   gather<R, K>(S, vn, p, lane, jv);
@@ -292,24 +295,17 @@ __global__ void __launch_bounds__(32 * kWarps) k_finish(BlobParams p, BlobState 
     build_stencil<R, K>(S, qh, p, true, lane);
     gather_lap<R, K>(S, dv, p, lane, g);
   }
-  if (lane == 0) {
-    load3(s.q, b, q);
-    double qn[3], u[3];
-    if (inertial)
-      load3(s.u, b, u);
-    else
-      for (int a = 0; a < 3; ++a) u[a] = jv[a];
-    bool bad = false, cfl = false;
-    for (int a = 0; a < 3; ++a) {
-      qn[a] = wrap_pos(fma(0.5 * p.dt, jv[a] + s.w1[3 * b + a], q[a]), p.box[a], p.inv_box[a]);
-      bad |= !isfinite(qn[a]) || !isfinite(u[a]);
-      cfl |= fabs(u[a]) * p.dt > p.h;
-    }
-    store3(s.q, b, qn);
-    store3(s.u, b, u);
-    store3(s.g, b, g);
-    if (bad) atomicOr(s.err, DEV_ERR_NONFINITE);
-    if (cfl) atomicOr(s.err, DEV_ERR_CFL);
+  if (lane < 3) {
+    const int a = lane;
+    const long long i = 3 * b + a;
+    const double jva = pick3(jv, a);
+    const double u = inertial ? s.u[i] : jva;
+    const double qn = wrap_pos(fma(0.5 * p.dt, jva + s.w1[i], s.q[i]), p.box[a], p.inv_box[a]);
+    s.q[i] = qn;
+    s.u[i] = u;
+    s.g[i] = pick3(g, a);
+    if (!isfinite(qn) || !isfinite(u)) atomicOr(s.err, DEV_ERR_NONFINITE);
+    if (fabs(u) * p.dt > p.h) atomicOr(s.err, DEV_ERR_CFL);
   }
 }
 

@@ -411,17 +411,19 @@ constexpr int kXPad = 16;   // x pass: one padding slot every 16 positions (bank
 __host__ __device__ constexpr int xrow(int n) { return n + n / kXPad; }
 __device__ __forceinline__ int xaddr(int l, int p, int N) { return l * xrow(N) + p + p / kXPad; }
 
-// One thread per first-stage item (3 components x R2 x NL), so the loads of all three
-// components are in flight together.
+// The z pass holds all three components of its tile, so it takes 8 kx lines
+// (64-byte rows in FP32) to keep two blocks per SM; one thread per first-stage item
+// (3 components x R2 x 8), so the loads of all three components are in flight together.
+constexpr int kZLines = 8;
 template <typename R, int N, int R1, int R2>
-constexpr int zsym2_threads() { return 3 * R2 * seg_lines<R>() > 1024 ? 1024 : 3 * R2 * seg_lines<R>(); }
+constexpr int zsym2_threads() { return 3 * R2 * kZLines > 1024 ? 1024 : 3 * R2 * kZLines; }
 
 template <typename R, int N, int R1, int R2>
-__global__ void __launch_bounds__(zsym2_threads<R, N, R1, R2>()) k_zsym2(cplx_t<R>* __restrict__ spec,
+__global__ void __launch_bounds__(zsym2_threads<R, N, R1, R2>(), sizeof(R) == 4 ? 2 : 1) k_zsym2(cplx_t<R>* __restrict__ spec,
                                                                         const cplx_t<R>* __restrict__ gtw,
                                                                         int ny, int kx, int kxp, SymParams<R> sp) {
   using C = cplx_t<R>;
-  constexpr int NL = seg_lines<R>();
+  constexpr int NL = kZLines;
   constexpr int NT = zsym2_threads<R, N, R1, R2>();
   constexpr bool HOLD3 = sizeof(R) == 4 && R2 <= 12;   // 3 x R2 complex in registers
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -741,7 +743,7 @@ __global__ void __launch_bounds__(kThreads) k_xinv2(const cplx_t<R>* __restrict_
   }
 }
 
-template <typename R, int N> size_t smem_z2() { return 3 * (size_t)N * seg_lines<R>() * sizeof(cplx_t<R>) + N * sizeof(cplx_t<R>); }
+template <typename R, int N> size_t smem_z2() { return 3 * (size_t)N * kZLines * sizeof(cplx_t<R>) + N * sizeof(cplx_t<R>); }
 template <typename R, int N> size_t smem_y2() { return (size_t)N * seg_lines<R>() * sizeof(cplx_t<R>) + N * sizeof(cplx_t<R>); }
 template <typename R, int N> size_t smem_x2() { return (size_t)kXLines * xrow(N) * sizeof(cplx_t<R>) + N * sizeof(cplx_t<R>); }
 
@@ -835,9 +837,10 @@ void fft_z_symbol(const FftCtx<R>& f, double a, double b, const double* k0sum, d
   sp.k0sum = k0sum;
   sp.k0mul = k0scale / (double)f.ncell;
   const cplx_t<R>* tw = (const cplx_t<R>*)f.pz.tw;
+  const int kxz = (f.kx + kZLines - 1) / kZLines;
   switch (f.nz) {
 #define ICM_CASE(N, R1, R2) \
-  case N: k_zsym2<R, N, R1, R2><<<dim3(kxt, f.ny), zsym2_threads<R, N, R1, R2>(), smem_z2<R, N>(), st>>>(f.spec, tw, f.ny, f.kx, f.kxp, sp); return;
+  case N: k_zsym2<R, N, R1, R2><<<dim3(kxz, f.ny), zsym2_threads<R, N, R1, R2>(), smem_z2<R, N>(), st>>>(f.spec, tw, f.ny, f.kx, f.kxp, sp); return;
     ICM_FFT_SIDES(ICM_CASE)
 #undef ICM_CASE
     default: break;
