@@ -96,6 +96,8 @@ struct icm_sim {
   AxisPlan px, py, pz;
   void *dx = nullptr, *ddx = nullptr, *dy = nullptr, *ddy = nullptr, *dz = nullptr, *ddz = nullptr;
   int kx = 0, kxp = 0;
+  alignas(64) unsigned char zmap[128];   // TMA descriptor of spec for the z pass
+  bool has_zmap = false;
   // blobs
   long long nb = 0, cap = 0;
   double* blob = nullptr;
@@ -175,6 +177,8 @@ FftCtx<R> fft_ctx(const icm_sim* s) {
   f.dy = (const cplx_t<R>*)s->dy; f.ddy = (const R*)s->ddy;
   f.dz = (const cplx_t<R>*)s->dz; f.ddz = (const R*)s->ddz;
   f.spec = (cplx_t<R>*)s->spec;
+  f.zmap = s->has_zmap ? s->zmap : nullptr;
+  f.err = s->err_dev;
   return f;
 }
 
@@ -512,6 +516,7 @@ icm_status check_device_errors(icm_sim* s) {
   if (err) {
     ICM_CK(cudaMemsetAsync(s->err_dev, 0, sizeof(int), s->stream));
     ICM_CK(cudaStreamSynchronize(s->stream));
+    if (err & DEV_ERR_TIMEOUT) return fail(ICM_ETIMEOUT, "a bounded device-side wait gave up");
     if (err & DEV_ERR_NONFINITE) return fail(ICM_ENONFINITE, "a non-finite blob position or velocity appeared");
     return fail(ICM_ECFL, "a blob moved more than one cell in a step (|u| dt / h > 1)");
   }
@@ -597,6 +602,7 @@ icm_status icm_create(const int32_t grid[3], double h, double rho, double eta, d
     icm_destroy(s);
     return fail(st, "%s", msg.c_str());
   }
+  s->has_zmap = make_zmap(s->zmap, s->spec, s->prec, s->kx, s->kxp, s->ny, s->nz);
   cudaMemsetAsync(s->v, 0, fbytes, s->stream);
   cudaMemsetAsync(s->adv, 0, fbytes, s->stream);
   cudaMemsetAsync(s->work, 0, fbytes, s->stream);

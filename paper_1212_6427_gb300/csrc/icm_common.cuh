@@ -150,6 +150,6 @@ template <typename R> struct Peskin<R, 4> {
 };
 
 // Status bits the device raises (read back by icm_sync).
-enum : int { DEV_ERR_CFL = 1, DEV_ERR_NONFINITE = 2 };
+enum : int { DEV_ERR_CFL = 1, DEV_ERR_NONFINITE = 2, DEV_ERR_TIMEOUT = 4 };
 
 }  // namespace icm

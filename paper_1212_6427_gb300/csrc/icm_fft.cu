@@ -19,6 +19,8 @@
 // operands read from and written back to the same shared-memory positions.
 #include <cstdio>
 
+#include <cuda.h>
+
 #include "icm_internal.h"
 #include "icm_fft_reg.cuh"
 
@@ -418,30 +420,26 @@ constexpr int kZLines = 8;
 template <typename R, int N, int R1, int R2>
 constexpr int zsym2_threads() { return 3 * R2 * kZLines > 1024 ? 1024 : 3 * R2 * kZLines; }
 
-template <typename R, int N, int R1, int R2>
-__global__ void __launch_bounds__(zsym2_threads<R, N, R1, R2>(), sizeof(R) == 4 ? 2 : 1) k_zsym2(cplx_t<R>* __restrict__ spec,
-                                                                        const cplx_t<R>* __restrict__ gtw,
-                                                                        int ny, int kx, int kxp, SymParams<R> sp) {
+// The work of one z tile (3 components x N z x NL kx lines, kx0..kx0+NL-1, storage y
+// position py): forward z FFT, symbol, inverse z FFT.  The first stage reads the tile
+// from global memory (FROM_SMEM false) or from `buf`, where a TMA copy has put it.
+template <typename R, int N, int R1, int R2, bool FROM_SMEM>
+__device__ __forceinline__ void zsym_tile(cplx_t<R>* __restrict__ buf, const cplx_t<R>* __restrict__ tw,
+                                          cplx_t<R>* __restrict__ base, size_t cs, size_t zs, int kx0, int py, int kx,
+                                          const SymParams<R>& sp, int tid) {
   using C = cplx_t<R>;
   constexpr int NL = kZLines;
   constexpr int NT = zsym2_threads<R, N, R1, R2>();
   constexpr bool HOLD3 = sizeof(R) == 4 && R2 <= 12;   // 3 x R2 complex in registers
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);   // [3][N][NL]
-  C* tw = buf + 3 * N * NL;                  // [N] first-stage twiddles, [k2][n1]
-  const int tid = threadIdx.x;
-  load_stage_twiddles<R, R1, R2>(tw, gtw, tid, NT);
-  const int kx0 = blockIdx.x * NL, py = blockIdx.y;
-  const size_t zs = (size_t)ny * kxp, cs = (size_t)N * zs;
-  C* base = spec + (size_t)py * kxp + kx0;
   const C zero = mk(R(0), R(0));
-  __syncthreads();
   for (int it = tid; it < 3 * R2 * NL; it += NT) {
     const int line = it % NL, rest = it / NL, n1 = rest % R2, c = rest / R2;
     const bool ok = kx0 + line < kx;
     C a[R1];
 #pragma unroll
-    for (int r = 0; r < R1; ++r) a[r] = ok ? base[c * cs + (size_t)(n1 + R2 * r) * zs + line] : zero;
+    for (int r = 0; r < R1; ++r)
+      a[r] = FROM_SMEM ? buf[(c * N + n1 + R2 * r) * NL + line]
+                       : (ok ? base[c * cs + (size_t)(n1 + R2 * r) * zs + line] : zero);
     stage_a_fwd<R, R1, R2>(a, tw + n1);
 #pragma unroll
     for (int k2 = 0; k2 < R1; ++k2) buf[(c * N + n1 + R2 * k2) * NL + line] = a[k2];
@@ -516,6 +514,128 @@ __global__ void __launch_bounds__(zsym2_threads<R, N, R1, R2>(), sizeof(R) == 4 
     stage_a_inv<R, R1, R2>(a, tw + n1);
 #pragma unroll
     for (int n2 = 0; n2 < R1; ++n2) base[c * cs + (size_t)(n1 + R2 * n2) * zs + line] = a[n2];
+  }
+}
+
+template <typename R, int N, int R1, int R2>
+__global__ void __launch_bounds__(zsym2_threads<R, N, R1, R2>(), sizeof(R) == 4 ? 2 : 1)
+    k_zsym2(cplx_t<R>* __restrict__ spec, const cplx_t<R>* __restrict__ gtw, int ny, int kx, int kxp, SymParams<R> sp) {
+  using C = cplx_t<R>;
+  constexpr int NL = kZLines;
+  constexpr int NT = zsym2_threads<R, N, R1, R2>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);   // [3][N][NL]
+  C* tw = buf + 3 * N * NL;                  // [N] first-stage twiddles, [k2][n1]
+  const int tid = threadIdx.x;
+  load_stage_twiddles<R, R1, R2>(tw, gtw, tid, NT);
+  const int kx0 = blockIdx.x * NL, py = blockIdx.y;
+  const size_t zs = (size_t)ny * kxp, cs = (size_t)N * zs;
+  __syncthreads();
+  zsym_tile<R, N, R1, R2, false>(buf, tw, spec + (size_t)py * kxp + kx0, cs, zs, kx0, py, kx, sp, tid);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent z pass fed by the tensor memory accelerator: a block loops over tiles,
+// and while it transforms one tile (three 16-float x N boxes, one per component)
+// the copy of its next tile lands in the other shared-memory buffer.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for phase `parity` of the barrier, giving up after half a second of global time.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > 500000000ull) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+      "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <typename R, int N, int R1, int R2>
+__global__ void __launch_bounds__(zsym2_threads<R, N, R1, R2>(), sizeof(R) == 4 ? 2 : 1)
+    k_zsym_tma(const __grid_constant__ CUtensorMap zmap, cplx_t<R>* __restrict__ spec,
+               const cplx_t<R>* __restrict__ gtw, int ny, int kx, int kxp, int ntx, SymParams<R> sp, int* err) {
+  using C = cplx_t<R>;
+  constexpr int NL = kZLines;
+  constexpr int NT = zsym2_threads<R, N, R1, R2>();
+  constexpr int TILE = 3 * N * NL;
+  constexpr uint32_t TILE_BYTES = TILE * sizeof(C);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // tensor copies land on 128-byte aligned shared addresses
+  unsigned char* aligned = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  C* bufs = reinterpret_cast<C*>(aligned);             // [2 stages][3][N][NL]
+  C* tw = bufs + 2 * TILE;                             // [N]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(tw + N);  // [2]
+  __shared__ int s_ok;
+  const int tid = threadIdx.x;
+  load_stage_twiddles<R, R1, R2>(tw, gtw, tid, NT);
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int ntiles = ntx * ny;
+  const size_t zs = (size_t)ny * kxp, cs = (size_t)N * zs;
+  auto issue = [&](int t, int st) {
+    const int kx0 = (t % ntx) * NL, py = t / ntx;
+    // order this block's earlier generic-proxy writes of the buffer before the copy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&mbar[st], TILE_BYTES);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) tma_load_4d(bufs + st * TILE + c * N * NL, &zmap, 2 * kx0, py, 0, c, &mbar[st]);
+  };
+  int t = blockIdx.x;
+  if (tid == 0 && t < ntiles) issue(t, 0);
+  int i = 0;
+  bool pending_other = false;
+  for (; t < ntiles; ++i, t += gridDim.x) {
+    const int st = i & 1;
+    if (tid == 0) {
+      pending_other = t + (int)gridDim.x < ntiles;
+      if (pending_other) issue(t + gridDim.x, st ^ 1);
+      s_ok = mbar_wait_bounded(&mbar[st], (i >> 1) & 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    const int kx0 = (t % ntx) * NL, py = t / ntx;
+    zsym_tile<R, N, R1, R2, true>(bufs + st * TILE, tw, spec + (size_t)py * kxp + kx0, cs, zs, kx0, py, kx, sp, tid);
+    __syncthreads();
+  }
+  if (tid == 0 && !s_ok && t < ntiles) {
+    atomicOr(err, DEV_ERR_TIMEOUT);
+    // the copy of the next tile may still be in flight: wait for it (bounded) before leaving
+    if (pending_other) mbar_wait_bounded(&mbar[(i & 1) ^ 1], ((i + 1) >> 1) & 1);
   }
 }
 
@@ -743,6 +863,7 @@ __global__ void __launch_bounds__(kThreads) k_xinv2(const cplx_t<R>* __restrict_
   }
 }
 
+template <typename R, int N> size_t smem_ztma() { return 2 * 3 * (size_t)N * kZLines * sizeof(cplx_t<R>) + N * sizeof(cplx_t<R>) + 16 + 128; }
 template <typename R, int N> size_t smem_z2() { return 3 * (size_t)N * kZLines * sizeof(cplx_t<R>) + N * sizeof(cplx_t<R>); }
 template <typename R, int N> size_t smem_y2() { return (size_t)N * seg_lines<R>() * sizeof(cplx_t<R>) + N * sizeof(cplx_t<R>); }
 template <typename R, int N> size_t smem_x2() { return (size_t)kXLines * xrow(N) * sizeof(cplx_t<R>) + N * sizeof(cplx_t<R>); }
@@ -768,6 +889,8 @@ void set_smem_attributes() {
   const int big = 227 * 1024;
 #define ICM_ATTR(N, R1, R2)                                                                               \
   cudaFuncSetAttribute(k_zsym2<R, N, R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);         \
+  if (N <= 256) /* exactly its need: the kernel also holds static shared memory */                          \
+    cudaFuncSetAttribute(k_zsym_tma<R, N, R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ztma<R, N>()); \
   cudaFuncSetAttribute(k_ypass2<R, N, R1, R2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big); \
   cudaFuncSetAttribute(k_ypass2<R, N, R1, R2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);  \
   cudaFuncSetAttribute(k_xfwd2<R, N, R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);         \
@@ -838,6 +961,31 @@ void fft_z_symbol(const FftCtx<R>& f, double a, double b, const double* k0sum, d
   sp.k0mul = k0scale / (double)f.ncell;
   const cplx_t<R>* tw = (const cplx_t<R>*)f.pz.tw;
   const int kxz = (f.kx + kZLines - 1) / kZLines;
+  if (f.zmap != nullptr && f.nz <= 256) {
+    static int nsm = 0;
+    if (nsm == 0) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      if (nsm <= 0) nsm = 1;
+    }
+    const int ntiles = kxz * f.ny;
+    const int grid = ntiles < 2 * nsm ? ntiles : 2 * nsm;
+    const CUtensorMap& map = *reinterpret_cast<const CUtensorMap*>(f.zmap);
+    switch (f.nz) {
+#define ICM_CASE(N, R1, R2)                                                                                            \
+  case N:                                                                                                              \
+    if (N <= 256) {                                                                                                    \
+      k_zsym_tma<R, N, R1, R2><<<grid, zsym2_threads<R, N, R1, R2>(), smem_ztma<R, N>(), st>>>(map, f.spec, tw, f.ny, \
+                                                                                           f.kx, f.kxp, kxz, sp, f.err); \
+      return;                                                                                                          \
+    }                                                                                                                  \
+    break;
+      ICM_FFT_SIDES(ICM_CASE)
+#undef ICM_CASE
+      default: break;
+    }
+  }
   switch (f.nz) {
 #define ICM_CASE(N, R1, R2) \
   case N: k_zsym2<R, N, R1, R2><<<dim3(kxz, f.ny), zsym2_threads<R, N, R1, R2>(), smem_z2<R, N>(), st>>>(f.spec, tw, f.ny, f.kx, f.kxp, sp); return;
@@ -877,6 +1025,41 @@ void spectral_solve(const FftCtx<R>& f, const R* src, R* dst, R* dst2, int mode,
   fft_z_symbol<R>(f, a, b, k0sum, k0scale, st);
   fft_y<R>(f, true, st);
   fft_x_inverse<R>(f, dst, dst2, mode, st);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The spectrum as a 4-D tensor (floats along kx, y, z, component) and the box one z
+// tile of one component occupies: 2 kZLines floats x 1 x nz x 1.  Wave numbers past
+// kx read as zeros.
+bool make_zmap(void* map, const void* spec, int precision, int kx, int kxp, int ny, int nz) {
+  int r1 = 0, r2 = 0;
+  if (nz > 256 || !fft_split(nz, r1, r2)) return false;
+  static EncodeTiledFn fn = nullptr;
+  if (fn == nullptr) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || p == nullptr) {
+      cudaGetLastError();
+      return false;
+    }
+    fn = (EncodeTiledFn)p;
+  }
+  const cuuint64_t es = precision == 32 ? 4 : 8;
+  const cuuint64_t dims[4] = {(cuuint64_t)(2 * kx), (cuuint64_t)ny, (cuuint64_t)nz, 3};
+  const cuuint64_t strides[3] = {2 * (cuuint64_t)kxp * es, 2 * (cuuint64_t)kxp * es * ny,
+                                 2 * (cuuint64_t)kxp * es * ny * nz};
+  const cuuint32_t box[4] = {2 * kZLines, 1, (cuuint32_t)nz, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = fn(reinterpret_cast<CUtensorMap*>(map),
+                        precision == 32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
+                        const_cast<void*>(spec), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
 void fft_prepare() {

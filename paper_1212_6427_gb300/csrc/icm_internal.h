@@ -59,7 +59,13 @@ struct FftCtx {
   const cplx_t<R>* dy; const R* ddy;
   const cplx_t<R>* dz; const R* ddz;
   cplx_t<R>* spec;   // 3 * nz * ny * kxp complex scratch
+  const void* zmap;  // host copy of the TMA descriptor of spec for the z pass (or null)
+  int* err;          // device error bits (bounded waits report here)
 };
+
+// Fill `map` (a 128-byte CUtensorMap) with the descriptor the TMA z pass uses for a
+// spectrum buffer; returns false if TMA is unavailable for this shape.
+bool make_zmap(void* map, const void* spec, int precision, int kx, int kxp, int ny, int nz);
 
 enum OutMode : int { OUT_STORE = 0, OUT_ADD_AND_STORE2 = 1 };
 
