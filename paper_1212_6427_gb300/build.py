@@ -13,7 +13,11 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libicm.so")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
-SOURCES = ["icm_api.cu", "icm_fft.cu", "icm_grid.cu", "icm_blob.cu", "icm_static.cu"]
+# (source, object name, extra flags): the FFT file is compiled as six shards in
+# parallel (x forward / y-z / x inverse passes, FP32 / FP64), the largest unit otherwise.
+SOURCES = [("icm_api.cu", "icm_api", ()), ("icm_grid.cu", "icm_grid", ()), ("icm_blob.cu", "icm_blob", ()),
+           ("icm_static.cu", "icm_static", ())] + [
+    ("icm_fft.cu", "icm_fft_%d" % k, ("-DICM_FFT_SHARD=%d" % k,)) for k in range(6)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
 
@@ -48,9 +52,10 @@ def build_library(force=False, verbose=False, extra_flags=()):
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, *extra_flags, "-I", INCLUDE, "-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(unit):
+        src, name, defs = unit
+        obj = os.path.join(BUILD, name + ".o")
+        cmd = [nvcc, *ARCH, *FLAGS, *defs, *extra_flags, "-I", INCLUDE, "-c", os.path.join(CSRC, src), "-o", obj]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, " ".join(cmd), res.stderr[-6000:]))

@@ -105,6 +105,14 @@ struct icm_sim {
          *w1 = nullptr, *jvt = nullptr, *du = nullptr, *dp = nullptr, *cdp = nullptr, *src = nullptr;
   std::vector<double> me_host, f_host;
   bool any_me = false, any_force = false;
+  // row-block bins of the blob work fused into the x passes (register FFT sides)
+  bool fused = false;
+  int nrowblk = 0;
+  int* bin_idx = nullptr;     // count [nrowblk], start [nrowblk + 1], cursor [nrowblk]
+  void* bin_blob = nullptr;   // list [kBinsPerBlob cap] ints, geometry [cap], accumulators [12 cap]
+  int* bin_list = nullptr;
+  void* geo = nullptr;
+  double* acc = nullptr;
   // scalars
   double* scal = nullptr;
   long long* step_dev = nullptr;
@@ -121,6 +129,13 @@ struct icm_sim {
 };
 
 namespace {
+
+// Per blob slot: the bin list (kBinsPerBlob ints), the stencil record and 4 (n,3)
+// FP64 accumulators.
+constexpr size_t kGeoBytes = kStencilBytes;
+constexpr int kAccPerBlob = 12;
+size_t bin_list_bytes(long long cap) { return ((size_t)kBinsPerBlob * 4 * cap + 255) / 256 * 256; }
+size_t bin_blob_bytes(long long cap) { return bin_list_bytes(cap) + (kGeoBytes + 8 * kAccPerBlob) * cap; }
 
 void* dalloc(icm_sim* s, size_t bytes) {
   void* p = nullptr;
@@ -377,6 +392,73 @@ void enqueue_step(icm_sim* s, Prof* prof) {
   ICM_STAGE("scalars", 0, scalars_before_step(s->scal, s->dt, s->rho, dvf, st));
   // step 1: midpoint predictor (Eq. particle_pred)
   ICM_STAGE("predict", 2 * gath + nb * 72, blob_predict<R>(bp, bs, v, st));
+  if (s->fused && s->nb > 0) {
+    // The blob work of steps 2-9 runs inside the x passes of the three solves: the
+    // spreads in the forward pass of the solve they feed, the interpolations in the
+    // inverse pass of the solve whose output they read (Sec. III.C).
+    RowBins bins;
+    bins.count = s->bin_idx;
+    bins.start = s->bin_idx + s->nrowblk;
+    bins.cursor = s->bin_idx + 2 * s->nrowblk + 1;
+    bins.list = s->bin_list;
+    bins.geo = s->geo;
+    bins.acc = s->acc;
+    bins.nacc = kAccPerBlob;
+    bins.nblocks = s->nrowblk;
+    bins.capacity = (long long)kBinsPerBlob * s->cap;
+    double* acc1 = s->acc;                 // J v~
+    double* acc2 = s->acc + 3 * s->nb;     // J dv~
+    double* acc3 = s->acc + 6 * s->nb;     // J dv
+    double* acc3l = s->acc + 9 * s->nb;    // J L dv (without 1/h^2)
+    const double geob = (double)(12 * sizeof(int) + 36 * sizeof(R));   // stencil record per blob
+    const double blobio = nb * (geob + 24.0);
+    RowBlobs rb;
+    rb.start = bins.start;
+    rb.list = s->bin_list;
+    rb.geo = s->geo;
+    rb.p = bp;
+    rb.vec = nullptr;
+    rb.acc = nullptr;
+    rb.acc_lap = nullptr;
+    ICM_STAGE("bins", nb * (24.0 + 2 * geob + 8.0 * kAccPerBlob), build_row_bins<R>(bp, s->nb, s->qh, bins, st));
+    // step 2: unperturbed fluid solve (Eq. provisional_step-1), forces spread in x_fwd
+    ICM_STAGE("rhs", 4 * F, explicit_rhs<R>(gp, v, adv, work, s->step_dev, s->hist_dev, st));
+    auto passes = [&](const char* tag, const R* src, const double* vec, double a, double b, const double* k0,
+                      R* dst, int mode, double* acc, double* acc_lap) {
+      std::string t(tag);
+      RowBlobs r = rb;
+      r.vec = vec;
+      r.acc = acc;
+      r.acc_lap = acc_lap;
+      if (vec)
+        ICM_STAGE((t + ".x_fwd").c_str(), (src ? F : 0.0) + S + blobio, fft_x_forward_blobs<R>(fc, src, r, st));
+      else
+        ICM_STAGE((t + ".x_fwd").c_str(), F + S, fft_x_forward<R>(fc, src, st));
+      ICM_STAGE((t + ".y_fwd").c_str(), 2 * S, fft_y<R>(fc, false, st));
+      ICM_STAGE((t + ".z_sym").c_str(), 2 * S, fft_z_symbol<R>(fc, a, b, k0, k0 ? k0scale : 0.0, st));
+      ICM_STAGE((t + ".y_inv").c_str(), 2 * S, fft_y<R>(fc, true, st));
+      const double out = mode == OUT_STORE ? F : (mode == OUT_ADD ? 2 * F : 0.0);
+      ICM_STAGE((t + ".x_inv").c_str(), S + out + blobio, fft_x_inverse_blobs<R>(fc, dst, mode, r, st));
+    };
+    passes("rt1", work, s->any_force ? s->f : nullptr, s->rho / s->dt, 0.5 * s->eta, s->scal + SC_K0, v, OUT_STORE,
+           acc1, nullptr);
+    if (s->any_me) {
+      // step 4: slip correction and momentum change (Eq. delta_u_nph_visc)
+      ICM_STAGE("dp", nb * 264, blob_dp_from(bp, bs, acc1, st));
+      // step 5: dv~ = m~_f / (rho (m~_f + m_e)) P S dp; only J dv~ is kept
+      passes("rt2", nullptr, s->cdp, 1.0, 0.0, nullptr, v, OUT_NONE, acc2, nullptr);
+      // steps 6 and 8 (blob side): source dp - m_e J dv~, u^{n+1}
+      ICM_STAGE("inertial", nb * 168, blob_inertial_from(bp, bs, acc2, st));
+      // step 6: (rho - dt/2 eta L) dv + dt grad dpi = S (dp - m_e J dv~); step 7: v = v~ + dv
+      passes("rt3", nullptr, s->src, s->rho, 0.5 * s->dt * s->eta, s->scal + SC_SUMSRC, v, OUT_ADD, acc3, acc3l);
+      // step 9 and the lagged slip term: J v^{n+1} = J v~ + J dv
+      ICM_STAGE("finish", nb * 216, blob_finish_from(bp, bs, s->jvt, acc3, acc3l, true, st));
+    } else {
+      ICM_STAGE("finish", nb * 144, blob_finish_from(bp, bs, nullptr, acc1, nullptr, false, st));
+    }
+    ICM_STAGE("scalars", 0, scalars_after_step(s->scal, s->dt, s->rho, dvf, s->any_me, s->step_dev, s->hist_dev, st));
+    return;
+  }
   // step 2: unperturbed fluid solve (Eq. provisional_step-1)
   ICM_STAGE("rhs", 4 * F, explicit_rhs<R>(gp, v, adv, work, s->step_dev, s->hist_dev, st));
   if (s->any_force) ICM_STAGE("spread", 2 * gath + nb * 48, blob_spread<R>(bp, s->nb, s->qh, s->f, work, st));
@@ -440,9 +522,25 @@ icm_status grow_blobs(icm_sim* s, long long need) {
       ICM_CK(cudaMemcpyAsync(arrs[i], old[i], sizeof(double) * 3 * s->nb, cudaMemcpyDeviceToDevice, s->stream));
     ICM_CK(cudaMemcpyAsync(me, s->me, sizeof(double) * s->nb, cudaMemcpyDeviceToDevice, s->stream));
   }
+  void* nbin = nullptr;
+  if (s->fused) {
+    nbin = dalloc(s, bin_blob_bytes(cap));
+    if (!nbin) {
+      ICM_CK(cudaStreamSynchronize(s->stream));
+      dfree(s, nbuf);
+      return fail(ICM_ENOMEM, "device allocation of the bins of %lld blob slots failed", cap);
+    }
+  }
   ICM_CK(cudaStreamSynchronize(s->stream));
   if (s->blob) dfree(s, s->blob);
   s->blob = nbuf;
+  if (s->fused) {
+    if (s->bin_blob) dfree(s, s->bin_blob);
+    s->bin_blob = nbin;
+    s->bin_list = (int*)nbin;
+    s->geo = (unsigned char*)nbin + bin_list_bytes(cap);
+    s->acc = (double*)((unsigned char*)s->geo + kGeoBytes * cap);
+  }
   s->cap = cap;
   s->q = arrs[0]; s->qh = arrs[1]; s->u = arrs[2]; s->f = arrs[3]; s->g = arrs[4]; s->w0 = arrs[5];
   s->w1 = arrs[6]; s->jvt = arrs[7]; s->du = arrs[8]; s->dp = arrs[9]; s->cdp = arrs[10]; s->src = arrs[11];
@@ -603,6 +701,16 @@ icm_status icm_create(const int32_t grid[3], double h, double rho, double eta, d
     return fail(st, "%s", msg.c_str());
   }
   s->has_zmap = make_zmap(s->zmap, s->spec, s->prec, s->kx, s->kxp, s->ny, s->nz);
+  s->fused = fft_has_blob_passes(s->nx);
+  if (s->fused) {
+    s->nrowblk = (int)((s->ny * (long long)s->nz + 31) / 32);
+    s->bin_idx = (int*)dalloc(s, sizeof(int) * (3 * (size_t)s->nrowblk + 1));
+    if (!s->bin_idx) {
+      icm_destroy(s);
+      return fail(ICM_ENOMEM, "device allocation of the row-block bins failed");
+    }
+    cudaMemsetAsync(s->bin_idx, 0, sizeof(int) * (3 * (size_t)s->nrowblk + 1), s->stream);
+  }
   cudaMemsetAsync(s->v, 0, fbytes, s->stream);
   cudaMemsetAsync(s->adv, 0, fbytes, s->stream);
   cudaMemsetAsync(s->work, 0, fbytes, s->stream);
@@ -1073,8 +1181,9 @@ int64_t icm_estimate_device_bytes(const int32_t grid[3], int32_t precision, int6
   const int64_t fields = 3 * (3 * ncell * rs);
   const int64_t spec = 3 * (int64_t)grid[2] * grid[1] * kxp * 2 * rs;
   const int64_t tables = 3 * (int64_t)kMaxSide * (3 * 2 * rs + 4) + 16 * 256;
-  const int64_t blobs = nblobs > 0 ? 37 * cap * 8 : 0;
-  return fields + spec + tables + blobs + 8 * 3 * 1024 + 4096;
+  const int64_t blobs = nblobs > 0 ? 37 * cap * 8 + (int64_t)bin_blob_bytes(cap) : 0;
+  const int64_t bins = 4 * (3 * ((int64_t)grid[1] * grid[2] / 32 + 1) + 1);
+  return fields + spec + tables + blobs + bins + 8 * 3 * 1024 + 4096;
 }
 
 icm_status icm_batch_create(void* cuda_stream, icm_batch** out) {

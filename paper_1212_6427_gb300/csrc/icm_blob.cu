@@ -9,6 +9,7 @@
 // Blob state (positions, velocities, masses, lagged slip terms) is FP64 in both
 // precision modes; only the grid values are R.
 #include "icm_internal.h"
+#include "icm_rows.cuh"
 
 namespace icm {
 namespace {
@@ -344,7 +345,143 @@ __global__ void __launch_bounds__(32 * kWarps) k_interp(BlobParams p, long long 
 
 inline unsigned nblocks(long long nb) { return (unsigned)((nb + kWarps - 1) / kWarps); }
 
+// ---------------------------------------------------------------------------
+// Row-block bins (count, scan, fill) and the elementwise updates of the fused step
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_bin_count(BlobParams p, long long nb, const double* __restrict__ q, RowBins bins) {
+  const long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  const double qb[3] = {q[3 * b], q[3 * b + 1], q[3 * b + 2]};
+  BlobStencil<R> rec;
+  const BlobSpan sp = make_stencil<R>(&rec, qb, p);
+  reinterpret_cast<BlobStencil<R>*>(bins.geo)[b] = rec;
+  for (int k = 0; k < bins.nacc; ++k) bins.acc[k * nb + b] = 0.0;
+  for_each_row_block(sp, p, [&](int blk) { atomicAdd(&bins.count[blk], 1); });
+}
+
+// Exclusive scan of the counts (one block); resets the counts for the next build.
+__global__ void __launch_bounds__(1024) k_bin_scan(RowBins bins) {
+  __shared__ int part[1024];
+  const int n = bins.nblocks, t = threadIdx.x;
+  const int per = (n + 1023) / 1024;
+  const int lo = min(t * per, n), hi = min(lo + per, n);
+  int sum = 0;
+  for (int i = lo; i < hi; ++i) sum += bins.count[i];
+  part[t] = sum;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const int v = t >= off ? part[t - off] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int run = part[t] - sum;
+  for (int i = lo; i < hi; ++i) {
+    const int c = bins.count[i];
+    bins.start[i] = run;
+    bins.cursor[i] = run;
+    bins.count[i] = 0;
+    run += c;
+  }
+  if (t == 1023) bins.start[n] = part[1023];
+}
+
+template <typename R>
+__global__ void k_bin_fill(BlobParams p, long long nb, const double* __restrict__ q, RowBins bins) {
+  const long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  const double qb[3] = {q[3 * b], q[3 * b + 1], q[3 * b + 2]};
+  const BlobSpan sp = make_stencil<R>(nullptr, qb, p);
+  for_each_row_block(sp, p, [&](int blk) {
+    const int pos = atomicAdd(&bins.cursor[blk], 1);
+    if (pos < bins.capacity) bins.list[pos] = (int)b;
+  });
+}
+
+// Step 4 from the gathered J v~: slip correction, momentum change, its weighted copy.
+__global__ void k_dp_from(BlobParams p, BlobState s, const double* __restrict__ jvt) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= 3 * s.nb) return;
+  const long long b = i / 3;
+  const double me = s.me[b];
+  const double visc = 0.5 * (p.eta / p.rho) * p.dt;
+  const double coef = p.mtf / (p.rho * (p.mtf + me));
+  const double jv = jvt[i];
+  double du = p.slip == 1 ? 0.0 : visc * s.g[i];
+  if (p.slip == 2) du += s.w1[i] - s.w0[i];
+  const double dp = me * (s.u[i] - jv - du);
+  s.jvt[i] = jv;
+  s.du[i] = du;
+  s.dp[i] = dp;
+  s.cdp[i] = coef * dp;
+}
+
+// Steps 6-8 from the gathered J dv~: source of the viscous correction, u^{n+1}, and
+// the grid sum of the source for the momentum bookkeeping.
+__global__ void __launch_bounds__(256) k_inertial_from(BlobParams p, BlobState s, const double* __restrict__ jdvt) {
+  __shared__ double red[3][256];
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int a = (int)(i % 3);
+  double sr = 0.0;
+  if (i < 3 * s.nb) {
+    const long long b = i / 3;
+    const double jd = jdvt[i];
+    sr = s.dp[i] - s.me[b] * jd;
+    s.src[i] = sr;
+    s.u[i] = s.jvt[i] + jd + s.du[i];
+  }
+  for (int c = 0; c < 3; ++c) red[c][threadIdx.x] = c == a ? sr : 0.0;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) atomicAdd(&s.scal[SC_SUMSRC + threadIdx.x], red[threadIdx.x][0]);
+}
+
+// Step 9 from the gathered J v^{n+1} (= base + add) and J L dv: positions,
+// velocities, the lagged slip term, checks.
+__global__ void k_finish_from(BlobParams p, BlobState s, const double* __restrict__ base,
+                              const double* __restrict__ add, const double* __restrict__ g, int inertial) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= 3 * s.nb) return;
+  const int a = (int)(i % 3);
+  const double jv = base ? base[i] + add[i] : add[i];
+  const double u = inertial ? s.u[i] : jv;
+  const double qn = wrap_pos(fma(0.5 * p.dt, jv + s.w1[i], s.q[i]), p.box[a], p.inv_box[a]);
+  s.q[i] = qn;
+  s.u[i] = u;
+  s.g[i] = inertial ? g[i] * (p.inv_h * p.inv_h) : 0.0;
+  if (!isfinite(qn) || !isfinite(u)) atomicOr(s.err, DEV_ERR_NONFINITE);
+  if (fabs(u) * p.dt > p.h) atomicOr(s.err, DEV_ERR_CFL);
+}
+
+inline unsigned eblocks(long long n) { return (unsigned)((n + 255) / 256); }
+
 }  // namespace
+
+template <typename R>
+void build_row_bins(const BlobParams& p, long long nb, const double* q, RowBins bins, cudaStream_t st) {
+  if (nb <= 0) return;
+  k_bin_count<R><<<eblocks(nb), 256, 0, st>>>(p, nb, q, bins);
+  k_bin_scan<<<1, 1024, 0, st>>>(bins);
+  k_bin_fill<R><<<eblocks(nb), 256, 0, st>>>(p, nb, q, bins);
+}
+template void build_row_bins<float>(const BlobParams&, long long, const double*, RowBins, cudaStream_t);
+template void build_row_bins<double>(const BlobParams&, long long, const double*, RowBins, cudaStream_t);
+
+void blob_dp_from(const BlobParams& p, BlobState s, const double* jvt, cudaStream_t st) {
+  if (s.nb > 0) k_dp_from<<<eblocks(3 * s.nb), 256, 0, st>>>(p, s, jvt);
+}
+void blob_inertial_from(const BlobParams& p, BlobState s, const double* jdvt, cudaStream_t st) {
+  if (s.nb > 0) k_inertial_from<<<eblocks(3 * s.nb), 256, 0, st>>>(p, s, jdvt);
+}
+void blob_finish_from(const BlobParams& p, BlobState s, const double* base, const double* add, const double* g,
+                      bool inertial, cudaStream_t st) {
+  if (s.nb > 0) k_finish_from<<<eblocks(3 * s.nb), 256, 0, st>>>(p, s, base, add, g, inertial ? 1 : 0);
+}
 
 #define ICM_KSWITCH(call3, call4) \
   if (p.kernel == 3) {            \

@@ -21,8 +21,13 @@
 
 #include <cuda.h>
 
+#include "icm.h"
 #include "icm_internal.h"
 #include "icm_fft_reg.cuh"
+#include "icm_rows.cuh"
+
+// Each shard uses only part of the helpers below.
+#pragma nv_diag_suppress 177
 
 namespace icm {
 namespace {
@@ -701,12 +706,15 @@ __global__ void __launch_bounds__(kThreads) k_ypass2(cplx_t<R>* __restrict__ spe
 }
 
 // x forward, two real rows per complex line; frequency k ends at position
-// R2 (k mod R1) + k div R1 of its line.
-template <typename R, int N, int R1, int R2>
+// R2 (k mod R1) + k div R1 of its line.  BLOBS: before the transform, the blobs of
+// this row block spread rb.vec into the rows (in shared memory, where the first
+// stage reads them), added to src if src is set.
+template <typename R, int N, int R1, int R2, bool BLOBS>
 __global__ void __launch_bounds__(kThreads) k_xfwd2(const R* __restrict__ src, cplx_t<R>* __restrict__ spec,
                                                     const cplx_t<R>* __restrict__ gtw, int nrows, long long ncell,
-                                                    int kx, int kxp) {
+                                                    int kx, int kxp, RowBlobs rb) {
   using C = cplx_t<R>;
+  static_assert(kRowBlock == 2 * kXLines, "row blocks are the x-pass blocks");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);   // [kXLines][xrow(N)]
   C* tw = buf + kXLines * xrow(N);
@@ -714,18 +722,55 @@ __global__ void __launch_bounds__(kThreads) k_xfwd2(const R* __restrict__ src, c
   load_stage_twiddles<R, R1, R2>(tw, gtw, tid, kThreads);
   const int comp = blockIdx.y;
   const long long row0 = (long long)blockIdx.x * (2 * kXLines);
-  const R* s = src + comp * ncell;
-  __syncthreads();
-  for (int it = tid; it < kXLines * R2; it += kThreads) {
-    const int n1 = it % R2, l = it / R2;
-    const long long r0 = row0 + 2 * l;
-    const R* p0 = s + r0 * N;
-    const bool ok0 = r0 < nrows, ok1 = r0 + 1 < nrows;
-    C a[R1];
+  const bool dense = !BLOBS || src != nullptr;
+  // one first-stage item (line l, offset n1) per thread; its loads are issued first
+  constexpr int ITEMS = kXLines * R2;
+  static_assert(ITEMS <= kThreads, "one first-stage item per thread");
+  const int n1 = tid % R2, l = tid / R2;
+  const long long r0 = row0 + 2 * l;
+  const R* p0 = src + comp * ncell + r0 * N;
+  const bool ok0 = dense && tid < ITEMS && r0 < nrows, ok1 = ok0 && r0 + 1 < nrows;
+  C a[R1];
 #pragma unroll
-    for (int r = 0; r < R1; ++r) {
-      const int x = n1 + R2 * r;
-      a[r] = mk(ok0 ? p0[x] : R(0), ok1 ? p0[N + x] : R(0));
+  for (int r = 0; r < R1; ++r) {
+    const int x = n1 + R2 * r;
+    a[r] = mk(ok0 ? p0[x] : R(0), ok1 ? p0[N + x] : R(0));
+  }
+  if (BLOBS) {
+    for (int i = tid; i < kXLines * xrow(N); i += kThreads) buf[i] = mk(R(0), R(0));
+    __syncthreads();
+    R* rows = reinterpret_cast<R*>(buf);
+    const BlobStencil<R>* rec = reinterpret_cast<const BlobStencil<R>*>(rb.geo);
+    const double inv_dvf = rb.p.inv_h * rb.p.inv_h * rb.p.inv_h;
+    const auto line = [](int ln, int x) { return xaddr(ln, x, N); };
+    const int e = rb.start[blockIdx.x + 1];
+    const bool plane = rb.p.ny % kRowBlock == 0;   // the block is part of one z plane
+    const int z0 = (int)row0 / rb.p.ny, y0 = (int)row0 % rb.p.ny;
+    for (int i = rb.start[blockIdx.x] + tid; i < e; i += kThreads) {
+      const int b = rb.list[i];
+      const R amp = (R)(rb.vec[3 * b + comp] * inv_dvf);
+      if (rb.p.kernel == 3) {
+        CompStencil<R, 3> S;
+        load_comp<R, 3>(S, rec + b, comp);
+        if (plane)
+          spread_plane<R, 3, N>(rows, z0, y0, S, amp, rb.p, line);
+        else
+          spread_task<R, 3, N>(rows, (int)row0, S, amp, rb.p, line);
+      } else {
+        CompStencil<R, 4> S;
+        load_comp<R, 4>(S, rec + b, comp);
+        if (plane)
+          spread_plane<R, 4, N>(rows, z0, y0, S, amp, rb.p, line);
+        else
+          spread_task<R, 4, N>(rows, (int)row0, S, amp, rb.p, line);
+      }
+    }
+  }
+  __syncthreads();
+  if (tid < ITEMS) {
+    if (BLOBS) {
+#pragma unroll
+      for (int r = 0; r < R1; ++r) a[r] = cadd(a[r], buf[xaddr(l, n1 + R2 * r, N)]);
     }
     stage_a_fwd<R, R1, R2>(a, tw + n1);
 #pragma unroll
@@ -756,13 +801,17 @@ __global__ void __launch_bounds__(kThreads) k_xfwd2(const R* __restrict__ src, c
   }
 }
 
-// MODE OUT_STORE: dst = x.  MODE OUT_ADD_AND_STORE2: dst += x, dst2 = x, with the old
-// dst values loaded at kernel start so that they are in flight during the FFT.
-template <typename R, int N, int R1, int R2, int MODE>
+// MODE OUT_STORE: dst = x.  OUT_ADD_AND_STORE2: dst += x, dst2 = x.  OUT_ADD: dst += x.
+// OUT_NONE: nothing stored.  The old dst values of the adding modes are loaded at
+// kernel start so that they are in flight during the FFT.  GATHER 1: the blobs of
+// this row block add the part of J x in these rows to rb.acc; GATHER 2: also J L x
+// (without 1/h^2) to rb.acc_lap.  x stays in shared memory for the gathers.
+template <typename R, int N, int R1, int R2, int MODE, int GATHER>
 __global__ void __launch_bounds__(kThreads) k_xinv2(const cplx_t<R>* __restrict__ spec, R* __restrict__ dst,
                                                     R* __restrict__ dst2, const cplx_t<R>* __restrict__ gtw,
-                                                    int nrows, long long ncell, int kxp) {
+                                                    int nrows, long long ncell, int kxp, RowBlobs rb) {
   using C = cplx_t<R>;
+  constexpr bool ADDS = MODE == OUT_ADD_AND_STORE2 || MODE == OUT_ADD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* tw = buf + kXLines * xrow(N);
@@ -775,8 +824,8 @@ __global__ void __launch_bounds__(kThreads) k_xinv2(const cplx_t<R>* __restrict_
   const size_t cb = (size_t)comp * ncell;
   // this thread's output positions: line l = tid / R2, x = n1 + R2 n2, rows r0 and r0 + 1
   constexpr int OUTS = (kXLines * R2 + kThreads - 1) / kThreads;
-  R old0[MODE == OUT_ADD_AND_STORE2 ? OUTS * R1 : 1], old1[MODE == OUT_ADD_AND_STORE2 ? OUTS * R1 : 1];
-  if (MODE == OUT_ADD_AND_STORE2) {
+  R old0[ADDS ? OUTS * R1 : 1], old1[ADDS ? OUTS * R1 : 1];
+  if (ADDS) {
 #pragma unroll
     for (int o = 0; o < OUTS; ++o) {
       const int it = tid + o * kThreads;
@@ -837,6 +886,12 @@ __global__ void __launch_bounds__(kThreads) k_xinv2(const cplx_t<R>* __restrict_
 #pragma unroll
     for (int k2 = 0; k2 < R1; ++k2) a[k2] = buf[xaddr(l, n1 + R2 * k2, N)];
     stage_a_inv<R, R1, R2>(a, tw + n1);
+    if (GATHER) {
+      // the same positions this thread read: in place
+#pragma unroll
+      for (int n2 = 0; n2 < R1; ++n2) buf[xaddr(l, n1 + R2 * n2, N)] = a[n2];
+    }
+    if (MODE == OUT_NONE) continue;
     const long long r0 = row0 + 2 * l;
 #pragma unroll
     for (int n2 = 0; n2 < R1; ++n2) {
@@ -847,7 +902,7 @@ __global__ void __launch_bounds__(kThreads) k_xinv2(const cplx_t<R>* __restrict_
           dst[ox] = a[n2].x;
         } else {
           dst[ox] = old0[o * R1 + n2] + a[n2].x;
-          dst2[ox] = a[n2].x;
+          if (MODE == OUT_ADD_AND_STORE2) dst2[ox] = a[n2].x;
         }
       }
       if (r0 + 1 < nrows) {
@@ -856,9 +911,45 @@ __global__ void __launch_bounds__(kThreads) k_xinv2(const cplx_t<R>* __restrict_
           dst[ox] = a[n2].y;
         } else {
           dst[ox] = old1[o * R1 + n2] + a[n2].y;
-          dst2[ox] = a[n2].y;
+          if (MODE == OUT_ADD_AND_STORE2) dst2[ox] = a[n2].y;
         }
       }
+    }
+  }
+  if (GATHER) {
+    __syncthreads();
+    const R* rows = reinterpret_cast<const R*>(buf);
+    const BlobStencil<R>* rec = reinterpret_cast<const BlobStencil<R>*>(rb.geo);
+    const auto line = [](int l, int x) { return xaddr(l, x, N); };
+    const int e = rb.start[blockIdx.x + 1];
+    const bool plane = rb.p.ny % kRowBlock == 0;   // the block is part of one z plane
+    const int z0 = (int)row0 / rb.p.ny, y0 = (int)row0 % rb.p.ny;
+    for (int i = rb.start[blockIdx.x] + tid; i < e; i += kThreads) {
+      const int b = rb.list[i];
+      R j, jl = R(0);
+      if (rb.p.kernel == 3) {
+        CompStencil<R, 3> S;
+        load_comp<R, 3>(S, rec + b, comp);
+        if (plane) {
+          j = gather_plane<R, 3, N>(rows, z0, y0, S, rb.p, line);
+          if (GATHER == 2) jl = gather_lap_plane<R, 3, N>(rows, z0, y0, S, rb.p, line);
+        } else {
+          j = gather_task<R, 3, N>(rows, (int)row0, S, rb.p, line);
+          if (GATHER == 2) jl = gather_lap_task<R, 3, N>(rows, (int)row0, S, rb.p, line);
+        }
+      } else {
+        CompStencil<R, 4> S;
+        load_comp<R, 4>(S, rec + b, comp);
+        if (plane) {
+          j = gather_plane<R, 4, N>(rows, z0, y0, S, rb.p, line);
+          if (GATHER == 2) jl = gather_lap_plane<R, 4, N>(rows, z0, y0, S, rb.p, line);
+        } else {
+          j = gather_task<R, 4, N>(rows, (int)row0, S, rb.p, line);
+          if (GATHER == 2) jl = gather_lap_task<R, 4, N>(rows, (int)row0, S, rb.p, line);
+        }
+      }
+      atomicAdd(&rb.acc[3 * b + comp], (double)j);
+      if (GATHER == 2) atomicAdd(&rb.acc_lap[3 * b + comp], (double)jl);
     }
   }
 }
@@ -885,27 +976,60 @@ template <typename R> size_t smem_y(int n) { return (size_t)n * seg_lines<R>() *
 template <typename R> size_t smem_z(int n) { return 3 * (size_t)n * seg_lines<R>() * sizeof(cplx_t<R>) + n * sizeof(cplx_t<R>); }
 
 template <typename R>
-void set_smem_attributes() {
+void set_xf_attributes() {
+  const int big = 227 * 1024;
+#define ICM_ATTR(N, R1, R2)                                                                                        \
+  cudaFuncSetAttribute(k_xfwd2<R, N, R1, R2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);           \
+  cudaFuncSetAttribute(k_xfwd2<R, N, R1, R2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  ICM_FFT_SIDES(ICM_ATTR)
+#undef ICM_ATTR
+  cudaFuncSetAttribute(k_xfwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+}
+
+template <typename R>
+void set_xi_attributes() {
+  const int big = 227 * 1024;
+#define ICM_ATTR(N, R1, R2)                                                                                        \
+  cudaFuncSetAttribute(k_xinv2<R, N, R1, R2, OUT_STORE, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);    \
+  cudaFuncSetAttribute(k_xinv2<R, N, R1, R2, OUT_ADD_AND_STORE2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big); \
+  cudaFuncSetAttribute(k_xinv2<R, N, R1, R2, OUT_STORE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);    \
+  cudaFuncSetAttribute(k_xinv2<R, N, R1, R2, OUT_NONE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);     \
+  cudaFuncSetAttribute(k_xinv2<R, N, R1, R2, OUT_ADD, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  ICM_FFT_SIDES(ICM_ATTR)
+#undef ICM_ATTR
+  cudaFuncSetAttribute(k_xinv<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+}
+
+template <typename R>
+void set_yz_attributes() {
   const int big = 227 * 1024;
 #define ICM_ATTR(N, R1, R2)                                                                               \
   cudaFuncSetAttribute(k_zsym2<R, N, R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);         \
   if (N <= 256) /* exactly its need: the kernel also holds static shared memory */                          \
     cudaFuncSetAttribute(k_zsym_tma<R, N, R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ztma<R, N>()); \
   cudaFuncSetAttribute(k_ypass2<R, N, R1, R2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big); \
-  cudaFuncSetAttribute(k_ypass2<R, N, R1, R2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);  \
-  cudaFuncSetAttribute(k_xfwd2<R, N, R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);         \
-  cudaFuncSetAttribute(k_xinv2<R, N, R1, R2, OUT_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);        \
-  cudaFuncSetAttribute(k_xinv2<R, N, R1, R2, OUT_ADD_AND_STORE2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_ypass2<R, N, R1, R2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   ICM_FFT_SIDES(ICM_ATTR)
 #undef ICM_ATTR
-  cudaFuncSetAttribute(k_xfwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  cudaFuncSetAttribute(k_xinv<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_ypass<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_ypass<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_zsym<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
 }  // namespace
+
+// This file is compiled as six objects in parallel (-DICM_FFT_SHARD=k): for FP32,
+// k = 0 the forward x passes and the precision-independent code, 1 the y and z
+// passes, 2 the inverse x passes; k = 3, 4, 5 the same for FP64.  Without the macro
+// one object holds everything.
+#ifndef ICM_FFT_SHARD
+#define ICM_FFT_SHARD -1
+#endif
+#define ICM_SHARD(k) (ICM_FFT_SHARD < 0 || ICM_FFT_SHARD == (k))
+
+template <typename R> void fft_prepare_xf() { set_xf_attributes<R>(); }
+template <typename R> void fft_prepare_xi() { set_xi_attributes<R>(); }
+template <typename R> void fft_prepare_yz() { set_yz_attributes<R>(); }
 
 template <typename R>
 void fft_x_forward(const FftCtx<R>& f, const R* src, cudaStream_t st) {
@@ -914,7 +1038,7 @@ void fft_x_forward(const FftCtx<R>& f, const R* src, cudaStream_t st) {
   const cplx_t<R>* tw = (const cplx_t<R>*)f.px.tw;
   switch (f.nx) {
 #define ICM_CASE(N, R1, R2) \
-  case N: k_xfwd2<R, N, R1, R2><<<dim3(xblocks, 3), kThreads, smem_x2<R, N>(), st>>>(src, f.spec, tw, nrows, f.ncell, f.kx, f.kxp); return;
+  case N: k_xfwd2<R, N, R1, R2, false><<<dim3(xblocks, 3), kThreads, smem_x2<R, N>(), st>>>(src, f.spec, tw, nrows, f.ncell, f.kx, f.kxp, RowBlobs{}); return;
     ICM_FFT_SIDES(ICM_CASE)
 #undef ICM_CASE
     default: break;
@@ -1005,9 +1129,9 @@ void fft_x_inverse(const FftCtx<R>& f, R* dst, R* dst2, int mode, cudaStream_t s
 #define ICM_CASE(N, R1, R2) \
   case N:                                                                                                              \
     if (mode == OUT_STORE)                                                                                             \
-      k_xinv2<R, N, R1, R2, OUT_STORE><<<dim3(xblocks, 3), kThreads, smem_x2<R, N>(), st>>>(f.spec, dst, dst2, tw, nrows, f.ncell, f.kxp); \
+      k_xinv2<R, N, R1, R2, OUT_STORE, 0><<<dim3(xblocks, 3), kThreads, smem_x2<R, N>(), st>>>(f.spec, dst, dst2, tw, nrows, f.ncell, f.kxp, RowBlobs{}); \
     else                                                                                                               \
-      k_xinv2<R, N, R1, R2, OUT_ADD_AND_STORE2><<<dim3(xblocks, 3), kThreads, smem_x2<R, N>(), st>>>(f.spec, dst, dst2, tw, nrows, f.ncell, f.kxp); \
+      k_xinv2<R, N, R1, R2, OUT_ADD_AND_STORE2, 0><<<dim3(xblocks, 3), kThreads, smem_x2<R, N>(), st>>>(f.spec, dst, dst2, tw, nrows, f.ncell, f.kxp, RowBlobs{}); \
     return;
     ICM_FFT_SIDES(ICM_CASE)
 #undef ICM_CASE
@@ -1015,6 +1139,51 @@ void fft_x_inverse(const FftCtx<R>& f, R* dst, R* dst2, int mode, cudaStream_t s
   }
   k_xinv<R><<<dim3(xblocks, 3), kThreads, smem_x<R>(f.nx), st>>>(f.spec, dst, dst2, mode, f.px, nrows, f.ncell,
                                                                  f.kxp);
+}
+
+#if ICM_SHARD(0)
+bool fft_has_blob_passes(int nx) {
+  int r1 = 0, r2 = 0;
+  return fft_split(nx, r1, r2);
+}
+#endif
+
+template <typename R>
+void fft_x_forward_blobs(const FftCtx<R>& f, const R* src, const RowBlobs& rb, cudaStream_t st) {
+  const int nrows = f.ny * f.nz;
+  const int xblocks = (nrows + 2 * kXLines - 1) / (2 * kXLines);
+  const cplx_t<R>* tw = (const cplx_t<R>*)f.px.tw;
+  switch (f.nx) {
+#define ICM_CASE(N, R1, R2) \
+  case N: k_xfwd2<R, N, R1, R2, true><<<dim3(xblocks, 3), kThreads, smem_x2<R, N>(), st>>>(src, f.spec, tw, nrows, f.ncell, f.kx, f.kxp, rb); return;
+    ICM_FFT_SIDES(ICM_CASE)
+#undef ICM_CASE
+    default: break;
+  }
+  record_error(ICM_EINVAL, "x pass with blob work requested for a side without register FFT kernels");
+}
+
+template <typename R>
+void fft_x_inverse_blobs(const FftCtx<R>& f, R* dst, int mode, const RowBlobs& rb, cudaStream_t st) {
+  const int nrows = f.ny * f.nz;
+  const int xblocks = (nrows + 2 * kXLines - 1) / (2 * kXLines);
+  const cplx_t<R>* tw = (const cplx_t<R>*)f.px.tw;
+  const dim3 grid(xblocks, 3);
+  switch (f.nx) {
+#define ICM_CASE(N, R1, R2)                                                                                              \
+  case N:                                                                                                                \
+    if (mode == OUT_STORE)                                                                                               \
+      k_xinv2<R, N, R1, R2, OUT_STORE, 1><<<grid, kThreads, smem_x2<R, N>(), st>>>(f.spec, dst, nullptr, tw, nrows, f.ncell, f.kxp, rb); \
+    else if (mode == OUT_NONE)                                                                                           \
+      k_xinv2<R, N, R1, R2, OUT_NONE, 1><<<grid, kThreads, smem_x2<R, N>(), st>>>(f.spec, dst, nullptr, tw, nrows, f.ncell, f.kxp, rb); \
+    else                                                                                                                 \
+      k_xinv2<R, N, R1, R2, OUT_ADD, 2><<<grid, kThreads, smem_x2<R, N>(), st>>>(f.spec, dst, nullptr, tw, nrows, f.ncell, f.kxp, rb); \
+    return;
+    ICM_FFT_SIDES(ICM_CASE)
+#undef ICM_CASE
+    default: break;
+  }
+  record_error(ICM_EINVAL, "x pass with blob work requested for a side without register FFT kernels");
 }
 
 template <typename R>
@@ -1027,6 +1196,7 @@ void spectral_solve(const FftCtx<R>& f, const R* src, R* dst, R* dst2, int mode,
   fft_x_inverse<R>(f, dst, dst2, mode, st);
 }
 
+#if ICM_SHARD(0)
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -1062,20 +1232,70 @@ bool make_zmap(void* map, const void* spec, int precision, int kx, int kxp, int 
   return r == CUDA_SUCCESS;
 }
 
+#endif
+
+#define ICM_INST_XF(R, KW)                                                                               \
+  KW template void fft_x_forward<R>(const FftCtx<R>&, const R*, cudaStream_t);                           \
+  KW template void fft_x_forward_blobs<R>(const FftCtx<R>&, const R*, const RowBlobs&, cudaStream_t);    \
+  KW template void fft_prepare_xf<R>();
+#define ICM_INST_XI(R, KW)                                                                               \
+  KW template void fft_x_inverse<R>(const FftCtx<R>&, R*, R*, int, cudaStream_t);                        \
+  KW template void fft_x_inverse_blobs<R>(const FftCtx<R>&, R*, int, const RowBlobs&, cudaStream_t);     \
+  KW template void fft_prepare_xi<R>();
+#define ICM_INST_YZ(R, KW)                                                                               \
+  KW template void fft_y<R>(const FftCtx<R>&, bool, cudaStream_t);                                       \
+  KW template void fft_z_symbol<R>(const FftCtx<R>&, double, double, const double*, double, cudaStream_t); \
+  KW template void fft_prepare_yz<R>();
+#define ICM_NONE
+#if ICM_SHARD(0)
+ICM_INST_XF(float, ICM_NONE)
+#else
+ICM_INST_XF(float, extern)
+#endif
+#if ICM_SHARD(1)
+ICM_INST_YZ(float, ICM_NONE)
+#else
+ICM_INST_YZ(float, extern)
+#endif
+#if ICM_SHARD(2)
+ICM_INST_XI(float, ICM_NONE)
+#else
+ICM_INST_XI(float, extern)
+#endif
+#if ICM_SHARD(3)
+ICM_INST_XF(double, ICM_NONE)
+#else
+ICM_INST_XF(double, extern)
+#endif
+#if ICM_SHARD(4)
+ICM_INST_YZ(double, ICM_NONE)
+#else
+ICM_INST_YZ(double, extern)
+#endif
+#if ICM_SHARD(5)
+ICM_INST_XI(double, ICM_NONE)
+#else
+ICM_INST_XI(double, extern)
+#endif
+
+#if ICM_SHARD(0)
 void fft_prepare() {
-  set_smem_attributes<float>();
-  set_smem_attributes<double>();
+  fft_prepare_xf<float>();
+  fft_prepare_yz<float>();
+  fft_prepare_xi<float>();
+  fft_prepare_xf<double>();
+  fft_prepare_yz<double>();
+  fft_prepare_xi<double>();
 }
 
-#define ICM_INST(R)                                                                                    \
-  template void spectral_solve<R>(const FftCtx<R>&, const R*, R*, R*, int, double, double, const double*, double, \
-                                  cudaStream_t);                                                        \
-  template void fft_x_forward<R>(const FftCtx<R>&, const R*, cudaStream_t);                             \
-  template void fft_y<R>(const FftCtx<R>&, bool, cudaStream_t);                                         \
-  template void fft_z_symbol<R>(const FftCtx<R>&, double, double, const double*, double, cudaStream_t); \
-  template void fft_x_inverse<R>(const FftCtx<R>&, R*, R*, int, cudaStream_t);
-ICM_INST(float)
-ICM_INST(double)
-#undef ICM_INST
+template void spectral_solve<float>(const FftCtx<float>&, const float*, float*, float*, int, double, double,
+                                    const double*, double, cudaStream_t);
+template void spectral_solve<double>(const FftCtx<double>&, const double*, double*, double*, int, double, double,
+                                     const double*, double, cudaStream_t);
+#endif
+#undef ICM_NONE
+#undef ICM_INST_XF
+#undef ICM_INST_XI
+#undef ICM_INST_YZ
 
 }  // namespace icm

@@ -67,7 +67,7 @@ struct FftCtx {
 // spectrum buffer; returns false if TMA is unavailable for this shape.
 bool make_zmap(void* map, const void* spec, int precision, int kx, int kxp, int ny, int nz);
 
-enum OutMode : int { OUT_STORE = 0, OUT_ADD_AND_STORE2 = 1 };
+enum OutMode : int { OUT_STORE = 0, OUT_ADD_AND_STORE2 = 1, OUT_ADD = 2, OUT_NONE = 3 };
 
 // x^ = P^ r^ / (a + b |d|^2) for the three components of src (real face field,
 // 3*ncell values).  OUT_STORE: dst = x.  OUT_ADD_AND_STORE2: dst += x, dst2 = x.
@@ -174,6 +174,54 @@ template <typename R> void blob_finish(const BlobParams& p, BlobState s, const R
                                        bool inertial, cudaStream_t st);
 template <typename R> void blob_interp(const BlobParams& p, long long nb, const double* q, const R* field,
                                        bool laplacian, double* out, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Blob work fused into the x passes (sides with register FFT kernels)
+// ---------------------------------------------------------------------------
+// Row-block bins: the blobs whose extended support touches each 32-row x-pass block.
+// The builder also writes each blob's stencil geometry (anchor cells and fractional
+// offsets, FP64 arithmetic done once) and zeroes the blob accumulators of the step.
+struct RowBins {
+  int* count;    // [nblocks], zero between builds
+  int* start;    // [nblocks + 1]
+  int* cursor;   // [nblocks]
+  int* list;     // [capacity] blob ids
+  void* geo;     // [nb] stencil records (R-typed, at most kStencilBytes each)
+  double* acc;   // [nacc * nb] accumulators zeroed by the build
+  int nacc;
+  int nblocks;
+  long long capacity;
+};
+constexpr int kBinsPerBlob = 49;   // capacity per blob: 7 x 7 (y, z) node pairs at most
+constexpr int kStencilBytes = 336; // per-blob stencil record (FP64: 12 ints + 36 doubles)
+
+// A blob source spread into the rows of x_fwd, or the accumulators x_inv gathers into.
+struct RowBlobs {
+  const int* start;
+  const int* list;
+  const void* geo;     // stencil records
+  const double* vec;   // spread: per-blob vectors (n,3), spread as phi vec / dV_f
+  double* acc;         // gather: J of the transform output, (n,3) accumulators
+  double* acc_lap;     // gather: J L of the transform output without 1/h^2, (n,3)
+  BlobParams p;
+};
+template <typename R>
+void build_row_bins(const BlobParams& p, long long nb, const double* q, RowBins bins, cudaStream_t st);
+// x passes with blob work: src may be null (the spread source only).
+template <typename R>
+void fft_x_forward_blobs(const FftCtx<R>& f, const R* src, const RowBlobs& rb, cudaStream_t st);
+// mode: OUT_STORE (dst = x), OUT_ADD (dst += x) or OUT_NONE; gathers J x into rb.acc
+// and, if rb.acc_lap is set, J L x (without 1/h^2) into rb.acc_lap.
+template <typename R>
+void fft_x_inverse_blobs(const FftCtx<R>& f, R* dst, int mode, const RowBlobs& rb, cudaStream_t st);
+bool fft_has_blob_passes(int nx);
+
+// Elementwise blob updates of the fused step (one thread per blob component).
+void blob_dp_from(const BlobParams& p, BlobState s, const double* jvt, cudaStream_t st);
+void blob_inertial_from(const BlobParams& p, BlobState s, const double* jdvt, cudaStream_t st);
+// jv = base + add (base may be null): J^{n+1/2} v^{n+1}; g: J L dv without 1/h^2.
+void blob_finish_from(const BlobParams& p, BlobState s, const double* base, const double* add, const double* g,
+                      bool inertial, cudaStream_t st);
 
 // Scalar bookkeeping kernels.
 void scalars_before_step(double* scal, double dt, double rho, double dvf, cudaStream_t st);

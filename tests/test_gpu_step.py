@@ -60,7 +60,14 @@ CASES = [
     ((32, 12, 18), 9, 4, 14, 0.0, 0.05, 1e-3, "visc", True),      # neutrally buoyant: steps 4-8 skipped
     ((9, 18, 16), 4, 4, 15, 2.0, 0.01, 5e-3, "visc", False),
     ((16, 16, 16), 0, 4, 16, 1.0, 0.0, 1e-3, "visc", True),       # fluid only
+    # x sides with register FFT passes: the blob work runs inside the x passes
+    ((32, 32, 16), 8, 4, 17, 1.0, 0.05, 1e-3, "visc", True),      # Ny % 32 == 0: one z plane per row block
+    ((32, 64, 8), 10, 3, 20, 1.0, 0.03, 1e-3, "visc", True),      # 3-point, 7-node span on an 8-node side
+    ((48, 24, 12), 7, 3, 18, 1.0, 0.02, 1e-3, "full", True),      # row blocks straddle z planes
+    ((64, 12, 9), 6, 4, 19, 2.0, 0.0, 2e-3, "zero", True),        # several z planes per row block
+    ((96, 32, 12), 9, 4, 22, 1.0, 0.04, 0.0, "visc", False),
 ]
+SEAM = {6, 7, 8, 9}    # cases that also put blobs on the periodic seams and corners
 
 
 @pytest.mark.parametrize("precision", [64, 32])
@@ -68,6 +75,12 @@ CASES = [
 def test_step_parity(precision, case):
     grid, nb, kernel, seed, me_scale, force, kT, slip, adv = case
     prm, st = _case(grid, nb, kernel, seed, me_scale, force, kT, slip=slip, advection=adv)
+    if CASES.index(case) in SEAM:
+        L = np.array(grid, dtype=float) * prm.h
+        st.q[0] = [0.0, 0.0, 0.0]
+        st.q[1] = L - 0.3 * prm.h
+        st.q[2] = [0.5 * prm.h, L[1] - 0.25 * prm.h, 1e-12]
+        st.q[3] = [L[0] - 0.5 * prm.h, 0.5 * prm.h, L[2] - 0.5 * prm.h]
     worst = _run_parity(prm, st, precision, nsteps=4)
     for k, e in worst.items():
         assert e < TOL[precision], (k, e, worst)
@@ -86,8 +99,8 @@ def test_plain_config_100_steps(precision):
 
 
 @pytest.mark.parametrize("precision", [64, 32])
-def test_momentum_conservation_and_impulse(precision):
-    grid = (24, 24, 24)
+@pytest.mark.parametrize("grid", [(24, 24, 24), (32, 32, 24)])
+def test_momentum_conservation_and_impulse(precision, grid):
     prm, st = _case(grid, 12, 4, 21, 1.0, 0.0, kT=1e-3)
     st.v += 0.01      # a nonzero total momentum
     sim = make_sim(prm, st, precision)
