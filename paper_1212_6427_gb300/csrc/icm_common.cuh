@@ -66,13 +66,15 @@ template <> struct BoxMuller<double> {
 };
 template <> struct BoxMuller<float> {
   __device__ __forceinline__ static void apply(uint32_t a, uint32_t b, float& z0, float& z1) {
-    // u from the top 24 bits plus the low 8 bits so that the uniform keeps its
-    // full 32-bit resolution near 0 (where the tail of the normal lives).
-    const float u1 = fmaf((float)(a >> 8), 5.9604644775390625e-08f, ((float)(a & 0xffu) + 0.5f) * 2.3283064365386963e-10f);
-    const float u2 = fmaf((float)(b >> 8), 5.9604644775390625e-08f, ((float)(b & 0xffu) + 0.5f) * 2.3283064365386963e-10f);
-    // -2 ln u1 = -2 ln(2) log2(u1); the hardware log2 is accurate to ~2^-22 absolute,
-    // far inside the FP32 path's tolerance (the uniforms themselves carry 2^-24)
-    const float rad = sqrtf(-1.38629436111989061f * __log2f(u1));
+    // u = (x + 1/2) 2^-32 with one rounding: exact for x < 2^23 (u < 2^-9, the tail
+    // of the normal), relative error <= 2^-24 above
+    const float u1 = fmaf(__uint2float_rn(a), 2.3283064365386963e-10f, 1.16415321826934814e-10f);
+    const float u2 = fmaf(__uint2float_rn(b), 2.3283064365386963e-10f, 1.16415321826934814e-10f);
+    // -2 ln u1 = -2 ln(2) log2(u1); the hardware log2 and reciprocal square root are
+    // accurate to ~2^-22 relative, far inside the FP32 path's tolerance.  u1 may round
+    // to 1, where the radius is 0: the floor keeps x * rsqrt(x) finite.
+    const float x = fmaxf(-1.38629436111989061f * __log2f(u1), 1e-30f);
+    const float rad = x * rsqrtf(x);
     float s, c;
     __sincosf(6.28318530717958648f * u2, &s, &c);
     z0 = rad * c;

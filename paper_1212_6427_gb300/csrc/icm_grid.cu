@@ -73,33 +73,41 @@ __device__ __forceinline__ void gen_plane(RhsSmem<R>& sm, int slot, int i0, int 
   }
 }
 
-// Global loads of one velocity plane (with halo) into registers: thread tid takes
-// halo cells tid, tid + NT, ...
-template <typename R>
-__device__ __forceinline__ void load_plane(R (&r)[PER][3], const R* __restrict__ v, int i0, int j0, int k,
-                                           const GridParams& g, int tid) {
-  const int kk = wrapi(k, g.nz);
+// Plane offsets (x + Nx y, wrapped) of the halo cells thread tid loads: cells tid,
+// tid + NT, ... of the (TX+2) x (TY+2) plane; -1 past the plane.
+__device__ __forceinline__ void plane_offsets(int (&off)[PER], int i0, int j0, const GridParams& g, int tid) {
 #pragma unroll
   for (int t = 0; t < PER; ++t) {
     const int idx = tid + t * NT;
-    if (idx < HALO) {
-      const int hx = idx % HX, hy = idx / HX;
-      const long long o = wrapi(i0 - 1 + hx, g.nx) + (long long)g.nx * (wrapi(j0 - 1 + hy, g.ny) + (long long)g.ny * kk);
+    const int hx = idx % HX, hy = idx / HX;
+    off[t] = idx < HALO ? wrapi(i0 - 1 + hx, g.nx) + g.nx * wrapi(j0 - 1 + hy, g.ny) : -1;
+  }
+}
+
+// Global loads of one velocity plane (with halo) into registers.
+template <typename R>
+__device__ __forceinline__ void load_plane(R (&r)[PER][3], const R* __restrict__ v, const int (&off)[PER], int k,
+                                           const GridParams& g) {
+  const long long zo = (long long)g.nx * g.ny * wrapi(k, g.nz);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) r[t][c] = v[c * g.ncell + o];
+  for (int t = 0; t < PER; ++t) {
+    if (off[t] >= 0) {
+      const R* p = v + zo + off[t];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) r[t][c] = p[c * g.ncell];
     }
   }
 }
 
+// The loaded plane into ring slot `slot` (the plane's cells are stored in load order).
 template <typename R>
 __device__ __forceinline__ void store_plane(RhsSmem<R>& sm, int slot, const R (&r)[PER][3], int tid) {
 #pragma unroll
   for (int t = 0; t < PER; ++t) {
     const int idx = tid + t * NT;
     if (idx < HALO) {
-      const int hx = idx % HX, hy = idx / HX;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) sm.v[slot][c][hy][hx] = r[t][c];
+      for (int c = 0; c < 3; ++c) (&sm.v[slot][c][0][0])[idx] = r[t][c];
     }
   }
 }
@@ -131,11 +139,13 @@ __global__ void __launch_bounds__(NT, 2) k_rhs(const R* __restrict__ v, R* __res
   const int lx = tx + 1, ly = ty + 1;
 
   R pre[PER][3];
-  load_plane<R>(pre, v, i0, j0, k0 - 1, g, tid);
+  int off[PER];
+  plane_offsets(off, i0, j0, g, tid);
+  load_plane<R>(pre, v, off, k0 - 1, g);
   store_plane<R>(sm, 0, pre, tid);
-  load_plane<R>(pre, v, i0, j0, k0, g, tid);
+  load_plane<R>(pre, v, off, k0, g);
   store_plane<R>(sm, 1, pre, tid);
-  load_plane<R>(pre, v, i0, j0, k0 + 1, g, tid);
+  load_plane<R>(pre, v, off, k0 + 1, g);
   if (NOISE) {
     gen_plane<R>(sm, 0, i0, j0, k0 - 1, g, step, tid);
     gen_plane<R>(sm, 1, i0, j0, k0, g, step, tid);
@@ -155,7 +165,7 @@ __global__ void __launch_bounds__(NT, 2) k_rhs(const R* __restrict__ v, R* __res
         ao[2] = adv[2 * nc + o];
       }
     }
-    if (k + 1 < kend) load_plane<R>(pre, v, i0, j0, k + 2, g, tid);   // in flight during the noise
+    if (k + 1 < kend) load_plane<R>(pre, v, off, k + 2, g);   // in flight during the noise
     if (NOISE) gen_plane<R>(sm, sn, i0, j0, k + 1, g, step, tid);
     __syncthreads();
     if (active) {
