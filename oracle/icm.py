@@ -281,10 +281,13 @@ class Params:
     """Physical and numerical parameters of one simulation."""
 
     def __init__(self, grid, h=1.0, rho=1.0, eta=1.0, kT=0.0, dt=0.05, kernel=4,
-                 seed=1, slip="visc", advection=True):
+                 seed=1, slip="visc", advection=True, trap_k=0.0, trap_center=(0.0, 0.0, 0.0)):
         self.grid = tuple(int(n) for n in grid)            # (Nx, Ny, Nz)
         self.h, self.rho, self.eta, self.kT, self.dt = float(h), float(rho), float(eta), float(kT), float(dt)
         self.kernel, self.seed, self.slip, self.advection = int(kernel), int(seed), slip, bool(advection)
+        # harmonic trap V = k r^2 / 2 of the temporal accuracy test (Sec. III.D)
+        self.trap_k = float(trap_k)
+        self.trap_center = np.asarray(trap_center, dtype=np.float64).reshape(3)
 
     @property
     def shape(self):
@@ -349,6 +352,18 @@ def explicit_rhs(v, adv_prev, step, prm):
     return r, adv_n
 
 
+def trap_force(q, prm):
+    """Force of the harmonic potential V(r) = k r^2 / 2 of the temporal accuracy test
+    (Sec. III.D, the experiment of Eq. E_dt_definition): F = -k (q - c).  Reading: in
+    the periodic box, q - c is the displacement to the nearest image of the centre c."""
+    q = np.atleast_2d(q)
+    if prm.trap_k == 0.0:
+        return np.zeros_like(q)
+    d = q - prm.trap_center
+    d = d - prm.box * np.round(d / prm.box)
+    return -prm.trap_k * d
+
+
 def icm_step(state, prm, trace=None):
     """Advance one ICM step, following the nine steps of Sec. III.C in order.
 
@@ -361,10 +376,11 @@ def icm_step(state, prm, trace=None):
     v, q, me = state.v, state.q, state.me
     nb = q.shape[0]
 
-    # Step 1, Eq. particle_pred: midpoint predictor; constant external forces.
+    # Step 1, Eq. particle_pred: midpoint predictor; forces at q^{n+1/2} (the constant
+    # external forces plus the harmonic trap, if any).
     jv_n = interpolate(v, q, kernel, h)
     q_half = wrap_positions(q + 0.5 * dt * jv_n, box)
-    force = state.force
+    force = state.force + trap_force(q_half, prm)
 
     # Step 2, Eq. provisional_step-1: unperturbed fluid solve.
     r, adv_n = explicit_rhs(v, state.adv_prev, state.step, prm)
@@ -412,5 +428,5 @@ def icm_step(state, prm, trace=None):
     q_new = wrap_positions(q + 0.5 * dt * interpolate(v_new + v, q_half, kernel, h), box)
 
     if trace is not None:
-        trace.update(dict(jv_n=jv_n, q_half=q_half, rhs=r, adv_n=adv_n, v_tilde=v_tilde), **extra)
-    return State(v_new, q_new, u_new, me, force, adv_n, g_new, state.step + 1)
+        trace.update(dict(jv_n=jv_n, q_half=q_half, force_half=force, rhs=r, adv_n=adv_n, v_tilde=v_tilde), **extra)
+    return State(v_new, q_new, u_new, me, state.force, adv_n, g_new, state.step + 1)

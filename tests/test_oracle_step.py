@@ -7,7 +7,10 @@
 * second-order temporal accuracy for neutrally buoyant blobs (Sec. III.D);
 * fluctuation-dissipation: equilibrium variance of the fluid, exact for any dt
   (Sec. III, the fluid solver of the scheme), and of a passive blob, (kT/rho) J P S;
-* J P S ~ (2/3) dV^-1 I within a few percent (Sec. III.A.2, Fig. JPS).
+* J P S ~ (2/3) dV^-1 I within a few percent (Sec. III.A.2, Fig. JPS);
+* the harmonic trap of the temporal accuracy test (Sec. III.D): the force at
+  q^{n+1/2} against hand values, its impulse, and the second-order decay of the
+  error E(dt) of Eq. E_dt_definition for a neutrally buoyant blob.
 """
 import numpy as np
 import pytest
@@ -179,3 +182,60 @@ def test_JPS_close_to_two_thirds_inverse_volume(kernel):
         dI = dvt * m - np.eye(3)
         assert np.abs(np.diag(dI)).max() < 0.05
         assert np.abs(dI - np.diag(np.diag(dI))).max() < 0.005
+
+
+def test_trap_force_hand_values_at_the_midpoint():
+    """F^{n+1/2} = F - k (q^{n+1/2} - c) to the nearest image; with v = 0, q^{n+1/2} = q."""
+    grid = (16, 16, 16)
+    prm = _prm(grid, kT=0.0, dt=0.5, trap_k=0.25, trap_center=(0.0, 0.0, 0.0))
+    q = [[10.0, 1.0, 15.5], [3.0, 8.5, 0.25]]
+    st = icm.State(np.zeros((3, 16, 16, 16)), q, np.zeros((2, 3)), [0.0, 0.0], [[0.1, 0.0, 0.0], [0.0, 0.0, 0.0]])
+    tr = {}
+    icm.icm_step(st, prm, tr)
+    # nearest-image displacements by hand: (-6, 1, -0.5) and (3, -7.5, 0.25)
+    want = np.array([[0.1 + 1.5, -0.25, 0.125], [-0.75, 1.875, -0.0625]])
+    np.testing.assert_allclose(tr["force_half"], want, rtol=0, atol=1e-15)
+
+
+def test_trap_impulse_changes_momentum():
+    """Appendix C: P^{n+1} - P^n = dt sum_i F_i^{n+1/2}, with the trap force at q^{n+1/2}."""
+    grid = (12, 12, 12)
+    st = _state(grid, 5, 77, me_scale=1.0, vamp=0.02, force=0.01)
+    prm = _prm(grid, kT=1e-3, dt=0.1, trap_k=0.05, trap_center=(6.0, 5.0, 7.0))
+    p0 = icm.total_momentum(st, prm)
+    tr = {}
+    st1 = icm.icm_step(st, prm, tr)
+    dP = icm.total_momentum(st1, prm) - p0
+    impulse = prm.dt * tr["force_half"].sum(axis=0)
+    assert np.abs(impulse).max() > 1e-3
+    np.testing.assert_allclose(dP, impulse, rtol=1e-11, atol=1e-15)
+
+
+def trap_trajectory(dt, T, me=0.0, k=0.01, slip="visc"):
+    """Positions after each step of a blob released from rest 10 cells from the trap
+    centre on a 16^3 grid (the setup of Sec. III.D, kT = 0)."""
+    grid = (16, 16, 16)
+    prm = _prm(grid, kT=0.0, dt=dt, kernel=4, slip=slip, trap_k=k, trap_center=(0.0, 0.0, 0.0))
+    st = icm.State(np.zeros((3, 16, 16, 16)), [[10.0, 0.0, 0.0]], [[0.0, 0.0, 0.0]], [me], [[0.0, 0.0, 0.0]])
+    out = []
+    for _ in range(int(round(T / dt))):
+        st = icm.icm_step(st, prm)
+        out.append(st.q[0].copy())
+    return np.array(out)
+
+
+def e_dt(qa, qb, box=16.0):
+    """Eq. E_dt_definition: mean distance between the dt run at step n and the dt/2 run at
+    step 2n (nearest image)."""
+    d = qa - qb[1::2]
+    d -= box * np.round(d / box)
+    return np.linalg.norm(d, axis=1).mean()
+
+
+def test_trap_error_decays_second_order_for_neutral_blob():
+    """Sec. III.D, Fig. convergenceShort (left): second order for m_e = 0."""
+    T = 16.0
+    q = {dt: trap_trajectory(dt, T) for dt in (1.0, 0.5, 0.25)}
+    assert np.linalg.norm(q[0.25][-1] - [10.0, 0.0, 0.0]) > 1e-3     # the blob moved
+    e1, e2 = e_dt(q[1.0], q[0.5]), e_dt(q[0.5], q[0.25])
+    assert 3.2 < e1 / e2 < 4.8
