@@ -109,6 +109,14 @@ icm_status icm_add_blobs(icm_sim* sim, int64_t n, const double* pos, const doubl
  * the next call: force[n_total*3].  Errors: ICM_EINVAL (NULL, non-finite). */
 icm_status icm_set_blob_forces(icm_sim* sim, const double* force);
 
+/* Add to every blob the force of the harmonic potential V(r) = k r^2 / 2 about
+ * center[3] (the temporal accuracy test of Sec. III.D, Eq. E_dt_definition),
+ * evaluated each step at q^{n+1/2}: F_i^{n+1/2} = F_i - k d_i, d_i = q_i^{n+1/2} - center
+ * taken to the nearest periodic image.  k = 0 removes the trap.  The total momentum
+ * bookkeeping includes the trap's impulse.  Errors: ICM_EINVAL (NULL center,
+ * non-finite values, k < 0). */
+icm_status icm_set_blob_trap(icm_sim* sim, double k, const double center[3]);
+
 /* Enqueue nsteps ICM steps (Sec. III.C steps 1-9) on the simulation's stream.
  * Asynchronous: errors detected on the device (ICM_ECFL, ICM_ENONFINITE) are
  * reported by the next icm_sync / icm_read_state.  Errors: ICM_EINVAL (nsteps<0). */

@@ -47,6 +47,7 @@ SIGNATURES = {
     "icm_last_error": (ctypes.c_char_p, []),
     "icm_add_blobs": (_c_i32, [_vp, _c_i64, _dp, _dp, _dp]),
     "icm_set_blob_forces": (_c_i32, [_vp, _dp]),
+    "icm_set_blob_trap": (_c_i32, [_vp, ctypes.c_double, _dp]),
     "icm_step": (_c_i32, [_vp, _c_i64]),
     "icm_sync": (_c_i32, [_vp]),
     "icm_read_state": (_c_i32, [_vp, _dp, _dp, _dp, _dp, ctypes.POINTER(_c_i64)]),
@@ -183,6 +184,11 @@ def icm_add_blobs(sim, pos, vel, excess_mass):
 def icm_set_blob_forces(sim, force):
     f, fp = _f64(force)
     _check(lib().icm_set_blob_forces(sim, fp))
+
+
+def icm_set_blob_trap(sim, k, center):
+    c = np.ascontiguousarray(center, dtype=np.float64).reshape(3)
+    _check(lib().icm_set_blob_trap(sim, float(k), c.ctypes.data_as(_dp)))
 
 
 def icm_step(sim, nsteps=1):
@@ -430,6 +436,9 @@ class Simulation:
 
     def set_forces(self, force):
         icm_set_blob_forces(self.handle, force)
+
+    def set_trap(self, k, center):
+        icm_set_blob_trap(self.handle, k, center)
 
     def step(self, n=1):
         icm_step(self.handle, n)

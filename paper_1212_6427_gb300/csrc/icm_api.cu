@@ -102,7 +102,8 @@ struct icm_sim {
   long long nb = 0, cap = 0;
   double* blob = nullptr;
   double *q = nullptr, *qh = nullptr, *u = nullptr, *me = nullptr, *f = nullptr, *g = nullptr, *w0 = nullptr,
-         *w1 = nullptr, *jvt = nullptr, *du = nullptr, *dp = nullptr, *cdp = nullptr, *src = nullptr;
+         *w1 = nullptr, *jvt = nullptr, *du = nullptr, *dp = nullptr, *cdp = nullptr, *src = nullptr, *fe = nullptr;
+  double trap_k = 0.0, trap_c[3] = {0.0, 0.0, 0.0};   // harmonic trap (Sec. III.D test)
   std::vector<double> me_host, f_host;
   bool any_me = false, any_force = false;
   // row-block bins of the blob work fused into the x passes (register FFT sides)
@@ -226,14 +227,16 @@ BlobParams blob_params(const icm_sim* s) {
   for (int a = 0; a < 3; ++a) {
     p.box[a] = n[a] * s->h;
     p.inv_box[a] = 1.0 / p.box[a];
+    p.trap_c[a] = s->trap_c[a];
   }
+  p.trap_k = s->trap_k;
   return p;
 }
 
 BlobState blob_state(const icm_sim* s) {
   BlobState b;
   b.nb = s->nb;
-  b.q = s->q; b.qh = s->qh; b.u = s->u; b.me = s->me; b.f = s->f; b.g = s->g;
+  b.q = s->q; b.qh = s->qh; b.u = s->u; b.me = s->me; b.f = s->f; b.fe = s->fe; b.g = s->g;
   b.w0 = s->w0; b.w1 = s->w1; b.jvt = s->jvt; b.du = s->du; b.dp = s->dp; b.cdp = s->cdp; b.src = s->src;
   b.scal = s->scal;
   b.err = s->err_dev;
@@ -389,6 +392,8 @@ void enqueue_step(icm_sim* s, Prof* prof) {
     ICM_STAGE((t + ".x_inv").c_str(), S + (mode == OUT_STORE ? F : 3 * F), fft_x_inverse<R>(fc, dst, dst2, mode, st));
   };
 
+  // forces at q^{n+1/2}: the constant ones, or with the trap those the predictor writes
+  const double* fvec = s->nb == 0 ? nullptr : (s->trap_k != 0.0 ? s->fe : (s->any_force ? s->f : nullptr));
   ICM_STAGE("scalars", 0, scalars_before_step(s->scal, s->dt, s->rho, dvf, st));
   // step 1: midpoint predictor (Eq. particle_pred)
   ICM_STAGE("predict", 2 * gath + nb * 72, blob_predict<R>(bp, bs, v, st));
@@ -440,8 +445,7 @@ void enqueue_step(icm_sim* s, Prof* prof) {
       const double out = mode == OUT_STORE ? F : (mode == OUT_ADD ? 2 * F : 0.0);
       ICM_STAGE((t + ".x_inv").c_str(), S + out + blobio, fft_x_inverse_blobs<R>(fc, dst, mode, r, st));
     };
-    passes("rt1", work, s->any_force ? s->f : nullptr, s->rho / s->dt, 0.5 * s->eta, s->scal + SC_K0, v, OUT_STORE,
-           acc1, nullptr);
+    passes("rt1", work, fvec, s->rho / s->dt, 0.5 * s->eta, s->scal + SC_K0, v, OUT_STORE, acc1, nullptr);
     if (s->any_me) {
       // step 4: slip correction and momentum change (Eq. delta_u_nph_visc)
       ICM_STAGE("dp", nb * 264, blob_dp_from(bp, bs, acc1, st));
@@ -461,7 +465,7 @@ void enqueue_step(icm_sim* s, Prof* prof) {
   }
   // step 2: unperturbed fluid solve (Eq. provisional_step-1)
   ICM_STAGE("rhs", 4 * F, explicit_rhs<R>(gp, v, adv, work, s->step_dev, s->hist_dev, st));
-  if (s->any_force) ICM_STAGE("spread", 2 * gath + nb * 48, blob_spread<R>(bp, s->nb, s->qh, s->f, work, st));
+  if (fvec) ICM_STAGE("spread", 2 * gath + nb * 48, blob_spread<R>(bp, s->nb, s->qh, fvec, work, st));
   solve("rt1", work, v, nullptr, OUT_STORE, s->rho / s->dt, 0.5 * s->eta, s->scal + SC_K0);
   if (s->any_me) {
     // step 4: slip correction and momentum change (Eq. delta_u_nph_visc)
@@ -509,16 +513,16 @@ icm_status grow_blobs(icm_sim* s, long long need) {
   if (need <= s->cap) return ICM_OK;
   long long cap = s->cap > 0 ? s->cap : 64;
   while (cap < need) cap *= 2;
-  const long long per = 12 * 3 + 1;  // 12 vector arrays + masses
+  const long long per = 13 * 3 + 1;  // 13 vector arrays + masses
   double* nbuf = (double*)dalloc(s, sizeof(double) * per * cap);
   if (!nbuf) return fail(ICM_ENOMEM, "device allocation of %lld blob slots failed", cap);
   ICM_CK(cudaMemsetAsync(nbuf, 0, sizeof(double) * per * cap, s->stream));
-  double* arrs[12];
-  for (int i = 0; i < 12; ++i) arrs[i] = nbuf + (size_t)i * 3 * cap;
-  double* me = nbuf + (size_t)36 * cap;
+  double* arrs[13];
+  for (int i = 0; i < 13; ++i) arrs[i] = nbuf + (size_t)i * 3 * cap;
+  double* me = nbuf + (size_t)39 * cap;
   if (s->nb > 0) {
-    double* old[12] = {s->q, s->qh, s->u, s->f, s->g, s->w0, s->w1, s->jvt, s->du, s->dp, s->cdp, s->src};
-    for (int i = 0; i < 12; ++i)
+    double* old[13] = {s->q, s->qh, s->u, s->f, s->g, s->w0, s->w1, s->jvt, s->du, s->dp, s->cdp, s->src, s->fe};
+    for (int i = 0; i < 13; ++i)
       ICM_CK(cudaMemcpyAsync(arrs[i], old[i], sizeof(double) * 3 * s->nb, cudaMemcpyDeviceToDevice, s->stream));
     ICM_CK(cudaMemcpyAsync(me, s->me, sizeof(double) * s->nb, cudaMemcpyDeviceToDevice, s->stream));
   }
@@ -544,6 +548,7 @@ icm_status grow_blobs(icm_sim* s, long long need) {
   s->cap = cap;
   s->q = arrs[0]; s->qh = arrs[1]; s->u = arrs[2]; s->f = arrs[3]; s->g = arrs[4]; s->w0 = arrs[5];
   s->w1 = arrs[6]; s->jvt = arrs[7]; s->du = arrs[8]; s->dp = arrs[9]; s->cdp = arrs[10]; s->src = arrs[11];
+  s->fe = arrs[12];
   s->me = me;
   return ICM_OK;
 }
@@ -796,6 +801,17 @@ icm_status icm_set_blob_forces(icm_sim* s, const double* force) {
     invalidate_graph(s);
   }
   // the copies read pageable host memory: they have completed when this returns
+  return ICM_OK;
+}
+
+icm_status icm_set_blob_trap(icm_sim* s, double k, const double center[3]) {
+  if (!s) return fail(ICM_EINVAL, "NULL simulation");
+  if (!center) return fail(ICM_EINVAL, "center must not be NULL");
+  if (!std::isfinite(k) || k < 0) return fail(ICM_EINVAL, "trap constant must be finite and >= 0");
+  if (!finite_all(center, 3)) return fail(ICM_EINVAL, "non-finite trap center");
+  s->trap_k = k;
+  for (int a = 0; a < 3; ++a) s->trap_c[a] = center[a];
+  invalidate_graph(s);
   return ICM_OK;
 }
 
@@ -1181,7 +1197,7 @@ int64_t icm_estimate_device_bytes(const int32_t grid[3], int32_t precision, int6
   const int64_t fields = 3 * (3 * ncell * rs);
   const int64_t spec = 3 * (int64_t)grid[2] * grid[1] * kxp * 2 * rs;
   const int64_t tables = 3 * (int64_t)kMaxSide * (3 * 2 * rs + 4) + 16 * 256;
-  const int64_t blobs = nblobs > 0 ? 37 * cap * 8 + (int64_t)bin_blob_bytes(cap) : 0;
+  const int64_t blobs = nblobs > 0 ? 40 * cap * 8 + (int64_t)bin_blob_bytes(cap) : 0;
   const int64_t bins = 4 * (3 * ((int64_t)grid[1] * grid[2] / 32 + 1) + 1);
   return fields + spec + tables + blobs + bins + 8 * 3 * 1024 + 4096;
 }

@@ -198,24 +198,48 @@ __device__ __forceinline__ double pick3(const double v[3], int a) { return a == 
 
 // Step 1 (Eq. particle_pred): w0 = J^n v^n, q^{n+1/2} = q^n + dt/2 w0; also
 // w1 = J^{n+1/2} v^n, needed by the position update (Eq. update_q) and the full slip.
+// With a harmonic trap (Sec. III.D), the force at q^{n+1/2}, F - k d (d to the nearest
+// image of the centre), goes to fe and dt times its trap part to the prescribed grid
+// sum K0 of the first solve (one atomic per block and component).
 template <typename R, int K>
 __global__ void __launch_bounds__(32 * kWarps) k_predict(BlobParams p, BlobState s, const R* __restrict__ v) {
-  ICM_WARP_SETUP
-  double q[3], w0[3], qh[3], w1[3];
-  load3(s.q, b, q);
-  build_stencil<R, K>(S, q, p, false, lane);
-  gather<R, K>(S, v, p, lane, w0);
-  // every lane needs q^{n+1/2} for the second stencil; lanes 0-2 compute one axis each
-  const int ax = lane < 3 ? lane : 0;
-  const double mine = wrap_pos(fma(0.5 * p.dt, pick3(w0, ax), pick3(q, ax)), p.box[ax], p.inv_box[ax]);
-  for (int a = 0; a < 3; ++a) qh[a] = __shfl_sync(0xffffffffu, mine, a);
-  __syncwarp();
-  build_stencil<R, K>(S, qh, p, false, lane);
-  gather<R, K>(S, v, p, lane, w1);
-  if (lane == 0) {
-    store3(s.w0, b, w0);
-    store3(s.qh, b, qh);
-    store3(s.w1, b, w1);
+  __shared__ WarpStencil<R, K> sten[kWarps];
+  __shared__ double red[kWarps][3];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long b = (long long)blockIdx.x * kWarps + wid;
+  double ftrap = 0.0;
+  if (b < s.nb) {
+    WarpStencil<R, K>& S = sten[wid];
+    double q[3], w0[3], qh[3], w1[3];
+    load3(s.q, b, q);
+    build_stencil<R, K>(S, q, p, false, lane);
+    gather<R, K>(S, v, p, lane, w0);
+    // every lane needs q^{n+1/2} for the second stencil; lanes 0-2 compute one axis each
+    const int ax = lane < 3 ? lane : 0;
+    const double mine = wrap_pos(fma(0.5 * p.dt, pick3(w0, ax), pick3(q, ax)), p.box[ax], p.inv_box[ax]);
+    for (int a = 0; a < 3; ++a) qh[a] = __shfl_sync(0xffffffffu, mine, a);
+    __syncwarp();
+    build_stencil<R, K>(S, qh, p, false, lane);
+    gather<R, K>(S, v, p, lane, w1);
+    if (lane == 0) {
+      store3(s.w0, b, w0);
+      store3(s.qh, b, qh);
+      store3(s.w1, b, w1);
+    }
+    if (p.trap_k != 0.0 && lane < 3) {
+      double d = mine - p.trap_c[lane];
+      d = fma(-p.box[lane], rint(d * p.inv_box[lane]), d);
+      ftrap = -p.trap_k * d;
+      s.fe[3 * b + lane] = s.f[3 * b + lane] + ftrap;
+    }
+  }
+  if (p.trap_k == 0.0) return;   // uniform over the launch
+  if (lane < 3) red[wid][lane] = ftrap;
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int w = 0; w < kWarps; ++w) t += red[w][threadIdx.x];
+    atomicAdd(&s.scal[SC_K0 + threadIdx.x], p.dt * t);
   }
 }
 

@@ -135,6 +135,8 @@ struct BlobParams {
   double inv_h;    // 1/h
   double box[3];   // periodic box lengths N h
   double inv_box[3];
+  double trap_k;   // harmonic trap V = k r^2 / 2 about trap_c (0: none)
+  double trap_c[3];
 };
 
 struct BlobState {
@@ -143,7 +145,8 @@ struct BlobState {
   double* qh;       // midpoint q^{n+1/2}
   double* u;        // velocities
   const double* me; // excess masses
-  const double* f;  // external forces
+  const double* f;  // external forces (constant part)
+  double* fe;       // forces at q^{n+1/2} (constant part + trap), written by the predictor
   double* g;        // lagged J L dv (slip term)
   double* w0;       // J^n v^n at q^n
   double* w1;       // J^{n+1/2} v^n

@@ -35,6 +35,8 @@ def make_sim(prm, state, precision):
     if state.q.shape[0]:
         sim.add_blobs(state.q, state.u, state.me)
         sim.set_forces(state.force)
+    if prm.trap_k != 0.0:
+        sim.set_trap(prm.trap_k, prm.trap_center)
     sim.write(state.q, state.u, state.v.ravel(), None if state.adv_prev is None else state.adv_prev.ravel(),
               state.slip_g, state.step)
     return sim
