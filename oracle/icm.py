@@ -260,7 +260,9 @@ def spectral_solve(rhs, a, b, h):
     (P^ w)_a = w_a - conj(d_a) (sum_b d_b w_b) / sum_b |d_b|^2 and P^ = I at k = 0.
     With (a, b) = (rho/dt, eta/2) this is the provisional solve (Eq.
     provisional_step-1); (1, 0) is the projection of step 5; (rho, dt eta/2) the
-    viscous correction (Eq. dv_eq_modified-1).
+    viscous correction (Eq. dv_eq_modified-1).  (0, eta) is the steady Stokes solve
+    of the mobility -J L^-1 S (Sec. III.A.2); there the k = 0 mode has no solution
+    on the periodic grid and is set to zero (zero mean flow; a reading).
     """
     shape = rhs.shape[1:]
     d = _symbols(shape, h)
@@ -270,8 +272,47 @@ def spectral_solve(rhs, a, b, h):
     safe = np.where(dd == 0.0, 1.0, dd)
     ratio = np.where(dd == 0.0, 0.0, div / safe)
     denom = a + b * dd
-    return np.stack([np.real(np.fft.ifftn((rh[c] - np.conj(d[c]) * ratio) / denom))
+    inv = np.where(denom == 0.0, 0.0, 1.0 / np.where(denom == 0.0, 1.0, denom))
+    return np.stack([np.real(np.fft.ifftn((rh[c] - np.conj(d[c]) * ratio) * inv))
                      for c in range(DIM)])
+
+
+# ---------------------------------------------------------------------------
+# Blob-grid operators of Sec. III.A.2 (translational invariance, mobility)
+# ---------------------------------------------------------------------------
+def coupling_matrix(qi, qj, grid, kernel, h, a=1.0, b=0.0):
+    """3x3 matrix M_ab = e_a . J_i (a - b L)^-1 P S_j e_b: column b is the interpolation
+    at qi of the solve of the spread of a unit force e_b at qj.  (a, b) = (1, 0) gives
+    J_i P S_j; (0, eta) the Stokes mobility -J_i (eta L)^-1 P S_j."""
+    shape = (grid[2], grid[1], grid[0])
+    qi = np.atleast_2d(qi)
+    qj = np.atleast_2d(qj)
+    m = np.zeros((DIM, DIM))
+    for col in range(DIM):
+        F = np.zeros((1, DIM))
+        F[0, col] = 1.0
+        x = spectral_solve(spread(F, qj, kernel, h, shape), a, b, h)
+        m[:, col] = interpolate(x, qi, kernel, h)[0]
+    return m
+
+
+def jps_deviation(q, grid, kernel, h):
+    """dI(q) = (3/2) dV (J P S)(q) - I (Sec. III.A.2, Fig. JPS: d dV J P S / (d-1) ~ I)."""
+    dv = blob_volume(kernel, h)
+    return 1.5 * dv * coupling_matrix(q, q, grid, kernel, h) - np.eye(DIM)
+
+
+def mobility(q, grid, kernel, h, eta):
+    """Single-blob mobility mu(q) = -J L^-1 S of the steady Stokes problem eta L v - grad pi
+    + S F = 0, div v = 0 (Sec. III.A.2), zero mean flow."""
+    return coupling_matrix(q, q, grid, kernel, h, a=0.0, b=eta)
+
+
+def hydrodynamic_radius(mu, eta, box_length):
+    """R_H of an isolated sphere from the mobility mu of its periodic images on a cubic
+    lattice of side L: 6 pi eta mu = 1/R_H - 2.8373/L (Hasimoto's first-order lattice
+    correction, J. Fluid Mech. 5 (1959); the paper extrapolates R_H without saying how)."""
+    return 1.0 / (6.0 * np.pi * eta * mu + 2.8373 / box_length)
 
 
 # ---------------------------------------------------------------------------
