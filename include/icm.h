@@ -213,9 +213,21 @@ icm_status icm_op_spread(icm_sim* sim, int64_t nb, const double* pos, const doub
 /* Helmholtz solve + projection by 3D FFT (Sec. III.D): solves
  * (a I - b L) x + G pi = rhs, D x = 0, i.e. x^ = P^ rhs^ / (a + b |d|^2) with P = I on
  * the mean.  (a, b) = (rho/dt, eta/2) is Eq. provisional_step-1, (1, 0) the
- * projection of step 5, (rho, dt eta/2) Eq. dv_eq_modified-1.  a > 0, b >= 0. */
+ * projection of step 5, (rho, dt eta/2) Eq. dv_eq_modified-1.  a = 0, b = eta is
+ * the steady Stokes solve of the mobility of Sec. III.A.2; there the mean mode has no
+ * solution and is set to zero.  a >= 0, b >= 0, a + b > 0; Errors: ICM_EINVAL. */
 icm_status icm_op_spectral_solve(icm_sim* sim, double a, double b, const double* rhs,
                                  double* out);
+
+/* Blob-grid coupling matrices of Sec. III.A.2: for each pair p, the 3x3 matrix
+ *   out[9p + 3r + c] = e_r . J(qi_p) (a I - b L)^-1 P S(qj_p) e_c
+ * (spread of a unit force e_c at qj_p, solve as icm_op_spectral_solve, interpolation
+ * at qi_p), row-major.  (a, b) = (1, 0) gives J_i P S_j (translational invariance,
+ * Fig. JPS); (0, eta) the Stokes mobility -J_i (eta L)^-1 P S_j.  qi, qj: n x 3
+ * positions (host).  Uses the simulation's grid, kernel and scratch; synchronises.
+ * Errors: ICM_EINVAL (NULL, n < 0, non-finite positions, a, b as above), ICM_ENOMEM. */
+icm_status icm_op_coupling(icm_sim* sim, int64_t n, const double* qi, const double* qj, double a, double b,
+                           double* out);
 
 /* Dense explicit right-hand side of Eq. provisional_step-1 at time level `step`:
  * r = (rho/dt) v + (eta/2) L v + div Sigma^n - (3/2 A^n - 1/2 A^{n-1}), and A^n.

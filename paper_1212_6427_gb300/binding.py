@@ -73,6 +73,7 @@ SIGNATURES = {
     "icm_op_interpolate_laplacian": (_c_i32, [_vp, _c_i64, _dp, _dp, _dp]),
     "icm_op_spread": (_c_i32, [_vp, _c_i64, _dp, _dp, _dp]),
     "icm_op_spectral_solve": (_c_i32, [_vp, _c_d, _c_d, _dp, _dp]),
+    "icm_op_coupling": (_c_i32, [_vp, _c_i64, _dp, _dp, _c_d, _c_d, _dp]),
     "icm_op_explicit_rhs": (_c_i32, [_vp, _dp, _dp, _c_i64, _dp, _dp]),
     "icm_op_stress_normals": (_c_i32, [_vp, _c_i64, _dp]),
     "icm_op_philox": (_c_i32, [_c_i64, _c_u32, _c_u32, _c_u32, _c_u32, _c_u32, _c_u32, ctypes.POINTER(_c_u32)]),
@@ -298,6 +299,18 @@ def icm_op_spectral_solve(sim, a, b, rhs):
     out, op = _out(r.size)
     _check(lib().icm_op_spectral_solve(sim, float(a), float(b), rp, op))
     return out
+
+
+def icm_op_coupling(sim, qi, qj, a, b):
+    """(n, 3, 3) matrices J(qi) (a - b L)^-1 P S(qj) of each pair of positions."""
+    qi = np.ascontiguousarray(qi, dtype=np.float64).reshape(-1, 3)
+    qj = np.ascontiguousarray(qj, dtype=np.float64).reshape(-1, 3)
+    n = qi.shape[0]
+    if qj.shape[0] != n:
+        raise ValueError("qi and qj must have the same number of positions")
+    out, op = _out(9 * n)
+    _check(lib().icm_op_coupling(sim, n, qi.ctypes.data_as(_dp), qj.ctypes.data_as(_dp), float(a), float(b), op))
+    return out.reshape(n, 3, 3)
 
 
 def icm_op_explicit_rhs(sim, fluid_v, adv_prev, step):

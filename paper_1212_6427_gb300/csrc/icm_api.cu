@@ -628,6 +628,24 @@ icm_status check_device_errors(icm_sim* s) {
 
 }  // namespace
 
+namespace {
+template <typename R>
+void enqueue_coupling(icm_sim* s, long long n, const double* qdev, const double* unit, double a, double b,
+                      double* outdev) {
+  const BlobParams bp = blob_params(s);
+  const FftCtx<R> fc = fft_ctx<R>(s);
+  R* work = (R*)s->work;
+  const size_t fbytes = 3 * (size_t)s->ncell * sizeof(R);
+  for (long long p = 0; p < n; ++p)
+    for (int c = 0; c < 3; ++c) {
+      cudaMemsetAsync(work, 0, fbytes, s->stream);
+      blob_spread<R>(bp, 1, qdev + 3 * (n + p), unit + 3 * c, work, s->stream);
+      spectral_solve<R>(fc, work, work, nullptr, OUT_STORE, a, b, nullptr, 0.0, s->stream);
+      blob_interp<R>(bp, 1, qdev + 3 * p, work, false, outdev + 9 * p + 3 * c, s->stream);   // column c
+    }
+}
+}  // namespace
+
 extern "C" {
 
 icm_status icm_set_default_allocator(icm_alloc_fn alloc, icm_free_fn release, void* ctx) {
@@ -1014,7 +1032,8 @@ icm_status icm_op_spread(icm_sim* s, int64_t nb, const double* pos, const double
 
 icm_status icm_op_spectral_solve(icm_sim* s, double a, double b, const double* rhs, double* out) {
   if (!s || !rhs || !out) return fail(ICM_EINVAL, "bad arguments");
-  if (!(a > 0) || !(b >= 0) || !std::isfinite(a) || !std::isfinite(b)) return fail(ICM_EINVAL, "need a > 0, b >= 0");
+  if (!(a >= 0) || !(b >= 0) || !(a + b > 0) || !std::isfinite(a) || !std::isfinite(b))
+    return fail(ICM_EINVAL, "need a >= 0, b >= 0, a + b > 0");
   icm_status st = upload_field(s, rhs, s->work);
   if (st != ICM_OK) return st;
   if (s->prec == 32)
@@ -1025,6 +1044,36 @@ icm_status icm_op_spectral_solve(icm_sim* s, double a, double b, const double* r
                            nullptr, 0.0, s->stream);
   ICM_CK(cudaGetLastError());
   return download_field(s, s->work, out);
+}
+
+icm_status icm_op_coupling(icm_sim* s, int64_t n, const double* qi, const double* qj, double a, double b,
+                           double* out) {
+  if (!s || n < 0 || (n > 0 && (!qi || !qj || !out))) return fail(ICM_EINVAL, "bad arguments");
+  if (!(a >= 0) || !(b >= 0) || !(a + b > 0) || !std::isfinite(a) || !std::isfinite(b))
+    return fail(ICM_EINVAL, "need a >= 0, b >= 0, a + b > 0");
+  if (n == 0) return ICM_OK;
+  if (!finite_all(qi, 3 * n) || !finite_all(qj, 3 * n)) return fail(ICM_EINVAL, "non-finite position");
+  std::vector<double> q(6 * (size_t)n);
+  memcpy(q.data(), qi, sizeof(double) * 3 * n);
+  memcpy(q.data() + 3 * n, qj, sizeof(double) * 3 * n);
+  wrap_host(q.data(), 2 * n, s);
+  const double unit[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  Tmp tq(s, sizeof(double) * q.size()), tu(s, sizeof(unit)), to(s, sizeof(double) * 9 * n);
+  if (!tq.p || !tu.p || !to.p) return fail(ICM_ENOMEM, "allocation failed");
+  ICM_CK(cudaMemcpyAsync(tq.p, q.data(), sizeof(double) * q.size(), cudaMemcpyHostToDevice, s->stream));
+  ICM_CK(cudaMemcpyAsync(tu.p, unit, sizeof(unit), cudaMemcpyHostToDevice, s->stream));
+  if (s->prec == 32)
+    enqueue_coupling<float>(s, n, (const double*)tq.p, (const double*)tu.p, a, b, (double*)to.p);
+  else
+    enqueue_coupling<double>(s, n, (const double*)tq.p, (const double*)tu.p, a, b, (double*)to.p);
+  ICM_CK(cudaGetLastError());
+  std::vector<double> colmajor(9 * (size_t)n);
+  ICM_CK(cudaMemcpyAsync(colmajor.data(), to.p, sizeof(double) * 9 * n, cudaMemcpyDeviceToHost, s->stream));
+  ICM_CK(cudaStreamSynchronize(s->stream));
+  for (long long p = 0; p < n; ++p)
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) out[9 * p + 3 * r + c] = colmajor[9 * p + 3 * c + r];
+  return ICM_OK;
 }
 
 icm_status icm_op_explicit_rhs(icm_sim* s, const double* fluid_v, const double* adv_prev, int64_t step,

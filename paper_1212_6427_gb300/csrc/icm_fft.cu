@@ -340,7 +340,8 @@ struct SymParams {
 };
 
 // P^ w / (a + b|d|^2) / ncell on one wave vector: (P^ w)_a = w_a - conj(d_a)(d . w)/|d|^2,
-// identity on the mean mode, whose value is replaced by the FP64 bookkeeping if given.
+// identity on the mean mode, whose value is replaced by the FP64 bookkeeping if given
+// (and which is zero when a = 0).
 template <typename R>
 __device__ __forceinline__ void apply_symbol(cplx_t<R>& c0, cplx_t<R>& c1, cplx_t<R>& c2, cplx_t<R> d0,
                                              cplx_t<R> d1, cplx_t<R> d2, R dd, const SymParams<R>& sp,
@@ -352,7 +353,9 @@ __device__ __forceinline__ void apply_symbol(cplx_t<R>& c0, cplx_t<R>& c1, cplx_
     c1 = csub(c1, cmul(cconj(d1), q));
     c2 = csub(c2, cmul(cconj(d2), q));
   }
-  const R scale = sp.inv_ntot / (sp.a + sp.b * dd);
+  // a = 0 (the steady Stokes solve): the mean mode has no solution and is dropped
+  const R den = sp.a + sp.b * dd;
+  const R scale = den > R(0) ? sp.inv_ntot / den : R(0);
   c0 = cscale(c0, scale);
   c1 = cscale(c1, scale);
   c2 = cscale(c2, scale);
