@@ -78,6 +78,44 @@ def phi(kernel, r):
     raise ValueError("kernel must be 3 or 4")
 
 
+def dphi3(r):
+    """Derivative of the Peskin 3-point function, from its closed form: -r/sqrt(1-3r^2)
+    for |r| <= 1/2; sign(r) (-3 - 3t/sqrt(1-3t^2))/6, t = 1-|r|, for 1/2 <= |r| <= 3/2."""
+    r = np.asarray(r, dtype=np.float64)
+    a = np.abs(r)
+    out = np.zeros_like(r)
+    inner = a <= 0.5
+    outer = (a > 0.5) & (a <= 1.5)
+    out[inner] = -r[inner] / np.sqrt(1.0 - 3.0 * r[inner] ** 2)
+    t = 1.0 - a[outer]
+    out[outer] = np.sign(r[outer]) * (-3.0 - 3.0 * t / np.sqrt(1.0 - 3.0 * t ** 2)) / 6.0
+    return out
+
+
+def dphi4(r):
+    """Derivative of the Peskin 4-point function, from its closed form:
+    sign(r) (-2 + (2-4|r|)/sqrt(1+4|r|-4r^2))/8 for |r| <= 1;
+    sign(r) (-2 - (6-4|r|)/sqrt(-7+12|r|-4r^2))/8 for 1 <= |r| <= 2."""
+    r = np.asarray(r, dtype=np.float64)
+    a = np.abs(r)
+    out = np.zeros_like(r)
+    inner = a <= 1.0
+    outer = (a > 1.0) & (a <= 2.0)
+    ai = a[inner]
+    out[inner] = np.sign(r[inner]) * (-2.0 + (2.0 - 4.0 * ai) / np.sqrt(1.0 + 4.0 * ai - 4.0 * ai ** 2)) / 8.0
+    ao = a[outer]
+    out[outer] = np.sign(r[outer]) * (-2.0 - (6.0 - 4.0 * ao) / np.sqrt(-7.0 + 12.0 * ao - 4.0 * ao ** 2)) / 8.0
+    return out
+
+
+def dphi(kernel, r):
+    if kernel == 3:
+        return dphi3(r)
+    if kernel == 4:
+        return dphi4(r)
+    raise ValueError("kernel must be 3 or 4")
+
+
 def kernel_sum_sq(kernel):
     """sum_k phi^2 along one axis: 1/2 (3-point), 3/8 (4-point)."""
     return {3: 0.5, 4: 0.375}[kernel]
@@ -155,6 +193,31 @@ def spread(force, q, kernel, h, shape):
         (ix, iy, iz), (wx, wy, wz) = _blob_stencil(q, comp, kernel, h, shape)
         wgt = wz[:, :, None, None] * wy[:, None, :, None] * wx[:, None, None, :]
         contrib = wgt * (force[:, comp] / dvf)[:, None, None, None]
+        zz = np.broadcast_to(iz[:, :, None, None], wgt.shape)
+        yy = np.broadcast_to(iy[:, None, :, None], wgt.shape)
+        xx = np.broadcast_to(ix[:, None, None, :], wgt.shape)
+        np.add.at(out[comp], (zz.ravel(), yy.ravel(), xx.ravel()), contrib.ravel())
+    return out
+
+
+def spread_drift(coef, q, kernel, h, shape):
+    """Thermal drift forcing of Appendix B.2 (Eq. thermal_drift, the kernel-derivative
+    form): component a of the field is dV_f^-1 sum_i coef_i d/dq_a phi(q_i - r_k), i.e.
+    (1/h) phi'(s_a) along the component's own axis times phi along the other two
+    (= -coef_i times the gradient of the kernel with respect to r)."""
+    q = np.atleast_2d(np.asarray(q, dtype=np.float64))
+    coef = np.asarray(coef, dtype=np.float64).reshape(q.shape[0])
+    out = np.zeros((DIM,) + tuple(shape))
+    dvf = h ** 3
+    for comp in range(DIM):
+        (ix, iy, iz), wts = _blob_stencil(q, comp, kernel, h, shape)
+        s = q[:, comp] / h                                    # the component's own axis: offset 0
+        nodes, _ = stencil_1d(s, kernel)
+        wts = list(wts)
+        wts[comp] = dphi(kernel, s[:, None] - nodes) / h
+        wx, wy, wz = wts
+        wgt = wz[:, :, None, None] * wy[:, None, :, None] * wx[:, None, None, :]
+        contrib = wgt * (coef / dvf)[:, None, None, None]
         zz = np.broadcast_to(iz[:, :, None, None], wgt.shape)
         yy = np.broadcast_to(iy[:, None, :, None], wgt.shape)
         xx = np.broadcast_to(ix[:, None, None, :], wgt.shape)
@@ -322,13 +385,16 @@ class Params:
     """Physical and numerical parameters of one simulation."""
 
     def __init__(self, grid, h=1.0, rho=1.0, eta=1.0, kT=0.0, dt=0.05, kernel=4,
-                 seed=1, slip="visc", advection=True, trap_k=0.0, trap_center=(0.0, 0.0, 0.0)):
+                 seed=1, slip="visc", advection=True, trap_k=0.0, trap_center=(0.0, 0.0, 0.0),
+                 thermal_drift=False):
         self.grid = tuple(int(n) for n in grid)            # (Nx, Ny, Nz)
         self.h, self.rho, self.eta, self.kT, self.dt = float(h), float(rho), float(eta), float(kT), float(dt)
         self.kernel, self.seed, self.slip, self.advection = int(kernel), int(seed), slip, bool(advection)
         # harmonic trap V = k r^2 / 2 of the temporal accuracy test (Sec. III.D)
         self.trap_k = float(trap_k)
         self.trap_center = np.asarray(trap_center, dtype=np.float64).reshape(3)
+        # thermal drift forcing kT m~_f/m~ d(delta_a)/dq (Appendix B.2, Eq. thermal_drift)
+        self.thermal_drift = bool(thermal_drift)
 
     @property
     def shape(self):
@@ -426,6 +492,10 @@ def icm_step(state, prm, trace=None):
     # Step 2, Eq. provisional_step-1: unperturbed fluid solve.
     r, adv_n = explicit_rhs(v, state.adv_prev, state.step, prm)
     r = r + spread(force, q_half, kernel, h, shape)
+    if prm.thermal_drift and prm.kT > 0.0 and nb > 0:
+        # Appendix B.2: the thermal drift, a forcing at q^{n+1/2} with weight kT m~_f / m~
+        mtf = fluid_dragged_mass(kernel, h, rho)
+        r = r + spread_drift(prm.kT * mtf / (mtf + me), q_half, kernel, h, shape)
     v_tilde = spectral_solve(r, rho / dt, 0.5 * prm.eta, h)
 
     if nb == 0 or np.all(me == 0.0):
