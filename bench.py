@@ -280,7 +280,8 @@ def run_ours(args, rank, world, dist):
     # per-kernel durations: every launch bracketed by CUDA events on the simulation stream
     nprof = min(args.steps, 10)
     prof = sim.profile(nprof)
-    launches_per_step = sum(1 for name, _, _ in prof if kernel_of(name) != "zero")   # memsets are not kernels
+    # kernels per stage: memsets are not kernels; the bin build is three (count, scan, fill)
+    launches_per_step = sum({"zero": 0, "bins": 3}.get(kernel_of(name), 1) for name, _, _ in prof)
     per_kernel = {}
     for name, ms_tot, by in prof:
         k = kernel_of(name)

@@ -61,6 +61,9 @@ typedef enum {
 #define ICM_FLAG_SLIP_VISC    0x0   /* slip correction Eq. delta_u_nph_visc (paper's default)   */
 #define ICM_FLAG_SLIP_ZERO    0x2   /* delta u = 0: first-order variant (Sec. III.C)            */
 #define ICM_FLAG_SLIP_FULL    0x4   /* Eq. delta_u_nph: viscous + centring correction           */
+#define ICM_FLAG_THERMAL_DRIFT 0x8  /* add the thermal drift kT m~_f/m~ d(delta_a)/dq at q^{n+1/2}
+                                       to the first solve (Appendix B.2, Eq. thermal_drift,
+                                       kernel-derivative form); no effect at kT = 0       */
 
 /* Allocator used for the device memory of simulations created afterwards.
  * alloc(ctx, bytes, stream) returns a device pointer aligned to >= 256 bytes or

@@ -19,6 +19,7 @@ ICM_OK, ICM_EINVAL, ICM_ENOMEM, ICM_ECUDA, ICM_ECFL, ICM_ENONFINITE, ICM_ETIMEOU
 STATUS_NAMES = {0: "ICM_OK", -1: "ICM_EINVAL", -2: "ICM_ENOMEM", -3: "ICM_ECUDA", -4: "ICM_ECFL",
                 -5: "ICM_ENONFINITE", -6: "ICM_ETIMEOUT", -7: "ICM_EBUSY"}
 FLAG_NO_ADVECTION, FLAG_SLIP_VISC, FLAG_SLIP_ZERO, FLAG_SLIP_FULL = 0x1, 0x0, 0x2, 0x4
+FLAG_THERMAL_DRIFT = 0x8
 
 # name -> (restype, argtypes)
 _c_d = ctypes.c_double

@@ -230,6 +230,7 @@ BlobParams blob_params(const icm_sim* s) {
     p.trap_c[a] = s->trap_c[a];
   }
   p.trap_k = s->trap_k;
+  p.kT = s->kT;
   return p;
 }
 
@@ -394,6 +395,8 @@ void enqueue_step(icm_sim* s, Prof* prof) {
 
   // forces at q^{n+1/2}: the constant ones, or with the trap those the predictor writes
   const double* fvec = s->nb == 0 ? nullptr : (s->trap_k != 0.0 ? s->fe : (s->any_force ? s->f : nullptr));
+  // thermal drift (Appendix B.2) at q^{n+1/2}, added to the right-hand side of the first solve
+  const bool drift = (s->flags & ICM_FLAG_THERMAL_DRIFT) && s->kT > 0.0 && s->nb > 0;
   ICM_STAGE("scalars", 0, scalars_before_step(s->scal, s->dt, s->rho, dvf, st));
   // step 1: midpoint predictor (Eq. particle_pred)
   ICM_STAGE("predict", 2 * gath + nb * 72, blob_predict<R>(bp, bs, v, st));
@@ -428,6 +431,7 @@ void enqueue_step(icm_sim* s, Prof* prof) {
     ICM_STAGE("bins", nb * (24.0 + 2 * geob + 8.0 * kAccPerBlob), build_row_bins<R>(bp, s->nb, s->qh, bins, st));
     // step 2: unperturbed fluid solve (Eq. provisional_step-1), forces spread in x_fwd
     ICM_STAGE("rhs", 4 * F, explicit_rhs<R>(gp, v, adv, work, s->step_dev, s->hist_dev, st));
+    if (drift) ICM_STAGE("drift", 2 * gath + nb * 32, blob_spread_drift<R>(bp, bs, work, st));
     auto passes = [&](const char* tag, const R* src, const double* vec, double a, double b, const double* k0,
                       R* dst, int mode, double* acc, double* acc_lap) {
       std::string t(tag);
@@ -465,6 +469,7 @@ void enqueue_step(icm_sim* s, Prof* prof) {
   }
   // step 2: unperturbed fluid solve (Eq. provisional_step-1)
   ICM_STAGE("rhs", 4 * F, explicit_rhs<R>(gp, v, adv, work, s->step_dev, s->hist_dev, st));
+  if (drift) ICM_STAGE("drift", 2 * gath + nb * 32, blob_spread_drift<R>(bp, bs, work, st));
   if (fvec) ICM_STAGE("spread", 2 * gath + nb * 48, blob_spread<R>(bp, s->nb, s->qh, fvec, work, st));
   solve("rt1", work, v, nullptr, OUT_STORE, s->rho / s->dt, 0.5 * s->eta, s->scal + SC_K0);
   if (s->any_me) {
@@ -673,7 +678,7 @@ icm_status icm_create(const int32_t grid[3], double h, double rho, double eta, d
   if (h <= 0 || rho <= 0 || eta <= 0 || dt <= 0) return fail(ICM_EINVAL, "h, rho, eta and dt must be > 0");
   if (kT < 0) return fail(ICM_EINVAL, "kT must be >= 0");
   if (precision != 32 && precision != 64) return fail(ICM_EINVAL, "precision must be 32 or 64");
-  if (flags & ~(ICM_FLAG_NO_ADVECTION | ICM_FLAG_SLIP_ZERO | ICM_FLAG_SLIP_FULL))
+  if (flags & ~(ICM_FLAG_NO_ADVECTION | ICM_FLAG_SLIP_ZERO | ICM_FLAG_SLIP_FULL | ICM_FLAG_THERMAL_DRIFT))
     return fail(ICM_EINVAL, "unknown flag bits 0x%x", flags);
   if ((flags & ICM_FLAG_SLIP_ZERO) && (flags & ICM_FLAG_SLIP_FULL))
     return fail(ICM_EINVAL, "choose one slip correction");

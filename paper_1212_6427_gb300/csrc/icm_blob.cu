@@ -367,6 +367,45 @@ __global__ void __launch_bounds__(32 * kWarps) k_interp(BlobParams p, long long 
   if (lane == 0) store3(out, b, r);
 }
 
+// Thermal drift (Appendix B.2, Eq. thermal_drift, kernel-derivative form): component c
+// gets kT m~_f/(m~_f + m_e) dV_f^-1 (1/h) phi'(s_c) phi(s_a) phi(s_b) at q^{n+1/2}.
+// One warp per blob; lanes 0-8 build the weights and, for the component's own axis,
+// the derivative weights.
+template <typename R, int K>
+__global__ void __launch_bounds__(32 * kWarps) k_spread_drift(BlobParams p, BlobState s, R* __restrict__ field) {
+  __shared__ WarpStencil<R, K> sten[kWarps];
+  __shared__ R dw[kWarps][3][K];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long b = (long long)blockIdx.x * kWarps + wid;
+  if (b >= s.nb) return;
+  WarpStencil<R, K>& S = sten[wid];
+  double q[3];
+  load3(s.qh, b, q);
+  build_stencil<R, K>(S, q, p, false, lane);
+  if (lane < 3) {   // derivative weights of component `lane` along its own axis (offset 0)
+    const double sa = q[lane] * p.inv_h;
+    const double anc = Peskin<R, K>::anchor(sa);
+    const R frac = (R)(sa - anc);
+#pragma unroll
+    for (int a = 0; a < K; ++a) dw[wid][lane][a] = Peskin<R, K>::dphi(frac + R(1 - a)) * (R)p.inv_h;
+  }
+  __syncwarp();
+  const double mtf = p.mtf;
+  const R amp = (R)(p.kT * mtf / (mtf + s.me[b]) / (p.h * p.h * p.h));
+  constexpr int W3 = K * K * K, ITEMS = 3 * W3;
+  for (int it = lane; it < ITEMS; it += 32) {
+    const int c = it / W3, r = it - c * W3;
+    const int a = r % K, bb = (r / K) % K, cz = r / (K * K);
+    const int ix = wrap_add(S.first[c][0], a, p.nx);
+    const int iy = wrap_add(S.first[c][1], bb, p.ny);
+    const int iz = wrap_add(S.first[c][2], cz, p.nz);
+    const R wx = c == 0 ? dw[wid][0][a] : S.w[c][0][a];
+    const R wy = c == 1 ? dw[wid][1][bb] : S.w[c][1][bb];
+    const R wz = c == 2 ? dw[wid][2][cz] : S.w[c][2][cz];
+    atomicAdd(field + c * p.ncell + ix + (long long)p.nx * (iy + (long long)p.ny * iz), wx * wy * wz * amp);
+  }
+}
+
 inline unsigned nblocks(long long nb) { return (unsigned)((nb + kWarps - 1) / kWarps); }
 
 // ---------------------------------------------------------------------------
@@ -552,13 +591,23 @@ void blob_interp(const BlobParams& p, long long nb, const double* q, const R* fi
               (k_interp<R, 4><<<nblocks(nb), 32 * kWarps, 0, st>>>(p, nb, q, field, laplacian ? 1 : 0, out)))
 }
 
+template <typename R>
+void blob_spread_drift(const BlobParams& p, BlobState s, R* field, cudaStream_t st) {
+  if (s.nb <= 0) return;
+  if (p.kernel == 3)
+    k_spread_drift<R, 3><<<nblocks(s.nb), 32 * kWarps, 0, st>>>(p, s, field);
+  else
+    k_spread_drift<R, 4><<<nblocks(s.nb), 32 * kWarps, 0, st>>>(p, s, field);
+}
+
 #define ICM_INST(R)                                                                                            \
   template void blob_predict<R>(const BlobParams&, BlobState, const R*, cudaStream_t);                        \
   template void blob_spread<R>(const BlobParams&, long long, const double*, const double*, R*, cudaStream_t); \
   template void blob_momentum_change<R>(const BlobParams&, BlobState, const R*, cudaStream_t);                \
   template void blob_inertial<R>(const BlobParams&, BlobState, const R*, cudaStream_t);                       \
   template void blob_finish<R>(const BlobParams&, BlobState, const R*, const R*, bool, cudaStream_t);          \
-  template void blob_interp<R>(const BlobParams&, long long, const double*, const R*, bool, double*, cudaStream_t);
+  template void blob_interp<R>(const BlobParams&, long long, const double*, const R*, bool, double*, cudaStream_t); \
+  template void blob_spread_drift<R>(const BlobParams&, BlobState, R*, cudaStream_t);
 ICM_INST(float)
 ICM_INST(double)
 #undef ICM_INST

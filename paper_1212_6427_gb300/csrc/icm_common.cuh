@@ -130,6 +130,17 @@ template <typename R> struct Peskin<R, 3> {
     }
     return R(0);
   }
+  // derivative: -r/sqrt(1-3r^2) inside, sign(r)(-3 - 3t/sqrt(1-3t^2))/6, t = 1-|r|, outside
+  __device__ __forceinline__ static R dphi(R r) {
+    const R a = fabs(r);
+    if (a <= R(0.5)) return -r / sqrt(R(1) - R(3) * r * r);
+    if (a <= R(1.5)) {
+      const R t = R(1) - a;
+      const R d = (R(-3) - R(3) * t / sqrt(R(1) - R(3) * t * t)) / R(6);   // d phi / d|r|
+      return r < R(0) ? -d : d;
+    }
+    return R(0);
+  }
   // first node of the support: round-half-up(s) - 1
   __device__ __forceinline__ static long long first(double s) { return (long long)floor(s + 0.5) - 1; }
   // the cell that fixes the support (its node 'first' + 1), as a double: round-half-up(s)
@@ -142,6 +153,19 @@ template <typename R> struct Peskin<R, 4> {
     if (r <= R(1)) return (R(3) - R(2) * r + rsqrt0<R>(R(1) + R(4) * r - R(4) * r * r)) / R(8);
     if (r <= R(2)) return (R(5) - R(2) * r - rsqrt0<R>(R(-7) + R(12) * r - R(4) * r * r)) / R(8);
     return R(0);
+  }
+  // derivative: sign(r)(-2 + (2-4|r|)/sqrt(1+4|r|-4r^2))/8 inside,
+  // sign(r)(-2 - (6-4|r|)/sqrt(-7+12|r|-4r^2))/8 outside
+  __device__ __forceinline__ static R dphi(R r) {
+    const R a = fabs(r);
+    R d;   // d phi / d|r|
+    if (a <= R(1))
+      d = (R(-2) + (R(2) - R(4) * a) / sqrt(R(1) + R(4) * a - R(4) * a * a)) / R(8);
+    else if (a <= R(2))
+      d = (R(-2) - (R(6) - R(4) * a) / sqrt(R(-7) + R(12) * a - R(4) * a * a)) / R(8);
+    else
+      return R(0);
+    return r < R(0) ? -d : d;
   }
   __device__ __forceinline__ static long long first(double s) { return (long long)floor(s) - 1; }
   __device__ __forceinline__ static double anchor(double s) { return floor(s); }

@@ -135,6 +135,7 @@ struct BlobParams {
   double inv_h;    // 1/h
   double box[3];   // periodic box lengths N h
   double inv_box[3];
+  double kT;       // thermal energy (the thermal drift's weight)
   double trap_k;   // harmonic trap V = k r^2 / 2 about trap_c (0: none)
   double trap_c[3];
 };
@@ -177,6 +178,9 @@ template <typename R> void blob_finish(const BlobParams& p, BlobState s, const R
                                        bool inertial, cudaStream_t st);
 template <typename R> void blob_interp(const BlobParams& p, long long nb, const double* q, const R* field,
                                        bool laplacian, double* out, cudaStream_t st);
+// Thermal drift (Appendix B.2, Eq. thermal_drift): adds kT m~_f/(m~_f + m_e) dV_f^-1
+// d/dq_a phi(q^{n+1/2} - r) to component a of field (atomics).
+template <typename R> void blob_spread_drift(const BlobParams& p, BlobState s, R* field, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Blob work fused into the x passes (sides with register FFT kernels)

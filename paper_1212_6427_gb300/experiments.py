@@ -6,6 +6,10 @@
 * Translational invariance of J P S (Sec. III.A.2, Fig. JPS left): statistics of
   dI(q) = (3/2) dV (J P S)(q) - I over random positions q.
 * Pair coupling (Fig. JPS right): (3/2) dV J_i P S_j for two blobs a distance l apart.
+* Thermal drift bias (Appendix B.2, Fig. DriftBias): freely diffusing, neutrally buoyant,
+  non-interacting blobs at equilibrium should fill a grid cell uniformly; without the
+  thermal drift forcing they favour the cell corners.  Reported: the ratio of the
+  occupation of the corner and centre octants of the cell (each 1/8 of its volume).
 * Single-blob mobility mu = -J L^-1 S of the steady Stokes problem and the effective
   hydrodynamic radius, from 6 pi eta mu = 1/R_H - 2.8373/L (the first-order lattice
   correction of a cubic array of spheres, Hasimoto 1959).
@@ -14,6 +18,7 @@
     python -m paper_1212_6427_gb300.experiments jps --grid 32 --kernel 3
     python -m paper_1212_6427_gb300.experiments pair --grid 32 --kernel 3
     python -m paper_1212_6427_gb300.experiments radius --grid 32 --kernel 3
+    python -m paper_1212_6427_gb300.experiments drift --grid 16 --kernel 3
 """
 import argparse
 import json
@@ -21,7 +26,7 @@ import math
 
 import numpy as np
 
-from .binding import Simulation, icm_op_coupling
+from .binding import FLAG_THERMAL_DRIFT, Simulation, icm_op_coupling
 
 HASIMOTO = 2.8373   # first-order coefficient of the periodic-lattice mobility correction
 
@@ -116,9 +121,41 @@ def hydrodynamic_radius(grid=(32, 32, 32), kernel=3, npos=16, seed=2, eta=1.0, p
             "mu_rel_spread": float(mus.std() / mu), "R_H": 1.0 / (6.0 * math.pi * eta * mu + HASIMOTO / L)}
 
 
+def drift_bias(grid=(16, 16, 16), kernel=3, nblobs=100, kT=1.0, dt=0.05, steps=100000, sample_every=10,
+               drift=True, seed=3, precision=32):
+    """Occupation of the corner and centre octants of the grid cell by the fractional
+    positions q/h - floor(q/h) of neutrally buoyant, non-interacting blobs (h = rho =
+    eta = 1, so the viscous CFL number is dt), sampled every `sample_every` steps after
+    a tenth of the run.  Returns the ratio corner/centre and its binomial error."""
+    rng = np.random.default_rng(seed)
+    q0 = rng.uniform(0.0, 1.0, size=(nblobs, 3)) * np.asarray(grid, dtype=float)
+    sim = Simulation(grid, 1.0, 1.0, 1.0, kT, dt, kernel, seed, precision, FLAG_THERMAL_DRIFT if drift else 0)
+    corner = centre = samples = 0
+    try:
+        sim.add_blobs(q0, None, np.zeros(nblobs))
+        burn = steps // 10
+        sim.step(burn)
+        for _ in range((steps - burn) // sample_every):
+            sim.step(sample_every)
+            f = sim.read()["pos"]
+            f = f - np.floor(f)
+            d_node = np.abs(f - np.round(f))
+            corner += int(np.all(d_node < 0.25, axis=1).sum())
+            centre += int(np.all(np.abs(f - 0.5) < 0.25, axis=1).sum())
+            samples += nblobs
+    finally:
+        sim.close()
+    ratio = corner / max(centre, 1)
+    err = ratio * math.sqrt(1.0 / max(corner, 1) + 1.0 / max(centre, 1))
+    return {"grid": list(grid), "kernel": kernel, "blobs": nblobs, "kT": kT, "dt": dt, "steps": steps,
+            "thermal_drift": drift, "samples": samples, "corner_fraction": corner / samples,
+            "centre_fraction": centre / samples, "corner_over_centre": ratio, "ratio_error_uncorrelated": err}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("experiment", choices=["trap", "jps", "pair", "radius"])
+    ap.add_argument("experiment", choices=["trap", "jps", "pair", "radius", "drift"])
+    ap.add_argument("--steps", type=int, default=100000)
     ap.add_argument("--precision", type=int, default=64, choices=[32, 64])
     ap.add_argument("--grid", type=int, default=32)
     ap.add_argument("--kernel", type=int, default=3, choices=[3, 4])
@@ -132,6 +169,8 @@ def main(argv=None):
     elif args.experiment == "pair":
         rows = [pair_coupling(g, args.kernel, direction=d, precision=args.precision)
                 for d in ((1.0, 0.0, 0.0), (1.0, 1.0, 1.0))]
+    elif args.experiment == "drift":
+        rows = [drift_bias(g, args.kernel, steps=args.steps, drift=d, precision=args.precision) for d in (False, True)]
     else:
         rows = [hydrodynamic_radius(g, args.kernel, min(args.positions, 32), precision=args.precision)]
     for r in rows:

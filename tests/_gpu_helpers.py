@@ -25,6 +25,8 @@ def min_image(d, box):
 def flags_of(prm):
     f = 0 if prm.advection else 0x1
     f |= {"visc": 0x0, "zero": 0x2, "full": 0x4}[prm.slip]
+    if prm.thermal_drift:
+        f |= 0x8
     return f
 
 
