@@ -386,7 +386,7 @@ class Params:
 
     def __init__(self, grid, h=1.0, rho=1.0, eta=1.0, kT=0.0, dt=0.05, kernel=4,
                  seed=1, slip="visc", advection=True, trap_k=0.0, trap_center=(0.0, 0.0, 0.0),
-                 thermal_drift=False):
+                 thermal_drift=False, wca_epsilon=0.0, wca_sigma=1.0):
         self.grid = tuple(int(n) for n in grid)            # (Nx, Ny, Nz)
         self.h, self.rho, self.eta, self.kT, self.dt = float(h), float(rho), float(eta), float(kT), float(dt)
         self.kernel, self.seed, self.slip, self.advection = int(kernel), int(seed), slip, bool(advection)
@@ -395,6 +395,8 @@ class Params:
         self.trap_center = np.asarray(trap_center, dtype=np.float64).reshape(3)
         # thermal drift forcing kT m~_f/m~ d(delta_a)/dq (Appendix B.2, Eq. thermal_drift)
         self.thermal_drift = bool(thermal_drift)
+        # purely repulsive truncated Lennard-Jones (WCA) pair potential (Sec. IV.A, Eq. WCA)
+        self.wca_epsilon, self.wca_sigma = float(wca_epsilon), float(wca_sigma)
 
     @property
     def shape(self):
@@ -471,6 +473,39 @@ def trap_force(q, prm):
     return -prm.trap_k * d
 
 
+def wca_energy(q, prm):
+    """U = sum over pairs i < j of V(r_ij), V(r) = 4 eps ((s/r)^12 - (s/r)^6) + eps for
+    r < 2^(1/6) s, 0 beyond (Sec. IV.A, Eq. WCA); r_ij to the nearest image."""
+    q = np.atleast_2d(q)
+    eps, sig = prm.wca_epsilon, prm.wca_sigma
+    u = 0.0
+    for i in range(q.shape[0]):
+        d = q[i] - q[i + 1:]
+        d -= prm.box * np.round(d / prm.box)
+        r = np.sqrt((d * d).sum(axis=1))
+        r = r[r < 2.0 ** (1.0 / 6.0) * sig]
+        u += np.sum(4.0 * eps * ((sig / r) ** 12 - (sig / r) ** 6) + eps)
+    return u
+
+
+def wca_force(q, prm):
+    """F_i = -dU/dq_i of the WCA potential: sum_j 24 eps (2 s^12/r^14 - s^6/r^8) d_ij over
+    the pairs within the cut-off, d_ij = q_i - q_j to the nearest image (all pairs)."""
+    q = np.atleast_2d(q)
+    nb = q.shape[0]
+    if prm.wca_epsilon == 0.0 or nb < 2:
+        return np.zeros_like(q)
+    eps, sig = prm.wca_epsilon, prm.wca_sigma
+    d = q[:, None, :] - q[None, :, :]
+    d -= prm.box * np.round(d / prm.box)
+    r2 = (d * d).sum(axis=2)
+    np.fill_diagonal(r2, np.inf)
+    inside = r2 < (2.0 ** (1.0 / 6.0) * sig) ** 2
+    s6 = np.where(inside, sig ** 6 / r2 ** 3, 0.0)
+    mag = np.where(inside, 24.0 * eps * (2.0 * s6 * s6 - s6) / r2, 0.0)
+    return (mag[:, :, None] * d).sum(axis=1)
+
+
 def icm_step(state, prm, trace=None):
     """Advance one ICM step, following the nine steps of Sec. III.C in order.
 
@@ -484,10 +519,10 @@ def icm_step(state, prm, trace=None):
     nb = q.shape[0]
 
     # Step 1, Eq. particle_pred: midpoint predictor; forces at q^{n+1/2} (the constant
-    # external forces plus the harmonic trap, if any).
+    # external forces plus the harmonic trap and the WCA pair forces, if any).
     jv_n = interpolate(v, q, kernel, h)
     q_half = wrap_positions(q + 0.5 * dt * jv_n, box)
-    force = state.force + trap_force(q_half, prm)
+    force = state.force + trap_force(q_half, prm) + wca_force(q_half, prm)
 
     # Step 2, Eq. provisional_step-1: unperturbed fluid solve.
     r, adv_n = explicit_rhs(v, state.adv_prev, state.step, prm)
