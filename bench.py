@@ -281,7 +281,7 @@ def run_ours(args, rank, world, dist):
     nprof = min(args.steps, 10)
     prof = sim.profile(nprof)
     # kernels per stage: memsets are not kernels; the bin build is three (count, scan, fill)
-    launches_per_step = sum({"zero": 0, "bins": 3}.get(kernel_of(name), 1) for name, _, _ in prof)
+    launches_per_step = sum({"zero": 0, "bins": 3, "wca": 4}.get(kernel_of(name), 1) for name, _, _ in prof)
     per_kernel = {}
     for name, ms_tot, by in prof:
         k = kernel_of(name)

@@ -120,6 +120,14 @@ icm_status icm_set_blob_forces(icm_sim* sim, const double* force);
  * non-finite values, k < 0). */
 icm_status icm_set_blob_trap(icm_sim* sim, double k, const double center[3]);
 
+/* Add the forces of the purely repulsive truncated Lennard-Jones (WCA) pair potential
+ * V(r) = 4 eps ((sigma/r)^12 - (sigma/r)^6) + eps for r < 2^(1/6) sigma, 0 beyond
+ * (Sec. IV.A, Eq. WCA), between every pair of blobs (nearest periodic image), evaluated
+ * each step at q^{n+1/2} through a cell list.  epsilon = 0 removes them.  Errors:
+ * ICM_EINVAL (non-finite, epsilon < 0, sigma <= 0, a box side shorter than twice the
+ * cut-off), ICM_ENOMEM. */
+icm_status icm_set_blob_wca(icm_sim* sim, double epsilon, double sigma);
+
 /* Enqueue nsteps ICM steps (Sec. III.C steps 1-9) on the simulation's stream.
  * Asynchronous: errors detected on the device (ICM_ECFL, ICM_ENONFINITE) are
  * reported by the next icm_sync / icm_read_state.  Errors: ICM_EINVAL (nsteps<0). */

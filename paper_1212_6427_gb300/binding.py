@@ -49,6 +49,7 @@ SIGNATURES = {
     "icm_add_blobs": (_c_i32, [_vp, _c_i64, _dp, _dp, _dp]),
     "icm_set_blob_forces": (_c_i32, [_vp, _dp]),
     "icm_set_blob_trap": (_c_i32, [_vp, ctypes.c_double, _dp]),
+    "icm_set_blob_wca": (_c_i32, [_vp, ctypes.c_double, ctypes.c_double]),
     "icm_step": (_c_i32, [_vp, _c_i64]),
     "icm_sync": (_c_i32, [_vp]),
     "icm_read_state": (_c_i32, [_vp, _dp, _dp, _dp, _dp, ctypes.POINTER(_c_i64)]),
@@ -191,6 +192,10 @@ def icm_set_blob_forces(sim, force):
 def icm_set_blob_trap(sim, k, center):
     c = np.ascontiguousarray(center, dtype=np.float64).reshape(3)
     _check(lib().icm_set_blob_trap(sim, float(k), c.ctypes.data_as(_dp)))
+
+
+def icm_set_blob_wca(sim, epsilon, sigma):
+    _check(lib().icm_set_blob_wca(sim, float(epsilon), float(sigma)))
 
 
 def icm_step(sim, nsteps=1):
@@ -453,6 +458,9 @@ class Simulation:
 
     def set_trap(self, k, center):
         icm_set_blob_trap(self.handle, k, center)
+
+    def set_wca(self, epsilon, sigma):
+        icm_set_blob_wca(self.handle, epsilon, sigma)
 
     def step(self, n=1):
         icm_step(self.handle, n)

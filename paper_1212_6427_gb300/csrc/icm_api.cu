@@ -104,6 +104,10 @@ struct icm_sim {
   double *q = nullptr, *qh = nullptr, *u = nullptr, *me = nullptr, *f = nullptr, *g = nullptr, *w0 = nullptr,
          *w1 = nullptr, *jvt = nullptr, *du = nullptr, *dp = nullptr, *cdp = nullptr, *src = nullptr, *fe = nullptr;
   double trap_k = 0.0, trap_c[3] = {0.0, 0.0, 0.0};   // harmonic trap (Sec. III.D test)
+  double wca_eps = 0.0, wca_sigma = 1.0;              // WCA pair potential (Sec. IV.A)
+  int wca_nc[3] = {1, 1, 1};
+  int* wca_idx = nullptr;                             // cell count, start, cursor
+  int* cell_list = nullptr;                           // [cap], in the blob allocation
   std::vector<double> me_host, f_host;
   bool any_me = false, any_force = false;
   // row-block bins of the blob work fused into the x passes (register FFT sides)
@@ -242,6 +246,28 @@ BlobState blob_state(const icm_sim* s) {
   b.scal = s->scal;
   b.err = s->err_dev;
   return b;
+}
+
+WcaParams wca_params(const icm_sim* s) {
+  WcaParams w;
+  w.eps = s->wca_eps;
+  w.sigma = s->wca_sigma;
+  const double rc = std::pow(2.0, 1.0 / 6.0) * s->wca_sigma;
+  w.rc2 = rc * rc;
+  const int n[3] = {s->nx, s->ny, s->nz};
+  w.ncells = 1;
+  for (int a = 0; a < 3; ++a) {
+    w.nc[a] = s->wca_nc[a];
+    w.cell_inv[a] = w.nc[a] / (n[a] * s->h);
+    w.lo[a] = w.nc[a] >= 3 ? -1 : 0;
+    w.hi[a] = w.nc[a] >= 2 ? 1 : 0;
+    w.ncells *= w.nc[a];
+  }
+  w.count = s->wca_idx;
+  w.start = s->wca_idx ? s->wca_idx + w.ncells : nullptr;
+  w.cursor = s->wca_idx ? s->wca_idx + 2 * w.ncells + 1 : nullptr;
+  w.list = s->cell_list;
+  return w;
 }
 
 // Build one axis plan: radices, twiddles (long double), digit-reversed order, and
@@ -394,12 +420,16 @@ void enqueue_step(icm_sim* s, Prof* prof) {
   };
 
   // forces at q^{n+1/2}: the constant ones, or with the trap those the predictor writes
-  const double* fvec = s->nb == 0 ? nullptr : (s->trap_k != 0.0 ? s->fe : (s->any_force ? s->f : nullptr));
+  const bool wca = s->wca_eps > 0.0 && s->nb > 1 && s->wca_idx != nullptr;
+  const double* fvec =
+      s->nb == 0 ? nullptr : ((s->trap_k != 0.0 || wca) ? s->fe : (s->any_force ? s->f : nullptr));
   // thermal drift (Appendix B.2) at q^{n+1/2}, added to the right-hand side of the first solve
   const bool drift = (s->flags & ICM_FLAG_THERMAL_DRIFT) && s->kT > 0.0 && s->nb > 0;
   ICM_STAGE("scalars", 0, scalars_before_step(s->scal, s->dt, s->rho, dvf, st));
   // step 1: midpoint predictor (Eq. particle_pred)
   ICM_STAGE("predict", 2 * gath + nb * 72, blob_predict<R>(bp, bs, v, st));
+  // pair forces at q^{n+1/2} (four kernels: cell count, scan, fill, forces)
+  if (wca) ICM_STAGE("wca", nb * 96, blob_wca_forces(bp, bs, wca_params(s), s->trap_k != 0.0, st));
   if (s->fused && s->nb > 0) {
     // The blob work of steps 2-9 runs inside the x passes of the three solves: the
     // spreads in the forward pass of the solve they feed, the interpolations in the
@@ -518,7 +548,7 @@ icm_status grow_blobs(icm_sim* s, long long need) {
   if (need <= s->cap) return ICM_OK;
   long long cap = s->cap > 0 ? s->cap : 64;
   while (cap < need) cap *= 2;
-  const long long per = 13 * 3 + 1;  // 13 vector arrays + masses
+  const long long per = 13 * 3 + 2;  // 13 vector arrays, masses, the WCA cell list (ints)
   double* nbuf = (double*)dalloc(s, sizeof(double) * per * cap);
   if (!nbuf) return fail(ICM_ENOMEM, "device allocation of %lld blob slots failed", cap);
   ICM_CK(cudaMemsetAsync(nbuf, 0, sizeof(double) * per * cap, s->stream));
@@ -554,6 +584,7 @@ icm_status grow_blobs(icm_sim* s, long long need) {
   s->q = arrs[0]; s->qh = arrs[1]; s->u = arrs[2]; s->f = arrs[3]; s->g = arrs[4]; s->w0 = arrs[5];
   s->w1 = arrs[6]; s->jvt = arrs[7]; s->du = arrs[8]; s->dp = arrs[9]; s->cdp = arrs[10]; s->src = arrs[11];
   s->fe = arrs[12];
+  s->cell_list = reinterpret_cast<int*>(nbuf + (size_t)40 * cap);
   s->me = me;
   return ICM_OK;
 }
@@ -834,6 +865,40 @@ icm_status icm_set_blob_trap(icm_sim* s, double k, const double center[3]) {
   if (!finite_all(center, 3)) return fail(ICM_EINVAL, "non-finite trap center");
   s->trap_k = k;
   for (int a = 0; a < 3; ++a) s->trap_c[a] = center[a];
+  invalidate_graph(s);
+  return ICM_OK;
+}
+
+icm_status icm_set_blob_wca(icm_sim* s, double epsilon, double sigma) {
+  if (!s) return fail(ICM_EINVAL, "NULL simulation");
+  if (!std::isfinite(epsilon) || !std::isfinite(sigma) || epsilon < 0 || !(sigma > 0))
+    return fail(ICM_EINVAL, "WCA needs epsilon >= 0 and sigma > 0, finite");
+  const double rc = std::pow(2.0, 1.0 / 6.0) * sigma;
+  const int n[3] = {s->nx, s->ny, s->nz};
+  int nc[3];
+  for (int a = 0; a < 3; ++a) {
+    const double L = n[a] * s->h;
+    if (epsilon > 0 && L < 2.0 * rc)
+      return fail(ICM_EINVAL, "box side %g is shorter than twice the WCA cut-off %g", L, rc);
+    nc[a] = std::max(1, std::min(64, (int)(L / rc)));
+  }
+  ICM_CK(cudaStreamSynchronize(s->stream));
+  if (s->wca_idx) {
+    dfree(s, s->wca_idx);
+    s->wca_idx = nullptr;
+  }
+  s->wca_eps = epsilon;
+  s->wca_sigma = sigma;
+  if (epsilon > 0) {
+    const size_t ncells = (size_t)nc[0] * nc[1] * nc[2];
+    s->wca_idx = (int*)dalloc(s, sizeof(int) * (3 * ncells + 1));
+    if (!s->wca_idx) {
+      s->wca_eps = 0.0;
+      return fail(ICM_ENOMEM, "device allocation of the WCA cell list failed");
+    }
+    ICM_CK(cudaMemsetAsync(s->wca_idx, 0, sizeof(int) * (3 * ncells + 1), s->stream));
+    for (int a = 0; a < 3; ++a) s->wca_nc[a] = nc[a];
+  }
   invalidate_graph(s);
   return ICM_OK;
 }
@@ -1251,7 +1316,7 @@ int64_t icm_estimate_device_bytes(const int32_t grid[3], int32_t precision, int6
   const int64_t fields = 3 * (3 * ncell * rs);
   const int64_t spec = 3 * (int64_t)grid[2] * grid[1] * kxp * 2 * rs;
   const int64_t tables = 3 * (int64_t)kMaxSide * (3 * 2 * rs + 4) + 16 * 256;
-  const int64_t blobs = nblobs > 0 ? 40 * cap * 8 + (int64_t)bin_blob_bytes(cap) : 0;
+  const int64_t blobs = nblobs > 0 ? 41 * cap * 8 + (int64_t)bin_blob_bytes(cap) : 0;
   const int64_t bins = 4 * (3 * ((int64_t)grid[1] * grid[2] / 32 + 1) + 1);
   return fields + spec + tables + blobs + bins + 8 * 3 * 1024 + 4096;
 }

@@ -523,6 +523,76 @@ __global__ void k_finish_from(BlobParams p, BlobState s, const double* __restric
 
 inline unsigned eblocks(long long n) { return (unsigned)((n + 255) / 256); }
 
+// ---------------------------------------------------------------------------
+// WCA pair forces (Sec. IV.A, Eq. WCA) through a cell list at q^{n+1/2}
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int wca_cell_axis(double x, double cell_inv, int n) {
+  const int c = (int)(x * cell_inv);
+  return c < 0 ? 0 : (c >= n ? n - 1 : c);
+}
+
+__global__ void k_wca_count(BlobState s, WcaParams w) {
+  const long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (b >= s.nb) return;
+  int c[3];
+  for (int a = 0; a < 3; ++a) c[a] = wca_cell_axis(s.qh[3 * b + a], w.cell_inv[a], w.nc[a]);
+  atomicAdd(&w.count[c[0] + w.nc[0] * (c[1] + w.nc[1] * c[2])], 1);
+}
+
+__global__ void k_wca_fill(BlobState s, WcaParams w) {
+  const long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (b >= s.nb) return;
+  int c[3];
+  for (int a = 0; a < 3; ++a) c[a] = wca_cell_axis(s.qh[3 * b + a], w.cell_inv[a], w.nc[a]);
+  const int pos = atomicAdd(&w.cursor[c[0] + w.nc[0] * (c[1] + w.nc[1] * c[2])], 1);
+  if (pos < s.nb) w.list[pos] = (int)b;
+}
+
+// F_i = sum_j 24 eps (2 s^12/r^14 - s^6/r^8) d_ij over the pairs within the cut-off,
+// d_ij = q_i - q_j to the nearest image (FP64).
+__global__ void __launch_bounds__(256) k_wca_force(BlobParams p, BlobState s, WcaParams w, int with_trap) {
+  __shared__ double red[3][256];
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double f[3] = {0.0, 0.0, 0.0};
+  if (i < s.nb) {
+    const double qi[3] = {s.qh[3 * i], s.qh[3 * i + 1], s.qh[3 * i + 2]};
+    int c[3];
+    for (int a = 0; a < 3; ++a) c[a] = wca_cell_axis(qi[a], w.cell_inv[a], w.nc[a]);
+    const double s2 = w.sigma * w.sigma;
+    for (int dz = w.lo[2]; dz <= w.hi[2]; ++dz)
+      for (int dy = w.lo[1]; dy <= w.hi[1]; ++dy)
+        for (int dx = w.lo[0]; dx <= w.hi[0]; ++dx) {
+          const int cx = (c[0] + dx + w.nc[0]) % w.nc[0], cy = (c[1] + dy + w.nc[1]) % w.nc[1];
+          const int cz = (c[2] + dz + w.nc[2]) % w.nc[2];
+          const int cell = cx + w.nc[0] * (cy + w.nc[1] * cz);
+          const int e = w.start[cell + 1];
+          for (int k = w.start[cell]; k < e; ++k) {
+            const int j = w.list[k];
+            if (j == i) continue;
+            double d[3], r2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+              const double x = qi[a] - s.qh[3 * j + a];
+              d[a] = fma(-p.box[a], rint(x * p.inv_box[a]), x);
+              r2 = fma(d[a], d[a], r2);
+            }
+            if (r2 >= w.rc2) continue;
+            const double s6 = (s2 / r2) * (s2 / r2) * (s2 / r2);
+            const double mag = 24.0 * w.eps * (2.0 * s6 * s6 - s6) / r2;
+            for (int a = 0; a < 3; ++a) f[a] = fma(mag, d[a], f[a]);
+          }
+        }
+    for (int a = 0; a < 3; ++a) s.fe[3 * i + a] = (with_trap ? s.fe[3 * i + a] : s.f[3 * i + a]) + f[a];
+  }
+  for (int a = 0; a < 3; ++a) red[a][threadIdx.x] = f[a];
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h)
+      for (int a = 0; a < 3; ++a) red[a][threadIdx.x] += red[a][threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) atomicAdd(&s.scal[SC_K0 + threadIdx.x], p.dt * red[threadIdx.x][0]);
+}
+
 }  // namespace
 
 template <typename R>
@@ -534,6 +604,24 @@ void build_row_bins(const BlobParams& p, long long nb, const double* q, RowBins 
 }
 template void build_row_bins<float>(const BlobParams&, long long, const double*, RowBins, cudaStream_t);
 template void build_row_bins<double>(const BlobParams&, long long, const double*, RowBins, cudaStream_t);
+
+void blob_wca_forces(const BlobParams& p, BlobState s, const WcaParams& w, bool with_trap, cudaStream_t st) {
+  if (s.nb <= 0) return;
+  k_wca_count<<<eblocks(s.nb), 256, 0, st>>>(s, w);
+  RowBins cells;
+  cells.count = w.count;
+  cells.start = w.start;
+  cells.cursor = w.cursor;
+  cells.list = w.list;
+  cells.geo = nullptr;
+  cells.acc = nullptr;
+  cells.nacc = 0;
+  cells.nblocks = w.ncells;
+  cells.capacity = s.nb;
+  k_bin_scan<<<1, 1024, 0, st>>>(cells);
+  k_wca_fill<<<eblocks(s.nb), 256, 0, st>>>(s, w);
+  k_wca_force<<<eblocks(s.nb), 256, 0, st>>>(p, s, w, with_trap ? 1 : 0);
+}
 
 void blob_dp_from(const BlobParams& p, BlobState s, const double* jvt, cudaStream_t st) {
   if (s.nb > 0) k_dp_from<<<eblocks(3 * s.nb), 256, 0, st>>>(p, s, jvt);

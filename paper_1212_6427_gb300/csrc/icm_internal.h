@@ -223,6 +223,22 @@ template <typename R>
 void fft_x_inverse_blobs(const FftCtx<R>& f, R* dst, int mode, const RowBlobs& rb, cudaStream_t st);
 bool fft_has_blob_passes(int nx);
 
+// WCA pair forces (Sec. IV.A, Eq. WCA) at q^{n+1/2} through a cell list of cells at
+// least the cut-off wide: count, scan (k_bin_scan on the cell arrays), fill, forces.
+struct WcaParams {
+  double eps, sigma, rc2;
+  int nc[3];          // cells per axis
+  double cell_inv[3]; // nc / L
+  int lo[3], hi[3];   // neighbour cell offsets per axis (distinct cells only)
+  int ncells;
+  int* count;         // [ncells], zero between builds
+  int* start;         // [ncells + 1]
+  int* cursor;        // [ncells]
+  int* list;          // [nb]
+};
+// fe = (with_trap ? fe : f) + F_wca; dt times the WCA total goes to the grid sum K0.
+void blob_wca_forces(const BlobParams& p, BlobState s, const WcaParams& w, bool with_trap, cudaStream_t st);
+
 // Elementwise blob updates of the fused step (one thread per blob component).
 void blob_dp_from(const BlobParams& p, BlobState s, const double* jvt, cudaStream_t st);
 void blob_inertial_from(const BlobParams& p, BlobState s, const double* jdvt, cudaStream_t st);

@@ -10,6 +10,9 @@
   non-interacting blobs at equilibrium should fill a grid cell uniformly; without the
   thermal drift forcing they favour the cell corners.  Reported: the ratio of the
   occupation of the corner and centre octants of the cell (each 1/8 of its volume).
+* Equilibrium radial distribution function (Sec. IV.A, Fig. RDF): blobs with WCA pair
+  forces in the fluctuating solvent; g(r) of the sampled configurations, to be compared
+  with Monte Carlo sampling of exp(-U/kT).
 * Single-blob mobility mu = -J L^-1 S of the steady Stokes problem and the effective
   hydrodynamic radius, from 6 pi eta mu = 1/R_H - 2.8373/L (the first-order lattice
   correction of a cubic array of spheres, Hasimoto 1959).
@@ -19,6 +22,7 @@
     python -m paper_1212_6427_gb300.experiments pair --grid 32 --kernel 3
     python -m paper_1212_6427_gb300.experiments radius --grid 32 --kernel 3
     python -m paper_1212_6427_gb300.experiments drift --grid 16 --kernel 3
+    python -m paper_1212_6427_gb300.experiments rdf --grid 32 --kernel 3
 """
 import argparse
 import json
@@ -152,9 +156,64 @@ def drift_bias(grid=(16, 16, 16), kernel=3, nblobs=100, kT=1.0, dt=0.05, steps=1
             "centre_fraction": centre / samples, "corner_over_centre": ratio, "ratio_error_uncorrelated": err}
 
 
+def pair_rdf(samples, box, dr=0.1, rmax=8.0):
+    """g(r) of a list of (n, 3) configurations in a periodic box (bin centres, g).  The
+    pair distances of each configuration are histogrammed with torch (on the GPU when
+    there is one): this is analysis of the sampled states, not part of the step."""
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    boxt = torch.tensor(np.asarray(box, dtype=float), dtype=torch.float64, device=dev)
+    nbins = int(round(rmax / dr))
+    hist = torch.zeros(nbins, dtype=torch.float64, device=dev)
+    n = samples[0].shape[0]
+    iu = torch.triu_indices(n, n, 1, device=dev)
+    for q in samples:
+        qt = torch.as_tensor(q, dtype=torch.float64, device=dev)
+        d = qt[iu[0]] - qt[iu[1]]
+        d -= boxt * torch.round(d / boxt)
+        r = torch.sqrt((d * d).sum(dim=1))
+        r = r[r < rmax]
+        hist += 2.0 * torch.bincount((r / dr).long(), minlength=nbins)[:nbins].double()
+    hist = hist.cpu().numpy()
+    box = np.asarray(box, dtype=float)
+    rho = n / box.prod()
+    edges = np.arange(nbins + 1) * dr
+    shell = 4.0 / 3.0 * np.pi * (edges[1:] ** 3 - edges[:-1] ** 3)
+    return edges[:-1] + 0.5 * dr, hist / (len(samples) * n * rho * shell)
+
+
+def rdf(grid=(32, 32, 32), kernel=3, n=1000, sigma=2.0, eps=1e-3, kT=1e-3, dt=1.0, me=0.0, burn=20000,
+        steps=100000, sample_every=100, seed=5, precision=32):
+    """g(r) of n blobs with WCA forces (Table tableRDF parameters by default: h = rho =
+    eta = 1, so the viscous CFL number is dt), started on a simple cubic lattice."""
+    side = int(math.ceil(n ** (1.0 / 3.0)))
+    idx = np.arange(n)
+    lattice = np.stack([idx % side, (idx // side) % side, idx // (side * side)], axis=1) + 0.5
+    q0 = lattice * (np.asarray(grid, dtype=float) / side)
+    import time
+    sim = Simulation(grid, 1.0, 1.0, 1.0, kT, dt, kernel, seed, precision, 0)
+    samples = []
+    try:
+        sim.add_blobs(q0, None, np.full(n, me))
+        sim.set_wca(eps, sigma)
+        sim.step(burn)
+        sim.sync()
+        t0 = time.perf_counter()
+        for _ in range(steps // sample_every):
+            sim.step(sample_every)
+            samples.append(sim.read()["pos"].copy())
+        t_steps = time.perf_counter() - t0
+    finally:
+        sim.close()
+    r, g = pair_rdf(samples, grid)
+    return {"grid": list(grid), "kernel": kernel, "n": n, "sigma": sigma, "eps": eps, "kT": kT, "dt": dt, "me": me,
+            "burn": burn, "steps": steps, "samples": len(samples), "ms_per_step": 1e3 * t_steps / steps,
+            "r": r.tolist(), "g": g.tolist()}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("experiment", choices=["trap", "jps", "pair", "radius", "drift"])
+    ap.add_argument("experiment", choices=["trap", "jps", "pair", "radius", "drift", "rdf"])
     ap.add_argument("--steps", type=int, default=100000)
     ap.add_argument("--precision", type=int, default=64, choices=[32, 64])
     ap.add_argument("--grid", type=int, default=32)
@@ -169,6 +228,9 @@ def main(argv=None):
     elif args.experiment == "pair":
         rows = [pair_coupling(g, args.kernel, direction=d, precision=args.precision)
                 for d in ((1.0, 0.0, 0.0), (1.0, 1.0, 1.0))]
+    elif args.experiment == "rdf":
+        mf = kernel_volume(args.kernel)   # m_f = rho dV
+        rows = [rdf(g, args.kernel, me=me, steps=args.steps, precision=args.precision) for me in (0.0, mf)]
     elif args.experiment == "drift":
         rows = [drift_bias(g, args.kernel, steps=args.steps, drift=d, precision=args.precision) for d in (False, True)]
     else:

@@ -39,6 +39,8 @@ def make_sim(prm, state, precision):
         sim.set_forces(state.force)
     if prm.trap_k != 0.0:
         sim.set_trap(prm.trap_k, prm.trap_center)
+    if prm.wca_epsilon != 0.0:
+        sim.set_wca(prm.wca_epsilon, prm.wca_sigma)
     sim.write(state.q, state.u, state.v.ravel(), None if state.adv_prev is None else state.adv_prev.ravel(),
               state.slip_g, state.step)
     return sim
