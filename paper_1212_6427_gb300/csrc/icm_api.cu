@@ -81,6 +81,9 @@ struct icm_sim {
   bool advection = true;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // second stream of the step graph: the blob-side prologue runs beside the RHS
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   icm_alloc_fn alloc = nullptr;
   icm_free_fn release = nullptr;
   void* actx = nullptr;
@@ -425,30 +428,48 @@ void enqueue_step(icm_sim* s, Prof* prof) {
       s->nb == 0 ? nullptr : ((s->trap_k != 0.0 || wca) ? s->fe : (s->any_force ? s->f : nullptr));
   // thermal drift (Appendix B.2) at q^{n+1/2}, added to the right-hand side of the first solve
   const bool drift = (s->flags & ICM_FLAG_THERMAL_DRIFT) && s->kT > 0.0 && s->nb > 0;
-  ICM_STAGE("scalars", 0, scalars_before_step(s->scal, s->dt, s->rho, dvf, st));
+  const bool fused = s->fused && s->nb > 0;
+  RowBins bins;
+  bins.count = s->bin_idx;
+  bins.start = s->bin_idx + s->nrowblk;
+  bins.cursor = s->bin_idx + 2 * s->nrowblk + 1;
+  bins.list = s->bin_list;
+  bins.geo = s->geo;
+  bins.acc = s->acc;
+  bins.nacc = kAccPerBlob;
+  bins.nblocks = s->nrowblk;
+  bins.capacity = (long long)kBinsPerBlob * s->cap;
+  const double geob = (double)(12 * sizeof(int) + 36 * sizeof(R));   // stencil record per blob
+
+  // The blob-side prologue (scalars, predictor, pair forces, bins) reads only v and the
+  // blob state: in the step graph it runs on a second stream beside the RHS and joins
+  // before the first solve.  Instrumented steps keep one stream.
+  const bool fork = prof == nullptr;
+  cudaStream_t sb = fork ? s->aux : st;
+  if (fork) {
+    cudaEventRecord(s->ev_fork, st);
+    cudaStreamWaitEvent(sb, s->ev_fork, 0);
+  }
+  ICM_STAGE("scalars", 0, scalars_before_step(s->scal, s->dt, s->rho, dvf, sb));
   // step 1: midpoint predictor (Eq. particle_pred)
-  ICM_STAGE("predict", 2 * gath + nb * 72, blob_predict<R>(bp, bs, v, st));
+  ICM_STAGE("predict", 2 * gath + nb * 72, blob_predict<R>(bp, bs, v, sb));
   // pair forces at q^{n+1/2} (four kernels: cell count, scan, fill, forces)
-  if (wca) ICM_STAGE("wca", nb * 96, blob_wca_forces(bp, bs, wca_params(s), s->trap_k != 0.0, st));
-  if (s->fused && s->nb > 0) {
+  if (wca) ICM_STAGE("wca", nb * 96, blob_wca_forces(bp, bs, wca_params(s), s->trap_k != 0.0, sb));
+  if (fused)
+    ICM_STAGE("bins", nb * (24.0 + 2 * geob + 8.0 * kAccPerBlob), build_row_bins<R>(bp, s->nb, s->qh, bins, sb));
+  if (fork) cudaEventRecord(s->ev_join, sb);
+  // step 2: unperturbed fluid solve (Eq. provisional_step-1)
+  ICM_STAGE("rhs", 4 * F, explicit_rhs<R>(gp, v, adv, work, s->step_dev, s->hist_dev, st));
+  if (fork) cudaStreamWaitEvent(st, s->ev_join, 0);
+  if (drift) ICM_STAGE("drift", 2 * gath + nb * 32, blob_spread_drift<R>(bp, bs, work, st));
+  if (fused) {
     // The blob work of steps 2-9 runs inside the x passes of the three solves: the
     // spreads in the forward pass of the solve they feed, the interpolations in the
     // inverse pass of the solve whose output they read (Sec. III.C).
-    RowBins bins;
-    bins.count = s->bin_idx;
-    bins.start = s->bin_idx + s->nrowblk;
-    bins.cursor = s->bin_idx + 2 * s->nrowblk + 1;
-    bins.list = s->bin_list;
-    bins.geo = s->geo;
-    bins.acc = s->acc;
-    bins.nacc = kAccPerBlob;
-    bins.nblocks = s->nrowblk;
-    bins.capacity = (long long)kBinsPerBlob * s->cap;
     double* acc1 = s->acc;                 // J v~
     double* acc2 = s->acc + 3 * s->nb;     // J dv~
     double* acc3 = s->acc + 6 * s->nb;     // J dv
     double* acc3l = s->acc + 9 * s->nb;    // J L dv (without 1/h^2)
-    const double geob = (double)(12 * sizeof(int) + 36 * sizeof(R));   // stencil record per blob
     const double blobio = nb * (geob + 24.0);
     RowBlobs rb;
     rb.start = bins.start;
@@ -458,10 +479,7 @@ void enqueue_step(icm_sim* s, Prof* prof) {
     rb.vec = nullptr;
     rb.acc = nullptr;
     rb.acc_lap = nullptr;
-    ICM_STAGE("bins", nb * (24.0 + 2 * geob + 8.0 * kAccPerBlob), build_row_bins<R>(bp, s->nb, s->qh, bins, st));
-    // step 2: unperturbed fluid solve (Eq. provisional_step-1), forces spread in x_fwd
-    ICM_STAGE("rhs", 4 * F, explicit_rhs<R>(gp, v, adv, work, s->step_dev, s->hist_dev, st));
-    if (drift) ICM_STAGE("drift", 2 * gath + nb * 32, blob_spread_drift<R>(bp, bs, work, st));
+    // forces spread in the first forward x pass
     auto passes = [&](const char* tag, const R* src, const double* vec, double a, double b, const double* k0,
                       R* dst, int mode, double* acc, double* acc_lap) {
       std::string t(tag);
@@ -497,9 +515,6 @@ void enqueue_step(icm_sim* s, Prof* prof) {
     ICM_STAGE("scalars", 0, scalars_after_step(s->scal, s->dt, s->rho, dvf, s->any_me, s->step_dev, s->hist_dev, st));
     return;
   }
-  // step 2: unperturbed fluid solve (Eq. provisional_step-1)
-  ICM_STAGE("rhs", 4 * F, explicit_rhs<R>(gp, v, adv, work, s->step_dev, s->hist_dev, st));
-  if (drift) ICM_STAGE("drift", 2 * gath + nb * 32, blob_spread_drift<R>(bp, bs, work, st));
   if (fvec) ICM_STAGE("spread", 2 * gath + nb * 48, blob_spread<R>(bp, s->nb, s->qh, fvec, work, st));
   solve("rt1", work, v, nullptr, OUT_STORE, s->rho / s->dt, 0.5 * s->eta, s->scal + SC_K0);
   if (s->any_me) {
@@ -731,6 +746,13 @@ icm_status icm_create(const int32_t grid[3], double h, double rho, double eta, d
     }
     s->own_stream = true;
   }
+  if (cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    icm_destroy(s);
+    return fail(ICM_ECUDA, "creation of the auxiliary stream failed");
+  }
   fft_prepare();
   grid_prepare();
   s->kx = s->nx / 2 + 1;
@@ -789,9 +811,13 @@ icm_status icm_create(const int32_t grid[3], double h, double rho, double eta, d
 void icm_destroy(icm_sim* s) {
   if (!s) return;
   if (s->stream) cudaStreamSynchronize(s->stream);
+  if (s->aux) cudaStreamSynchronize(s->aux);
   invalidate_graph(s);
   while (!s->allocs.empty()) dfree(s, s->allocs.back().first);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+  if (s->aux) cudaStreamDestroy(s->aux);
+  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+  if (s->ev_join) cudaEventDestroy(s->ev_join);
   delete s;
 }
 
