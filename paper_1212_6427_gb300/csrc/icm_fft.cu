@@ -420,6 +420,11 @@ __global__ void __launch_bounds__(kThreads) k_zsym(cplx_t<R>* __restrict__ spec,
 constexpr int kXPad = 16;   // x pass: one padding slot every 16 positions (bank spread)
 __host__ __device__ constexpr int xrow(int n) { return n + n / kXPad; }
 __device__ __forceinline__ int xaddr(int l, int p, int N) { return l * xrow(N) + p + p / kXPad; }
+// x passes with blob work: the staged task records follow the rows and twiddles
+template <typename R, int N> constexpr size_t stage_offset() {
+  return ((size_t)kXLines * xrow(N) * sizeof(cplx_t<R>) + N * sizeof(cplx_t<R>) + 15) / 16 * 16;
+}
+template <typename R, int N> size_t smem_x2b() { return stage_offset<R, N>() + kThreads * sizeof(StagedTask<R>); }
 
 // The z pass holds all three components of its tile, so it takes 8 kx lines
 // (64-byte rows in FP32) to keep two blocks per SM; one thread per first-stage item
@@ -740,33 +745,29 @@ __global__ void __launch_bounds__(kThreads) k_xfwd2(const R* __restrict__ src, c
     a[r] = mk(ok0 ? p0[x] : R(0), ok1 ? p0[N + x] : R(0));
   }
   if (BLOBS) {
+    // this block's tasks: records staged by cp.async while the buffer is zeroed
+    StagedTask<R>* stage = reinterpret_cast<StagedTask<R>*>(smem_raw + stage_offset<R, N>());
+    const BlobStencil<R>* rec = reinterpret_cast<const BlobStencil<R>*>(rb.geo);
+    const int s0 = rb.start[blockIdx.x], e = rb.start[blockIdx.x + 1];
+    const int nst = min(e - s0, kThreads);
+    if (tid < nst) stage_task<R>(&stage[tid], rec, rb.list[s0 + tid], comp, rb.vec);
+    cp_async_commit();
     for (int i = tid; i < kXLines * xrow(N); i += kThreads) buf[i] = mk(R(0), R(0));
+    cp_async_wait_all();
     __syncthreads();
     R* rows = reinterpret_cast<R*>(buf);
-    const BlobStencil<R>* rec = reinterpret_cast<const BlobStencil<R>*>(rb.geo);
     const double inv_dvf = rb.p.inv_h * rb.p.inv_h * rb.p.inv_h;
     const auto line = [](int ln, int x) { return xaddr(ln, x, N); };
-    const int e = rb.start[blockIdx.x + 1];
     const bool plane = rb.p.ny % kRowBlock == 0;   // the block is part of one z plane
     const int z0 = (int)row0 / rb.p.ny, y0 = (int)row0 % rb.p.ny;
-    for (int i = rb.start[blockIdx.x] + tid; i < e; i += kThreads) {
+    if (tid < nst) {
+      const StagedTask<R>& t = stage[tid];
+      spread_one<R, N>(rows, (int)row0, plane, z0, y0, t.first, t.w, (R)(t.vec * inv_dvf), rb.p, line);
+    }
+    for (int i = s0 + kThreads + tid; i < e; i += kThreads) {   // beyond the staged tasks
       const int b = rb.list[i];
-      const R amp = (R)(rb.vec[3 * b + comp] * inv_dvf);
-      if (rb.p.kernel == 3) {
-        CompStencil<R, 3> S;
-        load_comp<R, 3>(S, rec + b, comp);
-        if (plane)
-          spread_plane<R, 3, N>(rows, z0, y0, S, amp, rb.p, line);
-        else
-          spread_task<R, 3, N>(rows, (int)row0, S, amp, rb.p, line);
-      } else {
-        CompStencil<R, 4> S;
-        load_comp<R, 4>(S, rec + b, comp);
-        if (plane)
-          spread_plane<R, 4, N>(rows, z0, y0, S, amp, rb.p, line);
-        else
-          spread_task<R, 4, N>(rows, (int)row0, S, amp, rb.p, line);
-      }
+      spread_one<R, N>(rows, (int)row0, plane, z0, y0, *reinterpret_cast<const int4*>(rec[b].first[comp]),
+                       &rec[b].w[comp][0][0], (R)(rb.vec[3 * b + comp] * inv_dvf), rb.p, line);
     }
   }
   __syncthreads();
@@ -853,6 +854,16 @@ __global__ void __launch_bounds__(kThreads) k_xinv2(const cplx_t<R>* __restrict_
     av[j] = (it < kXLines * N && r1 < nrows) ? in[r1 * kxp + kk] : zero;
     bv[j] = (it < kXLines * N && r1 + 1 < nrows) ? in[(r1 + 1) * kxp + kk] : zero;
   }
+  // the gathers' records: staged by cp.async while the spectrum loads are in flight
+  int g0 = 0, ge = 0;
+  if (GATHER) {
+    StagedTask<R>* stage = reinterpret_cast<StagedTask<R>*>(smem_raw + stage_offset<R, N>());
+    g0 = rb.start[blockIdx.x];
+    ge = rb.start[blockIdx.x + 1];
+    if (tid < min(ge - g0, kThreads))
+      stage_task<R>(&stage[tid], reinterpret_cast<const BlobStencil<R>*>(rb.geo), rb.list[g0 + tid], comp, nullptr);
+    cp_async_commit();
+  }
 #pragma unroll
   for (int j = 0; j < LOADS; ++j) {
     const int it = tid + j * kThreads;
@@ -920,37 +931,26 @@ __global__ void __launch_bounds__(kThreads) k_xinv2(const cplx_t<R>* __restrict_
     }
   }
   if (GATHER) {
+    cp_async_wait_all();
     __syncthreads();
     const R* rows = reinterpret_cast<const R*>(buf);
+    const StagedTask<R>* stage = reinterpret_cast<const StagedTask<R>*>(smem_raw + stage_offset<R, N>());
     const BlobStencil<R>* rec = reinterpret_cast<const BlobStencil<R>*>(rb.geo);
     const auto line = [](int l, int x) { return xaddr(l, x, N); };
-    const int e = rb.start[blockIdx.x + 1];
     const bool plane = rb.p.ny % kRowBlock == 0;   // the block is part of one z plane
     const int z0 = (int)row0 / rb.p.ny, y0 = (int)row0 % rb.p.ny;
-    for (int i = rb.start[blockIdx.x] + tid; i < e; i += kThreads) {
+    if (tid < min(ge - g0, kThreads)) {
+      const StagedTask<R>& t = stage[tid];
+      R j, jl;
+      gather_one<R, N, GATHER == 2>(rows, (int)row0, plane, z0, y0, t.first, t.w, rb.p, line, j, jl);
+      atomicAdd(&rb.acc[3 * t.b + comp], (double)j);
+      if (GATHER == 2) atomicAdd(&rb.acc_lap[3 * t.b + comp], (double)jl);
+    }
+    for (int i = g0 + kThreads + tid; i < ge; i += kThreads) {   // beyond the staged tasks
       const int b = rb.list[i];
-      R j, jl = R(0);
-      if (rb.p.kernel == 3) {
-        CompStencil<R, 3> S;
-        load_comp<R, 3>(S, rec + b, comp);
-        if (plane) {
-          j = gather_plane<R, 3, N>(rows, z0, y0, S, rb.p, line);
-          if (GATHER == 2) jl = gather_lap_plane<R, 3, N>(rows, z0, y0, S, rb.p, line);
-        } else {
-          j = gather_task<R, 3, N>(rows, (int)row0, S, rb.p, line);
-          if (GATHER == 2) jl = gather_lap_task<R, 3, N>(rows, (int)row0, S, rb.p, line);
-        }
-      } else {
-        CompStencil<R, 4> S;
-        load_comp<R, 4>(S, rec + b, comp);
-        if (plane) {
-          j = gather_plane<R, 4, N>(rows, z0, y0, S, rb.p, line);
-          if (GATHER == 2) jl = gather_lap_plane<R, 4, N>(rows, z0, y0, S, rb.p, line);
-        } else {
-          j = gather_task<R, 4, N>(rows, (int)row0, S, rb.p, line);
-          if (GATHER == 2) jl = gather_lap_task<R, 4, N>(rows, (int)row0, S, rb.p, line);
-        }
-      }
+      R j, jl;
+      gather_one<R, N, GATHER == 2>(rows, (int)row0, plane, z0, y0, *reinterpret_cast<const int4*>(rec[b].first[comp]),
+                                    &rec[b].w[comp][0][0], rb.p, line, j, jl);
       atomicAdd(&rb.acc[3 * b + comp], (double)j);
       if (GATHER == 2) atomicAdd(&rb.acc_lap[3 * b + comp], (double)jl);
     }
@@ -1158,7 +1158,7 @@ void fft_x_forward_blobs(const FftCtx<R>& f, const R* src, const RowBlobs& rb, c
   const cplx_t<R>* tw = (const cplx_t<R>*)f.px.tw;
   switch (f.nx) {
 #define ICM_CASE(N, R1, R2) \
-  case N: k_xfwd2<R, N, R1, R2, true><<<dim3(xblocks, 3), kThreads, smem_x2<R, N>(), st>>>(src, f.spec, tw, nrows, f.ncell, f.kx, f.kxp, rb); return;
+  case N: k_xfwd2<R, N, R1, R2, true><<<dim3(xblocks, 3), kThreads, smem_x2b<R, N>(), st>>>(src, f.spec, tw, nrows, f.ncell, f.kx, f.kxp, rb); return;
     ICM_FFT_SIDES(ICM_CASE)
 #undef ICM_CASE
     default: break;
@@ -1176,11 +1176,11 @@ void fft_x_inverse_blobs(const FftCtx<R>& f, R* dst, int mode, const RowBlobs& r
 #define ICM_CASE(N, R1, R2)                                                                                              \
   case N:                                                                                                                \
     if (mode == OUT_STORE)                                                                                               \
-      k_xinv2<R, N, R1, R2, OUT_STORE, 1><<<grid, kThreads, smem_x2<R, N>(), st>>>(f.spec, dst, nullptr, tw, nrows, f.ncell, f.kxp, rb); \
+      k_xinv2<R, N, R1, R2, OUT_STORE, 1><<<grid, kThreads, smem_x2b<R, N>(), st>>>(f.spec, dst, nullptr, tw, nrows, f.ncell, f.kxp, rb); \
     else if (mode == OUT_NONE)                                                                                           \
-      k_xinv2<R, N, R1, R2, OUT_NONE, 1><<<grid, kThreads, smem_x2<R, N>(), st>>>(f.spec, dst, nullptr, tw, nrows, f.ncell, f.kxp, rb); \
+      k_xinv2<R, N, R1, R2, OUT_NONE, 1><<<grid, kThreads, smem_x2b<R, N>(), st>>>(f.spec, dst, nullptr, tw, nrows, f.ncell, f.kxp, rb); \
     else                                                                                                                 \
-      k_xinv2<R, N, R1, R2, OUT_ADD, 2><<<grid, kThreads, smem_x2<R, N>(), st>>>(f.spec, dst, nullptr, tw, nrows, f.ncell, f.kxp, rb); \
+      k_xinv2<R, N, R1, R2, OUT_ADD, 2><<<grid, kThreads, smem_x2b<R, N>(), st>>>(f.spec, dst, nullptr, tw, nrows, f.ncell, f.kxp, rb); \
     return;
     ICM_FFT_SIDES(ICM_CASE)
 #undef ICM_CASE

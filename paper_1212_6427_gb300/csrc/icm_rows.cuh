@@ -343,5 +343,99 @@ __device__ __forceinline__ R gather_lap_plane(const R* rows, int z0, int y0, con
   return acc;
 }
 
+// ---------------------------------------------------------------------------
+// Staging of a block's task records in shared memory (cp.async, issued at kernel
+// start so that the dependent loads bin start -> blob id -> record overlap the
+// block's field or spectrum loads).
+// ---------------------------------------------------------------------------
+template <typename R>
+struct __align__(16) StagedTask {
+  int4 first;     // first nodes of the component along x, y, z
+  R w[12];        // weights [axis][node]
+  double vec;     // spread source of the component (FP64); unused by gathers
+  int b;          // blob id
+};
+
+__device__ __forceinline__ uint32_t rows_smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(rows_smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(rows_smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Copy the record of component comp of blob b (and its source value) into slot.
+template <typename R>
+__device__ __forceinline__ void stage_task(StagedTask<R>* slot, const BlobStencil<R>* rec, int b, int comp,
+                                           const double* vec) {
+  cp_async16(&slot->first, &rec[b].first[comp][0]);
+  const char* w = reinterpret_cast<const char*>(&rec[b].w[comp][0][0]);
+  char* d = reinterpret_cast<char*>(slot->w);
+#pragma unroll
+  for (int k = 0; k < (int)(12 * sizeof(R) / 16); ++k) cp_async16(d + 16 * k, w + 16 * k);
+  if (vec != nullptr) cp_async8(&slot->vec, vec + 3 * b + comp);
+  slot->b = b;
+}
+
+template <typename R, int K>
+__device__ __forceinline__ void comp_from(CompStencil<R, K>& S, int4 f, const R* w) {
+  S.fx = f.x;
+  S.fy = f.y;
+  S.fz = f.z;
+#pragma unroll
+  for (int a = 0; a < K; ++a) {
+    S.wx[a] = w[a];
+    S.wy[a] = w[4 + a];
+    S.wz[a] = w[8 + a];
+  }
+}
+
+// One spread task: plane path when the block lies in one z plane, generic otherwise.
+template <typename R, int N, typename LINE>
+__device__ __forceinline__ void spread_one(R* rows, int row0, bool plane, int z0, int y0, int4 f, const R* w,
+                                           R amp, const BlobParams& p, LINE line) {
+  if (p.kernel == 3) {
+    CompStencil<R, 3> S;
+    comp_from<R, 3>(S, f, w);
+    if (plane)
+      spread_plane<R, 3, N>(rows, z0, y0, S, amp, p, line);
+    else
+      spread_task<R, 3, N>(rows, row0, S, amp, p, line);
+  } else {
+    CompStencil<R, 4> S;
+    comp_from<R, 4>(S, f, w);
+    if (plane)
+      spread_plane<R, 4, N>(rows, z0, y0, S, amp, p, line);
+    else
+      spread_task<R, 4, N>(rows, row0, S, amp, p, line);
+  }
+}
+
+// One gather task: the parts of J and (LAP) J L of the component in these rows.
+template <typename R, int N, bool LAP, typename LINE>
+__device__ __forceinline__ void gather_one(const R* rows, int row0, bool plane, int z0, int y0, int4 f,
+                                           const R* w, const BlobParams& p, LINE line, R& j, R& jl) {
+  jl = R(0);
+  if (p.kernel == 3) {
+    CompStencil<R, 3> S;
+    comp_from<R, 3>(S, f, w);
+    j = plane ? gather_plane<R, 3, N>(rows, z0, y0, S, p, line) : gather_task<R, 3, N>(rows, row0, S, p, line);
+    if (LAP)
+      jl = plane ? gather_lap_plane<R, 3, N>(rows, z0, y0, S, p, line)
+                 : gather_lap_task<R, 3, N>(rows, row0, S, p, line);
+  } else {
+    CompStencil<R, 4> S;
+    comp_from<R, 4>(S, f, w);
+    j = plane ? gather_plane<R, 4, N>(rows, z0, y0, S, p, line) : gather_task<R, 4, N>(rows, row0, S, p, line);
+    if (LAP)
+      jl = plane ? gather_lap_plane<R, 4, N>(rows, z0, y0, S, p, line)
+                 : gather_lap_task<R, 4, N>(rows, row0, S, p, line);
+  }
+}
+
 }  // namespace
 }  // namespace icm
