@@ -342,20 +342,27 @@ struct SymParams {
 // P^ w / (a + b|d|^2) / ncell on one wave vector: (P^ w)_a = w_a - conj(d_a)(d . w)/|d|^2,
 // identity on the mean mode, whose value is replaced by the FP64 bookkeeping if given
 // (and which is zero when a = 0).
+// 1/x: correctly rounded reciprocal in FP32 (one rounding more than a division per
+// use, far inside the FP32 path's tolerance), exact division in FP64.
+template <typename R> __device__ __forceinline__ R recip(R x);
+template <> __device__ __forceinline__ float recip<float>(float x) { return __frcp_rn(x); }
+template <> __device__ __forceinline__ double recip<double>(double x) { return 1.0 / x; }
+
 template <typename R>
 __device__ __forceinline__ void apply_symbol(cplx_t<R>& c0, cplx_t<R>& c1, cplx_t<R>& c2, cplx_t<R> d0,
                                              cplx_t<R> d1, cplx_t<R> d2, R dd, const SymParams<R>& sp,
                                              bool mean_mode) {
   if (dd > R(0)) {
     const cplx_t<R> div = cadd(cadd(cmul(d0, c0), cmul(d1, c1)), cmul(d2, c2));
-    const cplx_t<R> q = mk(div.x / dd, div.y / dd);
+    const R inv_dd = recip<R>(dd);
+    const cplx_t<R> q = mk(div.x * inv_dd, div.y * inv_dd);
     c0 = csub(c0, cmul(cconj(d0), q));
     c1 = csub(c1, cmul(cconj(d1), q));
     c2 = csub(c2, cmul(cconj(d2), q));
   }
   // a = 0 (the steady Stokes solve): the mean mode has no solution and is dropped
   const R den = sp.a + sp.b * dd;
-  const R scale = den > R(0) ? sp.inv_ntot / den : R(0);
+  const R scale = den > R(0) ? sp.inv_ntot * recip<R>(den) : R(0);
   c0 = cscale(c0, scale);
   c1 = cscale(c1, scale);
   c2 = cscale(c2, scale);
@@ -439,7 +446,8 @@ constexpr int zsym2_threads() { return 3 * R2 * kZLines > 1024 ? 1024 : 3 * R2 *
 template <typename R, int N, int R1, int R2, bool FROM_SMEM>
 __device__ __forceinline__ void zsym_tile(cplx_t<R>* __restrict__ buf, const cplx_t<R>* __restrict__ tw,
                                           cplx_t<R>* __restrict__ base, size_t cs, size_t zs, int kx0, int py, int kx,
-                                          const SymParams<R>& sp, int tid) {
+                                          const SymParams<R>& sp, const cplx_t<R>* __restrict__ dzt,
+                                          const R* __restrict__ ddzt, int tid) {
   using C = cplx_t<R>;
   constexpr int NL = kZLines;
   constexpr int NT = zsym2_threads<R, N, R1, R2>();
@@ -476,7 +484,7 @@ __device__ __forceinline__ void zsym_tile(cplx_t<R>* __restrict__ buf, const cpl
 #pragma unroll
       for (int k1 = 0; k1 < R2; ++k1) {
         const int pz = R2 * blk + k1;
-        apply_symbol<R>(b[0][k1], b[1][k1], b[2][k1], d0, dyv, sp.dz[pz], ddx + ddy + sp.ddz[pz], sp,
+        apply_symbol<R>(b[0][k1], b[1][k1], b[2][k1], d0, dyv, dzt[pz], ddx + ddy + ddzt[pz], sp,
                         k == 0 && py == 0 && pz == 0);
       }
 #pragma unroll
@@ -497,14 +505,18 @@ __device__ __forceinline__ void zsym_tile(cplx_t<R>* __restrict__ buf, const cpl
       for (int n = 0; n < R2; ++n) buf[(c * N + R2 * blk + n) * NL + line] = b[n];
     }
     __syncthreads();
+    // NT is a multiple of NL, so a thread keeps its line (and its x symbol) in every round
+    static_assert(NT % NL == 0, "fixed line per thread");
+    const int kt = kx0 + tid % NL;
+    const C dxt = sp.dx[kt < kx ? kt : 0];
+    const R dxy = sp.ddx[kt < kx ? kt : 0] + ddy;
     for (int it = tid; it < N * NL; it += NT) {
-      const int line = it % NL, pz = it / NL, k = kx0 + line;
-      if (k >= kx) continue;
+      const int pz = it / NL;
+      if (kt >= kx) continue;
       C& c0 = buf[it];
       C& c1 = buf[N * NL + it];
       C& c2 = buf[2 * N * NL + it];
-      apply_symbol<R>(c0, c1, c2, sp.dx[k], dyv, sp.dz[pz], sp.ddx[k] + ddy + sp.ddz[pz], sp,
-                      k == 0 && py == 0 && pz == 0);
+      apply_symbol<R>(c0, c1, c2, dxt, dyv, dzt[pz], dxy + ddzt[pz], sp, kt == 0 && py == 0 && pz == 0);
     }
     __syncthreads();
     for (int it = tid; it < 3 * R1 * NL; it += NT) {
@@ -544,7 +556,7 @@ __global__ void __launch_bounds__(zsym2_threads<R, N, R1, R2>(), sizeof(R) == 4 
   const int kx0 = blockIdx.x * NL, py = blockIdx.y;
   const size_t zs = (size_t)ny * kxp, cs = (size_t)N * zs;
   __syncthreads();
-  zsym_tile<R, N, R1, R2, false>(buf, tw, spec + (size_t)py * kxp + kx0, cs, zs, kx0, py, kx, sp, tid);
+  zsym_tile<R, N, R1, R2, false>(buf, tw, spec + (size_t)py * kxp + kx0, cs, zs, kx0, py, kx, sp, sp.dz, sp.ddz, tid);
 }
 
 // ---------------------------------------------------------------------------
@@ -608,10 +620,16 @@ __global__ void __launch_bounds__(zsym2_threads<R, N, R1, R2>(), sizeof(R) == 4 
   unsigned char* aligned = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   C* bufs = reinterpret_cast<C*>(aligned);             // [2 stages][3][N][NL]
   C* tw = bufs + 2 * TILE;                             // [N]
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(tw + N);  // [2]
+  C* zdz = tw + N;                                     // [N] z symbols (every tile uses them)
+  R* zddz = reinterpret_cast<R*>(zdz + N);             // [N]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(zdz + N) + (N * sizeof(R) + 7) / 8;   // [2]
   __shared__ int s_ok;
   const int tid = threadIdx.x;
   load_stage_twiddles<R, R1, R2>(tw, gtw, tid, NT);
+  for (int i = tid; i < N; i += NT) {
+    zdz[i] = sp.dz[i];
+    zddz[i] = sp.ddz[i];
+  }
   if (tid == 0) {
     mbar_init(&mbar[0], 1);
     mbar_init(&mbar[1], 1);
@@ -642,7 +660,8 @@ __global__ void __launch_bounds__(zsym2_threads<R, N, R1, R2>(), sizeof(R) == 4 
     __syncthreads();
     if (!s_ok) break;
     const int kx0 = (t % ntx) * NL, py = t / ntx;
-    zsym_tile<R, N, R1, R2, true>(bufs + st * TILE, tw, spec + (size_t)py * kxp + kx0, cs, zs, kx0, py, kx, sp, tid);
+    zsym_tile<R, N, R1, R2, true>(bufs + st * TILE, tw, spec + (size_t)py * kxp + kx0, cs, zs, kx0, py, kx, sp, zdz,
+                                  zddz, tid);
     __syncthreads();
   }
   if (tid == 0 && !s_ok && t < ntiles) {
@@ -792,8 +811,9 @@ __global__ void __launch_bounds__(kThreads) k_xfwd2(const R* __restrict__ src, c
   }
   __syncthreads();
   C* out = spec + (size_t)comp * nrows * kxp;
-  for (int it = tid; it < kXLines * kx; it += kThreads) {
-    const int k = it % kx, l = it / kx;
+  constexpr int KX = N / 2 + 1;   // = kx: a compile-time divisor for the index split
+  for (int it = tid; it < kXLines * KX; it += kThreads) {
+    const int k = it % KX, l = it / KX;
     const int km = k == 0 ? 0 : N - k;
     const C zk = buf[xaddr(l, R2 * (k % R1) + k / R1, N)];
     const C zm = buf[xaddr(l, R2 * (km % R1) + km / R1, N)];
@@ -957,7 +977,9 @@ __global__ void __launch_bounds__(kThreads) k_xinv2(const cplx_t<R>* __restrict_
   }
 }
 
-template <typename R, int N> size_t smem_ztma() { return 2 * 3 * (size_t)N * kZLines * sizeof(cplx_t<R>) + N * sizeof(cplx_t<R>) + 16 + 128; }
+template <typename R, int N> size_t smem_ztma() {
+  return 2 * 3 * (size_t)N * kZLines * sizeof(cplx_t<R>) + 2 * N * sizeof(cplx_t<R>) + (N * sizeof(R) + 7) / 8 * 8 + 16 + 128;
+}
 template <typename R, int N> size_t smem_z2() { return 3 * (size_t)N * kZLines * sizeof(cplx_t<R>) + N * sizeof(cplx_t<R>); }
 template <typename R, int N> size_t smem_y2() { return (size_t)N * seg_lines<R>() * sizeof(cplx_t<R>) + N * sizeof(cplx_t<R>); }
 template <typename R, int N> size_t smem_x2() { return (size_t)kXLines * xrow(N) * sizeof(cplx_t<R>) + N * sizeof(cplx_t<R>); }
