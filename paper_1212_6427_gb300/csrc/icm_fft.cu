@@ -443,6 +443,15 @@ constexpr int zsym2_threads() { return 3 * R2 * kZLines > 1024 ? 1024 : 3 * R2 *
 // The work of one z tile (3 components x N z x NL kx lines, kx0..kx0+NL-1, storage y
 // position py): forward z FFT, symbol, inverse z FFT.  The first stage reads the tile
 // from global memory (FROM_SMEM false) or from `buf`, where a TMA copy has put it.
+// Row of the z tile that holds spectral row R2 blk + n: within each block of R2 rows,
+// odd blocks swap adjacent rows (R2 even).  The second FFT stage reads the same n of
+// four consecutive blocks per warp; NL-line rows are 64 bytes in FP32, so without the
+// swap the two blocks a half-warp touches would share banks.
+template <int R2>
+__device__ __forceinline__ int zrow(int blk, int n) {
+  return R2 % 2 == 0 ? R2 * blk + (n ^ (blk & 1)) : R2 * blk + n;
+}
+
 template <typename R, int N, int R1, int R2, bool FROM_SMEM>
 __device__ __forceinline__ void zsym_tile(cplx_t<R>* __restrict__ buf, const cplx_t<R>* __restrict__ tw,
                                           cplx_t<R>* __restrict__ base, size_t cs, size_t zs, int kx0, int py, int kx,
@@ -453,8 +462,9 @@ __device__ __forceinline__ void zsym_tile(cplx_t<R>* __restrict__ buf, const cpl
   constexpr int NT = zsym2_threads<R, N, R1, R2>();
   constexpr bool HOLD3 = sizeof(R) == 4 && R2 <= 12;   // 3 x R2 complex in registers
   const C zero = mk(R(0), R(0));
-  for (int it = tid; it < 3 * R2 * NL; it += NT) {
-    const int line = it % NL, rest = it / NL, n1 = rest % R2, c = rest / R2;
+  static_assert(NT == 3 * R2 * NL, "one first-stage item per thread");
+  {
+    const int line = tid % NL, rest = tid / NL, n1 = rest % R2, c = rest / R2;
     const bool ok = kx0 + line < kx;
     C a[R1];
 #pragma unroll
@@ -462,8 +472,10 @@ __device__ __forceinline__ void zsym_tile(cplx_t<R>* __restrict__ buf, const cpl
       a[r] = FROM_SMEM ? buf[(c * N + n1 + R2 * r) * NL + line]
                        : (ok ? base[c * cs + (size_t)(n1 + R2 * r) * zs + line] : zero);
     stage_a_fwd<R, R1, R2>(a, tw + n1);
+    // the tile landed in natural row order: every thread reads before the swapped writes
+    if (FROM_SMEM && R2 % 2 == 0) __syncthreads();
 #pragma unroll
-    for (int k2 = 0; k2 < R1; ++k2) buf[(c * N + n1 + R2 * k2) * NL + line] = a[k2];
+    for (int k2 = 0; k2 < R1; ++k2) buf[(c * N + zrow<R2>(k2, n1)) * NL + line] = a[k2];
   }
   __syncthreads();
   const C dyv = sp.dy[py];
@@ -476,7 +488,7 @@ __device__ __forceinline__ void zsym_tile(cplx_t<R>* __restrict__ buf, const cpl
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
 #pragma unroll
-        for (int n = 0; n < R2; ++n) b[c][n] = buf[(c * N + R2 * blk + n) * NL + line];
+        for (int n = 0; n < R2; ++n) b[c][n] = buf[(c * N + zrow<R2>(blk, n)) * NL + line];
         SDft<R, R2>::run(b[c]);
       }
       const C d0 = sp.dx[k];
@@ -491,7 +503,7 @@ __device__ __forceinline__ void zsym_tile(cplx_t<R>* __restrict__ buf, const cpl
       for (int c = 0; c < 3; ++c) {
         sdft_inv<R, R2>(b[c]);
 #pragma unroll
-        for (int n = 0; n < R2; ++n) buf[(c * N + R2 * blk + n) * NL + line] = b[c][n];
+        for (int n = 0; n < R2; ++n) buf[(c * N + zrow<R2>(blk, n)) * NL + line] = b[c][n];
       }
     }
   } else {
@@ -499,10 +511,10 @@ __device__ __forceinline__ void zsym_tile(cplx_t<R>* __restrict__ buf, const cpl
       const int line = it % NL, rest = it / NL, blk = rest % R1, c = rest / R1;
       C b[R2];
 #pragma unroll
-      for (int n = 0; n < R2; ++n) b[n] = buf[(c * N + R2 * blk + n) * NL + line];
+      for (int n = 0; n < R2; ++n) b[n] = buf[(c * N + zrow<R2>(blk, n)) * NL + line];
       SDft<R, R2>::run(b);
 #pragma unroll
-      for (int n = 0; n < R2; ++n) buf[(c * N + R2 * blk + n) * NL + line] = b[n];
+      for (int n = 0; n < R2; ++n) buf[(c * N + zrow<R2>(blk, n)) * NL + line] = b[n];
     }
     __syncthreads();
     // NT is a multiple of NL, so a thread keeps its line (and its x symbol) in every round
@@ -511,7 +523,8 @@ __device__ __forceinline__ void zsym_tile(cplx_t<R>* __restrict__ buf, const cpl
     const C dxt = sp.dx[kt < kx ? kt : 0];
     const R dxy = sp.ddx[kt < kx ? kt : 0] + ddy;
     for (int it = tid; it < N * NL; it += NT) {
-      const int pz = it / NL;
+      const int pr = it / NL;                                  // row of the tile
+      const int pz = zrow<R2>(pr / R2, pr % R2);               // its spectral row (the swap is an involution)
       if (kt >= kx) continue;
       C& c0 = buf[it];
       C& c1 = buf[N * NL + it];
@@ -523,10 +536,10 @@ __device__ __forceinline__ void zsym_tile(cplx_t<R>* __restrict__ buf, const cpl
       const int line = it % NL, rest = it / NL, blk = rest % R1, c = rest / R1;
       C b[R2];
 #pragma unroll
-      for (int n = 0; n < R2; ++n) b[n] = buf[(c * N + R2 * blk + n) * NL + line];
+      for (int n = 0; n < R2; ++n) b[n] = buf[(c * N + zrow<R2>(blk, n)) * NL + line];
       sdft_inv<R, R2>(b);
 #pragma unroll
-      for (int n = 0; n < R2; ++n) buf[(c * N + R2 * blk + n) * NL + line] = b[n];
+      for (int n = 0; n < R2; ++n) buf[(c * N + zrow<R2>(blk, n)) * NL + line] = b[n];
     }
   }
   __syncthreads();
@@ -535,7 +548,7 @@ __device__ __forceinline__ void zsym_tile(cplx_t<R>* __restrict__ buf, const cpl
     if (kx0 + line >= kx) continue;
     C a[R1];
 #pragma unroll
-    for (int k2 = 0; k2 < R1; ++k2) a[k2] = buf[(c * N + n1 + R2 * k2) * NL + line];
+    for (int k2 = 0; k2 < R1; ++k2) a[k2] = buf[(c * N + zrow<R2>(k2, n1)) * NL + line];
     stage_a_inv<R, R1, R2>(a, tw + n1);
 #pragma unroll
     for (int n2 = 0; n2 < R1; ++n2) base[c * cs + (size_t)(n1 + R2 * n2) * zs + line] = a[n2];
