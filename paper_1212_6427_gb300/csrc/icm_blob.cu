@@ -424,22 +424,34 @@ __global__ void k_bin_count(BlobParams p, long long nb, const double* __restrict
 }
 
 // Exclusive scan of the counts (one block); resets the counts for the next build.
+// Each thread sums a contiguous chunk; the 1024 chunk sums are scanned with warp
+// shuffles and one shared array of warp totals (two barriers).
 __global__ void __launch_bounds__(1024) k_bin_scan(RowBins bins) {
-  __shared__ int part[1024];
-  const int n = bins.nblocks, t = threadIdx.x;
+  __shared__ int warp_tot[32];
+  const int n = bins.nblocks, t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int per = (n + 1023) / 1024;
   const int lo = min(t * per, n), hi = min(lo + per, n);
   int sum = 0;
   for (int i = lo; i < hi; ++i) sum += bins.count[i];
-  part[t] = sum;
-  __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    const int v = t >= off ? part[t - off] : 0;
-    __syncthreads();
-    part[t] += v;
-    __syncthreads();
+  int incl = sum;   // inclusive scan within the warp
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
   }
-  int run = part[t] - sum;
+  if (lane == 31) warp_tot[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    int x = warp_tot[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += v;
+    }
+    warp_tot[lane] = x;   // inclusive over warps
+  }
+  __syncthreads();
+  int run = incl - sum + (w > 0 ? warp_tot[w - 1] : 0);
   for (int i = lo; i < hi; ++i) {
     const int c = bins.count[i];
     bins.start[i] = run;
@@ -447,7 +459,7 @@ __global__ void __launch_bounds__(1024) k_bin_scan(RowBins bins) {
     bins.count[i] = 0;
     run += c;
   }
-  if (t == 1023) bins.start[n] = part[1023];
+  if (t == 1023) bins.start[n] = warp_tot[31];
 }
 
 template <typename R>
