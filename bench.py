@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--precision", type=int, default=None, choices=[32, 64])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64, cuFFT and CPU comparison legs")
+    ap.add_argument("--no-autotune", action="store_true", help="time the default plan instead of the tuned one")
     ap.add_argument("--cpu-budget", type=float, default=150.0, help="seconds of oracle time for the CPU legs")
     return ap.parse_args()
 
@@ -229,8 +230,15 @@ def run_ours(args, rank, world, dist):
             dist.barrier()
 
     log("[bench] simulation created (%.0f MB on device); warming up" % (icm.icm_device_bytes(sim.handle) / 1e6))
-    # warm-up (graph capture happens on the first step)
+    # warm-up (graph capture happens on the first step), then the autotuner picks the
+    # plan on this state (which it restores) and the plan's graph is warmed up
     sim.step(max(args.warmup, 3))
+    sim.sync()
+    plan = None
+    if not args.no_autotune:
+        plan, plan_ms = icm.icm_autotune(sim.handle, 3)
+        log("[bench] autotuned plan %s (%.4f ms/step)" % (plan, plan_ms))
+        sim.step(max(args.warmup, 3))
     sim.sync()
     barrier()
     torch.cuda.synchronize()
@@ -308,7 +316,7 @@ def run_ours(args, rank, world, dist):
     line = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == 32 else "f64", "data": "synthetic",
-            "config": workload_config(w, prec, world),
+            "config": dict(workload_config(w, prec, world), plan=plan or "default"),
             "blob_steps_per_s": nb * args.steps * world / (ms / 1e3),
             "step_hbm": {"algorithmic_bytes_per_step": step_bytes,
                          "achieved_GBps": step_bytes / (ms_step / 1e3) / 1e9,
@@ -401,6 +409,10 @@ def run_batch(args, rank, world, dist):
         launches += sum(1 for n, _, _ in prof if kernel_of(n) != "zero")
     b = icm.icm_batch_create()
     icm.icm_batch_set(b, [s.handle for s in sims])
+    plans = "default"
+    if not args.no_autotune:
+        icm.icm_batch_autotune(b, 3)
+        plans = sorted({str(icm.icm_get_plan(s.handle)) for s in sims})
     icm.icm_batch_step(b, max(args.warmup, 3))
     icm.icm_batch_sync(b)
     if dist is not None:
@@ -433,6 +445,7 @@ def run_batch(args, rank, world, dist):
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "icm-batch-64-replicas-sides-32-48-64-96-fp32", "replicas": 64 * world,
+                       "plans": plans,
                        "cells_per_replica_set": cells, "blobs": blobs, "parallelism": "replicas only",
                        "l2": "replica set of %.0f MB per field: timed on host clock around whole batch steps"
                              % (3 * cells * 4 / 1e6)},

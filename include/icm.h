@@ -128,6 +128,35 @@ icm_status icm_set_blob_trap(icm_sim* sim, double k, const double center[3]);
  * cut-off), ICM_ENOMEM. */
 icm_status icm_set_blob_wca(icm_sim* sim, double epsilon, double sigma);
 
+/* Execution plan: implementation choices that change the speed of a step but not its
+ * result beyond rounding (no counterpart in the paper).  Defaults: every choice on,
+ * rhs_kz = 16. */
+typedef struct icm_plan {
+  int32_t fused_blobs; /* 1: spreading and interpolation inside the x FFT passes through row-block
+                          bins (sides 32, 48, 64, 96, 128, 192, 256, 384, 512); 0: separate kernels */
+  int32_t tma_z;       /* 1: persistent z pass fed by TMA (z sides <= 256 with register kernels);
+                          0: one block per z tile                                                  */
+  int32_t rhs_kz;      /* z planes marched by each block of the right-hand-side kernel, 4..64       */
+  int32_t fork;        /* 1: the blob-side prologue runs on a second stream beside the RHS          */
+} icm_plan;
+
+/* The plan the next step will use.  Errors: ICM_EINVAL (NULL). */
+icm_status icm_get_plan(const icm_sim* sim, icm_plan* out);
+
+/* Fix the plan (choices the simulation cannot use fall back to the alternative).
+ * Errors: ICM_EINVAL (NULL, rhs_kz outside 4..64). */
+icm_status icm_set_plan(icm_sim* sim, const icm_plan* plan);
+
+/* Autotuner: time the candidate plans over nsteps steps each (one choice at a time,
+ * the others held at the best so far) on a copy of the current state, keep the
+ * fastest, restore the state, and record the plan in a process-wide table keyed by
+ * grid, precision, kernel, flags, blob count (power-of-two bucket) and whether blobs
+ * have excess mass, which simulations without a fixed plan use when they capture their
+ * step.  chosen and ms_per_step (the chosen plan's time) may be NULL.  Synchronises.
+ * Errors: ICM_EINVAL (nsteps < 1), ICM_ENOMEM (no room for the state copy), device
+ * errors of the trial steps (the state is restored first). */
+icm_status icm_autotune(icm_sim* sim, int32_t nsteps, icm_plan* chosen, double* ms_per_step);
+
 /* Enqueue nsteps ICM steps (Sec. III.C steps 1-9) on the simulation's stream.
  * Asynchronous: errors detected on the device (ICM_ECFL, ICM_ENONFINITE) are
  * reported by the next icm_sync / icm_read_state.  Errors: ICM_EINVAL (nsteps<0). */
@@ -274,6 +303,12 @@ icm_status icm_batch_set(icm_batch* batch, int32_t n, icm_sim* const* sims);
  * membership or a member's step sequence changed).  Asynchronous; later work on a
  * member's own stream is ordered after these steps. */
 icm_status icm_batch_step(icm_batch* batch, int64_t nsteps);
+
+/* Autotune the batch as a whole: candidate plans (one choice at a time, as
+ * icm_autotune) are applied to every member and timed over nsteps batch steps; every
+ * member's state is restored after each trial and the fastest plan is fixed on all
+ * members.  Synchronises.  Errors: as icm_autotune. */
+icm_status icm_batch_autotune(icm_batch* batch, int32_t nsteps);
 
 /* Wait for the batch; returns the first device-side error of any member. */
 icm_status icm_batch_sync(icm_batch* batch);

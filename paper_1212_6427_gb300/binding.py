@@ -32,6 +32,14 @@ _dp = ctypes.POINTER(ctypes.c_double)
 _ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
 
+class Plan(ctypes.Structure):
+    """icm_plan of include/icm.h."""
+    _fields_ = [("fused_blobs", _c_i32), ("tma_z", _c_i32), ("rhs_kz", _c_i32), ("fork", _c_i32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
 class JobDesc(ctypes.Structure):
     """icm_job_desc of include/icm.h."""
     _fields_ = [("grid", _c_i32 * 3), ("h", _c_d), ("rho", _c_d), ("eta", _c_d), ("kT", _c_d), ("dt", _c_d),
@@ -49,6 +57,10 @@ SIGNATURES = {
     "icm_add_blobs": (_c_i32, [_vp, _c_i64, _dp, _dp, _dp]),
     "icm_set_blob_forces": (_c_i32, [_vp, _dp]),
     "icm_set_blob_trap": (_c_i32, [_vp, ctypes.c_double, _dp]),
+    "icm_get_plan": (_c_i32, [_vp, ctypes.c_void_p]),
+    "icm_set_plan": (_c_i32, [_vp, ctypes.c_void_p]),
+    "icm_autotune": (_c_i32, [_vp, _c_i32, ctypes.c_void_p, _dp]),
+    "icm_batch_autotune": (_c_i32, [_vp, _c_i32]),
     "icm_set_blob_wca": (_c_i32, [_vp, ctypes.c_double, ctypes.c_double]),
     "icm_step": (_c_i32, [_vp, _c_i64]),
     "icm_sync": (_c_i32, [_vp]),
@@ -196,6 +208,29 @@ def icm_set_blob_trap(sim, k, center):
 
 def icm_set_blob_wca(sim, epsilon, sigma):
     _check(lib().icm_set_blob_wca(sim, float(epsilon), float(sigma)))
+
+
+def icm_get_plan(sim):
+    p = Plan()
+    _check(lib().icm_get_plan(sim, ctypes.byref(p)))
+    return p.as_dict()
+
+
+def icm_set_plan(sim, fused_blobs=1, tma_z=1, rhs_kz=16, fork=1):
+    p = Plan(int(fused_blobs), int(tma_z), int(rhs_kz), int(fork))
+    _check(lib().icm_set_plan(sim, ctypes.byref(p)))
+
+
+def icm_autotune(sim, nsteps=3):
+    """Tune the plan; returns (plan dict, ms per step of the chosen plan)."""
+    p = Plan()
+    ms = ctypes.c_double(0.0)
+    _check(lib().icm_autotune(sim, int(nsteps), ctypes.byref(p), ctypes.byref(ms)))
+    return p.as_dict(), ms.value
+
+
+def icm_batch_autotune(batch, nsteps=3):
+    _check(lib().icm_batch_autotune(batch, int(nsteps)))
 
 
 def icm_step(sim, nsteps=1):

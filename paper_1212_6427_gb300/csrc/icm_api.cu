@@ -13,6 +13,8 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -81,6 +83,9 @@ struct icm_sim {
   bool advection = true;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // execution plan (icm_plan) and where it came from
+  icm_plan plan = {1, 1, 16, 1};
+  int plan_src = 0;   // 0 default, 1 from the process-wide table, 2 set or tuned on this simulation
   // second stream of the step graph: the blob-side prologue runs beside the RHS
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -200,7 +205,7 @@ FftCtx<R> fft_ctx(const icm_sim* s) {
   f.dy = (const cplx_t<R>*)s->dy; f.ddy = (const R*)s->ddy;
   f.dz = (const cplx_t<R>*)s->dz; f.ddz = (const R*)s->ddz;
   f.spec = (cplx_t<R>*)s->spec;
-  f.zmap = s->has_zmap ? s->zmap : nullptr;
+  f.zmap = s->has_zmap && s->plan.tma_z ? s->zmap : nullptr;
   f.err = s->err_dev;
   return f;
 }
@@ -213,6 +218,7 @@ GridParams grid_params(const icm_sim* s) {
   g.key0 = (uint32_t)(s->seed & 0xffffffffu);
   g.key1 = (uint32_t)(s->seed >> 32);
   g.advection = s->advection ? 1 : 0;
+  g.kz = s->plan.rhs_kz;
   return g;
 }
 
@@ -428,7 +434,7 @@ void enqueue_step(icm_sim* s, Prof* prof) {
       s->nb == 0 ? nullptr : ((s->trap_k != 0.0 || wca) ? s->fe : (s->any_force ? s->f : nullptr));
   // thermal drift (Appendix B.2) at q^{n+1/2}, added to the right-hand side of the first solve
   const bool drift = (s->flags & ICM_FLAG_THERMAL_DRIFT) && s->kT > 0.0 && s->nb > 0;
-  const bool fused = s->fused && s->nb > 0;
+  const bool fused = s->fused && s->plan.fused_blobs && s->nb > 0;
   RowBins bins;
   bins.count = s->bin_idx;
   bins.start = s->bin_idx + s->nrowblk;
@@ -444,7 +450,7 @@ void enqueue_step(icm_sim* s, Prof* prof) {
   // The blob-side prologue (scalars, predictor, pair forces, bins) reads only v and the
   // blob state: in the step graph it runs on a second stream beside the RHS and joins
   // before the first solve.  Instrumented steps keep one stream.
-  const bool fork = prof == nullptr;
+  const bool fork = prof == nullptr && s->plan.fork;
   cudaStream_t sb = fork ? s->aux : st;
   if (fork) {
     cudaEventRecord(s->ev_fork, st);
@@ -539,8 +545,38 @@ void enqueue_step(icm_sim* s, Prof* prof) {
 }
 #undef ICM_STAGE
 
+// Process-wide table of tuned plans (icm_autotune), keyed by what the speed of a step
+// depends on.
+std::mutex g_plan_mu;
+std::map<std::string, icm_plan> g_plans;
+
+std::string plan_key(const icm_sim* s) {
+  int bucket = 0;
+  while ((1ll << bucket) < s->nb + 1) ++bucket;
+  char buf[160];
+  snprintf(buf, sizeof(buf), "%d,%d,%d,%d,%d,%d,%d,%d", s->nx, s->ny, s->nz, s->prec, s->kernel, s->flags, bucket,
+           s->any_me ? 1 : 0);
+  return buf;
+}
+
+// Before a capture: simulations without a plan of their own take the tuned plan of
+// their key, if there is one.
+void resolve_plan(icm_sim* s) {
+  if (s->plan_src == 2) return;
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  auto it = g_plans.find(plan_key(s));
+  if (it != g_plans.end()) {
+    s->plan = it->second;
+    s->plan_src = 1;
+  } else if (s->plan_src == 1) {
+    s->plan = icm_plan{1, 1, 16, 1};
+    s->plan_src = 0;
+  }
+}
+
 icm_status capture_graph(icm_sim* s) {
   invalidate_graph(s);
+  resolve_plan(s);
   cudaGraph_t graph = nullptr;
   ICM_CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
   if (s->prec == 32)
@@ -696,6 +732,40 @@ void enqueue_coupling(icm_sim* s, long long n, const double* qdev, const double*
     }
 }
 }  // namespace
+
+// A device copy of everything a step changes (fields, blob arrays, scalars, counters),
+// for the autotuner's trial steps.
+struct StateCopy {
+  icm_sim* s;
+  size_t fbytes, bbytes;
+  Tmp v, adv, blob, sc;
+  explicit StateCopy(icm_sim* s_)
+      : s(s_),
+        fbytes(3 * (size_t)s_->ncell * s_->rsize()),
+        bbytes(s_->blob ? sizeof(double) * (13 * 3 + 2) * (size_t)s_->cap : 0),
+        v(s_, fbytes),
+        adv(s_, fbytes),
+        blob(s_, bbytes),
+        sc(s_, sizeof(double) * SC_COUNT + 64) {}
+  bool ok() const { return v.p && adv.p && blob.p && sc.p; }
+  icm_status copy(bool save) {
+    auto cp = [&](void* dev, void* keep, size_t n) -> cudaError_t {
+      return n ? cudaMemcpyAsync(save ? keep : dev, save ? dev : keep, n, cudaMemcpyDeviceToDevice, s->stream)
+               : cudaSuccess;
+    };
+    char* k = (char*)sc.p;
+    ICM_CK(cp(s->v, v.p, fbytes));
+    ICM_CK(cp(s->adv, adv.p, fbytes));
+    ICM_CK(cp(s->blob, blob.p, bbytes));
+    ICM_CK(cp(s->scal, k, sizeof(double) * SC_COUNT));
+    ICM_CK(cp(s->step_dev, k + sizeof(double) * SC_COUNT, sizeof(long long)));
+    ICM_CK(cp(s->hist_dev, k + sizeof(double) * SC_COUNT + 8, sizeof(int)));
+    ICM_CK(cudaStreamSynchronize(s->stream));
+    return ICM_OK;
+  }
+  icm_status save() { return copy(true); }
+  icm_status restore() { return copy(false); }
+};
 
 extern "C" {
 
@@ -938,6 +1008,88 @@ icm_status icm_step(icm_sim* s, int64_t nsteps) {
     if (st != ICM_OK) return st;
   }
   for (int64_t i = 0; i < nsteps; ++i) ICM_CK(cudaGraphLaunch(s->gexec, s->stream));
+  return ICM_OK;
+}
+
+icm_status icm_get_plan(const icm_sim* s, icm_plan* out) {
+  if (!s || !out) return fail(ICM_EINVAL, "NULL argument");
+  *out = s->plan;
+  return ICM_OK;
+}
+
+icm_status icm_set_plan(icm_sim* s, const icm_plan* plan) {
+  if (!s || !plan) return fail(ICM_EINVAL, "NULL argument");
+  if (plan->rhs_kz < 4 || plan->rhs_kz > 64) return fail(ICM_EINVAL, "rhs_kz must be in 4..64");
+  s->plan = icm_plan{plan->fused_blobs ? 1 : 0, plan->tma_z ? 1 : 0, plan->rhs_kz, plan->fork ? 1 : 0};
+  s->plan_src = 2;
+  invalidate_graph(s);
+  return ICM_OK;
+}
+
+icm_status icm_autotune(icm_sim* s, int32_t nsteps, icm_plan* chosen, double* ms_per_step) {
+  if (!s) return fail(ICM_EINVAL, "NULL simulation");
+  if (nsteps < 1) return fail(ICM_EINVAL, "nsteps must be >= 1");
+  ICM_CK(cudaStreamSynchronize(s->stream));
+  ICM_CK(cudaStreamSynchronize(s->aux));
+  icm_status st = check_device_errors(s);
+  if (st != ICM_OK) return st;
+  StateCopy keep(s);
+  if (!keep.ok()) return fail(ICM_ENOMEM, "no device memory for the autotuner's state copy");
+  if ((st = keep.save()) != ICM_OK) return st;
+  auto copy_state = [&](bool) -> icm_status { return keep.restore(); };
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ICM_CK(cudaEventCreate(&e0));
+  ICM_CK(cudaEventCreate(&e1));
+  auto trial = [&](const icm_plan& p, double& ms) -> icm_status {
+    s->plan = p;
+    s->plan_src = 2;
+    icm_status r = capture_graph(s);
+    if (r != ICM_OK) return r;
+    ICM_CK(cudaGraphLaunch(s->gexec, s->stream));   // warm-up
+    ICM_CK(cudaEventRecord(e0, s->stream));
+    for (int i = 0; i < nsteps; ++i) ICM_CK(cudaGraphLaunch(s->gexec, s->stream));
+    ICM_CK(cudaEventRecord(e1, s->stream));
+    ICM_CK(cudaStreamSynchronize(s->stream));
+    float t = 0.0f;
+    ICM_CK(cudaEventElapsedTime(&t, e0, e1));
+    ms = t / nsteps;
+    r = check_device_errors(s);
+    const icm_status rs = copy_state(false);
+    return r != ICM_OK ? r : rs;
+  };
+  icm_plan best = s->plan;
+  double best_ms = 0.0;
+  st = trial(best, best_ms);
+  // one choice at a time, the others held at the best so far
+  std::vector<std::pair<int icm_plan::*, std::vector<int>>> knobs;
+  if (s->fused) knobs.push_back({&icm_plan::fused_blobs, {1, 0}});
+  if (s->has_zmap) knobs.push_back({&icm_plan::tma_z, {1, 0}});
+  knobs.push_back({&icm_plan::rhs_kz, {8, 16, 32}});
+  knobs.push_back({&icm_plan::fork, {1, 0}});
+  for (size_t k = 0; st == ICM_OK && k < knobs.size(); ++k)
+    for (int val : knobs[k].second) {
+      if (best.*(knobs[k].first) == val) continue;
+      icm_plan p = best;
+      p.*(knobs[k].first) = val;
+      double ms = 0.0;
+      if ((st = trial(p, ms)) != ICM_OK) break;
+      if (ms < best_ms) {
+        best = p;
+        best_ms = ms;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != ICM_OK) return st;
+  s->plan = best;
+  s->plan_src = 2;
+  invalidate_graph(s);
+  {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    g_plans[plan_key(s)] = best;
+  }
+  if (chosen) *chosen = best;
+  if (ms_per_step) *ms_per_step = best_ms;
   return ICM_OK;
 }
 
@@ -1383,6 +1535,11 @@ icm_status icm_batch_step(icm_batch* b, int64_t nsteps) {
   bool stale = !b->ok;
   for (size_t i = 0; !stale && i < b->sims.size(); ++i) stale = b->versions[i] != b->sims[i]->version;
   if (stale) {
+    for (icm_sim* m : b->sims) {
+      const icm_plan before = m->plan;
+      resolve_plan(m);
+      if (memcmp(&before, &m->plan, sizeof(icm_plan)) != 0) invalidate_graph(m);
+    }
     // work already queued on the members' own streams must precede the batch
     for (icm_sim* s : b->sims) cudaStreamSynchronize(s->stream);
     const icm_status st = batch_capture(b);
@@ -1393,6 +1550,75 @@ icm_status icm_batch_step(icm_batch* b, int64_t nsteps) {
   cudaEvent_t done = b->events.back();
   ICM_CK(cudaEventRecord(done, b->stream));
   for (icm_sim* s : b->sims) ICM_CK(cudaStreamWaitEvent(s->stream, done, 0));
+  return ICM_OK;
+}
+
+icm_status icm_batch_autotune(icm_batch* b, int32_t nsteps) {
+  if (!b || nsteps < 1) return fail(ICM_EINVAL, "bad arguments");
+  if (b->sims.empty()) return ICM_OK;
+  if (b->stream) ICM_CK(cudaStreamSynchronize(b->stream));
+  // the members' states, restored after every trial
+  std::vector<std::unique_ptr<StateCopy>> keep;
+  for (icm_sim* m : b->sims) {
+    ICM_CK(cudaStreamSynchronize(m->stream));
+    keep.emplace_back(new StateCopy(m));
+    if (!keep.back()->ok()) return fail(ICM_ENOMEM, "no device memory for the autotuner's state copy");
+    const icm_status st = keep.back()->save();
+    if (st != ICM_OK) return st;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ICM_CK(cudaEventCreate(&e0));
+  ICM_CK(cudaEventCreate(&e1));
+  // one plan for every member (what matters is how the members share the GPU)
+  auto trial = [&](const icm_plan& p, double& ms) -> icm_status {
+    for (icm_sim* m : b->sims) {
+      m->plan = p;
+      m->plan_src = 2;
+      invalidate_graph(m);
+    }
+    icm_status r = icm_batch_step(b, 1);   // capture and warm-up
+    if (r != ICM_OK) return r;
+    ICM_CK(cudaEventRecord(e0, b->stream));
+    if ((r = icm_batch_step(b, nsteps)) != ICM_OK) return r;
+    ICM_CK(cudaEventRecord(e1, b->stream));
+    ICM_CK(cudaStreamSynchronize(b->stream));
+    float t = 0.0f;
+    ICM_CK(cudaEventElapsedTime(&t, e0, e1));
+    ms = t / nsteps;
+    for (size_t i = 0; i < b->sims.size(); ++i) {
+      ICM_CK(cudaStreamSynchronize(b->sims[i]->stream));
+      if ((r = check_device_errors(b->sims[i])) != ICM_OK) return r;
+      if ((r = keep[i]->restore()) != ICM_OK) return r;
+    }
+    return ICM_OK;
+  };
+  icm_plan best = icm_plan{1, 1, 16, 1};
+  double best_ms = 0.0;
+  icm_status st = trial(best, best_ms);
+  const std::vector<std::pair<int icm_plan::*, std::vector<int>>> knobs = {
+      {&icm_plan::fused_blobs, {1, 0}}, {&icm_plan::tma_z, {1, 0}}, {&icm_plan::rhs_kz, {8, 16, 32}},
+      {&icm_plan::fork, {1, 0}}};
+  for (size_t k = 0; st == ICM_OK && k < knobs.size(); ++k)
+    for (int val : knobs[k].second) {
+      if (best.*(knobs[k].first) == val) continue;
+      icm_plan p = best;
+      p.*(knobs[k].first) = val;
+      double ms = 0.0;
+      if ((st = trial(p, ms)) != ICM_OK) break;
+      if (ms < best_ms) {
+        best = p;
+        best_ms = ms;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != ICM_OK) return st;
+  for (icm_sim* m : b->sims) {
+    m->plan = best;
+    m->plan_src = 2;
+    invalidate_graph(m);
+  }
+  batch_clear_graph(b);
   return ICM_OK;
 }
 

@@ -12,7 +12,6 @@ namespace icm {
 namespace {
 
 constexpr int TX = 32, TY = 16;     // cells per block in x and y (one thread each)
-constexpr int KZ = 16;              // z planes marched per block
 constexpr int HX = TX + 2, HY = TY + 2;
 constexpr int HALO = HX * HY;       // cells of one plane with a one-cell halo
 constexpr int NT = TX * TY;         // threads per block
@@ -112,7 +111,7 @@ __device__ __forceinline__ void store_plane(RhsSmem<R>& sm, int slot, const R (&
   }
 }
 
-// Marching block: TX x TY cells per plane, KZ planes.  Per plane: the loads of the
+// Marching block: TX x TY cells per plane, g.kz planes (a plan choice).  Per plane: the loads of the
 // plane after next are issued first, the stress normals of the next plane are
 // generated while they are in flight, then the current plane is computed entirely
 // from shared memory.
@@ -124,7 +123,7 @@ __global__ void __launch_bounds__(NT, 2) k_rhs(const R* __restrict__ v, R* __res
   RhsSmem<R>& sm = *reinterpret_cast<RhsSmem<R>*>(smem_raw);
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = tx + TX * ty;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * KZ;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * g.kz;
   const int i = i0 + tx, j = j0 + ty;
   const bool active = i < g.nx && j < g.ny;
   const uint32_t step = (uint32_t)(*step_dev);
@@ -150,7 +149,7 @@ __global__ void __launch_bounds__(NT, 2) k_rhs(const R* __restrict__ v, R* __res
     gen_plane<R>(sm, 0, i0, j0, k0 - 1, g, step, tid);
     gen_plane<R>(sm, 1, i0, j0, k0, g, step, tid);
   }
-  const int kend = min(k0 + KZ, g.nz);
+  const int kend = min(k0 + g.kz, g.nz);
   for (int k = k0; k < kend; ++k) {
     const int kk = k - k0;
     const int sp = kk % 3, sc = (kk + 1) % 3, sn = (kk + 2) % 3;
@@ -326,7 +325,7 @@ size_t rhs_smem() { return sizeof(RhsSmem<R>); }
 template <typename R>
 void explicit_rhs(const GridParams& g, const R* v, R* adv, R* rhs, const long long* step_dev, const int* hist_dev,
                   cudaStream_t st) {
-  const dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + KZ - 1) / KZ);
+  const dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + g.kz - 1) / g.kz);
   const dim3 block(TX, TY);
   if (g.kT > 0.0)
     k_rhs<R, true><<<grid, block, rhs_smem<R>(), st>>>(v, adv, rhs, g, step_dev, hist_dev);

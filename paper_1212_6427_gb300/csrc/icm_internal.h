@@ -98,6 +98,7 @@ struct GridParams {
   double h, rho, eta, kT, dt;
   uint32_t key0, key1;
   int advection;
+  int kz;           // z planes marched per block of the RHS kernel (>= 1)
 };
 
 // r = (rho/dt) v + (eta/2) L v + div Sigma^n - (3/2 A^n - 1/2 A^{n-1}); adv <- A^n.

@@ -45,7 +45,8 @@ def _alone(icm, j):
 
 
 @pytest.mark.parametrize("precision", [64, 32])
-def test_batch_matches_individual_runs(icm, precision):
+@pytest.mark.parametrize("tune", [False, True])
+def test_batch_matches_individual_runs(icm, precision, tune):
     jobs = _jobs(precision, 4)
     sims = []
     for j in jobs:
@@ -55,6 +56,9 @@ def test_batch_matches_individual_runs(icm, precision):
         sims.append(s)
     b = icm.icm_batch_create()
     icm.icm_batch_set(b, [s.handle for s in sims])
+    if tune:   # the batch autotuner runs trial steps and restores every member's state
+        icm.icm_batch_autotune(b, 2)
+        assert all(s.read()["step"] == 0 for s in sims)
     icm.icm_batch_step(b, 5)
     icm.icm_batch_sync(b)
     for j, s in zip(jobs, sims):
