@@ -1,0 +1,105 @@
+"""The full-size workloads (256^3 grid with 20000 blobs, 4-point kernel; 128^3 with 2000
+blobs, 3-point) in the launch configuration bench.py times, checked where the oracle
+cannot follow a whole step: one FP32 step against the FP64 GPU step from the same state
+(the FP64 path is itself held to the oracle at 1e-12), the conservation laws of the
+step, and the operators of the step against the oracle at full size."""
+import numpy as np
+import pytest
+
+import icm_workloads as wl
+from oracle import icm as oracle
+
+from _gpu_helpers import TOL, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def icm():
+    import paper_1212_6427_gb300 as m
+    from paper_1212_6427_gb300 import build
+    build.build_library()
+    return m
+
+
+@pytest.fixture(scope="module")
+def large():
+    w = wl.workload("large")
+    w["v0"] = wl.random_fluid(w["grid"], 0.05, 7)
+    return w
+
+
+def _sim(icm, w, precision):
+    s = icm.Simulation(w["grid"], w["h"], w["rho"], w["eta"], w["kT"], w["dt"], w["kernel"], w["seed"], precision)
+    s.add_blobs(w["q"], w["u"], w["me"])
+    s.set_forces(w["force"])
+    s.write(w["q"], w["u"], w["v0"].ravel(), None, None, 0)
+    return s
+
+
+def test_large_fp32_step_matches_fp64_step(icm, large):
+    """Two steps of the tuned FP32 step (the plan bench.py times) against the FP64 path."""
+    s32 = _sim(icm, large, 32)
+    icm.icm_autotune(s32.handle, 2)        # state restored; the plan bench.py uses
+    s64 = _sim(icm, large, 64)
+    s32.step(2)
+    s64.step(2)
+    a, b = s32.read(fluid=True), s64.read(fluid=True)
+    assert a["step"] == b["step"] == 2
+    assert rel(a["fluid"], b["fluid"]) < TOL[32]
+    assert rel(a["vel"], b["vel"]) < TOL[32]
+    L = np.array(large["grid"], dtype=float) * large["h"]
+    dq = a["pos"] - b["pos"]
+    dq -= L * np.round(dq / L)
+    disp = b["pos"] - large["q"]
+    disp -= L * np.round(disp / L)
+    assert np.linalg.norm(dq) < TOL[32] * np.linalg.norm(disp)
+    s32.close()
+    s64.close()
+
+
+def test_large_step_momentum_and_divergence(icm, large):
+    """P^{n+1} - P^n = dt sum F (FP64 bookkeeping) and D v^{n+1} = 0 to FP32 roundoff."""
+    s = _sim(icm, large, 32)
+    p0 = s.read()["momentum"]
+    s.step(1)
+    r = s.read(fluid=True)
+    dP = r["momentum"] - p0
+    want = large["dt"] * np.asarray(large["force"]).sum(axis=0)
+    np.testing.assert_allclose(dP, want, rtol=1e-9, atol=1e-12 * np.abs(p0).max())
+    nx, ny, nz = large["grid"]
+    v = r["fluid"].reshape(3, nz, ny, nx)
+    div = oracle.divergence(v, large["h"])
+    assert np.abs(div).max() < 1e-4 * np.abs(v).max() / large["h"]
+    s.close()
+
+
+def test_large_operators_match_oracle(icm, large):
+    """Solve, interpolation and spreading at 256^3 with 20000 blobs (FP32 bar)."""
+    w = large
+    s = icm.Simulation(w["grid"], w["h"], w["rho"], w["eta"], w["kT"], w["dt"], w["kernel"], w["seed"], 32)
+    v = w["v0"]
+    got = icm.icm_op_spectral_solve(s.handle, w["rho"] / w["dt"], 0.5 * w["eta"], v.ravel())
+    assert rel(got, oracle.spectral_solve(v, w["rho"] / w["dt"], 0.5 * w["eta"], w["h"])) < TOL[32] / 2
+    assert rel(icm.icm_op_interpolate(s.handle, w["q"], v.ravel()), oracle.interpolate(v, w["q"], 4, w["h"])) \
+        < TOL[32] / 2
+    shape = (w["grid"][2], w["grid"][1], w["grid"][0])
+    F = np.random.default_rng(3).standard_normal((len(w["q"]), 3))
+    assert rel(icm.icm_op_spread(s.handle, s.ncell, w["q"], F), oracle.spread(F, w["q"], 4, w["h"], shape)) \
+        < TOL[32] / 2
+    s.close()
+
+
+def test_bulk_rhs_matches_oracle(icm):
+    """The explicit right-hand side at 128^3 (stress normals, advection, AB2) against the oracle."""
+    w = wl.workload("bulk")
+    s = icm.Simulation(w["grid"], w["h"], w["rho"], w["eta"], w["kT"], w["dt"], w["kernel"], w["seed"], 32)
+    v = wl.random_fluid(w["grid"], 0.05, 8)
+    a_prev = wl.random_fluid(w["grid"], 0.01, 9)
+    r, a = icm.icm_op_explicit_rhs(s.handle, v.ravel(), a_prev.ravel(), 5)
+    prm = oracle.Params(w["grid"], h=w["h"], rho=w["rho"], eta=w["eta"], kT=w["kT"], dt=w["dt"], kernel=w["kernel"],
+                        seed=w["seed"])
+    rw, aw = oracle.explicit_rhs(v, a_prev, 5, prm)
+    assert rel(r, rw) < TOL[32] / 2
+    assert rel(a, aw) < TOL[32] / 2
+    s.close()
