@@ -401,20 +401,20 @@ def run_batch(args, rank, world, dist):
         sims.append(s)
     cells = sum(int(np.prod(r["grid"])) for r in reps)
     blobs = sum(len(r["q"]) for r in reps)
-    step_bytes = 0.0
-    launches = 0
-    for s in sims:
-        prof = s.profile(1)
-        step_bytes += sum(by for _, _, by in prof)
-        launches += sum(1 for n, _, _ in prof if kernel_of(n) != "zero")
     b = icm.icm_batch_create()
     icm.icm_batch_set(b, [s.handle for s in sims])
     plans = "default"
     if not args.no_autotune:
         icm.icm_batch_autotune(b, 3)
         plans = sorted({str(icm.icm_get_plan(s.handle)) for s in sims})
+    grouped = icm.icm_batch_get_grouped(b)
+    # algorithmic bytes of one step of every member, with the plans the batch runs
+    step_bytes = 0.0
+    for s in sims:
+        step_bytes += sum(by for _, _, by in s.profile(1))
     icm.icm_batch_step(b, max(args.warmup, 3))
     icm.icm_batch_sync(b)
+    launches = icm.icm_batch_kernels_per_step(b)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -445,7 +445,7 @@ def run_batch(args, rank, world, dist):
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "icm-batch-64-replicas-sides-32-48-64-96-fp32", "replicas": 64 * world,
-                       "plans": plans,
+                       "plans": plans, "group_solves": bool(grouped),
                        "cells_per_replica_set": cells, "blobs": blobs, "parallelism": "replicas only",
                        "l2": "replica set of %.0f MB per field: timed on host clock around whole batch steps"
                              % (3 * cells * 4 / 1e6)},

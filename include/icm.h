@@ -304,9 +304,25 @@ icm_status icm_batch_set(icm_batch* batch, int32_t n, icm_sim* const* sims);
  * member's own stream is ordered after these steps. */
 icm_status icm_batch_step(icm_batch* batch, int64_t nsteps);
 
+/* Group solves (grouped = 1; default 0): members on the same grid (precision,
+ * sides and cell width h) run each of the three fluid solves of a step (Sec. III.C,
+ * steps 2, 5 and 6) as one set of FFT launches over all of them, between which each
+ * member's own stencil and blob kernels run on its stream; members take the separate
+ * (unfused) blob path and the plain z pass.  A grid whose sides lack register FFT
+ * passes, or that only one member has, runs its step as usual.  Results agree with
+ * ungrouped steps to rounding.  Synchronises when the setting changes.
+ * Errors: ICM_EINVAL for grouped other than 0 or 1. */
+icm_status icm_batch_set_grouped(icm_batch* batch, int32_t grouped);
+/* The current setting (0 or 1), -1 for a NULL batch. */
+int32_t icm_batch_get_grouped(const icm_batch* batch);
+/* Kernel launches in one batch step of the captured graph (the graph is captured by
+ * the first icm_batch_step after a change); -1 before a capture or for NULL. */
+int64_t icm_batch_kernels_per_step(const icm_batch* batch);
+
 /* Autotune the batch as a whole: candidate plans (one choice at a time, as
- * icm_autotune) are applied to every member and timed over nsteps batch steps; every
- * member's state is restored after each trial and the fastest plan is fixed on all
+ * icm_autotune) are applied to every member and timed over nsteps batch steps,
+ * then group solves (icm_batch_set_grouped) with that plan; every member's state is
+ * restored after each trial and the fastest choice is fixed on the batch and all
  * members.  Synchronises.  Errors: as icm_autotune. */
 icm_status icm_batch_autotune(icm_batch* batch, int32_t nsteps);
 

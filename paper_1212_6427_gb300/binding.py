@@ -61,6 +61,9 @@ SIGNATURES = {
     "icm_set_plan": (_c_i32, [_vp, ctypes.c_void_p]),
     "icm_autotune": (_c_i32, [_vp, _c_i32, ctypes.c_void_p, _dp]),
     "icm_batch_autotune": (_c_i32, [_vp, _c_i32]),
+    "icm_batch_set_grouped": (_c_i32, [_vp, _c_i32]),
+    "icm_batch_get_grouped": (_c_i32, [_vp]),
+    "icm_batch_kernels_per_step": (_c_i64, [_vp]),
     "icm_set_blob_wca": (_c_i32, [_vp, ctypes.c_double, ctypes.c_double]),
     "icm_step": (_c_i32, [_vp, _c_i64]),
     "icm_sync": (_c_i32, [_vp]),
@@ -231,6 +234,18 @@ def icm_autotune(sim, nsteps=3):
 
 def icm_batch_autotune(batch, nsteps=3):
     _check(lib().icm_batch_autotune(batch, int(nsteps)))
+
+
+def icm_batch_set_grouped(batch, grouped):
+    _check(lib().icm_batch_set_grouped(batch, int(grouped)))
+
+
+def icm_batch_get_grouped(batch):
+    return int(lib().icm_batch_get_grouped(batch))
+
+
+def icm_batch_kernels_per_step(batch):
+    return int(lib().icm_batch_kernels_per_step(batch))
 
 
 def icm_step(sim, nsteps=1):

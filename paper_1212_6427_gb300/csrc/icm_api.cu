@@ -398,9 +398,44 @@ struct Prof {
     if (prof) prof->end(st);                   \
   } while (0)
 
-// The nine steps of Sec. III.C for one time level, enqueued on s->stream.
+// Segments 1-3 of a step whose three solves run as group launches over several
+// simulations (the separate blob path of enqueue_step between the solves).
 template <typename R>
-void enqueue_step(icm_sim* s, Prof* prof) {
+void enqueue_segment(icm_sim* s, int segment, int last) {
+  cudaStream_t st = s->stream;
+  const BlobParams bp = blob_params(s);
+  const BlobState bs = blob_state(s);
+  R* v = (R*)s->v;
+  R* work = (R*)s->work;
+  const double dvf = s->h * s->h * s->h;
+  const size_t fbytes = 3 * (size_t)s->ncell * sizeof(R);
+  if (segment == 1 && s->any_me) {
+    // step 4, and the spread of step 5
+    blob_momentum_change<R>(bp, bs, v, st);
+    cudaMemsetAsync(work, 0, fbytes, st);
+    blob_spread<R>(bp, s->nb, s->qh, s->cdp, work, st);
+  } else if (segment == 2) {
+    // steps 6 and 8 (blob side), and the spread of step 6
+    blob_inertial<R>(bp, bs, work, st);
+    cudaMemsetAsync(work, 0, fbytes, st);
+    blob_spread<R>(bp, s->nb, s->qh, s->src, work, st);
+  }
+  if (segment == last) {
+    // step 9
+    if (s->any_me)
+      blob_finish<R>(bp, bs, v, work, true, st);
+    else
+      blob_finish<R>(bp, bs, v, nullptr, false, st);
+    scalars_after_step(s->scal, s->dt, s->rho, dvf, s->any_me, s->step_dev, s->hist_dev, st);
+  }
+}
+
+// The nine steps of Sec. III.C for one time level, enqueued on s->stream.  With a
+// segment index (batched group solves) only the blob and stencil work between two
+// solves is enqueued: segment 0 ends before the first solve, segments 1 and 2 after
+// the first and second, segment 3 after the third; the caller runs the solves.
+template <typename R>
+void enqueue_step(icm_sim* s, Prof* prof, int segment = -1) {
   cudaStream_t st = s->stream;
   const FftCtx<R> fc = fft_ctx<R>(s);
   const GridParams gp = grid_params(s);
@@ -434,7 +469,7 @@ void enqueue_step(icm_sim* s, Prof* prof) {
       s->nb == 0 ? nullptr : ((s->trap_k != 0.0 || wca) ? s->fe : (s->any_force ? s->f : nullptr));
   // thermal drift (Appendix B.2) at q^{n+1/2}, added to the right-hand side of the first solve
   const bool drift = (s->flags & ICM_FLAG_THERMAL_DRIFT) && s->kT > 0.0 && s->nb > 0;
-  const bool fused = s->fused && s->plan.fused_blobs && s->nb > 0;
+  const bool fused = s->fused && s->plan.fused_blobs && s->nb > 0 && segment < 0;
   RowBins bins;
   bins.count = s->bin_idx;
   bins.start = s->bin_idx + s->nrowblk;
@@ -450,11 +485,17 @@ void enqueue_step(icm_sim* s, Prof* prof) {
   // The blob-side prologue (scalars, predictor, pair forces, bins) reads only v and the
   // blob state: in the step graph it runs on a second stream beside the RHS and joins
   // before the first solve.  Instrumented steps keep one stream.
-  const bool fork = prof == nullptr && s->plan.fork;
+  const bool grouped = segment >= 0;
+  const bool fork = prof == nullptr && s->plan.fork && !grouped;
   cudaStream_t sb = fork ? s->aux : st;
   if (fork) {
     cudaEventRecord(s->ev_fork, st);
     cudaStreamWaitEvent(sb, s->ev_fork, 0);
+  }
+  const int last = s->any_me ? 3 : 1;
+  if (segment > 0) {
+    enqueue_segment<R>(s, segment, last);
+    return;
   }
   ICM_STAGE("scalars", 0, scalars_before_step(s->scal, s->dt, s->rho, dvf, sb));
   // step 1: midpoint predictor (Eq. particle_pred)
@@ -522,6 +563,7 @@ void enqueue_step(icm_sim* s, Prof* prof) {
     return;
   }
   if (fvec) ICM_STAGE("spread", 2 * gath + nb * 48, blob_spread<R>(bp, s->nb, s->qh, fvec, work, st));
+  if (grouped) return;
   solve("rt1", work, v, nullptr, OUT_STORE, s->rho / s->dt, 0.5 * s->eta, s->scal + SC_K0);
   if (s->any_me) {
     // step 4: slip correction and momentum change (Eq. delta_u_nph_visc)
@@ -1394,14 +1436,24 @@ icm_status icm_op_philox(int64_t n, uint32_t ctr0, uint32_t ctr1, uint32_t ctr2,
 // join back), so one graph launch advances all of them and the GPU runs the
 // members' kernels side by side.
 // ---------------------------------------------------------------------------
+// With group solves on, members of the same grid (precision, sides and cell width,
+// hence the same FFT tables and symbols) run each of the three solves of a step as
+// one set of five launches over all of them, on a stream of the group: the members'
+// stencil and blob work runs on their own streams between the solves.  This divides
+// the number of FFT launches per step by the group size, for batches of many small
+// grids whose launches are too short to fill the GPU.
 struct icm_batch {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::vector<icm_sim*> sims;
   std::vector<long long> versions;
-  std::vector<cudaEvent_t> events;  // fork, joins, done
+  std::vector<cudaEvent_t> events;  // fork, joins, ..., done (last)
   cudaGraphExec_t gexec = nullptr;
   bool ok = false;
+  int grouped = 0;
+  long long kernels = -1;              // kernel nodes of the captured step graph
+  std::vector<cudaStream_t> gstreams;  // one per group of the last capture
+  void* reps = nullptr;                // device tables of the group solves
 };
 
 namespace {
@@ -1412,30 +1464,173 @@ void batch_clear_graph(icm_batch* b) {
   b->ok = false;
   for (cudaEvent_t e : b->events) cudaEventDestroy(e);
   b->events.clear();
+  if (b->reps) cudaFree(b->reps);
+  b->reps = nullptr;
+}
+
+struct SolveGroup {
+  std::vector<icm_sim*> members;  // every member: the first solve
+  std::vector<icm_sim*> inertial; // members with excess mass: the second and third
+  size_t table[3] = {0, 0, 0};    // offsets (in RepFft entries) of the three tables
+};
+
+bool same_grid(const icm_sim* a, const icm_sim* b) {
+  return a->prec == b->prec && a->nx == b->nx && a->ny == b->ny && a->nz == b->nz && a->h == b->h;
+}
+
+RepFft rep_entry(const icm_sim* s, int rt) {
+  RepFft r;
+  const double dvf = s->h * s->h * s->h;
+  const double k0mul = 1.0 / (s->rho * dvf) / (double)s->ncell;
+  r.src = s->work;
+  r.spec = s->spec;
+  r.dst2 = nullptr;
+  if (rt == 0) {        // (rho/dt - eta/2 L) v~ = rhs, projected
+    r.dst = s->v;
+    r.k0sum = s->scal + SC_K0;
+    r.a = s->rho / s->dt;
+    r.b = 0.5 * s->eta;
+    r.k0mul = k0mul;
+  } else if (rt == 1) { // P S dp
+    r.dst = s->work;
+    r.k0sum = nullptr;
+    r.a = 1.0;
+    r.b = 0.0;
+    r.k0mul = 0.0;
+  } else {              // (rho - dt/2 eta L) dv = S src, projected; v += dv
+    r.dst = s->v;
+    r.dst2 = s->work;
+    r.k0sum = s->scal + SC_SUMSRC;
+    r.a = s->rho;
+    r.b = 0.5 * s->dt * s->eta;
+    r.k0mul = k0mul;
+  }
+  return r;
+}
+
+template <typename R>
+void group_solve(const SolveGroup& g, const RepFft* reps, int rt, cudaStream_t st) {
+  const std::vector<icm_sim*>& m = rt == 0 ? g.members : g.inertial;
+  spectral_solve_group<R>(fft_ctx<R>(m[0]), reps + g.table[rt], (int)m.size(),
+                          rt == 2 ? OUT_ADD_AND_STORE2 : OUT_STORE, st);
 }
 
 icm_status batch_capture(icm_batch* b) {
   batch_clear_graph(b);
   const size_t n = b->sims.size();
-  b->events.resize(n + 2);
-  for (auto& e : b->events) ICM_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  // groups of two or more members on a grid with register FFT passes
+  std::vector<SolveGroup> groups;
+  std::vector<int> group_of(n, -1);
+  if (b->grouped) {
+    std::vector<int> leader(n, -1);   // first member on the same grid
+    for (size_t i = 0; i < n; ++i) {
+      const icm_sim* s = b->sims[i];
+      if (!fft_has_group_passes(s->nx, s->ny, s->nz)) continue;
+      leader[i] = (int)i;
+      for (size_t j = 0; j < i; ++j)
+        if (leader[j] == (int)j && same_grid(b->sims[j], s)) {
+          leader[i] = (int)j;
+          break;
+        }
+    }
+    std::map<int, int> gid;
+    for (size_t i = 0; i < n; ++i) {
+      if (leader[i] < 0 || std::count(leader.begin(), leader.end(), leader[i]) < 2) continue;
+      auto it = gid.find(leader[i]);
+      if (it == gid.end()) {
+        it = gid.emplace(leader[i], (int)groups.size()).first;
+        groups.emplace_back();
+      }
+      group_of[i] = it->second;
+      groups[it->second].members.push_back(b->sims[i]);
+      if (b->sims[i]->any_me) groups[it->second].inertial.push_back(b->sims[i]);
+    }
+  }
+  if (!groups.empty()) {
+    std::vector<RepFft> host;
+    for (SolveGroup& g : groups)
+      for (int rt = 0; rt < 3; ++rt) {
+        g.table[rt] = host.size();
+        for (icm_sim* m : rt == 0 ? g.members : g.inertial) host.push_back(rep_entry(m, rt));
+      }
+    ICM_CK(cudaMalloc(&b->reps, host.size() * sizeof(RepFft)));
+    ICM_CK(cudaMemcpy(b->reps, host.data(), host.size() * sizeof(RepFft), cudaMemcpyHostToDevice));
+    while (b->gstreams.size() < groups.size()) {
+      cudaStream_t gs = nullptr;
+      ICM_CK(cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking));
+      b->gstreams.push_back(gs);
+    }
+  }
+  const RepFft* reps = (const RepFft*)b->reps;
+  // events, created before the capture: fork, the edges into and out of every group
+  // solve, the joins, and last the one icm_batch_step records after its launches
+  size_t need = 1 + n + groups.size() + 1;
+  for (const SolveGroup& g : groups) need += g.members.size() + 1 + 2 * (g.inertial.size() + (g.inertial.empty() ? 0 : 1));
+  b->events.resize(need, nullptr);
+  for (auto& ev : b->events) ICM_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  size_t next_event = 0;
+  auto event = [&]() -> cudaEvent_t { return next_event < need ? b->events[next_event++] : nullptr; };
+  auto edge = [&](cudaStream_t from, cudaStream_t to) {
+    cudaEvent_t e = event();
+    cudaEventRecord(e, from);
+    cudaStreamWaitEvent(to, e, 0);
+  };
   cudaGraph_t graph = nullptr;
   ICM_CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-  cudaEventRecord(b->events[0], b->stream);
+  cudaEvent_t fork = event();
+  cudaEventRecord(fork, b->stream);
   for (size_t i = 0; i < n; ++i) {
     icm_sim* s = b->sims[i];
-    cudaStreamWaitEvent(s->stream, b->events[0], 0);
+    cudaStreamWaitEvent(s->stream, fork, 0);
+    const int seg = group_of[i] >= 0 ? 0 : -1;
     if (s->prec == 32)
-      enqueue_step<float>(s, nullptr);
+      enqueue_step<float>(s, nullptr, seg);
     else
-      enqueue_step<double>(s, nullptr);
-    cudaEventRecord(b->events[1 + i], s->stream);
-    cudaStreamWaitEvent(b->stream, b->events[1 + i], 0);
+      enqueue_step<double>(s, nullptr, seg);
   }
+  for (int rt = 0; rt < 3; ++rt) {
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+      const SolveGroup& g = groups[gi];
+      const std::vector<icm_sim*>& m = rt == 0 ? g.members : g.inertial;
+      if (m.empty()) continue;
+      cudaStream_t gs = b->gstreams[gi];
+      for (icm_sim* s : m) edge(s->stream, gs);
+      if (m[0]->prec == 32)
+        group_solve<float>(g, reps, rt, gs);
+      else
+        group_solve<double>(g, reps, rt, gs);
+      cudaEvent_t done = event();
+      cudaEventRecord(done, gs);
+      for (icm_sim* s : m) {
+        cudaStreamWaitEvent(s->stream, done, 0);
+        if (s->prec == 32)
+          enqueue_step<float>(s, nullptr, rt + 1);
+        else
+          enqueue_step<double>(s, nullptr, rt + 1);
+      }
+    }
+  }
+  for (size_t i = 0; i < n; ++i) edge(b->sims[i]->stream, b->stream);
+  for (size_t gi = 0; gi < groups.size(); ++gi) edge(b->gstreams[gi], b->stream);
+  event();   // recorded after the launches of icm_batch_step
   const cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(ICM_ECUDA, "batch graph capture failed: %s", cudaGetErrorString(e));
+  }
+  if (next_event != need) {
+    cudaGraphDestroy(graph);
+    return fail(ICM_ECUDA, "batch capture used %zu of %zu events", next_event, need);
+  }
+  size_t nn = 0;
+  b->kernels = 0;
+  if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn > 0) {
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
+      for (size_t i = 0; i < nn; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++b->kernels;
+      }
   }
   const cudaError_t e2 = cudaGraphInstantiate(&b->gexec, graph, 0);
   cudaGraphDestroy(graph);
@@ -1553,6 +1748,20 @@ icm_status icm_batch_step(icm_batch* b, int64_t nsteps) {
   return ICM_OK;
 }
 
+icm_status icm_batch_set_grouped(icm_batch* b, int32_t grouped) {
+  if (!b || (grouped != 0 && grouped != 1)) return fail(ICM_EINVAL, "bad arguments");
+  if (b->grouped != grouped) {
+    if (b->stream) ICM_CK(cudaStreamSynchronize(b->stream));
+    b->grouped = grouped;
+    batch_clear_graph(b);
+  }
+  return ICM_OK;
+}
+
+int32_t icm_batch_get_grouped(const icm_batch* b) { return b ? b->grouped : -1; }
+
+int64_t icm_batch_kernels_per_step(const icm_batch* b) { return b && b->ok ? b->kernels : -1; }
+
 icm_status icm_batch_autotune(icm_batch* b, int32_t nsteps) {
   if (!b || nsteps < 1) return fail(ICM_EINVAL, "bad arguments");
   if (b->sims.empty()) return ICM_OK;
@@ -1570,7 +1779,11 @@ icm_status icm_batch_autotune(icm_batch* b, int32_t nsteps) {
   ICM_CK(cudaEventCreate(&e0));
   ICM_CK(cudaEventCreate(&e1));
   // one plan for every member (what matters is how the members share the GPU)
-  auto trial = [&](const icm_plan& p, double& ms) -> icm_status {
+  auto trial = [&](const icm_plan& p, int grouped, double& ms) -> icm_status {
+    if (b->grouped != grouped) {
+      b->grouped = grouped;
+      batch_clear_graph(b);
+    }
     for (icm_sim* m : b->sims) {
       m->plan = p;
       m->plan_src = 2;
@@ -1593,8 +1806,9 @@ icm_status icm_batch_autotune(icm_batch* b, int32_t nsteps) {
     return ICM_OK;
   };
   icm_plan best = icm_plan{1, 1, 16, 1};
+  int best_grouped = 0;
   double best_ms = 0.0;
-  icm_status st = trial(best, best_ms);
+  icm_status st = trial(best, best_grouped, best_ms);
   const std::vector<std::pair<int icm_plan::*, std::vector<int>>> knobs = {
       {&icm_plan::fused_blobs, {1, 0}}, {&icm_plan::tma_z, {1, 0}}, {&icm_plan::rhs_kz, {8, 16, 32}},
       {&icm_plan::fork, {1, 0}}};
@@ -1604,12 +1818,26 @@ icm_status icm_batch_autotune(icm_batch* b, int32_t nsteps) {
       icm_plan p = best;
       p.*(knobs[k].first) = val;
       double ms = 0.0;
-      if ((st = trial(p, ms)) != ICM_OK) break;
+      if ((st = trial(p, best_grouped, ms)) != ICM_OK) break;
       if (ms < best_ms) {
         best = p;
         best_ms = ms;
       }
     }
+  // group solves (the members' own plans then matter only for the RHS z march)
+  if (st == ICM_OK) {
+    icm_plan p = best;
+    p.fused_blobs = 0;
+    p.tma_z = 0;
+    p.fork = 0;
+    double ms = 0.0;
+    st = trial(p, 1, ms);
+    if (st == ICM_OK && ms < best_ms) {
+      best = p;
+      best_grouped = 1;
+      best_ms = ms;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != ICM_OK) return st;
@@ -1618,6 +1846,7 @@ icm_status icm_batch_autotune(icm_batch* b, int32_t nsteps) {
     m->plan_src = 2;
     invalidate_graph(m);
   }
+  b->grouped = best_grouped;
   batch_clear_graph(b);
   return ICM_OK;
 }
@@ -1637,6 +1866,7 @@ void icm_batch_destroy(icm_batch* b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
   batch_clear_graph(b);
+  for (cudaStream_t gs : b->gstreams) cudaStreamDestroy(gs);
   if (b->own_stream) cudaStreamDestroy(b->stream);
   delete b;
 }

@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(kThreads) k_xfwd(const R* __restrict__ src, cp
   int* pof = reinterpret_cast<int*>(tw + N);
   const int tid = threadIdx.x;
   load_tables<R>(tw, pof, P, tid);
-  const int comp = blockIdx.y;
+  const int comp = blockIdx.y % 3;
   const long long row0 = (long long)blockIdx.x * (2 * kXLines);
   const R* s = src + comp * ncell;
   for (int idx = tid; idx < 2 * kXLines * N; idx += kThreads) {
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(kThreads) k_xinv(const cplx_t<R>* __restrict__
   const int tid = threadIdx.x;
   load_tables<R>(tw, pof, P, tid);
   __syncthreads();
-  const int comp = blockIdx.y;
+  const int comp = blockIdx.y % 3;
   const long long row0 = (long long)blockIdx.x * (2 * kXLines);
   const C* in = spec + (size_t)comp * nrows * kxp;
   const C zero = mk(R(0), R(0));
@@ -557,8 +557,17 @@ __device__ __forceinline__ void zsym_tile(cplx_t<R>* __restrict__ buf, const cpl
 
 template <typename R, int N, int R1, int R2>
 __global__ void __launch_bounds__(zsym2_threads<R, N, R1, R2>(), sizeof(R) == 4 ? 2 : 1)
-    k_zsym2(cplx_t<R>* __restrict__ spec, const cplx_t<R>* __restrict__ gtw, int ny, int kx, int kxp, SymParams<R> sp) {
+    k_zsym2(cplx_t<R>* __restrict__ spec, const cplx_t<R>* __restrict__ gtw, int ny, int kx, int kxp, SymParams<R> sp,
+            const RepFft* __restrict__ reps) {
   using C = cplx_t<R>;
+  if (reps != nullptr) {   // replica blockIdx.z of a group solve
+    const RepFft& rp = reps[blockIdx.z];
+    spec = reinterpret_cast<C*>(rp.spec);
+    sp.a = (R)rp.a;
+    sp.b = (R)rp.b;
+    sp.k0sum = rp.k0sum;
+    sp.k0mul = rp.k0mul;
+  }
   constexpr int NL = kZLines;
   constexpr int NT = zsym2_threads<R, N, R1, R2>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -686,15 +695,16 @@ __global__ void __launch_bounds__(zsym2_threads<R, N, R1, R2>(), sizeof(R) == 4 
 
 template <typename R, int N, int R1, int R2, bool INV>
 __global__ void __launch_bounds__(kThreads) k_ypass2(cplx_t<R>* __restrict__ spec, const cplx_t<R>* __restrict__ gtw,
-                                                     int nz, int kx, int kxp) {
+                                                     int nz, int kx, int kxp, const RepFft* __restrict__ reps) {
   using C = cplx_t<R>;
   constexpr int NL = seg_lines<R>();
+  if (reps != nullptr) spec = reinterpret_cast<C*>(reps[blockIdx.z / 3].spec);   // group solve: 3 components per replica
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);   // [N][NL]
   C* tw = buf + N * NL;
   const int tid = threadIdx.x;
   load_stage_twiddles<R, R1, R2>(tw, gtw, tid, kThreads);
-  const int kx0 = blockIdx.x * NL, z = blockIdx.y, comp = blockIdx.z;
+  const int kx0 = blockIdx.x * NL, z = blockIdx.y, comp = blockIdx.z % 3;
   C* base = spec + ((size_t)(comp * nz + z) * N) * kxp + kx0;
   const C zero = mk(R(0), R(0));
   __syncthreads();
@@ -752,15 +762,20 @@ __global__ void __launch_bounds__(kThreads) k_ypass2(cplx_t<R>* __restrict__ spe
 template <typename R, int N, int R1, int R2, bool BLOBS>
 __global__ void __launch_bounds__(kThreads) k_xfwd2(const R* __restrict__ src, cplx_t<R>* __restrict__ spec,
                                                     const cplx_t<R>* __restrict__ gtw, int nrows, long long ncell,
-                                                    int kx, int kxp, RowBlobs rb) {
+                                                    int kx, int kxp, RowBlobs rb, const RepFft* __restrict__ reps) {
   using C = cplx_t<R>;
+  if (!BLOBS && reps != nullptr) {   // replica blockIdx.y / 3 of a group solve
+    const RepFft& rp = reps[blockIdx.y / 3];
+    src = reinterpret_cast<const R*>(rp.src);
+    spec = reinterpret_cast<C*>(rp.spec);
+  }
   static_assert(kRowBlock == 2 * kXLines, "row blocks are the x-pass blocks");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);   // [kXLines][xrow(N)]
   C* tw = buf + kXLines * xrow(N);
   const int tid = threadIdx.x;
   load_stage_twiddles<R, R1, R2>(tw, gtw, tid, kThreads);
-  const int comp = blockIdx.y;
+  const int comp = blockIdx.y % 3;
   const long long row0 = (long long)blockIdx.x * (2 * kXLines);
   const bool dense = !BLOBS || src != nullptr;
   // one first-stage item (line l, offset n1) per thread; its loads are issued first
@@ -846,15 +861,22 @@ __global__ void __launch_bounds__(kThreads) k_xfwd2(const R* __restrict__ src, c
 template <typename R, int N, int R1, int R2, int MODE, int GATHER>
 __global__ void __launch_bounds__(kThreads) k_xinv2(const cplx_t<R>* __restrict__ spec, R* __restrict__ dst,
                                                     R* __restrict__ dst2, const cplx_t<R>* __restrict__ gtw,
-                                                    int nrows, long long ncell, int kxp, RowBlobs rb) {
+                                                    int nrows, long long ncell, int kxp, RowBlobs rb,
+                                                    const RepFft* __restrict__ reps) {
   using C = cplx_t<R>;
+  if (GATHER == 0 && reps != nullptr) {   // replica blockIdx.y / 3 of a group solve
+    const RepFft& rp = reps[blockIdx.y / 3];
+    spec = reinterpret_cast<const C*>(rp.spec);
+    dst = reinterpret_cast<R*>(rp.dst);
+    dst2 = reinterpret_cast<R*>(rp.dst2);
+  }
   constexpr bool ADDS = MODE == OUT_ADD_AND_STORE2 || MODE == OUT_ADD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* tw = buf + kXLines * xrow(N);
   const int tid = threadIdx.x;
   load_stage_twiddles<R, R1, R2>(tw, gtw, tid, kThreads);
-  const int comp = blockIdx.y;
+  const int comp = blockIdx.y % 3;
   const long long row0 = (long long)blockIdx.x * (2 * kXLines);
   const C* in = spec + (size_t)comp * nrows * kxp;
   const C zero = mk(R(0), R(0));
@@ -1076,7 +1098,7 @@ void fft_x_forward(const FftCtx<R>& f, const R* src, cudaStream_t st) {
   const cplx_t<R>* tw = (const cplx_t<R>*)f.px.tw;
   switch (f.nx) {
 #define ICM_CASE(N, R1, R2) \
-  case N: k_xfwd2<R, N, R1, R2, false><<<dim3(xblocks, 3), kThreads, smem_x2<R, N>(), st>>>(src, f.spec, tw, nrows, f.ncell, f.kx, f.kxp, RowBlobs{}); return;
+  case N: k_xfwd2<R, N, R1, R2, false><<<dim3(xblocks, 3), kThreads, smem_x2<R, N>(), st>>>(src, f.spec, tw, nrows, f.ncell, f.kx, f.kxp, RowBlobs{}, nullptr); return;
     ICM_FFT_SIDES(ICM_CASE)
 #undef ICM_CASE
     default: break;
@@ -1094,9 +1116,9 @@ void fft_y(const FftCtx<R>& f, bool inverse, cudaStream_t st) {
 #define ICM_CASE(N, R1, R2)                                                                                   \
   case N:                                                                                                     \
     if (inverse)                                                                                              \
-      k_ypass2<R, N, R1, R2, true><<<grid, kThreads, smem_y2<R, N>(), st>>>(f.spec, tw, f.nz, f.kx, f.kxp);  \
+      k_ypass2<R, N, R1, R2, true><<<grid, kThreads, smem_y2<R, N>(), st>>>(f.spec, tw, f.nz, f.kx, f.kxp, nullptr);  \
     else                                                                                                      \
-      k_ypass2<R, N, R1, R2, false><<<grid, kThreads, smem_y2<R, N>(), st>>>(f.spec, tw, f.nz, f.kx, f.kxp); \
+      k_ypass2<R, N, R1, R2, false><<<grid, kThreads, smem_y2<R, N>(), st>>>(f.spec, tw, f.nz, f.kx, f.kxp, nullptr); \
     return;
     ICM_FFT_SIDES(ICM_CASE)
 #undef ICM_CASE
@@ -1150,7 +1172,7 @@ void fft_z_symbol(const FftCtx<R>& f, double a, double b, const double* k0sum, d
   }
   switch (f.nz) {
 #define ICM_CASE(N, R1, R2) \
-  case N: k_zsym2<R, N, R1, R2><<<dim3(kxz, f.ny), zsym2_threads<R, N, R1, R2>(), smem_z2<R, N>(), st>>>(f.spec, tw, f.ny, f.kx, f.kxp, sp); return;
+  case N: k_zsym2<R, N, R1, R2><<<dim3(kxz, f.ny), zsym2_threads<R, N, R1, R2>(), smem_z2<R, N>(), st>>>(f.spec, tw, f.ny, f.kx, f.kxp, sp, nullptr); return;
     ICM_FFT_SIDES(ICM_CASE)
 #undef ICM_CASE
     default: break;
@@ -1167,9 +1189,9 @@ void fft_x_inverse(const FftCtx<R>& f, R* dst, R* dst2, int mode, cudaStream_t s
 #define ICM_CASE(N, R1, R2) \
   case N:                                                                                                              \
     if (mode == OUT_STORE)                                                                                             \
-      k_xinv2<R, N, R1, R2, OUT_STORE, 0><<<dim3(xblocks, 3), kThreads, smem_x2<R, N>(), st>>>(f.spec, dst, dst2, tw, nrows, f.ncell, f.kxp, RowBlobs{}); \
+      k_xinv2<R, N, R1, R2, OUT_STORE, 0><<<dim3(xblocks, 3), kThreads, smem_x2<R, N>(), st>>>(f.spec, dst, dst2, tw, nrows, f.ncell, f.kxp, RowBlobs{}, nullptr); \
     else                                                                                                               \
-      k_xinv2<R, N, R1, R2, OUT_ADD_AND_STORE2, 0><<<dim3(xblocks, 3), kThreads, smem_x2<R, N>(), st>>>(f.spec, dst, dst2, tw, nrows, f.ncell, f.kxp, RowBlobs{}); \
+      k_xinv2<R, N, R1, R2, OUT_ADD_AND_STORE2, 0><<<dim3(xblocks, 3), kThreads, smem_x2<R, N>(), st>>>(f.spec, dst, dst2, tw, nrows, f.ncell, f.kxp, RowBlobs{}, nullptr); \
     return;
     ICM_FFT_SIDES(ICM_CASE)
 #undef ICM_CASE
@@ -1184,6 +1206,11 @@ bool fft_has_blob_passes(int nx) {
   int r1 = 0, r2 = 0;
   return fft_split(nx, r1, r2);
 }
+
+bool fft_has_group_passes(int nx, int ny, int nz) {
+  int r1 = 0, r2 = 0;
+  return fft_split(nx, r1, r2) && fft_split(ny, r1, r2) && fft_split(nz, r1, r2);
+}
 #endif
 
 template <typename R>
@@ -1193,7 +1220,7 @@ void fft_x_forward_blobs(const FftCtx<R>& f, const R* src, const RowBlobs& rb, c
   const cplx_t<R>* tw = (const cplx_t<R>*)f.px.tw;
   switch (f.nx) {
 #define ICM_CASE(N, R1, R2) \
-  case N: k_xfwd2<R, N, R1, R2, true><<<dim3(xblocks, 3), kThreads, smem_x2b<R, N>(), st>>>(src, f.spec, tw, nrows, f.ncell, f.kx, f.kxp, rb); return;
+  case N: k_xfwd2<R, N, R1, R2, true><<<dim3(xblocks, 3), kThreads, smem_x2b<R, N>(), st>>>(src, f.spec, tw, nrows, f.ncell, f.kx, f.kxp, rb, nullptr); return;
     ICM_FFT_SIDES(ICM_CASE)
 #undef ICM_CASE
     default: break;
@@ -1211,11 +1238,11 @@ void fft_x_inverse_blobs(const FftCtx<R>& f, R* dst, int mode, const RowBlobs& r
 #define ICM_CASE(N, R1, R2)                                                                                              \
   case N:                                                                                                                \
     if (mode == OUT_STORE)                                                                                               \
-      k_xinv2<R, N, R1, R2, OUT_STORE, 1><<<grid, kThreads, smem_x2b<R, N>(), st>>>(f.spec, dst, nullptr, tw, nrows, f.ncell, f.kxp, rb); \
+      k_xinv2<R, N, R1, R2, OUT_STORE, 1><<<grid, kThreads, smem_x2b<R, N>(), st>>>(f.spec, dst, nullptr, tw, nrows, f.ncell, f.kxp, rb, nullptr); \
     else if (mode == OUT_NONE)                                                                                           \
-      k_xinv2<R, N, R1, R2, OUT_NONE, 1><<<grid, kThreads, smem_x2b<R, N>(), st>>>(f.spec, dst, nullptr, tw, nrows, f.ncell, f.kxp, rb); \
+      k_xinv2<R, N, R1, R2, OUT_NONE, 1><<<grid, kThreads, smem_x2b<R, N>(), st>>>(f.spec, dst, nullptr, tw, nrows, f.ncell, f.kxp, rb, nullptr); \
     else                                                                                                                 \
-      k_xinv2<R, N, R1, R2, OUT_ADD, 2><<<grid, kThreads, smem_x2b<R, N>(), st>>>(f.spec, dst, nullptr, tw, nrows, f.ncell, f.kxp, rb); \
+      k_xinv2<R, N, R1, R2, OUT_ADD, 2><<<grid, kThreads, smem_x2b<R, N>(), st>>>(f.spec, dst, nullptr, tw, nrows, f.ncell, f.kxp, rb, nullptr); \
     return;
     ICM_FFT_SIDES(ICM_CASE)
 #undef ICM_CASE
@@ -1232,6 +1259,96 @@ void spectral_solve(const FftCtx<R>& f, const R* src, R* dst, R* dst2, int mode,
   fft_z_symbol<R>(f, a, b, k0sum, k0scale, st);
   fft_y<R>(f, true, st);
   fft_x_inverse<R>(f, dst, dst2, mode, st);
+}
+
+// Group solve: the five passes of spectral_solve, each one launch over G replicas of
+// the same grid (register sides only; the plain z pass).  In the x passes blockIdx.y
+// is 3 x replica + component, in the y pass blockIdx.z, in the z pass blockIdx.z is
+// the replica; the pointers and symbol constants come from the table.
+template <typename R>
+void fft_x_forward_group(const FftCtx<R>& f, const RepFft* reps, int G, cudaStream_t st) {
+  const int nrows = f.ny * f.nz;
+  const int xblocks = (nrows + 2 * kXLines - 1) / (2 * kXLines);
+  const cplx_t<R>* tw = (const cplx_t<R>*)f.px.tw;
+  switch (f.nx) {
+#define ICM_CASE(N, R1, R2) \
+  case N: k_xfwd2<R, N, R1, R2, false><<<dim3(xblocks, 3 * G), kThreads, smem_x2<R, N>(), st>>>(nullptr, nullptr, tw, nrows, f.ncell, f.kx, f.kxp, RowBlobs{}, reps); return;
+    ICM_FFT_SIDES(ICM_CASE)
+#undef ICM_CASE
+    default: break;
+  }
+  record_error(ICM_EINVAL, "group solve on a side without register FFT kernels");
+}
+
+template <typename R>
+void fft_yz_group(const FftCtx<R>& f, const RepFft* reps, int G, int which, cudaStream_t st) {
+  const cplx_t<R>* twy = (const cplx_t<R>*)f.py.tw;
+  const cplx_t<R>* twz = (const cplx_t<R>*)f.pz.tw;
+  constexpr int NL = seg_lines<R>();
+  const int kxt = (f.kx + NL - 1) / NL;
+  const int kxz = (f.kx + kZLines - 1) / kZLines;
+  if (which == 1) {   // z FFT, symbol, inverse z FFT
+    SymParams<R> sp;
+    sp.a = R(0);
+    sp.b = R(0);
+    sp.inv_ntot = (R)(1.0 / (double)f.ncell);
+    sp.dx = f.dx; sp.ddx = f.ddx;
+    sp.dy = f.dy; sp.ddy = f.ddy;
+    sp.dz = f.dz; sp.ddz = f.ddz;
+    sp.k0sum = nullptr;
+    sp.k0mul = 0.0;
+    switch (f.nz) {
+#define ICM_CASE(N, R1, R2) \
+  case N: k_zsym2<R, N, R1, R2><<<dim3(kxz, f.ny, G), zsym2_threads<R, N, R1, R2>(), smem_z2<R, N>(), st>>>(nullptr, twz, f.ny, f.kx, f.kxp, sp, reps); return;
+      ICM_FFT_SIDES(ICM_CASE)
+#undef ICM_CASE
+      default: break;
+    }
+  } else {            // y FFT: which 0 forward, 2 inverse
+    switch (f.ny) {
+#define ICM_CASE(N, R1, R2)                                                                                             \
+  case N:                                                                                                               \
+    if (which == 2)                                                                                                     \
+      k_ypass2<R, N, R1, R2, true><<<dim3(kxt, f.nz, 3 * G), kThreads, smem_y2<R, N>(), st>>>(nullptr, twy, f.nz, f.kx, f.kxp, reps); \
+    else                                                                                                                \
+      k_ypass2<R, N, R1, R2, false><<<dim3(kxt, f.nz, 3 * G), kThreads, smem_y2<R, N>(), st>>>(nullptr, twy, f.nz, f.kx, f.kxp, reps); \
+    return;
+      ICM_FFT_SIDES(ICM_CASE)
+#undef ICM_CASE
+      default: break;
+    }
+  }
+  record_error(ICM_EINVAL, "group solve on a side without register FFT kernels");
+}
+
+template <typename R>
+void fft_x_inverse_group(const FftCtx<R>& f, const RepFft* reps, int G, int mode, cudaStream_t st) {
+  const int nrows = f.ny * f.nz;
+  const int xblocks = (nrows + 2 * kXLines - 1) / (2 * kXLines);
+  const cplx_t<R>* tw = (const cplx_t<R>*)f.px.tw;
+  const dim3 grid(xblocks, 3 * G);
+  switch (f.nx) {
+#define ICM_CASE(N, R1, R2)                                                                                             \
+  case N:                                                                                                               \
+    if (mode == OUT_STORE)                                                                                              \
+      k_xinv2<R, N, R1, R2, OUT_STORE, 0><<<grid, kThreads, smem_x2<R, N>(), st>>>(nullptr, nullptr, nullptr, tw, nrows, f.ncell, f.kxp, RowBlobs{}, reps); \
+    else                                                                                                                \
+      k_xinv2<R, N, R1, R2, OUT_ADD_AND_STORE2, 0><<<grid, kThreads, smem_x2<R, N>(), st>>>(nullptr, nullptr, nullptr, tw, nrows, f.ncell, f.kxp, RowBlobs{}, reps); \
+    return;
+    ICM_FFT_SIDES(ICM_CASE)
+#undef ICM_CASE
+    default: break;
+  }
+  record_error(ICM_EINVAL, "group solve on a side without register FFT kernels");
+}
+
+template <typename R>
+void spectral_solve_group(const FftCtx<R>& f, const RepFft* reps, int G, int mode, cudaStream_t st) {
+  fft_x_forward_group<R>(f, reps, G, st);
+  fft_yz_group<R>(f, reps, G, 0, st);
+  fft_yz_group<R>(f, reps, G, 1, st);
+  fft_yz_group<R>(f, reps, G, 2, st);
+  fft_x_inverse_group<R>(f, reps, G, mode, st);
 }
 
 #if ICM_SHARD(0)
@@ -1275,14 +1392,17 @@ bool make_zmap(void* map, const void* spec, int precision, int kx, int kxp, int 
 #define ICM_INST_XF(R, KW)                                                                               \
   KW template void fft_x_forward<R>(const FftCtx<R>&, const R*, cudaStream_t);                           \
   KW template void fft_x_forward_blobs<R>(const FftCtx<R>&, const R*, const RowBlobs&, cudaStream_t);    \
+  KW template void fft_x_forward_group<R>(const FftCtx<R>&, const RepFft*, int, cudaStream_t);            \
   KW template void fft_prepare_xf<R>();
 #define ICM_INST_XI(R, KW)                                                                               \
   KW template void fft_x_inverse<R>(const FftCtx<R>&, R*, R*, int, cudaStream_t);                        \
   KW template void fft_x_inverse_blobs<R>(const FftCtx<R>&, R*, int, const RowBlobs&, cudaStream_t);     \
+  KW template void fft_x_inverse_group<R>(const FftCtx<R>&, const RepFft*, int, int, cudaStream_t);       \
   KW template void fft_prepare_xi<R>();
 #define ICM_INST_YZ(R, KW)                                                                               \
   KW template void fft_y<R>(const FftCtx<R>&, bool, cudaStream_t);                                       \
   KW template void fft_z_symbol<R>(const FftCtx<R>&, double, double, const double*, double, cudaStream_t); \
+  KW template void fft_yz_group<R>(const FftCtx<R>&, const RepFft*, int, int, cudaStream_t);              \
   KW template void fft_prepare_yz<R>();
 #define ICM_NONE
 #if ICM_SHARD(0)
@@ -1330,6 +1450,8 @@ template void spectral_solve<float>(const FftCtx<float>&, const float*, float*, 
                                     const double*, double, cudaStream_t);
 template void spectral_solve<double>(const FftCtx<double>&, const double*, double*, double*, int, double, double,
                                      const double*, double, cudaStream_t);
+template void spectral_solve_group<float>(const FftCtx<float>&, const RepFft*, int, int, cudaStream_t);
+template void spectral_solve_group<double>(const FftCtx<double>&, const RepFft*, int, int, cudaStream_t);
 #endif
 #undef ICM_NONE
 #undef ICM_INST_XF

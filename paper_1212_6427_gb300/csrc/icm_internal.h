@@ -85,6 +85,21 @@ template <typename R>
 void fft_z_symbol(const FftCtx<R>& f, double a, double b, const double* k0sum, double k0scale, cudaStream_t st);
 template <typename R> void fft_x_inverse(const FftCtx<R>& f, R* dst, R* dst2, int mode, cudaStream_t st);
 
+// One replica of a group solve: the same grid for every replica, launched once for all.
+struct RepFft {
+  const void* src;      // real face field (3 ncell)
+  void* spec;           // spectrum scratch
+  void* dst;            // output field
+  void* dst2;           // second output (OUT_ADD_AND_STORE2)
+  const double* k0sum;  // prescribed grid sums of the mean mode (or null)
+  double a, b, k0mul;   // symbol a + b |d|^2 and k0sum scale (k0scale / ncell)
+};
+// spectral_solve for G replicas of the grid of f (register sides only, plain z pass):
+// every pass is one launch over all replicas; reps is a device array of G entries.
+template <typename R>
+void spectral_solve_group(const FftCtx<R>& f, const RepFft* reps, int G, int mode, cudaStream_t st);
+bool fft_has_group_passes(int nx, int ny, int nz);
+
 // Raise the dynamic shared-memory limits of the kernels (call once, outside capture).
 void fft_prepare();
 void grid_prepare();

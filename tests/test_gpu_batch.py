@@ -114,3 +114,51 @@ def test_server_rejects_job_larger_than_budget(icm):
                               np.zeros(1), None, 3)
     assert ei.value.status == icm.ICM_ENOMEM
     icm.icm_server_destroy(sv)
+
+
+def _grouped_jobs(precision):
+    # (side, h, kernel, blobs, excess mass): three 32^3 members of one group (one
+    # neutrally buoyant, so it skips the second and third solves), a 32^3 member with
+    # another cell width (a grid of its own: stepped ungrouped), two 48^3 members
+    # (a second group) and a 24^3 member (no register FFT passes: ungrouped)
+    spec = [(32, 1.0, 4, 7, (-0.5, 2.0)), (32, 1.0, 3, 12, None), (32, 1.0, 4, 5, (0.0, 1.0)),
+            (32, 0.5, 4, 6, (-0.5, 2.0)), (48, 1.0, 3, 4, (-0.5, 2.0)), (48, 1.0, 4, 9, (-0.5, 2.0)),
+            (24, 1.0, 4, 3, (-0.5, 2.0))]
+    out = []
+    for r, (side, h, kernel, nb, me_range) in enumerate(spec):
+        cfg = dict(grid=(side, side, side), h=h, rho=1.0, eta=1.0, kT=2e-3 * h ** 3, dt=0.05 * h * h, kernel=kernel,
+                   seed=70 + r, precision=precision, steps=5, nblobs=nb, me_range=me_range,
+                   force=(1e-3, 0.0, -2e-3), place_seed=170 + r, min_spacing=2.0)
+        out.append(wl._materialise(cfg))
+    return out
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_grouped_batch_matches_individual_runs(icm, precision):
+    jobs = _grouped_jobs(precision)
+    sims = []
+    for j in jobs:
+        s = icm.Simulation(j["grid"], j["h"], j["rho"], j["eta"], j["kT"], j["dt"], j["kernel"], j["seed"], precision)
+        s.add_blobs(j["q"], j["u"], j["me"])
+        s.set_forces(j["force"])
+        sims.append(s)
+    b = icm.icm_batch_create()
+    icm.icm_batch_set(b, [s.handle for s in sims])
+    assert icm.icm_batch_get_grouped(b) == 0
+    icm.icm_batch_set_grouped(b, 1)
+    assert icm.icm_batch_get_grouped(b) == 1
+    icm.icm_batch_step(b, 2)
+    icm.icm_batch_step(b, 3)   # replays the same graph
+    icm.icm_batch_sync(b)
+    for j, s in zip(jobs, sims):
+        got = s.read()
+        assert got["step"] == 5
+        want = _alone(icm, j)
+        assert rel(got["vel"], want["vel"]) < TOL[precision]
+        assert rel(got["pos"], want["pos"]) < TOL[precision] * 1e-2
+        np.testing.assert_allclose(got["momentum"], want["momentum"], rtol=1e-9, atol=1e-12)
+    with pytest.raises(icm.IcmError):
+        icm.icm_batch_set_grouped(b, 2)
+    icm.icm_batch_destroy(b)
+    for s in sims:
+        s.close()
