@@ -332,6 +332,7 @@ __global__ void __launch_bounds__(kThreads) k_ypass(cplx_t<R>* __restrict__ spec
 template <typename R>
 struct SymParams {
   R a, b, inv_ntot;
+  R mean_scale;   // the symbol's scale on the mean mode: 1/(a ncell), 0 when a = 0
   const cplx_t<R>* dx; const R* ddx;
   const cplx_t<R>* dy; const R* ddy;
   const cplx_t<R>* dz; const R* ddz;
@@ -342,8 +343,8 @@ struct SymParams {
 // P^ w / (a + b|d|^2) / ncell on one wave vector: (P^ w)_a = w_a - conj(d_a)(d . w)/|d|^2,
 // identity on the mean mode, whose value is replaced by the FP64 bookkeeping if given
 // (and which is zero when a = 0).
-// 1/x: correctly rounded reciprocal in FP32 (one rounding more than a division per
-// use, far inside the FP32 path's tolerance), exact division in FP64.
+// 1/x: correctly rounded reciprocal in FP32 (a few roundings more than two divisions
+// per wave vector, far inside the FP32 path's tolerance), exact division in FP64.
 template <typename R> __device__ __forceinline__ R recip(R x);
 template <> __device__ __forceinline__ float recip<float>(float x) { return __frcp_rn(x); }
 template <> __device__ __forceinline__ double recip<double>(double x) { return 1.0 / x; }
@@ -352,17 +353,25 @@ template <typename R>
 __device__ __forceinline__ void apply_symbol(cplx_t<R>& c0, cplx_t<R>& c1, cplx_t<R>& c2, cplx_t<R> d0,
                                              cplx_t<R> d1, cplx_t<R> d2, R dd, const SymParams<R>& sp,
                                              bool mean_mode) {
+  // FP32: one reciprocal r = 1/(|d|^2 (a + b|d|^2)) serves both divisions; |d|^2 = 0
+  // only on the mean mode, whose scale is precomputed.
+  const R den = sp.a + sp.b * dd;
+  const R prod = dd * den;
+  const R r = sizeof(R) == 4 ? recip<R>(prod > R(0) ? prod : R(1)) : R(0);
   if (dd > R(0)) {
     const cplx_t<R> div = cadd(cadd(cmul(d0, c0), cmul(d1, c1)), cmul(d2, c2));
-    const R inv_dd = recip<R>(dd);
+    const R inv_dd = sizeof(R) == 4 ? den * r : recip<R>(dd);
     const cplx_t<R> q = mk(div.x * inv_dd, div.y * inv_dd);
     c0 = csub(c0, cmul(cconj(d0), q));
     c1 = csub(c1, cmul(cconj(d1), q));
     c2 = csub(c2, cmul(cconj(d2), q));
   }
   // a = 0 (the steady Stokes solve): the mean mode has no solution and is dropped
-  const R den = sp.a + sp.b * dd;
-  const R scale = den > R(0) ? sp.inv_ntot * recip<R>(den) : R(0);
+  R scale;
+  if (sizeof(R) == 4)
+    scale = prod > R(0) ? sp.inv_ntot * (dd * r) : (dd > R(0) ? R(0) : sp.mean_scale);
+  else
+    scale = den > R(0) ? sp.inv_ntot * recip<R>(den) : R(0);
   c0 = cscale(c0, scale);
   c1 = cscale(c1, scale);
   c2 = cscale(c2, scale);
@@ -431,7 +440,13 @@ __device__ __forceinline__ int xaddr(int l, int p, int N) { return l * xrow(N) +
 template <typename R, int N> constexpr size_t stage_offset() {
   return ((size_t)kXLines * xrow(N) * sizeof(cplx_t<R>) + N * sizeof(cplx_t<R>) + 15) / 16 * 16;
 }
-template <typename R, int N> size_t smem_x2b() { return stage_offset<R, N>() + kThreads * sizeof(StagedTask<R>); }
+// Blob task records staged per block (the rest are read in place).  The forward x
+// pass stages 128, which keeps its FP32 blocks of sides up to 256 at four per SM
+// (registers capped to match); the inverse pass, which holds its loads in flight in
+// registers and would spill under that cap, stages one per thread.
+constexpr int kStageF = 128, kStageI = kThreads;
+template <typename R, int N, int S> size_t smem_x2b() { return stage_offset<R, N>() + S * sizeof(StagedTask<R>); }
+template <typename R, int N> constexpr int xf2_min_blocks() { return sizeof(R) == 4 && N <= 256 ? 4 : 1; }
 
 // The z pass holds all three components of its tile, so it takes 8 kx lines
 // (64-byte rows in FP32) to keep two blocks per SM; one thread per first-stage item
@@ -565,6 +580,7 @@ __global__ void __launch_bounds__(zsym2_threads<R, N, R1, R2>(), sizeof(R) == 4 
     spec = reinterpret_cast<C*>(rp.spec);
     sp.a = (R)rp.a;
     sp.b = (R)rp.b;
+    sp.mean_scale = rp.a > 0.0 ? (R)((double)sp.inv_ntot / rp.a) : R(0);
     sp.k0sum = rp.k0sum;
     sp.k0mul = rp.k0mul;
   }
@@ -760,7 +776,7 @@ __global__ void __launch_bounds__(kThreads) k_ypass2(cplx_t<R>* __restrict__ spe
 // this row block spread rb.vec into the rows (in shared memory, where the first
 // stage reads them), added to src if src is set.
 template <typename R, int N, int R1, int R2, bool BLOBS>
-__global__ void __launch_bounds__(kThreads) k_xfwd2(const R* __restrict__ src, cplx_t<R>* __restrict__ spec,
+__global__ void __launch_bounds__(kThreads, xf2_min_blocks<R, N>()) k_xfwd2(const R* __restrict__ src, cplx_t<R>* __restrict__ spec,
                                                     const cplx_t<R>* __restrict__ gtw, int nrows, long long ncell,
                                                     int kx, int kxp, RowBlobs rb, const RepFft* __restrict__ reps) {
   using C = cplx_t<R>;
@@ -796,7 +812,7 @@ __global__ void __launch_bounds__(kThreads) k_xfwd2(const R* __restrict__ src, c
     StagedTask<R>* stage = reinterpret_cast<StagedTask<R>*>(smem_raw + stage_offset<R, N>());
     const BlobStencil<R>* rec = reinterpret_cast<const BlobStencil<R>*>(rb.geo);
     const int s0 = rb.start[blockIdx.x], e = rb.start[blockIdx.x + 1];
-    const int nst = min(e - s0, kThreads);
+    const int nst = min(e - s0, kStageF);
     if (tid < nst) stage_task<R>(&stage[tid], rec, rb.list[s0 + tid], comp, rb.vec);
     cp_async_commit();
     for (int i = tid; i < kXLines * xrow(N); i += kThreads) buf[i] = mk(R(0), R(0));
@@ -811,7 +827,7 @@ __global__ void __launch_bounds__(kThreads) k_xfwd2(const R* __restrict__ src, c
       const StagedTask<R>& t = stage[tid];
       spread_one<R, N>(rows, (int)row0, plane, z0, y0, t.first, t.w, (R)(t.vec * inv_dvf), rb.p, line);
     }
-    for (int i = s0 + kThreads + tid; i < e; i += kThreads) {   // beyond the staged tasks
+    for (int i = s0 + kStageF + tid; i < e; i += kThreads) {   // beyond the staged tasks
       const int b = rb.list[i];
       spread_one<R, N>(rows, (int)row0, plane, z0, y0, *reinterpret_cast<const int4*>(rec[b].first[comp]),
                        &rec[b].w[comp][0][0], (R)(rb.vec[3 * b + comp] * inv_dvf), rb.p, line);
@@ -839,9 +855,8 @@ __global__ void __launch_bounds__(kThreads) k_xfwd2(const R* __restrict__ src, c
   }
   __syncthreads();
   C* out = spec + (size_t)comp * nrows * kxp;
-  constexpr int KX = N / 2 + 1;   // = kx: a compile-time divisor for the index split
-  for (int it = tid; it < kXLines * KX; it += kThreads) {
-    const int k = it % KX, l = it / KX;
+  // the two half spectra of line l at wavenumber k (kx = N/2 + 1 of them)
+  const auto split = [&](int l, int k) {
     const int km = k == 0 ? 0 : N - k;
     const C zk = buf[xaddr(l, R2 * (k % R1) + k / R1, N)];
     const C zm = buf[xaddr(l, R2 * (km % R1) + km / R1, N)];
@@ -850,7 +865,11 @@ __global__ void __launch_bounds__(kThreads) k_xfwd2(const R* __restrict__ src, c
     const long long r1 = row0 + 2 * l;
     if (r1 < nrows) out[r1 * kxp + k] = x1;
     if (r1 + 1 < nrows) out[(r1 + 1) * kxp + k] = x2;
-  }
+  };
+  // k < N/2 with a compile-time (mostly power-of-two) index split, then k = N/2
+  constexpr int H = N / 2;
+  for (int it = tid; it < kXLines * H; it += kThreads) split(it / H, it % H);
+  if (tid < kXLines) split(tid, H);
 }
 
 // MODE OUT_STORE: dst = x.  OUT_ADD_AND_STORE2: dst += x, dst2 = x.  OUT_ADD: dst += x.
@@ -915,7 +934,7 @@ __global__ void __launch_bounds__(kThreads) k_xinv2(const cplx_t<R>* __restrict_
     StagedTask<R>* stage = reinterpret_cast<StagedTask<R>*>(smem_raw + stage_offset<R, N>());
     g0 = rb.start[blockIdx.x];
     ge = rb.start[blockIdx.x + 1];
-    if (tid < min(ge - g0, kThreads))
+    if (tid < min(ge - g0, kStageI))
       stage_task<R>(&stage[tid], reinterpret_cast<const BlobStencil<R>*>(rb.geo), rb.list[g0 + tid], comp, nullptr);
     cp_async_commit();
   }
@@ -994,14 +1013,14 @@ __global__ void __launch_bounds__(kThreads) k_xinv2(const cplx_t<R>* __restrict_
     const auto line = [](int l, int x) { return xaddr(l, x, N); };
     const bool plane = rb.p.ny % kRowBlock == 0;   // the block is part of one z plane
     const int z0 = (int)row0 / rb.p.ny, y0 = (int)row0 % rb.p.ny;
-    if (tid < min(ge - g0, kThreads)) {
+    if (tid < min(ge - g0, kStageI)) {
       const StagedTask<R>& t = stage[tid];
       R j, jl;
       gather_one<R, N, GATHER == 2>(rows, (int)row0, plane, z0, y0, t.first, t.w, rb.p, line, j, jl);
       atomicAdd(&rb.acc[3 * t.b + comp], (double)j);
       if (GATHER == 2) atomicAdd(&rb.acc_lap[3 * t.b + comp], (double)jl);
     }
-    for (int i = g0 + kThreads + tid; i < ge; i += kThreads) {   // beyond the staged tasks
+    for (int i = g0 + kStageI + tid; i < ge; i += kThreads) {   // beyond the staged tasks
       const int b = rb.list[i];
       R j, jl;
       gather_one<R, N, GATHER == 2>(rows, (int)row0, plane, z0, y0, *reinterpret_cast<const int4*>(rec[b].first[comp]),
@@ -1138,6 +1157,7 @@ void fft_z_symbol(const FftCtx<R>& f, double a, double b, const double* k0sum, d
   sp.a = (R)a;
   sp.b = (R)b;
   sp.inv_ntot = (R)(1.0 / (double)f.ncell);
+  sp.mean_scale = a > 0.0 ? (R)(1.0 / (a * (double)f.ncell)) : R(0);
   sp.dx = f.dx; sp.ddx = f.ddx;
   sp.dy = f.dy; sp.ddy = f.ddy;
   sp.dz = f.dz; sp.ddz = f.ddz;
@@ -1220,7 +1240,7 @@ void fft_x_forward_blobs(const FftCtx<R>& f, const R* src, const RowBlobs& rb, c
   const cplx_t<R>* tw = (const cplx_t<R>*)f.px.tw;
   switch (f.nx) {
 #define ICM_CASE(N, R1, R2) \
-  case N: k_xfwd2<R, N, R1, R2, true><<<dim3(xblocks, 3), kThreads, smem_x2b<R, N>(), st>>>(src, f.spec, tw, nrows, f.ncell, f.kx, f.kxp, rb, nullptr); return;
+  case N: k_xfwd2<R, N, R1, R2, true><<<dim3(xblocks, 3), kThreads, smem_x2b<R, N, kStageF>(), st>>>(src, f.spec, tw, nrows, f.ncell, f.kx, f.kxp, rb, nullptr); return;
     ICM_FFT_SIDES(ICM_CASE)
 #undef ICM_CASE
     default: break;
@@ -1238,11 +1258,11 @@ void fft_x_inverse_blobs(const FftCtx<R>& f, R* dst, int mode, const RowBlobs& r
 #define ICM_CASE(N, R1, R2)                                                                                              \
   case N:                                                                                                                \
     if (mode == OUT_STORE)                                                                                               \
-      k_xinv2<R, N, R1, R2, OUT_STORE, 1><<<grid, kThreads, smem_x2b<R, N>(), st>>>(f.spec, dst, nullptr, tw, nrows, f.ncell, f.kxp, rb, nullptr); \
+      k_xinv2<R, N, R1, R2, OUT_STORE, 1><<<grid, kThreads, smem_x2b<R, N, kStageI>(), st>>>(f.spec, dst, nullptr, tw, nrows, f.ncell, f.kxp, rb, nullptr); \
     else if (mode == OUT_NONE)                                                                                           \
-      k_xinv2<R, N, R1, R2, OUT_NONE, 1><<<grid, kThreads, smem_x2b<R, N>(), st>>>(f.spec, dst, nullptr, tw, nrows, f.ncell, f.kxp, rb, nullptr); \
+      k_xinv2<R, N, R1, R2, OUT_NONE, 1><<<grid, kThreads, smem_x2b<R, N, kStageI>(), st>>>(f.spec, dst, nullptr, tw, nrows, f.ncell, f.kxp, rb, nullptr); \
     else                                                                                                                 \
-      k_xinv2<R, N, R1, R2, OUT_ADD, 2><<<grid, kThreads, smem_x2b<R, N>(), st>>>(f.spec, dst, nullptr, tw, nrows, f.ncell, f.kxp, rb, nullptr); \
+      k_xinv2<R, N, R1, R2, OUT_ADD, 2><<<grid, kThreads, smem_x2b<R, N, kStageI>(), st>>>(f.spec, dst, nullptr, tw, nrows, f.ncell, f.kxp, rb, nullptr); \
     return;
     ICM_FFT_SIDES(ICM_CASE)
 #undef ICM_CASE
@@ -1292,6 +1312,7 @@ void fft_yz_group(const FftCtx<R>& f, const RepFft* reps, int G, int which, cuda
     sp.a = R(0);
     sp.b = R(0);
     sp.inv_ntot = (R)(1.0 / (double)f.ncell);
+    sp.mean_scale = R(0);   // per replica, from the table
     sp.dx = f.dx; sp.ddx = f.ddx;
     sp.dy = f.dy; sp.ddy = f.ddy;
     sp.dz = f.dz; sp.ddz = f.ddz;

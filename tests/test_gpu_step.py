@@ -66,6 +66,9 @@ CASES = [
     ((48, 24, 12), 7, 3, 18, 1.0, 0.02, 1e-3, "full", True),      # row blocks straddle z planes
     ((64, 12, 9), 6, 4, 19, 2.0, 0.0, 2e-3, "zero", True),        # several z planes per row block
     ((96, 32, 12), 9, 4, 22, 1.0, 0.04, 0.0, "visc", False),
+    # dense: ~150 blob tasks per row block, past the staged records of an x-pass block
+    ((32, 32, 16), 600, 4, 23, 1.0, 0.02, 1e-3, "visc", True),
+    ((64, 32, 8), 800, 3, 24, 1.0, 0.02, 1e-3, "full", True),     # ~300 per block: past the inverse pass too
 ]
 SEAM = {6, 7, 8, 9}    # cases that also put blobs on the periodic seams and corners
 
