@@ -444,9 +444,18 @@ template <typename R, int N> constexpr size_t stage_offset() {
 // pass stages 128, which keeps its FP32 blocks of sides up to 256 at four per SM
 // (registers capped to match); the inverse pass, which holds its loads in flight in
 // registers and would spill under that cap, stages one per thread.
-constexpr int kStageF = 128, kStageI = kThreads;
+constexpr int kStageF = 128;
 template <typename R, int N, int S> size_t smem_x2b() { return stage_offset<R, N>() + S * sizeof(StagedTask<R>); }
 template <typename R, int N> constexpr int xf2_min_blocks() { return sizeof(R) == 4 && N <= 256 ? 4 : 1; }
+// The inverse x pass of FP32 sides up to 256 runs lean at four blocks per SM: its
+// spectrum loads go in two batches, the old values of the adding modes are loaded
+// just before the output, and 128 records are staged.  Otherwise (and for the
+// two-output mode, which would spill) all loads are in flight at once and one record
+// per thread is staged.
+template <typename R, int N, int MODE> constexpr bool xi2_lean() {
+  return sizeof(R) == 4 && N <= 256 && MODE != OUT_ADD_AND_STORE2;
+}
+template <typename R, int N, int MODE> constexpr int xi2_stage() { return xi2_lean<R, N, MODE>() ? 128 : kThreads; }
 
 // The z pass holds all three components of its tile, so it takes 8 kx lines
 // (64-byte rows in FP32) to keep two blocks per SM; one thread per first-stage item
@@ -874,11 +883,12 @@ __global__ void __launch_bounds__(kThreads, xf2_min_blocks<R, N>()) k_xfwd2(cons
 
 // MODE OUT_STORE: dst = x.  OUT_ADD_AND_STORE2: dst += x, dst2 = x.  OUT_ADD: dst += x.
 // OUT_NONE: nothing stored.  The old dst values of the adding modes are loaded at
-// kernel start so that they are in flight during the FFT.  GATHER 1: the blobs of
+// kernel start so that they are in flight during the FFT (lean variant: before the
+// last stage).  GATHER 1: the blobs of
 // this row block add the part of J x in these rows to rb.acc; GATHER 2: also J L x
 // (without 1/h^2) to rb.acc_lap.  x stays in shared memory for the gathers.
 template <typename R, int N, int R1, int R2, int MODE, int GATHER>
-__global__ void __launch_bounds__(kThreads) k_xinv2(const cplx_t<R>* __restrict__ spec, R* __restrict__ dst,
+__global__ void __launch_bounds__(kThreads, xi2_lean<R, N, MODE>() ? 4 : 1) k_xinv2(const cplx_t<R>* __restrict__ spec, R* __restrict__ dst,
                                                     R* __restrict__ dst2, const cplx_t<R>* __restrict__ gtw,
                                                     int nrows, long long ncell, int kxp, RowBlobs rb,
                                                     const RepFft* __restrict__ reps) {
@@ -890,6 +900,8 @@ __global__ void __launch_bounds__(kThreads) k_xinv2(const cplx_t<R>* __restrict_
     dst2 = reinterpret_cast<R*>(rp.dst2);
   }
   constexpr bool ADDS = MODE == OUT_ADD_AND_STORE2 || MODE == OUT_ADD;
+  constexpr bool LEAN = xi2_lean<R, N, MODE>();
+  constexpr int NST = xi2_stage<R, N, MODE>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* tw = buf + kXLines * xrow(N);
@@ -903,56 +915,62 @@ __global__ void __launch_bounds__(kThreads) k_xinv2(const cplx_t<R>* __restrict_
   // this thread's output positions: line l = tid / R2, x = n1 + R2 n2, rows r0 and r0 + 1
   constexpr int OUTS = (kXLines * R2 + kThreads - 1) / kThreads;
   R old0[ADDS ? OUTS * R1 : 1], old1[ADDS ? OUTS * R1 : 1];
-  if (ADDS) {
+  const auto load_old = [&](int o) {
+    const int it = tid + o * kThreads;
+    const int n1 = it % R2, l = it / R2;
+    const long long r0 = row0 + 2 * l;
 #pragma unroll
-    for (int o = 0; o < OUTS; ++o) {
-      const int it = tid + o * kThreads;
-      const int n1 = it % R2, l = it / R2;
-      const long long r0 = row0 + 2 * l;
-#pragma unroll
-      for (int n2 = 0; n2 < R1; ++n2) {
-        const int x = n1 + R2 * n2;
-        old0[o * R1 + n2] = (it < kXLines * R2 && r0 < nrows) ? dst[cb + (size_t)r0 * N + x] : R(0);
-        old1[o * R1 + n2] = (it < kXLines * R2 && r0 + 1 < nrows) ? dst[cb + (size_t)(r0 + 1) * N + x] : R(0);
-      }
+    for (int n2 = 0; n2 < R1; ++n2) {
+      const int x = n1 + R2 * n2;
+      old0[o * R1 + n2] = (it < kXLines * R2 && r0 < nrows) ? dst[cb + (size_t)r0 * N + x] : R(0);
+      old1[o * R1 + n2] = (it < kXLines * R2 && r0 + 1 < nrows) ? dst[cb + (size_t)(r0 + 1) * N + x] : R(0);
     }
-  }
-  constexpr int LOADS = (kXLines * N + kThreads - 1) / kThreads;   // compile-time: all loads in flight
-  C av[LOADS], bv[LOADS];
+  };
+  if (ADDS && !LEAN) {
 #pragma unroll
-  for (int j = 0; j < LOADS; ++j) {
-    const int it = tid + j * kThreads;
-    const int k = it % N, l = it / N;
-    const long long r1 = row0 + 2 * l;
-    const int kk = 2 * k <= N ? k : N - k;
-    av[j] = (it < kXLines * N && r1 < nrows) ? in[r1 * kxp + kk] : zero;
-    bv[j] = (it < kXLines * N && r1 + 1 < nrows) ? in[(r1 + 1) * kxp + kk] : zero;
+    for (int o = 0; o < OUTS; ++o) load_old(o);
   }
-  // the gathers' records: staged by cp.async while the spectrum loads are in flight
+  constexpr int LOADS = (kXLines * N + kThreads - 1) / kThreads;   // compile-time: loads in flight together
+  constexpr int BATCH = LEAN ? (LOADS + 1) / 2 : LOADS;
   int g0 = 0, ge = 0;
-  if (GATHER) {
-    StagedTask<R>* stage = reinterpret_cast<StagedTask<R>*>(smem_raw + stage_offset<R, N>());
-    g0 = rb.start[blockIdx.x];
-    ge = rb.start[blockIdx.x + 1];
-    if (tid < min(ge - g0, kStageI))
-      stage_task<R>(&stage[tid], reinterpret_cast<const BlobStencil<R>*>(rb.geo), rb.list[g0 + tid], comp, nullptr);
-    cp_async_commit();
-  }
 #pragma unroll
-  for (int j = 0; j < LOADS; ++j) {
-    const int it = tid + j * kThreads;
-    if (it >= kXLines * N) break;
-    const int k = it % N, l = it / N;
-    C a = av[j], b = bv[j];
-    if (2 * k > N) {
-      a = cconj(a);
-      b = cconj(b);
+  for (int j0 = 0; j0 < LOADS; j0 += BATCH) {
+    C av[BATCH], bv[BATCH];
+#pragma unroll
+    for (int j = 0; j < BATCH; ++j) {
+      const int it = tid + (j0 + j) * kThreads;
+      const int k = it % N, l = it / N;
+      const long long r1 = row0 + 2 * l;
+      const int kk = 2 * k <= N ? k : N - k;
+      const bool ok = j0 + j < LOADS && it < kXLines * N;
+      av[j] = (ok && r1 < nrows) ? in[r1 * kxp + kk] : zero;
+      bv[j] = (ok && r1 + 1 < nrows) ? in[(r1 + 1) * kxp + kk] : zero;
     }
-    if (k == 0 || 2 * k == N) {
-      a.y = R(0);
-      b.y = R(0);
+    // the gathers' records: staged by cp.async while the spectrum loads are in flight
+    if (GATHER && j0 == 0) {
+      StagedTask<R>* stage = reinterpret_cast<StagedTask<R>*>(smem_raw + stage_offset<R, N>());
+      g0 = rb.start[blockIdx.x];
+      ge = rb.start[blockIdx.x + 1];
+      if (tid < min(ge - g0, NST))
+        stage_task<R>(&stage[tid], reinterpret_cast<const BlobStencil<R>*>(rb.geo), rb.list[g0 + tid], comp, nullptr);
+      cp_async_commit();
     }
-    buf[xaddr(l, R2 * (k % R1) + k / R1, N)] = mk(a.x - b.y, a.y + b.x);
+#pragma unroll
+    for (int j = 0; j < BATCH; ++j) {
+      const int it = tid + (j0 + j) * kThreads;
+      if (j0 + j >= LOADS || it >= kXLines * N) continue;
+      const int k = it % N, l = it / N;
+      C a = av[j], b = bv[j];
+      if (2 * k > N) {
+        a = cconj(a);
+        b = cconj(b);
+      }
+      if (k == 0 || 2 * k == N) {
+        a.y = R(0);
+        b.y = R(0);
+      }
+      buf[xaddr(l, R2 * (k % R1) + k / R1, N)] = mk(a.x - b.y, a.y + b.x);
+    }
   }
   __syncthreads();
   for (int it = tid; it < kXLines * R1; it += kThreads) {
@@ -970,6 +988,7 @@ __global__ void __launch_bounds__(kThreads) k_xinv2(const cplx_t<R>* __restrict_
     const int it = tid + o * kThreads;
     if (it >= kXLines * R2) break;
     const int n1 = it % R2, l = it / R2;
+    if (ADDS && LEAN) load_old(o);   // in flight during the last stage
     C a[R1];
 #pragma unroll
     for (int k2 = 0; k2 < R1; ++k2) a[k2] = buf[xaddr(l, n1 + R2 * k2, N)];
@@ -1013,14 +1032,14 @@ __global__ void __launch_bounds__(kThreads) k_xinv2(const cplx_t<R>* __restrict_
     const auto line = [](int l, int x) { return xaddr(l, x, N); };
     const bool plane = rb.p.ny % kRowBlock == 0;   // the block is part of one z plane
     const int z0 = (int)row0 / rb.p.ny, y0 = (int)row0 % rb.p.ny;
-    if (tid < min(ge - g0, kStageI)) {
+    if (tid < min(ge - g0, NST)) {
       const StagedTask<R>& t = stage[tid];
       R j, jl;
       gather_one<R, N, GATHER == 2>(rows, (int)row0, plane, z0, y0, t.first, t.w, rb.p, line, j, jl);
       atomicAdd(&rb.acc[3 * t.b + comp], (double)j);
       if (GATHER == 2) atomicAdd(&rb.acc_lap[3 * t.b + comp], (double)jl);
     }
-    for (int i = g0 + kStageI + tid; i < ge; i += kThreads) {   // beyond the staged tasks
+    for (int i = g0 + NST + tid; i < ge; i += kThreads) {   // beyond the staged tasks
       const int b = rb.list[i];
       R j, jl;
       gather_one<R, N, GATHER == 2>(rows, (int)row0, plane, z0, y0, *reinterpret_cast<const int4*>(rec[b].first[comp]),
@@ -1258,11 +1277,11 @@ void fft_x_inverse_blobs(const FftCtx<R>& f, R* dst, int mode, const RowBlobs& r
 #define ICM_CASE(N, R1, R2)                                                                                              \
   case N:                                                                                                                \
     if (mode == OUT_STORE)                                                                                               \
-      k_xinv2<R, N, R1, R2, OUT_STORE, 1><<<grid, kThreads, smem_x2b<R, N, kStageI>(), st>>>(f.spec, dst, nullptr, tw, nrows, f.ncell, f.kxp, rb, nullptr); \
+      k_xinv2<R, N, R1, R2, OUT_STORE, 1><<<grid, kThreads, smem_x2b<R, N, xi2_stage<R, N, OUT_STORE>()>(), st>>>(f.spec, dst, nullptr, tw, nrows, f.ncell, f.kxp, rb, nullptr); \
     else if (mode == OUT_NONE)                                                                                           \
-      k_xinv2<R, N, R1, R2, OUT_NONE, 1><<<grid, kThreads, smem_x2b<R, N, kStageI>(), st>>>(f.spec, dst, nullptr, tw, nrows, f.ncell, f.kxp, rb, nullptr); \
+      k_xinv2<R, N, R1, R2, OUT_NONE, 1><<<grid, kThreads, smem_x2b<R, N, xi2_stage<R, N, OUT_NONE>()>(), st>>>(f.spec, dst, nullptr, tw, nrows, f.ncell, f.kxp, rb, nullptr); \
     else                                                                                                                 \
-      k_xinv2<R, N, R1, R2, OUT_ADD, 2><<<grid, kThreads, smem_x2b<R, N, kStageI>(), st>>>(f.spec, dst, nullptr, tw, nrows, f.ncell, f.kxp, rb, nullptr); \
+      k_xinv2<R, N, R1, R2, OUT_ADD, 2><<<grid, kThreads, smem_x2b<R, N, xi2_stage<R, N, OUT_ADD>()>(), st>>>(f.spec, dst, nullptr, tw, nrows, f.ncell, f.kxp, rb, nullptr); \
     return;
     ICM_FFT_SIDES(ICM_CASE)
 #undef ICM_CASE
