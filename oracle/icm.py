@@ -12,7 +12,7 @@ Paper: F. Balboa Usabiaga, R. Delgado-Buscalioni, B. E. Griffith, A. Donev,
 "Inertial coupling method for particles in an incompressible fluctuating
 fluid", arXiv:1212.6427.  Citations below are to its sections and equations.
 
-Readings of points the paper leaves open (all listed in the design doc):
+Readings of points the paper leaves open:
   * MAC grid (Sec. III.A): cell (i,j,k) centred at ((i+1/2)h, (j+1/2)h, (k+1/2)h);
     v_x[i,j,k] sits on the low x face (ih, (j+1/2)h, (k+1/2)h), likewise v_y, v_z.
     Arrays have shape (Nz, Ny, Nx) so the flat index is i + Nx (j + Ny k).
