@@ -109,7 +109,10 @@ icm_status icm_add_blobs(icm_sim* sim, int64_t n, const double* pos, const doubl
                          const double* excess_mass);
 
 /* Set the external force of every blob (Sec. III.C step 1: F^{n+1/2}), held until
- * the next call: force[n_total*3].  Errors: ICM_EINVAL (NULL, non-finite). */
+ * the next call: force[n_total*3].  The values are copied before the call returns
+ * (the caller may reuse the buffer at once); the device upload and the FP64 total
+ * force are queued on the simulation's stream, ordered before the next step.
+ * Errors: ICM_EINVAL (NULL, non-finite). */
 icm_status icm_set_blob_forces(icm_sim* sim, const double* force);
 
 /* Add to every blob the force of the harmonic potential V(r) = k r^2 / 2 about
@@ -171,8 +174,11 @@ icm_status icm_sync(icm_sim* sim);
  *   pos[n*3], vel[n*3] : blob positions (in [0, N h)) and velocities.
  *   fluid_v[3*N]       : face velocities, layout as in the header comment.
  *   momentum[3]        : total momentum P = rho dV_f sum_k v_k + sum_i m_e,i u_i
- *                        (Sec. II, after Eq. no_slip), from the FP64 bookkeeping.
- *   step               : number of steps taken (time level n). */
+ *                        (Sec. II, after Eq. no_slip), from the FP64 bookkeeping; the
+ *                        blob sum is an FP64 compensated sum on the device.
+ *   step               : number of steps taken (time level n).
+ * Everything is read into a page-locked staging buffer of the simulation with one
+ * wait.  Device errors of earlier steps are returned after the outputs are filled. */
 icm_status icm_read_state(icm_sim* sim, double* pos, double* vel, double* fluid_v,
                           double momentum[3], int64_t* step);
 

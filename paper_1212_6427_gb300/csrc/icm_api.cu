@@ -133,6 +133,13 @@ struct icm_sim {
   int* err_dev = nullptr;
   double* partial = nullptr;
   static constexpr int kPartials = 1024;
+  // page-locked host staging of the per-step host I/O: forces [3 cap], positions [3 cap],
+  // velocities [3 cap], scalars [8] (the total force, then what icm_read_state reads);
+  // the forces' slot is rewritten only once the copy out of it (ev_hforce) has passed
+  double* hstage = nullptr;
+  long long hstage_cap = -1;
+  cudaEvent_t ev_hforce = nullptr;
+  bool hforce_pending = false;
   // graph of one step
   cudaGraphExec_t gexec = nullptr;
   bool graph_ok = false;
@@ -741,10 +748,8 @@ icm_status recompute_pbar(icm_sim* s) {
   return ICM_OK;
 }
 
-icm_status check_device_errors(icm_sim* s) {
-  int err = 0;
-  ICM_CK(cudaMemcpyAsync(&err, s->err_dev, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
-  ICM_CK(cudaStreamSynchronize(s->stream));
+// The status of device error bits err (already read back); clears them on the device.
+icm_status device_error_status(icm_sim* s, int err) {
   if (err) {
     ICM_CK(cudaMemsetAsync(s->err_dev, 0, sizeof(int), s->stream));
     ICM_CK(cudaStreamSynchronize(s->stream));
@@ -752,6 +757,30 @@ icm_status check_device_errors(icm_sim* s) {
     if (err & DEV_ERR_NONFINITE) return fail(ICM_ENONFINITE, "a non-finite blob position or velocity appeared");
     return fail(ICM_ECFL, "a blob moved more than one cell in a step (|u| dt / h > 1)");
   }
+  return ICM_OK;
+}
+
+icm_status check_device_errors(icm_sim* s) {
+  int err = 0;
+  ICM_CK(cudaMemcpyAsync(&err, s->err_dev, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  ICM_CK(cudaStreamSynchronize(s->stream));
+  return device_error_status(s, err);
+}
+
+// The host staging buffer, sized for the current blob capacity.
+icm_status ensure_hstage(icm_sim* s) {
+  if (s->hstage && s->hstage_cap == s->cap) return ICM_OK;
+  ICM_CK(cudaStreamSynchronize(s->stream));
+  if (s->hstage) cudaFreeHost(s->hstage);
+  s->hstage = nullptr;
+  s->hforce_pending = false;
+  if (cudaMallocHost(&s->hstage, sizeof(double) * (9 * (size_t)s->cap + 16)) != cudaSuccess) {
+    s->hstage = nullptr;
+    cudaGetLastError();
+    return fail(ICM_ENOMEM, "no page-locked host memory for the staging buffer");
+  }
+  s->hstage_cap = s->cap;
+  if (!s->ev_hforce) ICM_CK(cudaEventCreateWithFlags(&s->ev_hforce, cudaEventDisableTiming));
   return ICM_OK;
 }
 
@@ -930,6 +959,8 @@ void icm_destroy(icm_sim* s) {
   if (s->aux) cudaStreamDestroy(s->aux);
   if (s->ev_fork) cudaEventDestroy(s->ev_fork);
   if (s->ev_join) cudaEventDestroy(s->ev_join);
+  if (s->ev_hforce) cudaEventDestroy(s->ev_hforce);
+  if (s->hstage) cudaFreeHost(s->hstage);
   delete s;
 }
 
@@ -974,25 +1005,33 @@ icm_status icm_set_blob_forces(icm_sim* s, const double* force) {
   if (!s) return fail(ICM_EINVAL, "NULL simulation");
   if (s->nb == 0) return ICM_OK;
   if (!force) return fail(ICM_EINVAL, "force must not be NULL");
-  if (!finite_all(force, 3 * s->nb)) return fail(ICM_EINVAL, "non-finite force");
+  icm_status st = ensure_hstage(s);
+  if (st != ICM_OK) return st;
+  // the previous copy out of the staging slot must have passed before it is rewritten
+  if (s->hforce_pending) ICM_CK(cudaEventSynchronize(s->ev_hforce));
+  s->hforce_pending = false;
+  // one pass: finiteness and the copy into the staging slot
+  double* fs = s->hstage;
+  const long long n3 = 3 * s->nb;
+  bool any = false, finite = true;
+  for (long long i = 0; i < n3; ++i) {
+    const double x = force[i];
+    finite &= std::isfinite(x);
+    any |= x != 0.0;
+    fs[i] = x;
+  }
+  if (!finite) return fail(ICM_EINVAL, "non-finite force");
+  ICM_CK(cudaMemcpyAsync(s->f, fs, sizeof(double) * n3, cudaMemcpyHostToDevice, s->stream));
+  ICM_CK(cudaEventRecord(s->ev_hforce, s->stream));
+  s->hforce_pending = true;
   // FP64 compensated total force for the momentum bookkeeping
-  double sum[3] = {0, 0, 0}, c[3] = {0, 0, 0};
-  bool any = false;
-  for (long long i = 0; i < s->nb; ++i)
-    for (int a = 0; a < 3; ++a) {
-      const double y = force[3 * i + a] - c[a];
-      const double t = sum[a] + y;
-      c[a] = (t - sum[a]) - y;
-      sum[a] = t;
-      any |= force[3 * i + a] != 0.0;
-    }
-  ICM_CK(cudaMemcpyAsync(s->f, force, sizeof(double) * 3 * s->nb, cudaMemcpyHostToDevice, s->stream));
-  ICM_CK(cudaMemcpyAsync(s->scal + SC_SUMF, sum, sizeof(sum), cudaMemcpyHostToDevice, s->stream));
+  rows_sum3(s->f, nullptr, s->nb, nullptr, s->scal + SC_SUMF, s->partial, icm_sim::kPartials, s->stream);
+  ICM_CK(cudaGetLastError());
   if (any != s->any_force) {
     s->any_force = any;
     invalidate_graph(s);
   }
-  // the copies read pageable host memory: they have completed when this returns
+  // the caller's buffer has been copied when this returns
   return ICM_OK;
 }
 
@@ -1143,33 +1182,36 @@ icm_status icm_sync(icm_sim* s) {
 
 icm_status icm_read_state(icm_sim* s, double* pos, double* vel, double* fluid_v, double momentum[3], int64_t* step) {
   if (!s) return fail(ICM_EINVAL, "NULL simulation");
+  icm_status st = ensure_hstage(s);
+  if (st != ICM_OK) return st;
+  // every read goes into the page-locked staging buffer behind the queued work; one wait
+  double* ps = s->hstage + 3 * s->cap;
+  double* us = s->hstage + 6 * s->cap;
+  double* sc = s->hstage + 9 * s->cap + 3;   // total momentum [3], step, error bits
+  const size_t bb = sizeof(double) * 3 * s->nb;
+  if (pos && s->nb) ICM_CK(cudaMemcpyAsync(ps, s->q, bb, cudaMemcpyDeviceToHost, s->stream));
+  if (vel && s->nb) ICM_CK(cudaMemcpyAsync(us, s->u, bb, cudaMemcpyDeviceToHost, s->stream));
+  if (momentum) {
+    // P = (FP64 fluid bookkeeping) + sum_i m_e,i u_i, compensated, on the device
+    rows_sum3(s->u, s->me, s->nb, s->scal + SC_PBAR, s->scal + SC_PTOT, s->partial, icm_sim::kPartials, s->stream);
+    ICM_CK(cudaGetLastError());
+    ICM_CK(cudaMemcpyAsync(sc, s->scal + SC_PTOT, 3 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  }
+  ICM_CK(cudaMemcpyAsync(sc + 3, s->step_dev, sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
+  ICM_CK(cudaMemcpyAsync(sc + 4, s->err_dev, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
   ICM_CK(cudaStreamSynchronize(s->stream));
-  const icm_status dev = check_device_errors(s);
-  std::vector<double> u(3 * s->nb);
-  if (pos && s->nb) ICM_CK(cudaMemcpyAsync(pos, s->q, sizeof(double) * 3 * s->nb, cudaMemcpyDeviceToHost, s->stream));
-  if (s->nb) ICM_CK(cudaMemcpyAsync(u.data(), s->u, sizeof(double) * 3 * s->nb, cudaMemcpyDeviceToHost, s->stream));
-  double pbar[3];
+  int err = 0;
   long long stp = 0;
-  ICM_CK(cudaMemcpyAsync(pbar, s->scal + SC_PBAR, sizeof(pbar), cudaMemcpyDeviceToHost, s->stream));
-  ICM_CK(cudaMemcpyAsync(&stp, s->step_dev, sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
-  ICM_CK(cudaStreamSynchronize(s->stream));
+  memcpy(&err, sc + 4, sizeof(int));
+  memcpy(&stp, sc + 3, sizeof(long long));
+  const icm_status dev = device_error_status(s, err);
   if (fluid_v) {
-    const icm_status st = download_field(s, s->v, fluid_v);
+    st = download_field(s, s->v, fluid_v);
     if (st != ICM_OK) return st;
   }
-  if (vel && s->nb) memcpy(vel, u.data(), sizeof(double) * 3 * s->nb);
-  if (momentum) {
-    for (int a = 0; a < 3; ++a) {
-      double sum = pbar[a], c = 0.0;
-      for (long long i = 0; i < s->nb; ++i) {
-        const double y = s->me_host[i] * u[3 * i + a] - c;
-        const double t = sum + y;
-        c = (t - sum) - y;
-        sum = t;
-      }
-      momentum[a] = sum;
-    }
-  }
+  if (pos && s->nb) memcpy(pos, ps, bb);
+  if (vel && s->nb) memcpy(vel, us, bb);
+  if (momentum) memcpy(momentum, sc, 3 * sizeof(double));
   if (step) *step = stp;
   return dev;
 }

@@ -665,6 +665,66 @@ void blob_spread(const BlobParams& p, long long nb, const double* q, const doubl
   ICM_KSWITCH((k_spread<R, 3><<<nblocks(nb), 32 * kWarps, 0, st>>>(p, nb, q, vec, field)),
               (k_spread<R, 4><<<nblocks(nb), 32 * kWarps, 0, st>>>(p, nb, q, vec, field)))
 }
+namespace {
+// Block tree sum of three per-thread values into red[3][256]; the result is in red[.][0].
+__device__ __forceinline__ void block_sum3(double (&red)[3][256], const double v[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) red[a][threadIdx.x] = v[a];
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) red[a][threadIdx.x] += red[a][threadIdx.x + h];
+    __syncthreads();
+  }
+}
+
+// Per-block compensated sums of w_i x[3 i + a] -> partial[a * gridDim.x + block].
+__global__ void __launch_bounds__(256) k_rows_partial(const double* __restrict__ x, const double* __restrict__ w,
+                                                      long long n, double* __restrict__ partial) {
+  __shared__ double red[3][256];
+  double s[3] = {0.0, 0.0, 0.0}, c[3] = {0.0, 0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double wi = w ? w[i] : 1.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double y = wi * x[3 * i + a] - c[a];
+      const double t = s[a] + y;
+      c[a] = (t - s[a]) - y;
+      s[a] = t;
+    }
+  }
+  block_sum3(red, s);
+  if (threadIdx.x < 3) partial[threadIdx.x * gridDim.x + blockIdx.x] = red[threadIdx.x][0];
+}
+
+// out[a] = init[a] + compensated sum of the np partials of component a.
+__global__ void __launch_bounds__(256) k_rows_final(const double* __restrict__ partial, int np,
+                                                    const double* __restrict__ init, double* __restrict__ out) {
+  __shared__ double red[3][256];
+  double s[3] = {0.0, 0.0, 0.0}, c[3] = {0.0, 0.0, 0.0};
+  for (int i = threadIdx.x; i < np; i += blockDim.x)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double y = partial[a * np + i] - c[a];
+      const double t = s[a] + y;
+      c[a] = (t - s[a]) - y;
+      s[a] = t;
+    }
+  block_sum3(red, s);
+  if (threadIdx.x < 3) out[threadIdx.x] = (init ? init[threadIdx.x] : 0.0) + red[threadIdx.x][0];
+}
+}  // namespace
+
+void rows_sum3(const double* x, const double* w, long long n, const double* init, double* out, double* partial,
+               int npartial, cudaStream_t st) {
+  long long g = (n + 255) / 256;
+  if (g > npartial) g = npartial;
+  if (g < 1) g = 1;
+  k_rows_partial<<<(unsigned)g, 256, 0, st>>>(x, w, n, partial);
+  k_rows_final<<<1, 256, 0, st>>>(partial, (int)g, init, out);
+}
+
 template <typename R>
 void blob_momentum_change(const BlobParams& p, BlobState s, const R* vt, cudaStream_t st) {
   if (s.nb <= 0) return;

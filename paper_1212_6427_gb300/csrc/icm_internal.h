@@ -182,13 +182,19 @@ enum ScalarSlot : int {
   SC_SUMSRC = 6,    // [3] sum_i (dp_i - m_e,i J dv~_i) of this step
   SC_K0 = 9,        // [3] prescribed grid sum of the provisional solve output
   SC_K0B = 12,      // [3] prescribed grid sum of the viscous correction output
-  SC_COUNT = 16
+  SC_PTOT = 16,     // [3] total momentum (fluid + blob excess) for a host read
+  SC_COUNT = 20
 };
 
 template <typename R> void blob_predict(const BlobParams& p, BlobState s, const R* v, cudaStream_t st);
 template <typename R> void blob_spread(const BlobParams& p, long long nb, const double* q, const double* vec,
                                        R* field, cudaStream_t st);
 template <typename R> void blob_momentum_change(const BlobParams& p, BlobState s, const R* vt, cudaStream_t st);
+// out[a] = init[a] (0 if init is null) + sum_i w_i x[3 i + a] (w_i = 1 if w is null),
+// FP64 compensated sums per thread, then over blocks (partial: 3 npartial doubles of
+// scratch); out may not alias x, w or init.
+void rows_sum3(const double* x, const double* w, long long n, const double* init, double* out, double* partial,
+               int npartial, cudaStream_t st);
 template <typename R> void blob_inertial(const BlobParams& p, BlobState s, const R* dvt, cudaStream_t st);
 template <typename R> void blob_finish(const BlobParams& p, BlobState s, const R* v_new, const R* dv,
                                        bool inertial, cudaStream_t st);
