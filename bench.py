@@ -370,8 +370,8 @@ def extras(args, w, prec, sim, line, torch, icm, per_kernel):
     e1.synchronize()
     del y
     cufft_ms = e0.elapsed_time(e1) / 10
-    ours_rt = sum(per_kernel[k]["ms"] for k in ("x_fwd", "y_fwd", "z_sym", "y_inv", "x_inv")) / \
-        max(1, per_kernel["z_sym"]["launches"])
+    ours_rt = sum(per_kernel[k]["ms"] for k in ("x_fwd", "y_fwd", "xy_fwd", "z_sym", "y_inv", "x_inv")
+                  if k in per_kernel) / max(1, per_kernel["z_sym"]["launches"])
     line["fft_roundtrip"] = {"ours_ms": ours_rt, "cufft_ms": cufft_ms,
                              "note": "ours includes the fused Helmholtz/projection symbol; cuFFT is R2C+C2R only"}
     log("[bench] extras: oracle on the host")

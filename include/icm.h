@@ -141,6 +141,8 @@ typedef struct icm_plan {
                           0: one block per z tile                                                  */
   int32_t rhs_kz;      /* z planes marched by each block of the right-hand-side kernel, 4..64       */
   int32_t fork;        /* 1: the blob-side prologue runs on a second stream beside the RHS          */
+  int32_t fused_xy;    /* 1: forward x and y FFT passes fused on thread-block clusters (FP32,
+                          Nx = Ny in 32, 64, 128, 256); 0 (default): two passes                    */
 } icm_plan;
 
 /* The plan the next step will use.  Errors: ICM_EINVAL (NULL). */

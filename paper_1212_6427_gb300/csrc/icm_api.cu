@@ -84,7 +84,7 @@ struct icm_sim {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   // execution plan (icm_plan) and where it came from
-  icm_plan plan = {1, 1, 16, 1};
+  icm_plan plan = {1, 1, 16, 1, 0};
   int plan_src = 0;   // 0 default, 1 from the process-wide table, 2 set or tuned on this simulation
   // second stream of the step graph: the blob-side prologue runs beside the RHS
   cudaStream_t aux = nullptr;
@@ -461,10 +461,16 @@ void enqueue_step(icm_sim* s, Prof* prof, int segment = -1) {
   const double w3l = (double)(s->kernel + 2) * (s->kernel + 2) * (s->kernel + 2);
   const double nb = (double)s->nb;
   const double gath = nb * 3.0 * w3 * sizeof(R);
+  // forward x and y passes fused on clusters (a plan choice on grids that allow it)
+  const bool xy = s->plan.fused_xy && fft_has_xy_passes(s->prec, s->nx, s->ny);
   auto solve = [&](const char* tag, const R* src, R* dst, R* dst2, int mode, double a, double b, const double* k0) {
     std::string t(tag);
-    ICM_STAGE((t + ".x_fwd").c_str(), F + S, fft_x_forward<R>(fc, src, st));
-    ICM_STAGE((t + ".y_fwd").c_str(), 2 * S, fft_y<R>(fc, false, st));
+    if (xy) {
+      ICM_STAGE((t + ".xy_fwd").c_str(), F + S, fft_xy_forward<R>(fc, src, nullptr, st));
+    } else {
+      ICM_STAGE((t + ".x_fwd").c_str(), F + S, fft_x_forward<R>(fc, src, st));
+      ICM_STAGE((t + ".y_fwd").c_str(), 2 * S, fft_y<R>(fc, false, st));
+    }
     ICM_STAGE((t + ".z_sym").c_str(), 2 * S, fft_z_symbol<R>(fc, a, b, k0, k0 ? k0scale : 0.0, st));
     ICM_STAGE((t + ".y_inv").c_str(), 2 * S, fft_y<R>(fc, true, st));
     ICM_STAGE((t + ".x_inv").c_str(), S + (mode == OUT_STORE ? F : 3 * F), fft_x_inverse<R>(fc, dst, dst2, mode, st));
@@ -541,11 +547,16 @@ void enqueue_step(icm_sim* s, Prof* prof, int segment = -1) {
       r.vec = vec;
       r.acc = acc;
       r.acc_lap = acc_lap;
-      if (vec)
-        ICM_STAGE((t + ".x_fwd").c_str(), (src ? F : 0.0) + S + blobio, fft_x_forward_blobs<R>(fc, src, r, st));
-      else
-        ICM_STAGE((t + ".x_fwd").c_str(), F + S, fft_x_forward<R>(fc, src, st));
-      ICM_STAGE((t + ".y_fwd").c_str(), 2 * S, fft_y<R>(fc, false, st));
+      if (xy) {
+        ICM_STAGE((t + ".xy_fwd").c_str(), (src ? F : 0.0) + S + (vec ? blobio : 0.0),
+                  fft_xy_forward<R>(fc, src, vec ? &r : nullptr, st));
+      } else {
+        if (vec)
+          ICM_STAGE((t + ".x_fwd").c_str(), (src ? F : 0.0) + S + blobio, fft_x_forward_blobs<R>(fc, src, r, st));
+        else
+          ICM_STAGE((t + ".x_fwd").c_str(), F + S, fft_x_forward<R>(fc, src, st));
+        ICM_STAGE((t + ".y_fwd").c_str(), 2 * S, fft_y<R>(fc, false, st));
+      }
       ICM_STAGE((t + ".z_sym").c_str(), 2 * S, fft_z_symbol<R>(fc, a, b, k0, k0 ? k0scale : 0.0, st));
       ICM_STAGE((t + ".y_inv").c_str(), 2 * S, fft_y<R>(fc, true, st));
       const double out = mode == OUT_STORE ? F : (mode == OUT_ADD ? 2 * F : 0.0);
@@ -618,7 +629,7 @@ void resolve_plan(icm_sim* s) {
     s->plan = it->second;
     s->plan_src = 1;
   } else if (s->plan_src == 1) {
-    s->plan = icm_plan{1, 1, 16, 1};
+    s->plan = icm_plan{1, 1, 16, 1, 0};
     s->plan_src = 0;
   }
 }
@@ -1101,7 +1112,8 @@ icm_status icm_get_plan(const icm_sim* s, icm_plan* out) {
 icm_status icm_set_plan(icm_sim* s, const icm_plan* plan) {
   if (!s || !plan) return fail(ICM_EINVAL, "NULL argument");
   if (plan->rhs_kz < 4 || plan->rhs_kz > 64) return fail(ICM_EINVAL, "rhs_kz must be in 4..64");
-  s->plan = icm_plan{plan->fused_blobs ? 1 : 0, plan->tma_z ? 1 : 0, plan->rhs_kz, plan->fork ? 1 : 0};
+  s->plan = icm_plan{plan->fused_blobs ? 1 : 0, plan->tma_z ? 1 : 0, plan->rhs_kz, plan->fork ? 1 : 0,
+                     plan->fused_xy ? 1 : 0};
   s->plan_src = 2;
   invalidate_graph(s);
   return ICM_OK;
@@ -1147,6 +1159,7 @@ icm_status icm_autotune(icm_sim* s, int32_t nsteps, icm_plan* chosen, double* ms
   if (s->has_zmap) knobs.push_back({&icm_plan::tma_z, {1, 0}});
   knobs.push_back({&icm_plan::rhs_kz, {8, 16, 32}});
   knobs.push_back({&icm_plan::fork, {1, 0}});
+  if (fft_has_xy_passes(s->prec, s->nx, s->ny)) knobs.push_back({&icm_plan::fused_xy, {0, 1}});
   for (size_t k = 0; st == ICM_OK && k < knobs.size(); ++k)
     for (int val : knobs[k].second) {
       if (best.*(knobs[k].first) == val) continue;
@@ -1847,13 +1860,13 @@ icm_status icm_batch_autotune(icm_batch* b, int32_t nsteps) {
     }
     return ICM_OK;
   };
-  icm_plan best = icm_plan{1, 1, 16, 1};
+  icm_plan best = icm_plan{1, 1, 16, 1, 0};
   int best_grouped = 0;
   double best_ms = 0.0;
   icm_status st = trial(best, best_grouped, best_ms);
   const std::vector<std::pair<int icm_plan::*, std::vector<int>>> knobs = {
       {&icm_plan::fused_blobs, {1, 0}}, {&icm_plan::tma_z, {1, 0}}, {&icm_plan::rhs_kz, {8, 16, 32}},
-      {&icm_plan::fork, {1, 0}}};
+      {&icm_plan::fork, {1, 0}}, {&icm_plan::fused_xy, {0, 1}}};
   for (size_t k = 0; st == ICM_OK && k < knobs.size(); ++k)
     for (int val : knobs[k].second) {
       if (best.*(knobs[k].first) == val) continue;

@@ -19,6 +19,7 @@
 // operands read from and written back to the same shared-memory positions.
 #include <cstdio>
 
+#include <cooperative_groups.h>
 #include <cuda.h>
 
 #include "icm.h"
@@ -780,28 +781,19 @@ __global__ void __launch_bounds__(kThreads) k_ypass2(cplx_t<R>* __restrict__ spe
   }
 }
 
-// x forward, two real rows per complex line; frequency k ends at position
-// R2 (k mod R1) + k div R1 of its line.  BLOBS: before the transform, the blobs of
-// this row block spread rb.vec into the rows (in shared memory, where the first
-// stage reads them), added to src if src is set.
-template <typename R, int N, int R1, int R2, bool BLOBS>
-__global__ void __launch_bounds__(kThreads, xf2_min_blocks<R, N>()) k_xfwd2(const R* __restrict__ src, cplx_t<R>* __restrict__ spec,
-                                                    const cplx_t<R>* __restrict__ gtw, int nrows, long long ncell,
-                                                    int kx, int kxp, RowBlobs rb, const RepFft* __restrict__ reps) {
+// The x forward transform of the 32 rows row0.. (16 complex lines, two real rows each)
+// of component comp into buf: frequency k of line l ends at position
+// R2 (k mod R1) + k div R1 of the line.  BLOBS: before the transform, the blobs of row
+// block `bin` spread rb.vec into the rows (in shared memory, where the first stage
+// reads them; NST records staged by cp.async in `stage_mem`), added to src if src is
+// set.  The first-stage twiddles tw are loaded by the caller; ends with a block barrier.
+template <typename R, int N, int R1, int R2, bool BLOBS, int NST>
+__device__ __forceinline__ void x_forward_rows(cplx_t<R>* __restrict__ buf, const cplx_t<R>* __restrict__ tw,
+                                               unsigned char* stage_mem, const R* __restrict__ src, long long row0,
+                                               int nrows, long long ncell, int comp, int bin, const RowBlobs& rb,
+                                               int tid) {
   using C = cplx_t<R>;
-  if (!BLOBS && reps != nullptr) {   // replica blockIdx.y / 3 of a group solve
-    const RepFft& rp = reps[blockIdx.y / 3];
-    src = reinterpret_cast<const R*>(rp.src);
-    spec = reinterpret_cast<C*>(rp.spec);
-  }
   static_assert(kRowBlock == 2 * kXLines, "row blocks are the x-pass blocks");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);   // [kXLines][xrow(N)]
-  C* tw = buf + kXLines * xrow(N);
-  const int tid = threadIdx.x;
-  load_stage_twiddles<R, R1, R2>(tw, gtw, tid, kThreads);
-  const int comp = blockIdx.y % 3;
-  const long long row0 = (long long)blockIdx.x * (2 * kXLines);
   const bool dense = !BLOBS || src != nullptr;
   // one first-stage item (line l, offset n1) per thread; its loads are issued first
   constexpr int ITEMS = kXLines * R2;
@@ -818,10 +810,10 @@ __global__ void __launch_bounds__(kThreads, xf2_min_blocks<R, N>()) k_xfwd2(cons
   }
   if (BLOBS) {
     // this block's tasks: records staged by cp.async while the buffer is zeroed
-    StagedTask<R>* stage = reinterpret_cast<StagedTask<R>*>(smem_raw + stage_offset<R, N>());
+    StagedTask<R>* stage = reinterpret_cast<StagedTask<R>*>(stage_mem);
     const BlobStencil<R>* rec = reinterpret_cast<const BlobStencil<R>*>(rb.geo);
-    const int s0 = rb.start[blockIdx.x], e = rb.start[blockIdx.x + 1];
-    const int nst = min(e - s0, kStageF);
+    const int s0 = rb.start[bin], e = rb.start[bin + 1];
+    const int nst = min(e - s0, NST);
     if (tid < nst) stage_task<R>(&stage[tid], rec, rb.list[s0 + tid], comp, rb.vec);
     cp_async_commit();
     for (int i = tid; i < kXLines * xrow(N); i += kThreads) buf[i] = mk(R(0), R(0));
@@ -836,7 +828,7 @@ __global__ void __launch_bounds__(kThreads, xf2_min_blocks<R, N>()) k_xfwd2(cons
       const StagedTask<R>& t = stage[tid];
       spread_one<R, N>(rows, (int)row0, plane, z0, y0, t.first, t.w, (R)(t.vec * inv_dvf), rb.p, line);
     }
-    for (int i = s0 + kStageF + tid; i < e; i += kThreads) {   // beyond the staged tasks
+    for (int i = s0 + NST + tid; i < e; i += kThreads) {   // beyond the staged tasks
       const int b = rb.list[i];
       spread_one<R, N>(rows, (int)row0, plane, z0, y0, *reinterpret_cast<const int4*>(rec[b].first[comp]),
                        &rec[b].w[comp][0][0], (R)(rb.vec[3 * b + comp] * inv_dvf), rb.p, line);
@@ -863,14 +855,45 @@ __global__ void __launch_bounds__(kThreads, xf2_min_blocks<R, N>()) k_xfwd2(cons
     for (int k1 = 0; k1 < R2; ++k1) buf[xaddr(l, R2 * blk + k1, N)] = b[k1];
   }
   __syncthreads();
+}
+
+// The two half spectra of line l at wavenumber k from the transformed lines in buf.
+template <typename R, int N, int R1, int R2>
+__device__ __forceinline__ void split_half_spectra(const cplx_t<R>* __restrict__ buf, int l, int k, cplx_t<R>& x1,
+                                                   cplx_t<R>& x2) {
+  using C = cplx_t<R>;
+  const int km = k == 0 ? 0 : N - k;
+  const C zk = buf[xaddr(l, R2 * (k % R1) + k / R1, N)];
+  const C zm = buf[xaddr(l, R2 * (km % R1) + km / R1, N)];
+  x1 = mk((zk.x + zm.x) * R(0.5), (zk.y - zm.y) * R(0.5));
+  x2 = cmul_mi(mk((zk.x - zm.x) * R(0.5), (zk.y + zm.y) * R(0.5)));
+}
+
+// x forward pass: x_forward_rows, then the half spectra of the rows to spec.
+template <typename R, int N, int R1, int R2, bool BLOBS>
+__global__ void __launch_bounds__(kThreads, xf2_min_blocks<R, N>()) k_xfwd2(const R* __restrict__ src, cplx_t<R>* __restrict__ spec,
+                                                    const cplx_t<R>* __restrict__ gtw, int nrows, long long ncell,
+                                                    int kx, int kxp, RowBlobs rb, const RepFft* __restrict__ reps) {
+  using C = cplx_t<R>;
+  if (!BLOBS && reps != nullptr) {   // replica blockIdx.y / 3 of a group solve
+    const RepFft& rp = reps[blockIdx.y / 3];
+    src = reinterpret_cast<const R*>(rp.src);
+    spec = reinterpret_cast<C*>(rp.spec);
+  }
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);   // [kXLines][xrow(N)]
+  C* tw = buf + kXLines * xrow(N);
+  const int tid = threadIdx.x;
+  load_stage_twiddles<R, R1, R2>(tw, gtw, tid, kThreads);
+  const int comp = blockIdx.y % 3;
+  const long long row0 = (long long)blockIdx.x * (2 * kXLines);
+  x_forward_rows<R, N, R1, R2, BLOBS, kStageF>(buf, tw, smem_raw + stage_offset<R, N>(), src, row0, nrows, ncell,
+                                               comp, blockIdx.x, rb, tid);
   C* out = spec + (size_t)comp * nrows * kxp;
   // the two half spectra of line l at wavenumber k (kx = N/2 + 1 of them)
   const auto split = [&](int l, int k) {
-    const int km = k == 0 ? 0 : N - k;
-    const C zk = buf[xaddr(l, R2 * (k % R1) + k / R1, N)];
-    const C zm = buf[xaddr(l, R2 * (km % R1) + km / R1, N)];
-    const C x1 = mk((zk.x + zm.x) * R(0.5), (zk.y - zm.y) * R(0.5));
-    const C x2 = cmul_mi(mk((zk.x - zm.x) * R(0.5), (zk.y + zm.y) * R(0.5)));
+    C x1, x2;
+    split_half_spectra<R, N, R1, R2>(buf, l, k, x1, x2);
     const long long r1 = row0 + 2 * l;
     if (r1 < nrows) out[r1 * kxp + k] = x1;
     if (r1 + 1 < nrows) out[(r1 + 1) * kxp + k] = x2;
@@ -880,6 +903,93 @@ __global__ void __launch_bounds__(kThreads, xf2_min_blocks<R, N>()) k_xfwd2(cons
   for (int it = tid; it < kXLines * H; it += kThreads) split(it / H, it % H);
   if (tid < kXLines) split(tid, H);
 }
+
+// ---------------------------------------------------------------------------
+// Forward x and y passes fused on thread-block clusters (FP32, Nx = Ny = N, N a
+// multiple of 32).  A cluster of N/32 blocks holds one z plane of one component:
+// block r transforms rows y = 32 r .. 32 r + 31 along x (with the blob spread, as
+// k_xfwd2) and keeps their half spectra in its shared memory; after a cluster barrier
+// it transforms kx columns 16 r .. 16 r + 15 along y (rank 0 also the Nyquist column
+// N/2), reading the rows of every block of the cluster through distributed shared
+// memory, and writes them to the spectrum exactly as the y pass does.  The half
+// spectrum thus never makes the round trip through HBM between the two passes.
+// ---------------------------------------------------------------------------
+constexpr int kYL = 17;   // lines of the y buffer: 16 kx columns (+ the Nyquist column)
+template <int N> constexpr int xy_pitch() { return N / 2 + 1; }
+template <int N> size_t smem_xyf() {
+  return (size_t)(kYL * N + N + kRowBlock * xy_pitch<N>()) * sizeof(cplx_t<float>);
+}
+
+template <int N, int R1, int R2, bool BLOBS>
+__global__ void __launch_bounds__(kThreads, 3) k_xyf(const float* __restrict__ src, cplx_t<float>* __restrict__ spec,
+                                                     const cplx_t<float>* __restrict__ gtw, int nz, long long ncell,
+                                                     int kxp, RowBlobs rb) {
+  using R = float;
+  using C = cplx_t<R>;
+  namespace cg = cooperative_groups;
+  constexpr int CL = N / kRowBlock;   // blocks per cluster
+  constexpr int XP = xy_pitch<N>();
+  constexpr int H = N / 2;
+  static_assert(kYL * N == kXLines * xrow(N), "the y lines overlay the x rows");
+  static_assert(kRowBlock % R2 == 0, "a first-stage item's rows lie in one block");
+  static_assert(R1 * 16 <= kThreads && R2 * 16 <= kThreads, "one y item per thread");
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);   // x rows [16][xrow(N)], later the y lines [N][kYL]
+  C* tw = buf + kYL * N;                     // first-stage twiddles (the y side is the x side)
+  C* X = tw + N;                             // half spectra of this block's rows [32][XP]
+  const int tid = threadIdx.x;
+  const int rank = blockIdx.x, z = blockIdx.y, comp = blockIdx.z;
+  load_stage_twiddles<R, R1, R2>(tw, gtw, tid, kThreads);
+  const long long row0 = (long long)z * N + kRowBlock * rank;
+  x_forward_rows<R, N, R1, R2, BLOBS, 0>(buf, tw, nullptr, src, row0, N * nz, ncell, comp, z * CL + rank, rb, tid);
+  for (int it = tid; it < kXLines * H; it += kThreads) {
+    const int l = it / H, k = it % H;
+    C x1, x2;
+    split_half_spectra<R, N, R1, R2>(buf, l, k, x1, x2);
+    X[(2 * l) * XP + k] = x1;
+    X[(2 * l + 1) * XP + k] = x2;
+  }
+  if (tid < kXLines) {
+    C x1, x2;
+    split_half_spectra<R, N, R1, R2>(buf, tid, H, x1, x2);
+    X[(2 * tid) * XP + H] = x1;
+    X[(2 * tid + 1) * XP + H] = x2;
+  }
+  cluster.sync();   // the half spectra of every block are complete; buf is free
+  C* Y = buf;
+  const int kx0 = 16 * rank;
+  // y, first stage: item (line, n1) reads rows n1 + R2 r of column k from their blocks
+  const auto stage_a = [&](int line, int n1, int k) {
+    C a[R1];
+#pragma unroll
+    for (int r = 0; r < R1; ++r) {
+      constexpr int kR = kRowBlock;
+      const int sblk = (R2 * r) / kR;
+      const C* Xs = cluster.map_shared_rank(X, sblk);
+      a[r] = Xs[(n1 + R2 * r - kR * sblk) * XP + k];
+    }
+    stage_a_fwd<R, R1, R2>(a, tw + n1);
+#pragma unroll
+    for (int k2 = 0; k2 < R1; ++k2) Y[(n1 + R2 * k2) * kYL + line] = a[k2];
+  };
+  if (tid < R2 * 16) stage_a(tid % 16, tid / 16, kx0 + tid % 16);
+  if (rank == 0 && tid < R2) stage_a(16, tid, H);
+  cluster.sync();   // every remote read is done (blocks may leave); the y lines are complete
+  C* base = spec + ((size_t)(comp * nz + z) * N) * kxp;
+  // y, second stage: to the spectrum in storage order, as the y pass writes it
+  const auto stage_b = [&](int line, int blk, int k) {
+    C b[R2];
+#pragma unroll
+    for (int n = 0; n < R2; ++n) b[n] = Y[(R2 * blk + n) * kYL + line];
+    SDft<R, R2>::run(b);
+#pragma unroll
+    for (int k1 = 0; k1 < R2; ++k1) base[(size_t)(R2 * blk + k1) * kxp + k] = b[k1];
+  };
+  if (tid < R1 * 16) stage_b(tid % 16, tid / 16, kx0 + tid % 16);
+  if (rank == 0 && tid < R1) stage_b(16, tid, H);
+}
+#define ICM_XY_SIDES(X) X(32, 8, 4) X(64, 8, 8) X(128, 16, 8) X(256, 16, 16)
 
 // MODE OUT_STORE: dst = x.  OUT_ADD_AND_STORE2: dst += x, dst2 = x.  OUT_ADD: dst += x.
 // OUT_NONE: nothing stored.  The old dst values of the adding modes are loaded at
@@ -1073,6 +1183,9 @@ template <typename R> size_t smem_x(int n) { return (size_t)n * kXLS * sizeof(cp
 template <typename R> size_t smem_y(int n) { return (size_t)n * seg_lines<R>() * sizeof(cplx_t<R>) + n * sizeof(cplx_t<R>); }
 template <typename R> size_t smem_z(int n) { return 3 * (size_t)n * seg_lines<R>() * sizeof(cplx_t<R>) + n * sizeof(cplx_t<R>); }
 
+// Sides of the fused x-y forward pass whose clusters the device can hold.
+int g_xy_sides = 0;   // bit per entry of ICM_XY_SIDES
+
 template <typename R>
 void set_xf_attributes() {
   const int big = 227 * 1024;
@@ -1082,6 +1195,36 @@ void set_xf_attributes() {
   ICM_FFT_SIDES(ICM_ATTR)
 #undef ICM_ATTR
   cudaFuncSetAttribute(k_xfwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if constexpr (sizeof(R) == 4) {
+  int bit = 0, sides = 0;
+#define ICM_ATTR(N, R1, R2)                                                                                        \
+  {                                                                                                                \
+    bool ok = true;                                                                                                \
+    for (int b = 0; b < 2; ++b) {                                                                                  \
+      const void* fn = b ? (const void*)k_xyf<N, R1, R2, true> : (const void*)k_xyf<N, R1, R2, false>;             \
+      ok &= cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_xyf<N>()) == cudaSuccess; \
+      cudaLaunchConfig_t cfg = {};                                                                                 \
+      cfg.gridDim = dim3(N / kRowBlock, 1, 3);                                                                     \
+      cfg.blockDim = dim3(kThreads);                                                                               \
+      cfg.dynamicSmemBytes = smem_xyf<N>();                                                                        \
+      cudaLaunchAttribute at;                                                                                      \
+      at.id = cudaLaunchAttributeClusterDimension;                                                                 \
+      at.val.clusterDim.x = N / kRowBlock;                                                                         \
+      at.val.clusterDim.y = 1;                                                                                     \
+      at.val.clusterDim.z = 1;                                                                                     \
+      cfg.attrs = &at;                                                                                             \
+      cfg.numAttrs = 1;                                                                                            \
+      int nc = 0;                                                                                                  \
+      ok &= cudaOccupancyMaxActiveClusters(&nc, fn, &cfg) == cudaSuccess && nc > 0;                                \
+    }                                                                                                              \
+    if (ok) sides |= 1 << bit;                                                                                     \
+    ++bit;                                                                                                         \
+  }
+  ICM_XY_SIDES(ICM_ATTR)
+#undef ICM_ATTR
+  cudaGetLastError();
+  g_xy_sides = sides;
+  }
 }
 
 template <typename R>
@@ -1267,6 +1410,59 @@ void fft_x_forward_blobs(const FftCtx<R>& f, const R* src, const RowBlobs& rb, c
   record_error(ICM_EINVAL, "x pass with blob work requested for a side without register FFT kernels");
 }
 
+#if ICM_SHARD(0)
+bool fft_has_xy_passes(int precision, int nx, int ny) {
+  if (precision != 32 || nx != ny) return false;
+  int bit = 0;
+#define ICM_CASE(N, R1, R2) \
+  if (nx == N) return (g_xy_sides >> bit) & 1; \
+  ++bit;
+  ICM_XY_SIDES(ICM_CASE)
+#undef ICM_CASE
+  return false;
+}
+#endif
+
+template <typename R>
+void fft_xy_forward(const FftCtx<R>& f, const R* src, const RowBlobs* rb, cudaStream_t st) {
+  if constexpr (sizeof(R) != 4) {
+    record_error(ICM_EINVAL, "fused x-y pass in FP64");
+  } else {
+  if (!fft_has_xy_passes(32, f.nx, f.ny)) {
+    record_error(ICM_EINVAL, "fused x-y pass on an unsupported grid");
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at;
+  at.id = cudaLaunchAttributeClusterDimension;
+  at.val.clusterDim.y = 1;
+  at.val.clusterDim.z = 1;
+  cfg.blockDim = dim3(kThreads);
+  cfg.stream = st;
+  cfg.attrs = &at;
+  cfg.numAttrs = 1;
+  const float* s32 = reinterpret_cast<const float*>(src);
+  cplx_t<float>* sp = reinterpret_cast<cplx_t<float>*>(f.spec);
+  const cplx_t<float>* tw = reinterpret_cast<const cplx_t<float>*>(f.px.tw);
+  const RowBlobs none{};
+  switch (f.nx) {
+#define ICM_CASE(N, R1, R2)                                                                                          \
+  case N:                                                                                                            \
+    cfg.gridDim = dim3(N / kRowBlock, f.nz, 3);                                                                      \
+    cfg.dynamicSmemBytes = smem_xyf<N>();                                                                            \
+    at.val.clusterDim.x = N / kRowBlock;                                                                             \
+    if (rb)                                                                                                          \
+      cudaLaunchKernelEx(&cfg, k_xyf<N, R1, R2, true>, s32, sp, tw, f.nz, f.ncell, f.kxp, *rb);                      \
+    else                                                                                                             \
+      cudaLaunchKernelEx(&cfg, k_xyf<N, R1, R2, false>, s32, sp, tw, f.nz, f.ncell, f.kxp, none);                    \
+    return;
+    ICM_XY_SIDES(ICM_CASE)
+#undef ICM_CASE
+    default: break;
+  }
+  }
+}
+
 template <typename R>
 void fft_x_inverse_blobs(const FftCtx<R>& f, R* dst, int mode, const RowBlobs& rb, cudaStream_t st) {
   const int nrows = f.ny * f.nz;
@@ -1433,6 +1629,7 @@ bool make_zmap(void* map, const void* spec, int precision, int kx, int kxp, int 
   KW template void fft_x_forward<R>(const FftCtx<R>&, const R*, cudaStream_t);                           \
   KW template void fft_x_forward_blobs<R>(const FftCtx<R>&, const R*, const RowBlobs&, cudaStream_t);    \
   KW template void fft_x_forward_group<R>(const FftCtx<R>&, const RepFft*, int, cudaStream_t);            \
+  KW template void fft_xy_forward<R>(const FftCtx<R>&, const R*, const RowBlobs*, cudaStream_t);         \
   KW template void fft_prepare_xf<R>();
 #define ICM_INST_XI(R, KW)                                                                               \
   KW template void fft_x_inverse<R>(const FftCtx<R>&, R*, R*, int, cudaStream_t);                        \

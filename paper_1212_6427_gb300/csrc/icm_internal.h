@@ -239,6 +239,12 @@ void build_row_bins(const BlobParams& p, long long nb, const double* q, RowBins 
 // x passes with blob work: src may be null (the spread source only).
 template <typename R>
 void fft_x_forward_blobs(const FftCtx<R>& f, const R* src, const RowBlobs& rb, cudaStream_t st);
+// Forward x and y passes fused on thread-block clusters (FP32, Nx = Ny in 32, 64, 128,
+// 256, clusters the device can hold): the spectrum fft_x_forward(_blobs) + fft_y
+// leave, without its HBM round trip in between.  rb: the blob spread, or null.
+bool fft_has_xy_passes(int precision, int nx, int ny);
+template <typename R>
+void fft_xy_forward(const FftCtx<R>& f, const R* src, const RowBlobs* rb, cudaStream_t st);
 // mode: OUT_STORE (dst = x), OUT_ADD (dst += x) or OUT_NONE; gathers J x into rb.acc
 // and, if rb.acc_lap is set, J L x (without 1/h^2) into rb.acc_lap.
 template <typename R>

@@ -19,11 +19,11 @@ def built():
 
 
 PLANS = [
-    dict(fused_blobs=1, tma_z=1, rhs_kz=16, fork=1),
-    dict(fused_blobs=0, tma_z=1, rhs_kz=16, fork=1),     # separate blob kernels on a fused-capable side
-    dict(fused_blobs=1, tma_z=0, rhs_kz=8, fork=0),      # one block per z tile, short RHS march
-    dict(fused_blobs=0, tma_z=0, rhs_kz=32, fork=0),
-    dict(fused_blobs=1, tma_z=1, rhs_kz=4, fork=1),
+    dict(fused_blobs=1, tma_z=1, rhs_kz=16, fork=1, fused_xy=1),
+    dict(fused_blobs=0, tma_z=1, rhs_kz=16, fork=1, fused_xy=1),     # separate blob kernels on a fused-capable side
+    dict(fused_blobs=1, tma_z=0, rhs_kz=8, fork=0, fused_xy=0),      # one block per z tile, short RHS march
+    dict(fused_blobs=0, tma_z=0, rhs_kz=32, fork=0, fused_xy=0),
+    dict(fused_blobs=1, tma_z=1, rhs_kz=4, fork=1, fused_xy=0),
 ]
 
 

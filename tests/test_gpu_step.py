@@ -29,8 +29,11 @@ def _case(grid, nb, kernel, seed, me_scale=1.0, force=0.0, kT=1e-3, dt=0.05, vam
     return prm, st
 
 
-def _run_parity(prm, st0, precision, nsteps):
+def _run_parity(prm, st0, precision, nsteps, plan=None):
     sim = make_sim(prm, st0, precision)
+    if plan is not None:
+        import paper_1212_6427_gb300 as icm
+        icm.icm_set_plan(sim.handle, **plan)
     state = st0.copy()
     worst = {}
     for _ in range(nsteps):
@@ -69,8 +72,13 @@ CASES = [
     # dense: ~150 blob tasks per row block, past the staged records of an x-pass block
     ((32, 32, 16), 600, 4, 23, 1.0, 0.02, 1e-3, "visc", True),
     ((64, 32, 8), 800, 3, 24, 1.0, 0.02, 1e-3, "full", True),     # ~300 per block: past the inverse pass too
+    # Nx = Ny: run with the x and y forward passes fused on clusters of Ny/32 blocks (FP32)
+    ((64, 64, 8), 20, 4, 25, 1.0, 0.02, 1e-3, "visc", True),
+    ((128, 128, 8), 30, 3, 26, 1.0, 0.02, 1e-3, "full", True),
+    ((256, 256, 8), 40, 4, 27, 1.0, 0.02, 1e-3, "visc", True),
 ]
-SEAM = {6, 7, 8, 9}    # cases that also put blobs on the periodic seams and corners
+SEAM = {6, 7, 8, 9, 13}    # cases that also put blobs on the periodic seams and corners
+XY = {13, 14, 15}          # cases stepped with the fused x-y plan
 
 
 @pytest.mark.parametrize("precision", [64, 32])
@@ -84,7 +92,8 @@ def test_step_parity(precision, case):
         st.q[1] = L - 0.3 * prm.h
         st.q[2] = [0.5 * prm.h, L[1] - 0.25 * prm.h, 1e-12]
         st.q[3] = [L[0] - 0.5 * prm.h, 0.5 * prm.h, L[2] - 0.5 * prm.h]
-    worst = _run_parity(prm, st, precision, nsteps=4)
+    plan = dict(fused_xy=1) if CASES.index(case) in XY else None
+    worst = _run_parity(prm, st, precision, nsteps=4, plan=plan)
     for k, e in worst.items():
         assert e < TOL[precision], (k, e, worst)
 
