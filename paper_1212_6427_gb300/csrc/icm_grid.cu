@@ -19,13 +19,16 @@ constexpr int PER = (HALO + NT - 1) / NT;   // halo cells loaded per thread
 
 __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
-// Shared-memory rings of the marching block: three velocity planes (k-1, k, k+1) of
-// the three components and three planes of the six stress normals, each with a
-// one-cell halo in x and y.
+// Shared-memory rings of the marching block: velocity planes of the three components
+// and planes of the six stress normals, each with a one-cell halo in x and y.  Plane k
+// reads slots k-1, k, k+1 and writes k+2 (mod 4): with four slots the slot it writes
+// was last read by plane k-2, which every thread has finished when it passes plane
+// k's first barrier, so one barrier per plane suffices.
+constexpr int kRing = 4;
 template <typename R>
 struct RhsSmem {
-  R v[3][3][HY][HX];
-  R z[3][6][HY][HX];
+  R v[kRing][3][HY][HX];
+  R z[kRing][6][HY][HX];
 };
 
 // One plane of stress normals (with halo) into ring slot `slot`.  Each thread first
@@ -152,7 +155,7 @@ __global__ void __launch_bounds__(NT, 2) k_rhs(const R* __restrict__ v, R* __res
   const int kend = min(k0 + g.kz, g.nz);
   for (int k = k0; k < kend; ++k) {
     const int kk = k - k0;
-    const int sp = kk % 3, sc = (kk + 1) % 3, sn = (kk + 2) % 3;
+    const int sp = kk % kRing, sc = (kk + 1) % kRing, sn = (kk + 2) % kRing;
     store_plane<R>(sm, sn, pre, tid);                       // plane k+1
     long long o = 0;
     R ao[3] = {R(0), R(0), R(0)};
@@ -228,7 +231,6 @@ __global__ void __launch_bounds__(NT, 2) k_rhs(const R* __restrict__ v, R* __res
       rhs[nc + o] = rho_dt * y_c + half_eta * lapy + fy - (R(1.5) * ay - R(0.5) * ao[1]);
       rhs[2 * nc + o] = rho_dt * z_c + half_eta * lapz + fz - (R(1.5) * az - R(0.5) * ao[2]);
     }
-    __syncthreads();
   }
 }
 

@@ -110,3 +110,39 @@ def test_explicit_rhs(icm, precision, grid, kT, hist, adv):
     if adv:
         assert rel(a, aw) < TOL[precision] / 2
     sim.close()
+
+
+def test_host_io_buffers_are_the_callers(icm):
+    """icm_set_blob_forces has copied the caller's (page-locked) buffer when it returns,
+    and icm_read_state's total momentum (the device sum of m_e u plus the FP64 fluid
+    bookkeeping) equals the same sum formed on the host from what it returned."""
+    import torch
+    import icm_workloads as wl
+    grid, nb = (32, 32, 16), 40
+    q = wl.random_sequential_addition(nb, grid, 1.0, 2.0, 5)
+    rng = np.random.default_rng(5)
+    u = 0.02 * rng.standard_normal((nb, 3))
+    me = rng.uniform(-0.5, 2.0, size=nb)
+    f = 1e-3 * rng.standard_normal((nb, 3))
+    out = []
+    for overwrite in (False, True):
+        sim = icm.Simulation(grid, 1.0, 1.0, 1.0, 1e-3, 0.05, 4, 11, 32)
+        sim.add_blobs(q, u, me)
+        pinned = torch.empty((nb, 3), dtype=torch.float64, pin_memory=True).numpy()
+        for step in range(3):
+            pinned[:] = f * (step + 1)
+            sim.set_forces(pinned)
+            if overwrite:   # the library's copy is already taken: this must not reach the step
+                pinned[:] = np.nan
+            sim.step(1)
+        r = sim.read(fluid=True)
+        fv = r["fluid"].reshape(3, -1)
+        fluid_p = fv.sum(axis=1)   # rho dV_f = 1
+        blob_p = (me[:, None] * r["vel"]).sum(axis=0)
+        # the FP64 bookkeeping and the FP32 field's own sum differ by the field's rounding
+        scale = np.abs(fv).sum() + np.abs(me[:, None] * r["vel"]).sum()
+        assert np.abs(r["momentum"] - (fluid_p + blob_p)).max() < 1e-6 * scale
+        out.append(r)
+        sim.close()
+    for k in ("pos", "vel", "momentum"):
+        np.testing.assert_array_equal(out[0][k], out[1][k])
