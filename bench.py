@@ -47,6 +47,18 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
+def max_over_ranks(x, dist):
+    """The largest x over the ranks of the process group (x itself without one): the
+    timed region of a multi-rank run is its slowest rank's."""
+    if dist is None:
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -257,10 +269,7 @@ def run_ours(args, rank, world, dist):
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     sim.sync()   # raises on a CFL / non-finite error raised during the timed steps
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
     ms_step = ms / args.steps
     value = ncell * args.steps * world / (ms / 1e3)
 
@@ -276,10 +285,7 @@ def run_ours(args, rank, world, dist):
         sim.step(1)
         sim.read()
     e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist)
     e2e = {"value": ncell * args.steps * world / e2e_s, "unit": "cell-updates/s",
            "h2d_bytes_per_step": nb * 3 * 8, "d2h_bytes_per_step": nb * 6 * 8 + 3 * 8 + 8,
            "calls_per_step": "icm_set_blob_forces + icm_step(1) + icm_read_state(pos, vel, momentum)"}
@@ -434,10 +440,7 @@ def run_batch(args, rank, world, dist):
     for s in sims:
         s.sync()
     seq = (time.perf_counter() - t1) / max(3, args.steps // 10)
-    if dist is not None:
-        t = torch.tensor([sec], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        sec = float(t.item())
+    sec = max_over_ranks(sec, dist)
     ms_step = sec / args.steps * 1e3
     peak, peak_kind = measured_peaks()
     achieved = step_bytes / (ms_step / 1e3) / 1e9
