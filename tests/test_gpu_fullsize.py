@@ -103,3 +103,38 @@ def test_bulk_rhs_matches_oracle(icm):
     assert rel(r, rw) < TOL[32] / 2
     assert rel(a, aw) < TOL[32] / 2
     s.close()
+
+
+@pytest.fixture(scope="module")
+def widest():
+    # the largest register sides along x and y (512, 384) with a 256 z side: 50M cells
+    cfg = dict(grid=(512, 384, 256), h=1.0, rho=1.0, eta=1.0, kT=1e-3, dt=0.01, kernel=4, seed=41, precision=32,
+               steps=1, nblobs=20000, me_range=(-0.5, 2.0), force=(1e-4, 0.0, -5e-5), place_seed=42,
+               min_spacing=2.0)
+    w = wl._materialise(cfg)
+    w["v0"] = wl.random_fluid(w["grid"], 0.05, 43)
+    return w
+
+
+def test_widest_sides_step(icm, widest):
+    """One tuned FP32 step on a 512 x 384 x 256 grid against the FP64 step, with the
+    conservation laws of the step."""
+    w = widest
+    s32 = _sim(icm, w, 32)
+    icm.icm_autotune(s32.handle, 1)
+    p0 = s32.read()["momentum"]
+    s64 = _sim(icm, w, 64)
+    s32.step(1)
+    s64.step(1)
+    a, b = s32.read(fluid=True), s64.read(fluid=True)
+    s32.close()
+    s64.close()
+    assert rel(a["fluid"], b["fluid"]) < TOL[32]
+    assert rel(a["vel"], b["vel"]) < TOL[32]
+    dP = a["momentum"] - p0
+    want = w["dt"] * np.asarray(w["force"]).sum(axis=0)
+    np.testing.assert_allclose(dP, want, rtol=1e-9, atol=1e-12 * np.abs(p0).max())
+    nx, ny, nz = w["grid"]
+    v = a["fluid"].reshape(3, nz, ny, nx)
+    div = oracle.divergence(v, w["h"])
+    assert np.abs(div).max() < 1e-4 * np.abs(v).max() / w["h"]
