@@ -464,6 +464,13 @@ template <typename R, int N, int MODE> constexpr int xi2_stage() { return xi2_le
 constexpr int kZLines = 8;
 template <typename R, int N, int R1, int R2>
 constexpr int zsym2_threads() { return 3 * R2 * kZLines > 1024 ? 1024 : 3 * R2 * kZLines; }
+// Threads of the plain z pass: one first-stage item each, except where the second stage
+// with the symbol in registers (R1 items per line) would leave most of them idle: then
+// R1 per line, and the first stage loops over its items.
+template <typename R, int N, int R1, int R2>
+constexpr int zplain_threads() {
+  return (sizeof(R) == 4 && R2 <= 12 && 2 * R1 < 3 * R2) ? R1 * kZLines : zsym2_threads<R, N, R1, R2>();
+}
 
 // The work of one z tile (3 components x N z x NL kx lines, kx0..kx0+NL-1, storage y
 // position py): forward z FFT, symbol, inverse z FFT.  The first stage reads the tile
@@ -477,30 +484,37 @@ __device__ __forceinline__ int zrow(int blk, int n) {
   return R2 % 2 == 0 ? R2 * blk + (n ^ (blk & 1)) : R2 * blk + n;
 }
 
-template <typename R, int N, int R1, int R2, bool FROM_SMEM>
+template <typename R, int N, int R1, int R2, bool FROM_SMEM, int NT>
 __device__ __forceinline__ void zsym_tile(cplx_t<R>* __restrict__ buf, const cplx_t<R>* __restrict__ tw,
                                           cplx_t<R>* __restrict__ base, size_t cs, size_t zs, int kx0, int py, int kx,
                                           const SymParams<R>& sp, const cplx_t<R>* __restrict__ dzt,
                                           const R* __restrict__ ddzt, int tid) {
   using C = cplx_t<R>;
   constexpr int NL = kZLines;
-  constexpr int NT = zsym2_threads<R, N, R1, R2>();
   constexpr bool HOLD3 = sizeof(R) == 4 && R2 <= 12;   // 3 x R2 complex in registers
   const C zero = mk(R(0), R(0));
-  static_assert(NT == 3 * R2 * NL, "one first-stage item per thread");
-  {
+  if constexpr (FROM_SMEM) {
+    static_assert(NT == 3 * R2 * NL, "one first-stage item per thread");
     const int line = tid % NL, rest = tid / NL, n1 = rest % R2, c = rest / R2;
-    const bool ok = kx0 + line < kx;
     C a[R1];
 #pragma unroll
-    for (int r = 0; r < R1; ++r)
-      a[r] = FROM_SMEM ? buf[(c * N + n1 + R2 * r) * NL + line]
-                       : (ok ? base[c * cs + (size_t)(n1 + R2 * r) * zs + line] : zero);
+    for (int r = 0; r < R1; ++r) a[r] = buf[(c * N + n1 + R2 * r) * NL + line];
     stage_a_fwd<R, R1, R2>(a, tw + n1);
     // the tile landed in natural row order: every thread reads before the swapped writes
-    if (FROM_SMEM && R2 % 2 == 0) __syncthreads();
+    if (R2 % 2 == 0) __syncthreads();
 #pragma unroll
     for (int k2 = 0; k2 < R1; ++k2) buf[(c * N + zrow<R2>(k2, n1)) * NL + line] = a[k2];
+  } else {
+    for (int it = tid; it < 3 * R2 * NL; it += NT) {
+      const int line = it % NL, rest = it / NL, n1 = rest % R2, c = rest / R2;
+      const bool ok = kx0 + line < kx;
+      C a[R1];
+#pragma unroll
+      for (int r = 0; r < R1; ++r) a[r] = ok ? base[c * cs + (size_t)(n1 + R2 * r) * zs + line] : zero;
+      stage_a_fwd<R, R1, R2>(a, tw + n1);
+#pragma unroll
+      for (int k2 = 0; k2 < R1; ++k2) buf[(c * N + zrow<R2>(k2, n1)) * NL + line] = a[k2];
+    }
   }
   __syncthreads();
   const C dyv = sp.dy[py];
@@ -581,7 +595,7 @@ __device__ __forceinline__ void zsym_tile(cplx_t<R>* __restrict__ buf, const cpl
 }
 
 template <typename R, int N, int R1, int R2>
-__global__ void __launch_bounds__(zsym2_threads<R, N, R1, R2>(), sizeof(R) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(zplain_threads<R, N, R1, R2>(), sizeof(R) == 4 ? 2 : 1)
     k_zsym2(cplx_t<R>* __restrict__ spec, const cplx_t<R>* __restrict__ gtw, int ny, int kx, int kxp, SymParams<R> sp,
             const RepFft* __restrict__ reps) {
   using C = cplx_t<R>;
@@ -595,7 +609,7 @@ __global__ void __launch_bounds__(zsym2_threads<R, N, R1, R2>(), sizeof(R) == 4 
     sp.k0mul = rp.k0mul;
   }
   constexpr int NL = kZLines;
-  constexpr int NT = zsym2_threads<R, N, R1, R2>();
+  constexpr int NT = zplain_threads<R, N, R1, R2>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);   // [3][N][NL]
   C* tw = buf + 3 * N * NL;                  // [N] first-stage twiddles, [k2][n1]
@@ -604,7 +618,7 @@ __global__ void __launch_bounds__(zsym2_threads<R, N, R1, R2>(), sizeof(R) == 4 
   const int kx0 = blockIdx.x * NL, py = blockIdx.y;
   const size_t zs = (size_t)ny * kxp, cs = (size_t)N * zs;
   __syncthreads();
-  zsym_tile<R, N, R1, R2, false>(buf, tw, spec + (size_t)py * kxp + kx0, cs, zs, kx0, py, kx, sp, sp.dz, sp.ddz, tid);
+  zsym_tile<R, N, R1, R2, false, NT>(buf, tw, spec + (size_t)py * kxp + kx0, cs, zs, kx0, py, kx, sp, sp.dz, sp.ddz, tid);
 }
 
 // ---------------------------------------------------------------------------
@@ -708,7 +722,7 @@ __global__ void __launch_bounds__(zsym2_threads<R, N, R1, R2>(), sizeof(R) == 4 
     __syncthreads();
     if (!s_ok) break;
     const int kx0 = (t % ntx) * NL, py = t / ntx;
-    zsym_tile<R, N, R1, R2, true>(bufs + st * TILE, tw, spec + (size_t)py * kxp + kx0, cs, zs, kx0, py, kx, sp, zdz,
+    zsym_tile<R, N, R1, R2, true, NT>(bufs + st * TILE, tw, spec + (size_t)py * kxp + kx0, cs, zs, kx0, py, kx, sp, zdz,
                                   zddz, tid);
     __syncthreads();
   }
@@ -1354,7 +1368,7 @@ void fft_z_symbol(const FftCtx<R>& f, double a, double b, const double* k0sum, d
   }
   switch (f.nz) {
 #define ICM_CASE(N, R1, R2) \
-  case N: k_zsym2<R, N, R1, R2><<<dim3(kxz, f.ny), zsym2_threads<R, N, R1, R2>(), smem_z2<R, N>(), st>>>(f.spec, tw, f.ny, f.kx, f.kxp, sp, nullptr); return;
+  case N: k_zsym2<R, N, R1, R2><<<dim3(kxz, f.ny), zplain_threads<R, N, R1, R2>(), smem_z2<R, N>(), st>>>(f.spec, tw, f.ny, f.kx, f.kxp, sp, nullptr); return;
     ICM_FFT_SIDES(ICM_CASE)
 #undef ICM_CASE
     default: break;
@@ -1535,7 +1549,7 @@ void fft_yz_group(const FftCtx<R>& f, const RepFft* reps, int G, int which, cuda
     sp.k0mul = 0.0;
     switch (f.nz) {
 #define ICM_CASE(N, R1, R2) \
-  case N: k_zsym2<R, N, R1, R2><<<dim3(kxz, f.ny, G), zsym2_threads<R, N, R1, R2>(), smem_z2<R, N>(), st>>>(nullptr, twz, f.ny, f.kx, f.kxp, sp, reps); return;
+  case N: k_zsym2<R, N, R1, R2><<<dim3(kxz, f.ny, G), zplain_threads<R, N, R1, R2>(), smem_z2<R, N>(), st>>>(nullptr, twz, f.ny, f.kx, f.kxp, sp, reps); return;
       ICM_FFT_SIDES(ICM_CASE)
 #undef ICM_CASE
       default: break;

@@ -120,10 +120,11 @@ def _grouped_jobs(precision):
     # (side, h, kernel, blobs, excess mass): three 32^3 members of one group (one
     # neutrally buoyant, so it skips the second and third solves), a 32^3 member with
     # another cell width (a grid of its own: stepped ungrouped), two 48^3 members
-    # (a second group) and a 24^3 member (no register FFT passes: ungrouped)
+    # (a second group), a 24^3 member (no register FFT passes: ungrouped) and two 64^3
+    # members (a third group, one of them neutrally buoyant)
     spec = [(32, 1.0, 4, 7, (-0.5, 2.0)), (32, 1.0, 3, 12, None), (32, 1.0, 4, 5, (0.0, 1.0)),
             (32, 0.5, 4, 6, (-0.5, 2.0)), (48, 1.0, 3, 4, (-0.5, 2.0)), (48, 1.0, 4, 9, (-0.5, 2.0)),
-            (24, 1.0, 4, 3, (-0.5, 2.0))]
+            (24, 1.0, 4, 3, (-0.5, 2.0)), (64, 1.0, 4, 8, (-0.5, 2.0)), (64, 1.0, 3, 5, None)]
     out = []
     for r, (side, h, kernel, nb, me_range) in enumerate(spec):
         cfg = dict(grid=(side, side, side), h=h, rho=1.0, eta=1.0, kT=2e-3 * h ** 3, dt=0.05 * h * h, kernel=kernel,

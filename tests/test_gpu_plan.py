@@ -38,9 +38,10 @@ def _case(grid, nb, seed):
 
 @pytest.mark.parametrize("precision", [64, 32])
 @pytest.mark.parametrize("plan", PLANS, ids=[str(i) for i in range(len(PLANS))])
-def test_every_plan_matches_the_oracle(precision, plan):
+@pytest.mark.parametrize("grid", [(32, 32, 48), (24, 16, 64)])
+def test_every_plan_matches_the_oracle(precision, plan, grid):
     import paper_1212_6427_gb300 as icm
-    prm, st = _case((32, 32, 48), 10, 91)
+    prm, st = _case(grid, 10, 91)
     sim = make_sim(prm, st, precision)
     icm.icm_set_plan(sim.handle, **plan)
     assert icm.icm_get_plan(sim.handle) == plan
