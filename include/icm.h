@@ -139,7 +139,8 @@ typedef struct icm_plan {
                           bins (sides 32, 48, 64, 96, 128, 192, 256, 384, 512); 0: separate kernels */
   int32_t tma_z;       /* 1: persistent z pass fed by TMA (z sides <= 256 with register kernels);
                           0: one block per z tile                                                  */
-  int32_t rhs_kz;      /* z planes marched by each block of the right-hand-side kernel, 4..64       */
+  int32_t rhs_kz;      /* z planes marched by each block of the right-hand-side kernel, 4..64
+                          (default 8 for Nz <= 48, 32 for Nz >= 256, else 16)                       */
   int32_t fork;        /* 1: the blob-side prologue runs on a second stream beside the RHS          */
   int32_t fused_xy;    /* 1: forward x and y FFT passes fused on thread-block clusters (FP32,
                           Nx = Ny in 32, 64, 128, 256); 0 (default): two passes                    */

@@ -619,6 +619,13 @@ std::string plan_key(const icm_sim* s) {
   return buf;
 }
 
+// The plan of a simulation nobody tuned: everything on; the RHS blocks march 8 z planes
+// on short z sides, 32 on sides of 256 and more (what the autotuners pick there), else 16.
+icm_plan default_plan(const icm_sim* s) {
+  const int kz = s->nz <= 48 ? 8 : (s->nz >= 256 ? 32 : 16);
+  return icm_plan{1, 1, kz, 1, 0};
+}
+
 // Before a capture: simulations without a plan of their own take the tuned plan of
 // their key, if there is one.
 void resolve_plan(icm_sim* s) {
@@ -629,7 +636,7 @@ void resolve_plan(icm_sim* s) {
     s->plan = it->second;
     s->plan_src = 1;
   } else if (s->plan_src == 1) {
-    s->plan = icm_plan{1, 1, 16, 1, 0};
+    s->plan = default_plan(s);
     s->plan_src = 0;
   }
 }
@@ -884,6 +891,7 @@ icm_status icm_create(const int32_t grid[3], double h, double rho, double eta, d
   icm_sim* s = new icm_sim();
   s->nx = grid[0]; s->ny = grid[1]; s->nz = grid[2];
   s->ncell = (long long)s->nx * s->ny * s->nz;
+  s->plan = default_plan(s);
   s->h = h; s->rho = rho; s->eta = eta; s->kT = kT; s->dt = dt;
   s->kernel = kernel; s->seed = seed; s->prec = precision; s->flags = flags;
   s->advection = !(flags & ICM_FLAG_NO_ADVECTION);

@@ -55,11 +55,16 @@ def read_oracle_state(sim, prm, me, force):
 
 
 def compare_states(got, want, prm, q_prev):
-    """Errors of v, u and the blob displacement q^{n+1} - q^n."""
+    """Errors of v, u and the blob displacement q^{n+1} - q^n.  The displacement error is
+    taken beyond the floor that FP64 positions in [0, L) set (two ulps of L per
+    component): both sides round q^{n+1} = q^n + dt/2 J(...) to such positions, so a
+    displacement can never be compared more finely than that."""
     box = prm.box
     err = dict(v=rel(got.v, want.v))
     if want.q.shape[0]:
         err["u"] = rel(got.u, want.u)
-        err["dq"] = rel(min_image(got.q - q_prev, box), min_image(want.q - q_prev, box))
+        dq_got, dq_want = min_image(got.q - q_prev, box), min_image(want.q - q_prev, box)
+        floor = 2.0 * np.finfo(np.float64).eps * float(np.max(box)) * np.sqrt(want.q.size)
+        err["dq"] = float(max(0.0, np.linalg.norm(dq_got - dq_want) - floor) / np.linalg.norm(dq_want))
         err["q"] = float(np.linalg.norm(min_image(got.q - want.q, box)) / np.linalg.norm(want.q))
     return err
