@@ -200,15 +200,16 @@ def test_checkpoint_resume_matches_uninterrupted_run():
     c.close()
 
 
-def test_bulk_config_sampled_parity():
-    """The 128^3 bulk configuration (2000 blobs, 3-point kernel, dt = 0.02) for 1000 FP64
+@pytest.mark.parametrize("precision", [64, 32])
+def test_bulk_config_sampled_parity(precision):
+    """The 128^3 bulk configuration (2000 blobs, 3-point kernel, dt = 0.02) for 1000
     steps; at each of the first 10 steps and then every 100th, the GPU's state is
     loaded into the oracle, advanced one step, and compared with the GPU's next state."""
     w = wl.workload("bulk")
     prm = oracle.Params(w["grid"], h=w["h"], rho=w["rho"], eta=w["eta"], kT=w["kT"], dt=w["dt"],
                         kernel=w["kernel"], seed=w["seed"])
     st0 = oracle.State(np.zeros((3,) + prm.shape), w["q"], w["u"], w["me"], w["force"])
-    sim = make_sim(prm, st0, 64)
+    sim = make_sim(prm, st0, precision)
     nsteps = w["steps"]
     samples = sorted(set(range(10)) | set(range(100, nsteps, 100)))
     worst = {}
@@ -231,4 +232,4 @@ def test_bulk_config_sampled_parity():
     assert sim.read()["step"] == nsteps
     sim.close()
     for k, e in worst.items():
-        assert e < TOL[64], (k, e, worst)
+        assert e < TOL[precision], (k, e, worst)
