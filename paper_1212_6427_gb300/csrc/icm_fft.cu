@@ -733,61 +733,74 @@ __global__ void __launch_bounds__(zsym2_threads<R, N, R1, R2>(), sizeof(R) == 4 
   }
 }
 
+// z planes per block of the y pass: short FP32 sides take several, so that the first
+// stage (R2 items per line and plane) finds work for most of the block's threads.
+template <typename R, int N, int R2>
+constexpr int y_planes() {
+  return sizeof(R) != 4 || N > 64 ? 1 : (R2 * seg_lines<R>() * 4 <= kThreads ? 4 : 2);
+}
+
 template <typename R, int N, int R1, int R2, bool INV>
 __global__ void __launch_bounds__(kThreads) k_ypass2(cplx_t<R>* __restrict__ spec, const cplx_t<R>* __restrict__ gtw,
                                                      int nz, int kx, int kxp, const RepFft* __restrict__ reps) {
   using C = cplx_t<R>;
   constexpr int NL = seg_lines<R>();
+  constexpr int ZB = y_planes<R, N, R2>();
   if (reps != nullptr) spec = reinterpret_cast<C*>(reps[blockIdx.z / 3].spec);   // group solve: 3 components per replica
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);   // [N][NL]
-  C* tw = buf + N * NL;
+  C* buf = reinterpret_cast<C*>(smem_raw);   // [ZB][N][NL]
+  C* tw = buf + ZB * N * NL;
   const int tid = threadIdx.x;
   load_stage_twiddles<R, R1, R2>(tw, gtw, tid, kThreads);
-  const int kx0 = blockIdx.x * NL, z = blockIdx.y, comp = blockIdx.z % 3;
-  C* base = spec + ((size_t)(comp * nz + z) * N) * kxp + kx0;
+  const int kx0 = blockIdx.x * NL, z0 = blockIdx.y * ZB, comp = blockIdx.z % 3;
+  // plane z0 + zb of the component, columns kx0..
+  C* base0 = spec + ((size_t)(comp * nz + z0) * N) * kxp + kx0;
   const C zero = mk(R(0), R(0));
   __syncthreads();
   if (!INV) {
-    for (int it = tid; it < R2 * NL; it += kThreads) {
-      const int line = it % NL, n1 = it / NL;
-      const bool ok = kx0 + line < kx;
+    for (int it = tid; it < ZB * R2 * NL; it += kThreads) {
+      const int line = it % NL, rest = it / NL, n1 = rest % R2, zb = rest / R2;
+      const bool ok = kx0 + line < kx && z0 + zb < nz;
+      const C* base = base0 + (size_t)zb * N * kxp;
       C a[R1];
 #pragma unroll
       for (int r = 0; r < R1; ++r) a[r] = ok ? base[(size_t)(n1 + R2 * r) * kxp + line] : zero;
       stage_a_fwd<R, R1, R2>(a, tw + n1);
 #pragma unroll
-      for (int k2 = 0; k2 < R1; ++k2) buf[(n1 + R2 * k2) * NL + line] = a[k2];
+      for (int k2 = 0; k2 < R1; ++k2) buf[(zb * N + n1 + R2 * k2) * NL + line] = a[k2];
     }
     __syncthreads();
-    for (int it = tid; it < R1 * NL; it += kThreads) {
-      const int line = it % NL, blk = it / NL;
-      if (kx0 + line >= kx) continue;
+    for (int it = tid; it < ZB * R1 * NL; it += kThreads) {
+      const int line = it % NL, rest = it / NL, blk = rest % R1, zb = rest / R1;
+      if (kx0 + line >= kx || z0 + zb >= nz) continue;
+      C* base = base0 + (size_t)zb * N * kxp;
       C b[R2];
 #pragma unroll
-      for (int n = 0; n < R2; ++n) b[n] = buf[(R2 * blk + n) * NL + line];
+      for (int n = 0; n < R2; ++n) b[n] = buf[(zb * N + R2 * blk + n) * NL + line];
       SDft<R, R2>::run(b);
 #pragma unroll
       for (int k1 = 0; k1 < R2; ++k1) base[(size_t)(R2 * blk + k1) * kxp + line] = b[k1];
     }
   } else {
-    for (int it = tid; it < R1 * NL; it += kThreads) {
-      const int line = it % NL, blk = it / NL;
-      const bool ok = kx0 + line < kx;
+    for (int it = tid; it < ZB * R1 * NL; it += kThreads) {
+      const int line = it % NL, rest = it / NL, blk = rest % R1, zb = rest / R1;
+      const bool ok = kx0 + line < kx && z0 + zb < nz;
+      const C* base = base0 + (size_t)zb * N * kxp;
       C b[R2];
 #pragma unroll
       for (int k1 = 0; k1 < R2; ++k1) b[k1] = ok ? base[(size_t)(R2 * blk + k1) * kxp + line] : zero;
       sdft_inv<R, R2>(b);
 #pragma unroll
-      for (int n = 0; n < R2; ++n) buf[(R2 * blk + n) * NL + line] = b[n];
+      for (int n = 0; n < R2; ++n) buf[(zb * N + R2 * blk + n) * NL + line] = b[n];
     }
     __syncthreads();
-    for (int it = tid; it < R2 * NL; it += kThreads) {
-      const int line = it % NL, n1 = it / NL;
-      if (kx0 + line >= kx) continue;
+    for (int it = tid; it < ZB * R2 * NL; it += kThreads) {
+      const int line = it % NL, rest = it / NL, n1 = rest % R2, zb = rest / R2;
+      if (kx0 + line >= kx || z0 + zb >= nz) continue;
+      C* base = base0 + (size_t)zb * N * kxp;
       C a[R1];
 #pragma unroll
-      for (int k2 = 0; k2 < R1; ++k2) a[k2] = buf[(n1 + R2 * k2) * NL + line];
+      for (int k2 = 0; k2 < R1; ++k2) a[k2] = buf[(zb * N + n1 + R2 * k2) * NL + line];
       stage_a_inv<R, R1, R2>(a, tw + n1);
 #pragma unroll
       for (int n2 = 0; n2 < R1; ++n2) base[(size_t)(n1 + R2 * n2) * kxp + line] = a[n2];
@@ -1178,7 +1191,9 @@ template <typename R, int N> size_t smem_ztma() {
   return 2 * 3 * (size_t)N * kZLines * sizeof(cplx_t<R>) + 2 * N * sizeof(cplx_t<R>) + (N * sizeof(R) + 7) / 8 * 8 + 16 + 128;
 }
 template <typename R, int N> size_t smem_z2() { return 3 * (size_t)N * kZLines * sizeof(cplx_t<R>) + N * sizeof(cplx_t<R>); }
-template <typename R, int N> size_t smem_y2() { return (size_t)N * seg_lines<R>() * sizeof(cplx_t<R>) + N * sizeof(cplx_t<R>); }
+template <typename R, int N, int R2> size_t smem_y2() {
+  return (size_t)y_planes<R, N, R2>() * N * seg_lines<R>() * sizeof(cplx_t<R>) + N * sizeof(cplx_t<R>);
+}
 template <typename R, int N> size_t smem_x2() { return (size_t)kXLines * xrow(N) * sizeof(cplx_t<R>) + N * sizeof(cplx_t<R>); }
 
 // Every side with register kernels, as (N, R1, R2); must agree with fft_split.
@@ -1311,9 +1326,9 @@ void fft_y(const FftCtx<R>& f, bool inverse, cudaStream_t st) {
 #define ICM_CASE(N, R1, R2)                                                                                   \
   case N:                                                                                                     \
     if (inverse)                                                                                              \
-      k_ypass2<R, N, R1, R2, true><<<grid, kThreads, smem_y2<R, N>(), st>>>(f.spec, tw, f.nz, f.kx, f.kxp, nullptr);  \
+      k_ypass2<R, N, R1, R2, true><<<dim3(kxt, (f.nz + y_planes<R, N, R2>() - 1) / y_planes<R, N, R2>(), 3), kThreads, smem_y2<R, N, R2>(), st>>>(f.spec, tw, f.nz, f.kx, f.kxp, nullptr);  \
     else                                                                                                      \
-      k_ypass2<R, N, R1, R2, false><<<grid, kThreads, smem_y2<R, N>(), st>>>(f.spec, tw, f.nz, f.kx, f.kxp, nullptr); \
+      k_ypass2<R, N, R1, R2, false><<<dim3(kxt, (f.nz + y_planes<R, N, R2>() - 1) / y_planes<R, N, R2>(), 3), kThreads, smem_y2<R, N, R2>(), st>>>(f.spec, tw, f.nz, f.kx, f.kxp, nullptr); \
     return;
     ICM_FFT_SIDES(ICM_CASE)
 #undef ICM_CASE
@@ -1559,9 +1574,9 @@ void fft_yz_group(const FftCtx<R>& f, const RepFft* reps, int G, int which, cuda
 #define ICM_CASE(N, R1, R2)                                                                                             \
   case N:                                                                                                               \
     if (which == 2)                                                                                                     \
-      k_ypass2<R, N, R1, R2, true><<<dim3(kxt, f.nz, 3 * G), kThreads, smem_y2<R, N>(), st>>>(nullptr, twy, f.nz, f.kx, f.kxp, reps); \
+      k_ypass2<R, N, R1, R2, true><<<dim3(kxt, (f.nz + y_planes<R, N, R2>() - 1) / y_planes<R, N, R2>(), 3 * G), kThreads, smem_y2<R, N, R2>(), st>>>(nullptr, twy, f.nz, f.kx, f.kxp, reps); \
     else                                                                                                                \
-      k_ypass2<R, N, R1, R2, false><<<dim3(kxt, f.nz, 3 * G), kThreads, smem_y2<R, N>(), st>>>(nullptr, twy, f.nz, f.kx, f.kxp, reps); \
+      k_ypass2<R, N, R1, R2, false><<<dim3(kxt, (f.nz + y_planes<R, N, R2>() - 1) / y_planes<R, N, R2>(), 3 * G), kThreads, smem_y2<R, N, R2>(), st>>>(nullptr, twy, f.nz, f.kx, f.kxp, reps); \
     return;
       ICM_FFT_SIDES(ICM_CASE)
 #undef ICM_CASE
