@@ -448,6 +448,12 @@ template <typename R, int N> constexpr size_t stage_offset() {
 constexpr int kStageF = 128;
 template <typename R, int N, int S> size_t smem_x2b() { return stage_offset<R, N>() + S * sizeof(StagedTask<R>); }
 template <typename R, int N> constexpr int xf2_min_blocks() { return sizeof(R) == 4 && N <= 256 ? 4 : 1; }
+// Complex lines per block of the x passes without blob work: FP32 sides up to 128 take
+// more than 16, so that the first stage (R2 items per line) fills the block's threads.
+// With blob work a block is one 32-row bin (16 lines).
+template <typename R, int N, int R2> constexpr int x_plain_lines() {
+  return sizeof(R) != 4 || N > 128 ? kXLines : (kThreads / R2 >= 64 ? 64 : 32);
+}
 // The inverse x pass of FP32 sides up to 256 runs lean at four blocks per SM: its
 // spectrum loads go in two batches, the old values of the adding modes are loaded
 // just before the output, and 128 records are staged.  Otherwise (and for the
@@ -814,16 +820,17 @@ __global__ void __launch_bounds__(kThreads) k_ypass2(cplx_t<R>* __restrict__ spe
 // block `bin` spread rb.vec into the rows (in shared memory, where the first stage
 // reads them; NST records staged by cp.async in `stage_mem`), added to src if src is
 // set.  The first-stage twiddles tw are loaded by the caller; ends with a block barrier.
-template <typename R, int N, int R1, int R2, bool BLOBS, int NST>
+template <typename R, int N, int R1, int R2, bool BLOBS, int NST, int L = kXLines>
 __device__ __forceinline__ void x_forward_rows(cplx_t<R>* __restrict__ buf, const cplx_t<R>* __restrict__ tw,
                                                unsigned char* stage_mem, const R* __restrict__ src, long long row0,
                                                int nrows, long long ncell, int comp, int bin, const RowBlobs& rb,
                                                int tid) {
   using C = cplx_t<R>;
   static_assert(kRowBlock == 2 * kXLines, "row blocks are the x-pass blocks");
+  static_assert(!BLOBS || L == kXLines, "blob work takes one row block per block");
   const bool dense = !BLOBS || src != nullptr;
   // one first-stage item (line l, offset n1) per thread; its loads are issued first
-  constexpr int ITEMS = kXLines * R2;
+  constexpr int ITEMS = L * R2;
   static_assert(ITEMS <= kThreads, "one first-stage item per thread");
   const int n1 = tid % R2, l = tid / R2;
   const long long r0 = row0 + 2 * l;
@@ -843,7 +850,7 @@ __device__ __forceinline__ void x_forward_rows(cplx_t<R>* __restrict__ buf, cons
     const int nst = min(e - s0, NST);
     if (tid < nst) stage_task<R>(&stage[tid], rec, rb.list[s0 + tid], comp, rb.vec);
     cp_async_commit();
-    for (int i = tid; i < kXLines * xrow(N); i += kThreads) buf[i] = mk(R(0), R(0));
+    for (int i = tid; i < L * xrow(N); i += kThreads) buf[i] = mk(R(0), R(0));
     cp_async_wait_all();
     __syncthreads();
     R* rows = reinterpret_cast<R*>(buf);
@@ -872,7 +879,7 @@ __device__ __forceinline__ void x_forward_rows(cplx_t<R>* __restrict__ buf, cons
     for (int k2 = 0; k2 < R1; ++k2) buf[xaddr(l, n1 + R2 * k2, N)] = a[k2];
   }
   __syncthreads();
-  for (int it = tid; it < kXLines * R1; it += kThreads) {
+  for (int it = tid; it < L * R1; it += kThreads) {
     const int blk = it % R1, l = it / R1;
     C b[R2];
 #pragma unroll
@@ -907,14 +914,15 @@ __global__ void __launch_bounds__(kThreads, xf2_min_blocks<R, N>()) k_xfwd2(cons
     src = reinterpret_cast<const R*>(rp.src);
     spec = reinterpret_cast<C*>(rp.spec);
   }
+  constexpr int L = BLOBS ? kXLines : x_plain_lines<R, N, R2>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);   // [kXLines][xrow(N)]
-  C* tw = buf + kXLines * xrow(N);
+  C* buf = reinterpret_cast<C*>(smem_raw);   // [L][xrow(N)]
+  C* tw = buf + L * xrow(N);
   const int tid = threadIdx.x;
   load_stage_twiddles<R, R1, R2>(tw, gtw, tid, kThreads);
   const int comp = blockIdx.y % 3;
-  const long long row0 = (long long)blockIdx.x * (2 * kXLines);
-  x_forward_rows<R, N, R1, R2, BLOBS, kStageF>(buf, tw, smem_raw + stage_offset<R, N>(), src, row0, nrows, ncell,
+  const long long row0 = (long long)blockIdx.x * (2 * L);
+  x_forward_rows<R, N, R1, R2, BLOBS, kStageF, L>(buf, tw, smem_raw + stage_offset<R, N>(), src, row0, nrows, ncell,
                                                comp, blockIdx.x, rb, tid);
   C* out = spec + (size_t)comp * nrows * kxp;
   // the two half spectra of line l at wavenumber k (kx = N/2 + 1 of them)
@@ -927,8 +935,8 @@ __global__ void __launch_bounds__(kThreads, xf2_min_blocks<R, N>()) k_xfwd2(cons
   };
   // k < N/2 with a compile-time (mostly power-of-two) index split, then k = N/2
   constexpr int H = N / 2;
-  for (int it = tid; it < kXLines * H; it += kThreads) split(it / H, it % H);
-  if (tid < kXLines) split(tid, H);
+  for (int it = tid; it < L * H; it += kThreads) split(it / H, it % H);
+  if (tid < L) split(tid, H);
 }
 
 // ---------------------------------------------------------------------------
@@ -1039,18 +1047,20 @@ __global__ void __launch_bounds__(kThreads, xi2_lean<R, N, MODE>() ? 4 : 1) k_xi
   constexpr bool ADDS = MODE == OUT_ADD_AND_STORE2 || MODE == OUT_ADD;
   constexpr bool LEAN = xi2_lean<R, N, MODE>();
   constexpr int NST = xi2_stage<R, N, MODE>();
+  // (the two-output mode keeps 16 lines: more would hold all its loads in registers)
+  constexpr int L = GATHER || MODE == OUT_ADD_AND_STORE2 ? kXLines : x_plain_lines<R, N, R2>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
-  C* tw = buf + kXLines * xrow(N);
+  C* tw = buf + L * xrow(N);
   const int tid = threadIdx.x;
   load_stage_twiddles<R, R1, R2>(tw, gtw, tid, kThreads);
   const int comp = blockIdx.y % 3;
-  const long long row0 = (long long)blockIdx.x * (2 * kXLines);
+  const long long row0 = (long long)blockIdx.x * (2 * L);
   const C* in = spec + (size_t)comp * nrows * kxp;
   const C zero = mk(R(0), R(0));
   const size_t cb = (size_t)comp * ncell;
   // this thread's output positions: line l = tid / R2, x = n1 + R2 n2, rows r0 and r0 + 1
-  constexpr int OUTS = (kXLines * R2 + kThreads - 1) / kThreads;
+  constexpr int OUTS = (L * R2 + kThreads - 1) / kThreads;
   R old0[ADDS ? OUTS * R1 : 1], old1[ADDS ? OUTS * R1 : 1];
   const auto load_old = [&](int o) {
     const int it = tid + o * kThreads;
@@ -1059,15 +1069,15 @@ __global__ void __launch_bounds__(kThreads, xi2_lean<R, N, MODE>() ? 4 : 1) k_xi
 #pragma unroll
     for (int n2 = 0; n2 < R1; ++n2) {
       const int x = n1 + R2 * n2;
-      old0[o * R1 + n2] = (it < kXLines * R2 && r0 < nrows) ? dst[cb + (size_t)r0 * N + x] : R(0);
-      old1[o * R1 + n2] = (it < kXLines * R2 && r0 + 1 < nrows) ? dst[cb + (size_t)(r0 + 1) * N + x] : R(0);
+      old0[o * R1 + n2] = (it < L * R2 && r0 < nrows) ? dst[cb + (size_t)r0 * N + x] : R(0);
+      old1[o * R1 + n2] = (it < L * R2 && r0 + 1 < nrows) ? dst[cb + (size_t)(r0 + 1) * N + x] : R(0);
     }
   };
   if (ADDS && !LEAN) {
 #pragma unroll
     for (int o = 0; o < OUTS; ++o) load_old(o);
   }
-  constexpr int LOADS = (kXLines * N + kThreads - 1) / kThreads;   // compile-time: loads in flight together
+  constexpr int LOADS = (L * N + kThreads - 1) / kThreads;   // compile-time: loads in flight together
   constexpr int BATCH = LEAN ? (LOADS + 1) / 2 : LOADS;
   int g0 = 0, ge = 0;
 #pragma unroll
@@ -1079,7 +1089,7 @@ __global__ void __launch_bounds__(kThreads, xi2_lean<R, N, MODE>() ? 4 : 1) k_xi
       const int k = it % N, l = it / N;
       const long long r1 = row0 + 2 * l;
       const int kk = 2 * k <= N ? k : N - k;
-      const bool ok = j0 + j < LOADS && it < kXLines * N;
+      const bool ok = j0 + j < LOADS && it < L * N;
       av[j] = (ok && r1 < nrows) ? in[r1 * kxp + kk] : zero;
       bv[j] = (ok && r1 + 1 < nrows) ? in[(r1 + 1) * kxp + kk] : zero;
     }
@@ -1095,7 +1105,7 @@ __global__ void __launch_bounds__(kThreads, xi2_lean<R, N, MODE>() ? 4 : 1) k_xi
 #pragma unroll
     for (int j = 0; j < BATCH; ++j) {
       const int it = tid + (j0 + j) * kThreads;
-      if (j0 + j >= LOADS || it >= kXLines * N) continue;
+      if (j0 + j >= LOADS || it >= L * N) continue;
       const int k = it % N, l = it / N;
       C a = av[j], b = bv[j];
       if (2 * k > N) {
@@ -1110,7 +1120,7 @@ __global__ void __launch_bounds__(kThreads, xi2_lean<R, N, MODE>() ? 4 : 1) k_xi
     }
   }
   __syncthreads();
-  for (int it = tid; it < kXLines * R1; it += kThreads) {
+  for (int it = tid; it < L * R1; it += kThreads) {
     const int blk = it % R1, l = it / R1;
     C b[R2];
 #pragma unroll
@@ -1123,7 +1133,7 @@ __global__ void __launch_bounds__(kThreads, xi2_lean<R, N, MODE>() ? 4 : 1) k_xi
 #pragma unroll
   for (int o = 0; o < OUTS; ++o) {
     const int it = tid + o * kThreads;
-    if (it >= kXLines * R2) break;
+    if (it >= L * R2) break;
     const int n1 = it % R2, l = it / R2;
     if (ADDS && LEAN) load_old(o);   // in flight during the last stage
     C a[R1];
@@ -1194,7 +1204,12 @@ template <typename R, int N> size_t smem_z2() { return 3 * (size_t)N * kZLines *
 template <typename R, int N, int R2> size_t smem_y2() {
   return (size_t)y_planes<R, N, R2>() * N * seg_lines<R>() * sizeof(cplx_t<R>) + N * sizeof(cplx_t<R>);
 }
-template <typename R, int N> size_t smem_x2() { return (size_t)kXLines * xrow(N) * sizeof(cplx_t<R>) + N * sizeof(cplx_t<R>); }
+template <typename R, int N, int L> size_t smem_x2() { return (size_t)L * xrow(N) * sizeof(cplx_t<R>) + N * sizeof(cplx_t<R>); }
+// Blocks of a plain x pass over nrows rows (2 x_plain_lines rows per block).
+template <typename R, int N, int R2> int xgrid(int nrows) {
+  constexpr int L = x_plain_lines<R, N, R2>();
+  return (nrows + 2 * L - 1) / (2 * L);
+}
 
 // Every side with register kernels, as (N, R1, R2); must agree with fft_split.
 #define ICM_FFT_SIDES(X) \
@@ -1308,7 +1323,7 @@ void fft_x_forward(const FftCtx<R>& f, const R* src, cudaStream_t st) {
   const cplx_t<R>* tw = (const cplx_t<R>*)f.px.tw;
   switch (f.nx) {
 #define ICM_CASE(N, R1, R2) \
-  case N: k_xfwd2<R, N, R1, R2, false><<<dim3(xblocks, 3), kThreads, smem_x2<R, N>(), st>>>(src, f.spec, tw, nrows, f.ncell, f.kx, f.kxp, RowBlobs{}, nullptr); return;
+  case N: k_xfwd2<R, N, R1, R2, false><<<dim3(xgrid<R, N, R2>(nrows), 3), kThreads, smem_x2<R, N, x_plain_lines<R, N, R2>()>(), st>>>(src, f.spec, tw, nrows, f.ncell, f.kx, f.kxp, RowBlobs{}, nullptr); return;
     ICM_FFT_SIDES(ICM_CASE)
 #undef ICM_CASE
     default: break;
@@ -1400,9 +1415,9 @@ void fft_x_inverse(const FftCtx<R>& f, R* dst, R* dst2, int mode, cudaStream_t s
 #define ICM_CASE(N, R1, R2) \
   case N:                                                                                                              \
     if (mode == OUT_STORE)                                                                                             \
-      k_xinv2<R, N, R1, R2, OUT_STORE, 0><<<dim3(xblocks, 3), kThreads, smem_x2<R, N>(), st>>>(f.spec, dst, dst2, tw, nrows, f.ncell, f.kxp, RowBlobs{}, nullptr); \
+      k_xinv2<R, N, R1, R2, OUT_STORE, 0><<<dim3(xgrid<R, N, R2>(nrows), 3), kThreads, smem_x2<R, N, x_plain_lines<R, N, R2>()>(), st>>>(f.spec, dst, dst2, tw, nrows, f.ncell, f.kxp, RowBlobs{}, nullptr); \
     else                                                                                                               \
-      k_xinv2<R, N, R1, R2, OUT_ADD_AND_STORE2, 0><<<dim3(xblocks, 3), kThreads, smem_x2<R, N>(), st>>>(f.spec, dst, dst2, tw, nrows, f.ncell, f.kxp, RowBlobs{}, nullptr); \
+      k_xinv2<R, N, R1, R2, OUT_ADD_AND_STORE2, 0><<<dim3((nrows + 2 * kXLines - 1) / (2 * kXLines), 3), kThreads, smem_x2<R, N, kXLines>(), st>>>(f.spec, dst, dst2, tw, nrows, f.ncell, f.kxp, RowBlobs{}, nullptr); \
     return;
     ICM_FFT_SIDES(ICM_CASE)
 #undef ICM_CASE
@@ -1532,11 +1547,10 @@ void spectral_solve(const FftCtx<R>& f, const R* src, R* dst, R* dst2, int mode,
 template <typename R>
 void fft_x_forward_group(const FftCtx<R>& f, const RepFft* reps, int G, cudaStream_t st) {
   const int nrows = f.ny * f.nz;
-  const int xblocks = (nrows + 2 * kXLines - 1) / (2 * kXLines);
   const cplx_t<R>* tw = (const cplx_t<R>*)f.px.tw;
   switch (f.nx) {
 #define ICM_CASE(N, R1, R2) \
-  case N: k_xfwd2<R, N, R1, R2, false><<<dim3(xblocks, 3 * G), kThreads, smem_x2<R, N>(), st>>>(nullptr, nullptr, tw, nrows, f.ncell, f.kx, f.kxp, RowBlobs{}, reps); return;
+  case N: k_xfwd2<R, N, R1, R2, false><<<dim3(xgrid<R, N, R2>(nrows), 3 * G), kThreads, smem_x2<R, N, x_plain_lines<R, N, R2>()>(), st>>>(nullptr, nullptr, tw, nrows, f.ncell, f.kx, f.kxp, RowBlobs{}, reps); return;
     ICM_FFT_SIDES(ICM_CASE)
 #undef ICM_CASE
     default: break;
@@ -1589,16 +1603,14 @@ void fft_yz_group(const FftCtx<R>& f, const RepFft* reps, int G, int which, cuda
 template <typename R>
 void fft_x_inverse_group(const FftCtx<R>& f, const RepFft* reps, int G, int mode, cudaStream_t st) {
   const int nrows = f.ny * f.nz;
-  const int xblocks = (nrows + 2 * kXLines - 1) / (2 * kXLines);
   const cplx_t<R>* tw = (const cplx_t<R>*)f.px.tw;
-  const dim3 grid(xblocks, 3 * G);
   switch (f.nx) {
 #define ICM_CASE(N, R1, R2)                                                                                             \
   case N:                                                                                                               \
     if (mode == OUT_STORE)                                                                                              \
-      k_xinv2<R, N, R1, R2, OUT_STORE, 0><<<grid, kThreads, smem_x2<R, N>(), st>>>(nullptr, nullptr, nullptr, tw, nrows, f.ncell, f.kxp, RowBlobs{}, reps); \
+      k_xinv2<R, N, R1, R2, OUT_STORE, 0><<<dim3(xgrid<R, N, R2>(nrows), 3 * G), kThreads, smem_x2<R, N, x_plain_lines<R, N, R2>()>(), st>>>(nullptr, nullptr, nullptr, tw, nrows, f.ncell, f.kxp, RowBlobs{}, reps); \
     else                                                                                                                \
-      k_xinv2<R, N, R1, R2, OUT_ADD_AND_STORE2, 0><<<grid, kThreads, smem_x2<R, N>(), st>>>(nullptr, nullptr, nullptr, tw, nrows, f.ncell, f.kxp, RowBlobs{}, reps); \
+      k_xinv2<R, N, R1, R2, OUT_ADD_AND_STORE2, 0><<<dim3((nrows + 2 * kXLines - 1) / (2 * kXLines), 3 * G), kThreads, smem_x2<R, N, kXLines>(), st>>>(nullptr, nullptr, nullptr, tw, nrows, f.ncell, f.kxp, RowBlobs{}, reps); \
     return;
     ICM_FFT_SIDES(ICM_CASE)
 #undef ICM_CASE
