@@ -14,13 +14,11 @@ sizes and distributions of the five configurations the library is measured on:
 """
 import numpy as np
 
-# sum of phi^2 along one axis for each Peskin kernel: 1/2 (3-point), 3/8 (4-point)
-_SUM_SQ = {3: 0.5, 4: 0.375}
-
-
-def dragged_mass(kernel, h=1.0, rho=1.0):
-    """rho * 3/2 * h^3 / (sum phi^2)^3: the incompressible added fluid mass of a blob."""
-    return 1.5 * rho * h ** 3 / _SUM_SQ[kernel] ** 3
+# The incompressible dragged fluid mass m~_f of a blob in units of rho h^3, a plain
+# number per kernel, used only to size the initial velocity spread of the recipes:
+# 12 for the 3-point kernel (3/2 of the blob volume 8 h^3 the paper gives) and
+# 768/27 for the 4-point kernel (3/2 of its volume (8/3)^3 h^3).
+DRAGGED_MASS_PER_RHO_H3 = {3: 12.0, 4: 768.0 / 27.0}
 
 
 def random_sequential_addition(n, grid, h, min_spacing, seed, max_tries=200):
@@ -107,7 +105,7 @@ def _materialise(cfg):
         lo, hi = cfg["me_range"]
         me = rng.uniform(lo, hi, size=nb) * rho * h ** 3
     # equilibrium blob velocity variance kT / m~ with m~ = m_e + m~_f
-    mt = me + dragged_mass(cfg["kernel"], h, rho)
+    mt = me + DRAGGED_MASS_PER_RHO_H3[cfg["kernel"]] * rho * h ** 3
     if cfg["kT"] > 0.0 and cfg["me_range"] is not None:
         u = rng.standard_normal((nb, 3)) * np.sqrt(cfg["kT"] / mt)[:, None]
     else:

@@ -169,8 +169,18 @@ icm_status icm_autotune(icm_sim* sim, int32_t nsteps, icm_plan* chosen, double* 
 icm_status icm_step(icm_sim* sim, int64_t nsteps);
 
 /* Wait for the simulation's stream; report device-side errors raised since the
- * last report (ICM_ECFL: some blob had |u| dt/h > 1, Sec. III.D; ICM_ENONFINITE). */
+ * last report (ICM_ECFL: some blob had |u| dt/h > 1, Sec. III.D; ICM_ENONFINITE;
+ * ICM_ETIMEOUT: a bounded device-side wait for a tensor-memory copy gave up, after
+ * which the step's results are undefined and the simulation must be destroyed). */
 icm_status icm_sync(icm_sim* sim);
+
+/* Failure-path check, no counterpart in the paper: enqueue on the simulation's stream
+ * a one-thread kernel that waits, with the same bounded mbarrier wait the TMA z pass
+ * uses, for a transaction that is never issued.  After limit_ns nanoseconds
+ * (1 <= limit_ns <= 2e9) it raises the simulation's timeout bit, so the next icm_sync
+ * returns ICM_ETIMEOUT, as a copy that never lands would.  Nothing faults, nothing
+ * stays in flight and the context stays usable.  Errors: ICM_EINVAL, ICM_ECUDA. */
+icm_status icm_debug_wait_timeout(icm_sim* sim, int64_t limit_ns);
 
 /* Read the state at the current time level (synchronises).  Any pointer may be
  * NULL to skip that output.
@@ -212,8 +222,10 @@ icm_status icm_profile_steps(icm_sim* sim, int64_t nsteps, int32_t max_stages, i
 
 /* Total momentum P = rho h^3 sum_k v_k of a face field that is already on the device,
  * for callers that must not allocate device memory.  The paper has no counterpart:
- * this is a service of the library, the same FP64 compensated sum that gives the
- * fluid part of icm_read_state's momentum.  Callers that cannot allocate include
+ * this is a service of the library.  It uses the compensated FP64 scheme of the fluid
+ * part of icm_read_state's momentum with a different block partition (fixed chunks of
+ * 8192 cells per block), so the two agree to FP64 rounding, not bit for bit (tested
+ * to 1e-12 relative).  Callers that cannot allocate include
  * code running while a stream capture is open (cudaMalloc is refused there),
  * processes whose device memory is already reserved by a framework's pool, and
  * loops that must not take the device-wide synchronisation of cudaMalloc/cudaFree.
@@ -223,17 +235,33 @@ icm_status icm_profile_steps(icm_sim* sim, int64_t nsteps, int32_t max_stages, i
  *   ncell       : Nx*Ny*Nz, 1 <= ncell <= 134217728 (512^3); larger is ICM_EINVAL.
  *   rho, h      : density and grid spacing (the factor rho h^3).
  *   cuda_stream : stream to run on (NULL = legacy default stream); synchronised.
+ *                 It must not be capturing (ICM_EINVAL).  While any capture is open,
+ *                 pass a non-blocking stream of your own, not NULL: the legacy
+ *                 stream is refused (ICM_EINVAL) while a blocking stream captures.
+ *                 The call ends with a copy to the host and a wait on this stream;
+ *                 open other threads' captures in relaxed mode, since global-mode
+ *                 captures may forbid that wait.
  *   momentum[3] : host output.
  * Allocates nothing: its scratch is a fixed array of 3*16384+8 doubles (~384 KB)
  * that the library declares in device memory, held by every GPU that loads the
  * library until the process exits.  The first call on each device looks up that
  * array's device address (once, with that device current); make that first call
- * before any stream capture.  All calls share the array and each overwrites what
+ * before any stream capture.  That address is cached per device for the life of the
+ * process: do not use the library across a cudaDeviceReset (or a reset of the primary
+ * context), which would leave the cached address stale.  All calls share the array and each overwrites what
  * the previous one left there, so calls that overlap on the GPU (other streams or
  * threads at the same time) race and must be serialised by the caller.
  * Errors: ICM_EINVAL (NULL pointer, bad precision, ncell out of range), ICM_ECUDA. */
 icm_status icm_fluid_momentum_static(const void* fluid_v_dev, int32_t precision, int64_t ncell, double rho,
                                      double h, void* cuda_stream, double momentum[3]);
+
+/* The blob volume dV = (J S 1)^-1 = h^3 / (sum_k phi(k)^2)^3 of a Peskin kernel (Sec.
+ * III.A.1, after Eq. JS_invariance): 8 h^3 for the 3-point kernel (as the paper states)
+ * and (8/3)^3 h^3 for the 4-point kernel.  The rest mass m_f = rho dV and the
+ * incompressible dragged mass m~_f = 3 rho dV / 2 (Appendix A) follow from it.
+ *   kernel : 3 or 4;  h : grid spacing > 0;  volume : host output.
+ * Errors: ICM_EINVAL (bad kernel, h <= 0 or not finite, NULL volume). */
+icm_status icm_kernel_volume(int32_t kernel, double h, double* volume);
 
 /* Number of blobs and bytes of device memory the simulation holds. */
 int64_t icm_num_blobs(const icm_sim* sim);
@@ -375,10 +403,18 @@ icm_status icm_server_submit(icm_server* server, const icm_job_desc* job, int64_
  * output pointer may be NULL; n_finished counts jobs retired by this call. */
 icm_status icm_server_pump(icm_server* server, int32_t steps_per_pump, int32_t* n_active, int32_t* n_waiting,
                            int32_t* n_finished);
-/* state: 0 waiting, 1 active, 2 done, 3 failed.  When done: pos, vel (nblobs*3),
- * momentum[3] and latency_s (submit to completion, seconds), each may be NULL. */
+/* state: 0 waiting, 1 active, 2 done, 3 failed, 4 cancelled.  When done: pos, vel
+ * (nblobs*3), momentum[3] and latency_s (submit to completion, seconds), each may be
+ * NULL.  A job the device has no memory for at admission (ICM_ENOMEM from the
+ * allocator) stays first in line and is retried at the next pump. */
 icm_status icm_server_result(icm_server* server, int64_t job_id, int32_t* state, double* pos, double* vel,
                              double momentum[3], double* latency_s);
+/* Withdraw a job between pumps.  A waiting job leaves the queue; an active job's
+ * already enqueued steps (at most one pump's worth) are waited for on its own stream,
+ * then its simulation is destroyed and its bytes return to the budget.  Other jobs
+ * are neither waited for nor changed.  Its state becomes 4 (cancelled); a job that
+ * has already finished is left as it is.  Errors: ICM_EINVAL (unknown id), ICM_ECUDA. */
+icm_status icm_server_cancel(icm_server* server, int64_t job_id);
 int64_t icm_server_bytes_in_use(const icm_server* server);
 void icm_server_destroy(icm_server* server);
 

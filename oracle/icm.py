@@ -316,7 +316,22 @@ def _symbols(shape, h):
     return (dx[None, None, :], dy[None, :, None], dz[:, None, None])
 
 
-def spectral_solve(rhs, a, b, h):
+def dft3(f):
+    """The 3D discrete Fourier transform by its definition, an explicit O(N^2) sum:
+    F[k] = sum_j f[j] exp(-2 pi i (kx jx / Nx + ky jy / Ny + kz jz / Nz)) over every
+    pair (k, j) of grid points, as one dense matrix (small grids only)."""
+    shape = f.shape
+    idx = np.indices(shape).reshape(len(shape), -1)          # (3, N): (z, y, x) of every point
+    phase = sum(np.outer(idx[a], idx[a]) / shape[a] for a in range(len(shape)))
+    return (np.exp(-2j * np.pi * phase) @ f.reshape(-1)).reshape(shape)
+
+
+def idft3(F):
+    """Inverse of dft3 by its definition: f[j] = N^-1 sum_k F[k] exp(+2 pi i k.j/N)."""
+    return np.conj(dft3(np.conj(F))) / F.size
+
+
+def spectral_solve(rhs, a, b, h, fft=np.fft.fftn, ifft=np.fft.ifftn):
     """Solve (a I - b L) x + G pi = rhs, D x = 0 on the periodic MAC grid.
 
     In Fourier space x^ = P^ rhs^ / (a + b sum_a |d_a|^2), with
@@ -326,18 +341,25 @@ def spectral_solve(rhs, a, b, h):
     viscous correction (Eq. dv_eq_modified-1).  (0, eta) is the steady Stokes solve
     of the mobility -J L^-1 S (Sec. III.A.2); there the k = 0 mode has no solution
     on the periodic grid and is set to zero (zero mean flow; a reading).
+    The transform pair is numpy's FFT; spectral_solve_dft passes the plain DFT sums.
     """
     shape = rhs.shape[1:]
     d = _symbols(shape, h)
-    rh = [np.fft.fftn(rhs[c]) for c in range(DIM)]
+    rh = [fft(rhs[c]) for c in range(DIM)]
     dd = sum(np.abs(dc) ** 2 for dc in d)
     div = sum(d[c] * rh[c] for c in range(DIM))
     safe = np.where(dd == 0.0, 1.0, dd)
     ratio = np.where(dd == 0.0, 0.0, div / safe)
     denom = a + b * dd
     inv = np.where(denom == 0.0, 0.0, 1.0 / np.where(denom == 0.0, 1.0, denom))
-    return np.stack([np.real(np.fft.ifftn((rh[c] - np.conj(d[c]) * ratio) * inv))
+    return np.stack([np.real(ifft((rh[c] - np.conj(d[c]) * ratio) * inv))
                      for c in range(DIM)])
+
+
+def spectral_solve_dft(rhs, a, b, h):
+    """spectral_solve with the transforms done by the plain O(N^2) DFT sums (dft3,
+    idft3) instead of an FFT: the slow statement of the same solve, for small grids."""
+    return spectral_solve(rhs, a, b, h, fft=dft3, ifft=idft3)
 
 
 # ---------------------------------------------------------------------------

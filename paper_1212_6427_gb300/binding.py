@@ -74,6 +74,7 @@ SIGNATURES = {
     "icm_profile_steps": (_c_i32, [_vp, _c_i64, _c_i32, ctypes.POINTER(_c_i32), ctypes.c_char_p, _dp, _dp]),
     "icm_fluid_momentum_static": (_c_i32, [_vp, _c_i32, _c_i64, _c_d, _c_d, _vp, _dp]),
     "icm_num_blobs": (_c_i64, [_vp]),
+    "icm_kernel_volume": (_c_i32, [_c_i32, _c_d, _dp]),
     "icm_batch_create": (_c_i32, [_vp, ctypes.POINTER(_vp)]),
     "icm_batch_set": (_c_i32, [_vp, _c_i32, ctypes.POINTER(_vp)]),
     "icm_batch_step": (_c_i32, [_vp, _c_i64]),
@@ -85,6 +86,8 @@ SIGNATURES = {
     "icm_server_pump": (_c_i32, [_vp, _c_i32, ctypes.POINTER(_c_i32), ctypes.POINTER(_c_i32), ctypes.POINTER(_c_i32)]),
     "icm_server_result": (_c_i32, [_vp, _c_i64, ctypes.POINTER(_c_i32), _dp, _dp, _dp, _dp]),
     "icm_server_bytes_in_use": (_c_i64, [_vp]),
+    "icm_server_cancel": (_c_i32, [_vp, _c_i64]),
+    "icm_debug_wait_timeout": (_c_i32, [_vp, _c_i64]),
     "icm_server_destroy": (None, [_vp]),
     "icm_device_bytes": (_c_i64, [_vp]),
     "icm_op_interpolate": (_c_i32, [_vp, _c_i64, _dp, _dp, _dp]),
@@ -257,6 +260,10 @@ def icm_sync(sim):
     _check(lib().icm_sync(sim))
 
 
+def icm_debug_wait_timeout(sim, limit_ns):
+    _check(lib().icm_debug_wait_timeout(sim, int(limit_ns)))
+
+
 def icm_profile_steps(sim, nsteps, max_stages=128):
     """[(stage name, total ms over nsteps, algorithmic bytes per launch)] of one step's launches."""
     n = _c_i32()
@@ -278,6 +285,13 @@ def icm_fluid_momentum_static(fluid_v_dev_ptr, precision, ncell, rho, h, cuda_st
     _check(lib().icm_fluid_momentum_static(ctypes.c_void_p(int(fluid_v_dev_ptr)), int(precision), int(ncell),
                                            float(rho), float(h), cuda_stream, op))
     return out
+
+
+def icm_kernel_volume(kernel, h=1.0):
+    """dV = h^3 / (sum phi^2)^3 of the Peskin kernel, as the library computes it."""
+    out, op = _out(1)
+    _check(lib().icm_kernel_volume(int(kernel), float(h), op))
+    return float(out[0])
 
 
 def icm_num_blobs(sim):
@@ -459,6 +473,10 @@ def icm_server_result(server, job_id, nblobs):
 
 def icm_server_bytes_in_use(server):
     return int(lib().icm_server_bytes_in_use(server))
+
+
+def icm_server_cancel(server, job_id):
+    _check(lib().icm_server_cancel(server, int(job_id)))
 
 
 def icm_server_destroy(server):

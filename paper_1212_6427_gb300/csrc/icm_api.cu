@@ -1201,6 +1201,14 @@ icm_status icm_sync(icm_sim* s) {
   return check_device_errors(s);
 }
 
+icm_status icm_debug_wait_timeout(icm_sim* s, int64_t limit_ns) {
+  if (!s) return fail(ICM_EINVAL, "NULL simulation");
+  if (limit_ns < 1 || limit_ns > 2000000000ll) return fail(ICM_EINVAL, "limit_ns must be in [1, 2e9]");
+  debug_wait_timeout(s->err_dev, (long long)limit_ns, s->stream);
+  ICM_CK(cudaGetLastError());
+  return ICM_OK;
+}
+
 icm_status icm_read_state(icm_sim* s, double* pos, double* vel, double* fluid_v, double momentum[3], int64_t* step) {
   if (!s) return fail(ICM_EINVAL, "NULL simulation");
   icm_status st = ensure_hstage(s);
@@ -1311,6 +1319,15 @@ icm_status icm_profile_steps(icm_sim* s, int64_t nsteps, int32_t max_stages, int
   }
   *nstages = n;
   return check_device_errors(s);
+}
+
+icm_status icm_kernel_volume(int32_t kernel, double h, double* volume) {
+  if (volume == nullptr) return fail(ICM_EINVAL, "volume must not be NULL");
+  if (kernel != 3 && kernel != 4) return fail(ICM_EINVAL, "kernel must be 3 or 4");
+  if (!(h > 0.0) || !std::isfinite(h)) return fail(ICM_EINVAL, "h must be finite and > 0");
+  const double q = kernel_sum_sq(kernel);
+  *volume = h * h * h / (q * q * q);
+  return ICM_OK;
 }
 
 int64_t icm_num_blobs(const icm_sim* s) { return s ? s->nb : -1; }
@@ -2014,11 +2031,15 @@ icm_status icm_server_pump(icm_server* sv, int32_t steps_per_pump, int32_t* n_ac
     icm_sim* s = nullptr;
     icm_status st = icm_create(j->grid, j->h, j->rho, j->eta, j->kT, j->dt, j->kernel, j->seed, j->precision, j->flags,
                                nullptr, &s);
-    if (st == ICM_ENOMEM) break;
     const int64_t nb = (int64_t)j->me.size();
     if (st == ICM_OK && nb > 0)
       st = icm_add_blobs(s, nb, j->pos.data(), j->vel.empty() ? nullptr : j->vel.data(), j->me.data());
     if (st == ICM_OK && nb > 0 && !j->force.empty()) st = icm_set_blob_forces(s, j->force.data());
+    if (st == ICM_ENOMEM) {
+      // out of device memory now: the job stays first in line for the next pump
+      if (s) icm_destroy(s);
+      break;
+    }
     if (st == ICM_OK && cudaEventCreateWithFlags(&j->done, cudaEventDisableTiming) != cudaSuccess) st = ICM_ECUDA;
     sv->waiting.pop_front();
     if (st != ICM_OK) {
@@ -2063,6 +2084,44 @@ icm_status icm_server_result(icm_server* sv, int64_t job_id, int32_t* state, dou
     if (momentum) memcpy(momentum, j->out_mom, sizeof(j->out_mom));
     if (latency_s) latency_s[0] = std::chrono::duration<double>(j->t_done - j->t_submit).count();
   }
+  return ICM_OK;
+}
+
+icm_status icm_server_cancel(icm_server* sv, int64_t job_id) {
+  if (!sv) return fail(ICM_EINVAL, "NULL server");
+  auto it = sv->jobs.find(job_id);
+  if (it == sv->jobs.end()) return fail(ICM_EINVAL, "unknown job id %lld", (long long)job_id);
+  icm_server::Job* j = it->second;
+  if (j->state == 0) {
+    for (auto w = sv->waiting.begin(); w != sv->waiting.end(); ++w)
+      if (*w == j) {
+        sv->waiting.erase(w);
+        break;
+      }
+  } else if (j->state == 1) {
+    // the steps already enqueued for this job (one pump's worth at most) run out on its
+    // own stream before its memory goes back to the budget; other jobs are not waited for
+    const cudaError_t e = cudaStreamSynchronize(j->sim->stream);
+    for (auto a = sv->active.begin(); a != sv->active.end(); ++a)
+      if (*a == j) {
+        sv->active.erase(a);
+        break;
+      }
+    sv->used -= j->bytes;
+    if (j->done) cudaEventDestroy(j->done);
+    j->done = nullptr;
+    icm_destroy(j->sim);
+    j->sim = nullptr;
+    if (e != cudaSuccess) {
+      j->state = 3;
+      j->t_done = std::chrono::steady_clock::now();
+      return fail(ICM_ECUDA, "%s", cudaGetErrorString(e));
+    }
+  } else {
+    return ICM_OK;   // already done, failed or cancelled
+  }
+  j->state = 4;
+  j->t_done = std::chrono::steady_clock::now();
   return ICM_OK;
 }
 

@@ -657,12 +657,14 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Wait for phase `parity` of the barrier, giving up after half a second of global time.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Wait for phase `parity` of the barrier, giving up after limit_ns of global time
+// (half a second unless given).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint64_t limit_ns = 500000000ull) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   while (!mbar_try_wait(bar, parity))
-    if (global_ns() - t0 > 500000000ull) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   return true;
 }
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
@@ -733,9 +735,15 @@ __global__ void __launch_bounds__(zsym2_threads<R, N, R1, R2>(), sizeof(R) == 4 
     __syncthreads();
   }
   if (tid == 0 && !s_ok && t < ntiles) {
+    // A copy that has not landed after half a second: report it and leave.  Before
+    // leaving, give both copies that may still be in flight into this block's shared
+    // memory (the next tile's and the late one) another bounded wait.  If either is
+    // still outstanding after that, the block's shared memory may yet be written after
+    // it exits: the step's results are undefined and the host, which sees ICM_ETIMEOUT
+    // at its next icm_sync, must destroy the simulation (as after ICM_ECUDA).
     atomicOr(err, DEV_ERR_TIMEOUT);
-    // the copy of the next tile may still be in flight: wait for it (bounded) before leaving
     if (pending_other) mbar_wait_bounded(&mbar[(i & 1) ^ 1], ((i + 1) >> 1) & 1);
+    mbar_wait_bounded(&mbar[i & 1], (i >> 1) & 1);
   }
 }
 
@@ -1629,6 +1637,23 @@ void spectral_solve_group(const FftCtx<R>& f, const RepFft* reps, int G, int mod
 }
 
 #if ICM_SHARD(0)
+// Failure-path check of the bounded wait (no GPU fault): one thread arms an mbarrier
+// for 16 bytes of a transaction that is never issued, so its phase cannot complete;
+// the bounded wait gives up after limit_ns and raises the timeout bit, exactly as the
+// TMA z pass does when a copy does not land.  No copy is in flight when it returns.
+__global__ void k_wait_timeout(int* err, unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  mbar_expect_tx(&bar, 16);
+  if (!mbar_wait_bounded(&bar, 0, limit_ns)) atomicOr(err, DEV_ERR_TIMEOUT);
+}
+
+void debug_wait_timeout(int* err, long long limit_ns, cudaStream_t st) {
+  k_wait_timeout<<<1, 32, 0, st>>>(err, (unsigned long long)limit_ns);
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);

@@ -100,6 +100,10 @@ template <typename R>
 void spectral_solve_group(const FftCtx<R>& f, const RepFft* reps, int G, int mode, cudaStream_t st);
 bool fft_has_group_passes(int nx, int ny, int nz);
 
+// One-thread kernel whose bounded mbarrier wait runs out (a transaction that is never
+// issued): raises DEV_ERR_TIMEOUT in err after limit_ns.  Tests the failure path only.
+void debug_wait_timeout(int* err, long long limit_ns, cudaStream_t st);
+
 // Raise the dynamic shared-memory limits of the kernels (call once, outside capture).
 void fft_prepare();
 void grid_prepare();

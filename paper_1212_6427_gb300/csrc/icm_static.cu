@@ -73,7 +73,10 @@ __global__ void k_static_final(int nblk, double scale, double* __restrict__ scra
 icm_status say(icm_status st, const char* msg) { return (icm_status)icm::record_error((int)st, msg); }
 
 // Device address of the scratch array for the current device, looked up once per
-// device (the host-side name of a __device__ array is not a device address).
+// device (the host-side name of a __device__ array is not a device address).  The
+// cached address belongs to the device's primary context as it was at the lookup: a
+// cudaDeviceReset (or a primary-context reset) in the process unloads the module and
+// leaves a stale address behind, so the library must not be used across one.
 icm_status scratch_address(double** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return say(ICM_ECUDA, "cudaGetDevice failed");
@@ -98,10 +101,21 @@ extern "C" icm_status icm_fluid_momentum_static(const void* fluid_v_dev, int32_t
   if (ncell < 1) return say(ICM_EINVAL, "ncell must be >= 1");
   if (ncell > kStaticMaxCells)
     return say(ICM_EINVAL, "ncell exceeds the 134217728 cells (512^3) the static scratch array can reduce");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  // The call ends with a copy to the host and a wait, neither of which may enter a
+  // graph: refuse a stream that is capturing.  The legacy default stream (NULL) also
+  // reports an error here while a blocking stream of the process is capturing.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  const cudaError_t ce = cudaStreamIsCapturing(s, &cap);
+  if (ce != cudaSuccess) {
+    (void)cudaGetLastError();
+    return say(ICM_EINVAL, "cuda_stream cannot be used while a capture is open (use a non-blocking stream)");
+  }
+  if (cap != cudaStreamCaptureStatusNone)
+    return say(ICM_EINVAL, "cuda_stream is capturing a graph: pass a stream that is not capturing");
   double* scratch = nullptr;
   const icm_status st = scratch_address(&scratch);
   if (st != ICM_OK) return st;
-  cudaStream_t s = (cudaStream_t)cuda_stream;
   const int nblk = (int)((ncell + kCellsPerPartial - 1) / kCellsPerPartial);
   // every partial slot read below is written first, so nothing needs clearing
   if (precision == 32)

@@ -30,15 +30,14 @@ import math
 
 import numpy as np
 
-from .binding import FLAG_THERMAL_DRIFT, Simulation, icm_op_coupling
+from .binding import FLAG_THERMAL_DRIFT, Simulation, icm_kernel_volume, icm_op_coupling
 
 HASIMOTO = 2.8373   # first-order coefficient of the periodic-lattice mobility correction
 
 
 def kernel_volume(kernel, h=1.0):
-    """dV = h^3 / (sum phi^2)^3: sum phi^2 = 1/2 (three-point), 3/8 (four-point)."""
-    s = 0.5 if kernel == 3 else 0.375
-    return h ** 3 / s ** 3
+    """The blob volume dV of the Peskin kernel, from the library (icm_kernel_volume)."""
+    return icm_kernel_volume(kernel, h)
 
 
 def trap_trajectory(dt, T, me=0.0, k=0.01, precision=64, slip_flags=0, grid=(16, 16, 16), r0=10.0):

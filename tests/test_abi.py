@@ -66,3 +66,15 @@ def test_create_rejects_invalid_arguments(lib, bad):
 def test_philox_rejects_negative_count(lib):
     with pytest.raises(lib.IcmError):
         lib.icm_op_philox(-1, (0, 0, 0, 0), (0, 0))
+
+
+def test_kernel_volume_host_arithmetic(lib):
+    """dV = h^3 / (sum phi^2)^3: the paper's 8 h^3 for the 3-point kernel and (8/3)^3 h^3
+    for the 4-point kernel (host arithmetic, no GPU)."""
+    assert lib.icm_kernel_volume(3, 1.0) == 8.0
+    assert abs(lib.icm_kernel_volume(3, 0.5) - 1.0) < 1e-15
+    assert abs(lib.icm_kernel_volume(4, 1.0) - 512.0 / 27.0) < 1e-13
+    for kernel, h in ((5, 1.0), (3, 0.0), (4, float("inf"))):
+        with pytest.raises(lib.IcmError) as ei:
+            lib.icm_kernel_volume(kernel, h)
+        assert ei.value.status == lib.ICM_EINVAL

@@ -1,15 +1,16 @@
 """The full-size workloads (256^3 grid with 20000 blobs, 4-point kernel; 128^3 with 2000
-blobs, 3-point) in the launch configuration bench.py times, checked where the oracle
-cannot follow a whole step: one FP32 step against the FP64 GPU step from the same state
-(the FP64 path is itself held to the oracle at 1e-12), the conservation laws of the
-step, and the operators of the step against the oracle at full size."""
+blobs, 3-point) in the launch configuration bench.py times: whole steps of the 256^3
+configuration against the oracle at sampled time levels (an oracle step takes tens of
+seconds there), one FP32 step against the FP64 GPU step from the same state, the
+conservation laws of the step, and the operators of the step against the oracle at
+full size."""
 import numpy as np
 import pytest
 
 import icm_workloads as wl
 from oracle import icm as oracle
 
-from _gpu_helpers import TOL, rel
+from _gpu_helpers import TOL, compare_states, make_sim, read_oracle_state, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -27,6 +28,57 @@ def large():
     w = wl.workload("large")
     w["v0"] = wl.random_fluid(w["grid"], 0.05, 7)
     return w
+
+
+def _large_prm(w):
+    return oracle.Params(w["grid"], h=w["h"], rho=w["rho"], eta=w["eta"], kT=w["kT"], dt=w["dt"], kernel=w["kernel"],
+                         seed=w["seed"])
+
+
+@pytest.fixture(scope="module")
+def large_samples(icm, large):
+    """Two sampled time levels of the 256^3 configuration with the oracle's next step:
+    level 0 (the synthetic state, no history) and level 5 (read back from five FP64 GPU
+    steps, so the Adams-Bashforth history and the lagged slip term are in play)."""
+    w = large
+    prm = _large_prm(w)
+    st0 = oracle.State(w["v0"], w["q"], w["u"], w["me"], w["force"])
+    sim = make_sim(prm, st0, 64)
+    sim.step(5)
+    st5, _ = read_oracle_state(sim, prm, w["me"], w["force"])
+    sim.close()
+    assert st5.step == 5 and st5.adv_prev is not None
+    return prm, [(st0, oracle.icm_step(st0, prm)), (st5, oracle.icm_step(st5, prm))]
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_large_config_steps_match_oracle(icm, large_samples, precision):
+    """The 256^3 / 20000-blob / 4-point configuration bench.py times (FP32 in the plan the
+    autotuner picks there, FP64 in the default plan, as bench.py's FP64 leg): at each
+    sampled level the state is written into the simulation, one GPU step is taken, and
+    v, u, the blob displacement and the total momentum are compared with the oracle's
+    step from the same state (FP32 at 2e-5, FP64 at 1e-12, norm-wise)."""
+    prm, samples = large_samples
+    st0 = samples[0][0]
+    sim = make_sim(prm, st0, precision)
+    if precision == 32:
+        icm.icm_autotune(sim.handle, 2)      # state restored; the plan bench.py uses
+    worst = {}
+    for cur, want in samples:
+        sim.write(cur.q, cur.u, cur.v.ravel(), None if cur.adv_prev is None else cur.adv_prev.ravel(), cur.slip_g,
+                  cur.step)
+        sim.step(1)
+        got, mom = read_oracle_state(sim, prm, cur.me, cur.force)
+        assert got.step == cur.step + 1
+        err = compare_states(got, want, prm, cur.q)
+        scale = prm.rho * prm.h ** 3 * np.abs(want.v).sum() + np.abs(want.me[:, None] * want.u).sum()
+        err["P"] = float(np.abs(mom - oracle.total_momentum(want, prm)).max() / scale)
+        for k, e in err.items():
+            worst[k] = max(worst.get(k, 0.0), e)
+    sim.close()
+    print("256^3 step vs oracle, FP%d: %s" % (precision, {k: "%.2e" % e for k, e in worst.items()}))
+    for k, e in worst.items():
+        assert e < TOL[precision], (k, e, worst)
 
 
 def _sim(icm, w, precision):

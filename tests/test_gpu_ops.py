@@ -71,6 +71,20 @@ def test_spectral_solve(icm, precision, grid, ab):
 
 
 @pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("grid,kernel", [((8, 8, 8), 4), ((6, 6, 6), 3), ((12, 12, 12), 3), ((12, 8, 6), 3)])
+def test_spectral_solve_against_naive_dft(icm, precision, grid, kernel):
+    """The GPU solve against the solve whose transforms are the plain O(N^2) DFT sums
+    (no FFT on either side of the comparison), on 8^3, 6^3, 12^3 and a mixed grid."""
+    sim = _sim(icm, grid, precision, kernel=kernel, h=0.9)
+    nx, ny, nz = grid
+    r = np.random.default_rng(6).standard_normal((3, nz, ny, nx))
+    for a, b in ((20.0, 0.5), (1.0, 0.0), (1.3, 0.0175)):
+        got = icm.icm_op_spectral_solve(sim.handle, a, b, r.ravel())
+        assert rel(got, oracle.spectral_solve_dft(r, a, b, 0.9)) < TOL[precision] / 2, (a, b)
+    sim.close()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
 @pytest.mark.parametrize("kernel", [3, 4])
 @pytest.mark.parametrize("grid", [(16, 16, 16), (9, 18, 8), (48, 32, 27)])
 def test_interpolate_spread_and_laplacian_gather(icm, precision, kernel, grid):

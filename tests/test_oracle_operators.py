@@ -74,6 +74,43 @@ def test_spectral_solve_real_space_residual(ab, shape):
     np.testing.assert_allclose(resid.reshape(3, -1).mean(axis=1), 0.0, atol=1e-13 * scale)
 
 
+def test_naive_dft_closed_forms():
+    """The plain DFT sums: a delta at the origin transforms to all ones, a constant to
+    N at k = 0 only, a single plane wave to N at its own wave vector; and idft3 undoes
+    dft3 on random data (sides 8, 6 and 12 and a mixed grid)."""
+    for shape in ((8, 8, 8), (6, 6, 6), (12, 12, 12), (6, 8, 12)):
+        n = int(np.prod(shape))
+        delta = np.zeros(shape)
+        delta[0, 0, 0] = 1.0
+        np.testing.assert_allclose(icm.dft3(delta), np.ones(shape), atol=1e-13)
+        const = icm.dft3(np.ones(shape))
+        assert const[0, 0, 0] == pytest.approx(n, rel=1e-13)
+        const[0, 0, 0] = 0.0
+        assert np.abs(const).max() < 1e-10
+        kz, ky, kx = 1, shape[1] - 2, 3 % shape[2]
+        z, y, x = np.indices(shape)
+        wave = np.exp(2j * np.pi * (kz * z / shape[0] + ky * y / shape[1] + kx * x / shape[2]))
+        spec = icm.dft3(wave)
+        assert spec[kz, ky, kx] == pytest.approx(n, rel=1e-12)
+        spec[kz, ky, kx] = 0.0
+        assert np.abs(spec).max() < 1e-9
+        rng = np.random.default_rng(n)
+        f = rng.standard_normal(shape)
+        np.testing.assert_allclose(icm.idft3(icm.dft3(f)).real, f, atol=1e-12)
+
+
+@pytest.mark.parametrize("shape", [(8, 8, 8), (6, 6, 6), (12, 12, 12), (6, 8, 12)])
+def test_fft_solve_equals_naive_dft_solve(shape):
+    """numpy's FFT, the library transform of the oracle's solves, against the plain
+    O(N^2) DFT sums, through the whole Helmholtz / projection solve on 8^3, 6^3 and 12^3
+    grids (radix 2 and 3) and a mixed one."""
+    rng = np.random.default_rng(5)
+    r = rng.standard_normal((3,) + shape)
+    for a, b in ((20.0, 0.5), (1.0, 0.0), (0.0, 0.8)):
+        want = icm.spectral_solve_dft(r, a, b, 0.9)
+        np.testing.assert_allclose(icm.spectral_solve(r, a, b, 0.9), want, rtol=0, atol=1e-13 * np.abs(want).max())
+
+
 def test_projection_is_orthogonal_projector():
     rng = np.random.default_rng(4)
     shape = (6, 8, 10)

@@ -19,25 +19,35 @@ import icm_workloads as wl
 from oracle import icm
 
 
+# Physical parameters (h, rho, eta) every step pin runs at: unit values, and values far
+# from 1 so that a dropped or misplaced h, rho or eta (nu = eta/rho, dV_f = h^3, the
+# stress amplitude, the rho of the inertial coefficients, rho h^3 in the momentum)
+# changes the outcome.
+PHYS = [dict(h=1.0, rho=1.0, eta=1.0), dict(h=0.7, rho=1.3, eta=0.6)]
+PHYS_IDS = ["unit", "h0.7-rho1.3-eta0.6"]
+
+
 def _prm(grid, **kw):
     return icm.Params(grid, **kw)
 
 
-def _state(grid, nb, seed, me_scale=1.0, vamp=0.05, force=0.0, kernel=4):
+def _state(grid, nb, seed, me_scale=1.0, vamp=0.05, force=0.0, kernel=4, h=1.0, rho=1.0):
     rng = np.random.default_rng(seed)
-    q = wl.random_sequential_addition(nb, grid, 1.0, 3.0, seed)
+    q = wl.random_sequential_addition(nb, grid, h, 3.0 * h, seed)
     u = 0.05 * rng.standard_normal((nb, 3))
-    me = me_scale * rng.uniform(-0.5, 2.0, size=nb)
+    me = me_scale * rng.uniform(-0.5, 2.0, size=nb) * rho * h ** 3
     F = force * rng.standard_normal((nb, 3))
     v = wl.random_fluid(grid, vamp, seed + 1)
     return icm.State(v, q, u, me, F)
 
 
+@pytest.mark.parametrize("phys", PHYS, ids=PHYS_IDS)
 @pytest.mark.parametrize("slip", ["visc", "full", "zero"])
-def test_momentum_conserved_without_force(slip):
+def test_momentum_conserved_without_force(slip, phys):
     grid = (12, 10, 14)
-    prm = _prm(grid, kT=1e-3, dt=0.1, kernel=4, seed=9, slip=slip)
-    st = _state(grid, 6, 21)
+    prm = _prm(grid, kT=1e-3, dt=0.1 * phys["rho"] * phys["h"] ** 2 / phys["eta"], kernel=4, seed=9, slip=slip,
+               **phys)
+    st = _state(grid, 6, 21, h=phys["h"], rho=phys["rho"])
     p0 = icm.total_momentum(st, prm)
     assert np.abs(p0).max() > 1e-3      # a non-trivial momentum to conserve
     for _ in range(4):
@@ -45,15 +55,27 @@ def test_momentum_conserved_without_force(slip):
         np.testing.assert_allclose(icm.total_momentum(st, prm), p0, rtol=0, atol=1e-13 * np.abs(p0).max() * 50)
 
 
-def test_momentum_change_equals_impulse_of_force():
+@pytest.mark.parametrize("phys", PHYS, ids=PHYS_IDS)
+def test_momentum_change_equals_impulse_of_force(phys):
     grid = (10, 12, 10)
-    prm = _prm(grid, kT=0.0, dt=0.07, kernel=3)
-    st = _state(grid, 5, 31, force=0.3)
+    prm = _prm(grid, kT=0.0, dt=0.07, kernel=3, **phys)
+    st = _state(grid, 5, 31, force=0.3, h=phys["h"], rho=phys["rho"])
     for _ in range(3):
         p0 = icm.total_momentum(st, prm)
         st2 = icm.icm_step(st, prm)
         np.testing.assert_allclose(icm.total_momentum(st2, prm) - p0, prm.dt * st.force.sum(axis=0), atol=1e-13)
         st = st2
+
+
+def test_momentum_of_a_resting_fluid_cell_is_rho_h3_v():
+    """P = rho dV_f sum_k v_k + sum_i m_e,i u_i by hand: one face of a 6^3 grid moving at
+    0.5 with h = 0.7, rho = 1.3, plus one blob of excess mass 2 moving at (0, 1, -1)."""
+    grid = (6, 6, 6)
+    prm = _prm(grid, h=0.7, rho=1.3, eta=0.6)
+    v = np.zeros((3, 6, 6, 6))
+    v[0, 1, 2, 3] = 0.5
+    st = icm.State(v, [[1.0, 1.0, 1.0]], [[0.0, 1.0, -1.0]], [2.0], [[0.0, 0.0, 0.0]])
+    np.testing.assert_allclose(icm.total_momentum(st, prm), [1.3 * 0.343 * 0.5, 2.0, -2.0], rtol=1e-15)
 
 
 def test_no_slip_exact_for_neutral_blobs():
@@ -95,35 +117,44 @@ def test_second_order_in_time_for_neutral_blob():
     assert 3.0 < e1 / e2 < 5.0
 
 
-def _final_slip(me, dt, T=1.6):
+def _final_slip(me, dt, T=1.6, h=1.0, rho=1.0, eta=1.0):
+    """The no-slip violation after time T (in units of the viscous time h^2 rho/eta) of a
+    blob pulled by a constant force, started at rest; excess mass me in rho h^3."""
     grid = (16, 16, 16)
-    st = icm.State(np.zeros((3, 16, 16, 16)), [[5.3, 7.1, 8.9]], [[0, 0, 0]], [me], [[0.02, 0.01, -0.015]])
-    prm = _prm(grid, kT=0.0, dt=dt, kernel=4, slip="visc")
+    tv = rho * h * h / eta
+    st = icm.State(np.zeros((3, 16, 16, 16)), [[5.3 * h, 7.1 * h, 8.9 * h]], [[0, 0, 0]], [me * rho * h ** 3],
+                   [[0.02, 0.01, -0.015]])
+    prm = _prm(grid, kT=0.0, dt=dt * tv, kernel=4, slip="visc", h=h, rho=rho, eta=eta)
     for _ in range(int(round(T / dt))):
         tr = {}
         st = icm.icm_step(st, prm, tr)
-    return np.linalg.norm(st.u - icm.interpolate(st.v, tr["q_half"], 4, 1.0))
+    return np.linalg.norm(st.u - icm.interpolate(st.v, tr["q_half"], 4, h))
 
 
-def test_slip_is_order_me_dt2_for_inertial_blob():
+@pytest.mark.parametrize("phys", PHYS, ids=PHYS_IDS)
+def test_slip_is_order_me_dt2_for_inertial_blob(phys):
     """Appendix C: the no-slip violation u^{n+1} - J^{n+1/2} v^{n+1} (viscous slip option)
     is O(m_e dt^2): zero for m_e = 0, linear in m_e, and at least second order in dt
-    (it falls ~dt^3 here because dv itself shrinks with dt on this smooth problem)."""
-    assert _final_slip(0.0, 0.2) == 0.0
-    s1, s2 = _final_slip(0.3, 0.2), _final_slip(0.6, 0.2)
+    (it falls ~dt^3 here because dv itself shrinks with dt on this smooth problem; a
+    wrong viscosity nu in the slip correction, or a wrong rho in the inertial
+    coefficients, leaves an O(dt) slip)."""
+    assert _final_slip(0.0, 0.2, **phys) == 0.0
+    s1, s2 = _final_slip(0.3, 0.2, **phys), _final_slip(0.6, 0.2, **phys)
     assert s1 > 0 and s2 / s1 == pytest.approx(2.0, rel=0.05)
-    a, b, c = (_final_slip(0.6, dt) for dt in (0.2, 0.1, 0.05))
-    assert a / b > 4.0 and b / c > 4.0
+    a, b, c = (_final_slip(0.6, dt, **phys) for dt in (0.2, 0.1, 0.05))
+    assert a / b > 5.0 and b / c > 5.0
 
 
 @pytest.mark.slow
-def test_fluid_equilibrium_variance_exact_for_any_dt():
+@pytest.mark.parametrize("phys", PHYS, ids=PHYS_IDS)
+def test_fluid_equilibrium_variance_exact_for_any_dt(phys):
     """Linear fluctuating Stokes (no advection, no blobs): every transverse mode has
-    variance kT/(rho dV_f) for any dt, so a face carries (2/3)(1 - N^-3) kT/(rho dV_f)."""
+    variance kT/(rho dV_f) for any dt, so a face carries (2/3)(1 - N^-3) kT/(rho h^3)."""
     grid = (8, 8, 8)
     kT = 1e-3
-    for dt in (0.5, 5.0):
-        prm = _prm(grid, kT=kT, dt=dt, kernel=4, seed=123, advection=False)
+    h, rho, eta = phys["h"], phys["rho"], phys["eta"]
+    for beta in (0.5, 5.0):
+        prm = _prm(grid, kT=kT, dt=beta * rho * h * h / eta, kernel=4, seed=123, advection=False, **phys)
         st = icm.State(np.zeros((3, 8, 8, 8)), np.zeros((0, 3)), np.zeros((0, 3)), np.zeros(0), np.zeros((0, 3)))
         acc, cnt = 0.0, 0
         for n in range(260):
@@ -131,7 +162,7 @@ def test_fluid_equilibrium_variance_exact_for_any_dt():
             if n >= 20:
                 acc += np.mean(st.v ** 2)
                 cnt += 1
-        want = (2.0 / 3.0) * (1.0 - 8.0 ** -3) * kT
+        want = (2.0 / 3.0) * (1.0 - 8.0 ** -3) * kT / (rho * h ** 3)
         assert acc / cnt == pytest.approx(want, rel=0.03)
 
 
@@ -239,3 +270,62 @@ def test_trap_error_decays_second_order_for_neutral_blob():
     assert np.linalg.norm(q[0.25][-1] - [10.0, 0.0, 0.0]) > 1e-3     # the blob moved
     e1, e2 = e_dt(q[1.0], q[0.5]), e_dt(q[0.5], q[0.25])
     assert 3.2 < e1 / e2 < 4.8
+
+
+def _gibbs_blob_covariance(q, me, grid, kernel, h, rho):
+    """<U U^T> / kT of the blob velocities U = J v at fixed positions q, for the Gibbs
+    measure exp(-E/kT) of the discrete kinetic energy E = rho dV_f |v|^2 / 2 +
+    sum_i m_e,i |J_i v|^2 / 2 on the faces with D v = 0 and zero total momentum
+    rho dV_f sum v + sum_i m_e,i J_i v (Sec. II "Equipartition of Energy" states the
+    continuum form).  With A = rho dV_f, G = J Q J^T (Q the projector onto the
+    constrained faces) and M_e = diag(m_e): <U U^T> / kT = G (A I + M_e G)^-1.  J Q J^T
+    is reduced to the pair matrices dV_f J_i P S_j, the only place the solver enters;
+    the mean-mode constraint is removed with the 3 x 3 Schur complement."""
+    nb = len(q)
+    dvf = h ** 3
+    ncell = int(np.prod(grid))
+    g0 = np.zeros((3 * nb, 3 * nb))
+    for i in range(nb):
+        for j in range(nb):
+            g0[3 * i:3 * i + 3, 3 * j:3 * j + 3] = dvf * icm.coupling_matrix(q[i], q[j], grid, kernel, h)
+    a = rho * dvf
+    mvec = np.repeat(me, 3)
+    e = np.tile(np.eye(3), (1, nb))
+    cpj = a * e + (e * mvec) @ g0
+    cpc = (a * a * ncell + 2.0 * a * me.sum()) * np.eye(3) + (e * mvec) @ g0 @ (e * mvec).T
+    g = g0 - cpj.T @ np.linalg.solve(cpc, cpj)
+    return g @ np.linalg.inv(a * np.eye(3 * nb) + mvec[:, None] * g)
+
+
+@pytest.mark.slow
+def test_inertial_blob_velocity_variance_is_kT_over_m_tilde():
+    """Sec. II "Equipartition of Energy" (Eq. m_eff_incomp) and Sec. IV "Velocity
+    Autocorrelation": a blob with excess mass m_e in an incompressible fluid has
+    <u_a^2> = kT / m~, m~ = m_e + 3 m_f / 2, for small alpha and beta.  With m_e = m_f
+    (m_f = rho dV, dV = 8 h^3 for the 3-point kernel) this is the VACF intercept
+    C(0+) = 0.8 kT / m, m = m_e + m_f.  Eight such blobs on 16^3 at h, rho, eta far from 1,
+    beta = nu dt / h^2 = 1/8, no advection, 2900 sampled steps: the measured variance is
+    held to 4% of kT/m~ and to 2.5% of the exact finite-box Gibbs value (about 0.5%
+    below kT/m~), which exercises steps 4-8 of the scheme (slip, dp, the inertial
+    perturbation and the viscous correction)."""
+    grid = (16, 16, 16)
+    h, rho, eta, kT = 0.8, 1.3, 0.7, 1e-3
+    dt = 0.125 * rho * h * h / eta
+    mf = rho * 8.0 * h ** 3
+    nb = 8
+    me = np.full(nb, mf)
+    prm = _prm(grid, h=h, rho=rho, eta=eta, kT=kT, dt=dt, kernel=3, seed=11, advection=False)
+    q0 = wl.random_sequential_addition(nb, grid, h, 5.0 * h, 3)
+    st = icm.State(np.zeros((3, 16, 16, 16)), q0, np.zeros((nb, 3)), me, np.zeros((nb, 3)))
+    acc = []
+    for n in range(3000):
+        st = icm.icm_step(st, prm)
+        if n >= 100:
+            acc.append(np.mean(st.u ** 2))
+    var = float(np.mean(acc))
+    m_tilde = mf + 1.5 * mf
+    assert var == pytest.approx(kT / m_tilde, rel=0.04)
+    assert var == pytest.approx(0.8 * kT / (2.0 * mf), rel=0.04)
+    exact = kT * np.trace(_gibbs_blob_covariance(st.q, me, grid, 3, h, rho)) / (3 * nb)
+    assert exact == pytest.approx(kT / m_tilde, rel=0.02)
+    assert var == pytest.approx(exact, rel=0.025)
