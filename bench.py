@@ -174,6 +174,20 @@ def kernel_of(stage):
     return stage.split(".", 1)[1] if "." in stage else stage
 
 
+def fft_flops_per_step(grid, inertial):
+    """Floating-point operations of the FFT passes of one step by the 5 n log2 n model of
+    a complex n-point transform: per solve, forward and inverse lines along x (two real
+    rows packed as one complex line), y and z (Nx/2+1 wave numbers) of 3 components;
+    three solves when any blob has excess mass, else one."""
+    nx, ny, nz = grid
+    kx = nx // 2 + 1
+
+    def line(n):
+        return 5.0 * n * np.log2(n)
+    per_solve = 2 * 3 * ((ny * nz / 2) * line(nx) + kx * nz * line(ny) + kx * ny * line(nz))
+    return per_solve * (3 if inertial else 1)
+
+
 def oracle_step_rate(w, budget_s, max_steps):
     """Time the FP64 numpy oracle on the workload: (seconds per step, steps timed)."""
     from oracle import icm as oracle
@@ -358,8 +372,24 @@ def extras(args, w, prec, sim, line, torch, icm, per_kernel):
         e1.synchronize()
         ms64 = e0.elapsed_time(e1) / n64
         s64.close()
+        peak64 = icm.icm_peak_fma(64, s64.stream.cuda_stream if hasattr(s64.stream, "cuda_stream") else None)
+        flops = fft_flops_per_step(grid, any(np.asarray(w["me"]) != 0.0))
+        step_bytes64 = 2.0 * line["step_hbm"]["algorithmic_bytes_per_step"]
+        hbm_peak, hbm_kind = measured_peaks()
         line["fp64_gpu"] = {"ms_per_step": ms64, "value": ncell / (ms64 / 1e3), "unit": "cell-updates/s",
-                            "speedup_fp32_over_fp64": ms64 / line["ms_per_step"]}
+                            "speedup_fp32_over_fp64": ms64 / line["ms_per_step"],
+                            "roofline": {"bound": "fp64", "kernel": "whole FP64 step",
+                                         "achieved": flops / (ms64 / 1e3) / 1e12, "peak": peak64 / 1e12,
+                                         "unit": "TFLOP/s", "frac": flops / (ms64 / 1e3) / peak64,
+                                         "peak_kind": "measured (icm_peak_fma: FP64 FMA chains, CUDA events)",
+                                         "flops_per_step": flops,
+                                         "flop_model": "5 n log2 n per complex n-point FFT line, forward and "
+                                                       "inverse along x, y and z for each solve; nothing else "
+                                                       "counted"},
+                            "hbm": {"algorithmic_bytes_per_step": step_bytes64,
+                                    "achieved_GBps": step_bytes64 / (ms64 / 1e3) / 1e9,
+                                    "frac": step_bytes64 / (ms64 / 1e3) / 1e9 / hbm_peak, "peak_kind": hbm_kind}}
+        line["fp32_fma_peak_tflops"] = icm.icm_peak_fma(32) / 1e12
     log("[bench] extras: cuFFT round trip")
     # cuFFT (through torch.fft) R2C + C2R round trip of the three components, against ours
     x = torch.randn((3,) + tuple(reversed(grid)), device="cuda",
@@ -380,6 +410,19 @@ def extras(args, w, prec, sim, line, torch, icm, per_kernel):
                   if k in per_kernel) / max(1, per_kernel["z_sym"]["launches"])
     line["fft_roundtrip"] = {"ours_ms": ours_rt, "cufft_ms": cufft_ms,
                              "note": "ours includes the fused Helmholtz/projection symbol; cuFFT is R2C+C2R only"}
+    log("[bench] extras: batched replicas")
+    b = measure_batch(args, 0, 1, None, min(args.steps, 20))
+    line["batch"] = {"workload": b["config"]["workload"], "ms_per_step": b["ms_per_step"], "value": b["value"],
+                     "unit": "cell-updates/s", "blob_steps_per_s": b["blob_steps_per_s"],
+                     "launches_per_step": b["launches_per_step"], "group_solves": b["config"]["group_solves"],
+                     "step_hbm_frac": b["roofline"]["frac"], "speedup_over_unbatched": b["speedup_over_unbatched"],
+                     "steps": b["steps"], "clocks": b["clocks"]}
+    log("[bench] extras: served stream")
+    v = measure_served(args, 0, 1, args.jobs)
+    line["served"] = {"workload": v["config"]["workload"], "value": v["value"], "unit": "cell-updates/s",
+                      "blob_steps_per_s": v["blob_steps_per_s"], "jobs_per_s": v["jobs_per_s"],
+                      "latency_p50_s": v["latency_p50_s"], "latency_p99_s": v["latency_p99_s"],
+                      "peak_device_bytes": v["peak_device_bytes"], "wall_s": v["wall_s"], "clocks": v["clocks"]}
     log("[bench] extras: oracle on the host")
     # the FP64 numpy oracle on the host cores, one bounded sample of the same workload
     sec, n = oracle_step_rate(w, min(args.cpu_budget, 60.0), 1)
@@ -398,6 +441,15 @@ def run_batch(args, rank, world, dist):
     if dist is not None:
         dist.barrier()
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    line = measure_batch(args, rank, world, dist, args.steps)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def measure_batch(args, rank, world, dist, steps):
+    """The batch workload's JSON line (the members stepped `steps` batch steps)."""
+    import torch
+    import paper_1212_6427_gb300 as icm
     icm.use_torch_allocator()
     reps = wl.batch_replicas(64, seed0=1 + 64 * rank)
     sims = []
@@ -428,42 +480,41 @@ def run_batch(args, rank, world, dist):
     clocks.start()
     time.sleep(0.3)
     t0 = time.perf_counter()
-    icm.icm_batch_step(b, args.steps)
+    icm.icm_batch_step(b, steps)
     icm.icm_batch_sync(b)
     sec = time.perf_counter() - t0
     clk = clocks.stop()
     # the same replicas stepped one after another without batching
     t1 = time.perf_counter()
-    for _ in range(max(3, args.steps // 10)):
+    for _ in range(max(3, steps // 10)):
         for s in sims:
             s.step(1)
     for s in sims:
         s.sync()
-    seq = (time.perf_counter() - t1) / max(3, args.steps // 10)
+    seq = (time.perf_counter() - t1) / max(3, steps // 10)
     sec = max_over_ranks(sec, dist)
-    ms_step = sec / args.steps * 1e3
+    ms_step = sec / steps * 1e3
     peak, peak_kind = measured_peaks()
     achieved = step_bytes / (ms_step / 1e3) / 1e9
-    line = {"metric": METRIC, "value": cells * args.steps * world / sec, "unit": "cell-updates/s", "n_gpus": world,
-            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
+    line = {"metric": METRIC, "value": cells * steps * world / sec, "unit": "cell-updates/s", "n_gpus": world,
+            "steps": steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "icm-batch-64-replicas-sides-32-48-64-96-fp32", "replicas": 64 * world,
                        "plans": plans, "group_solves": bool(grouped),
                        "cells_per_replica_set": cells, "blobs": blobs, "parallelism": "replicas only",
                        "l2": "replica set of %.0f MB per field: timed on host clock around whole batch steps"
                              % (3 * cells * 4 / 1e6)},
-            "blob_steps_per_s": blobs * args.steps * world / sec,
+            "blob_steps_per_s": blobs * steps * world / sec,
             "roofline": {"bound": "hbm", "kernel": "whole batched step", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None},
             "unbatched_ms_per_step": seq * 1e3, "speedup_over_unbatched": seq * 1e3 / ms_step,
-            "clocks": clk, "gpu_launches": launches * args.steps,
-            "e2e": {"value": cells * args.steps * world / sec, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+            "clocks": clk, "gpu_launches": launches * steps, "launches_per_step": launches,
+            "e2e": {"value": cells * steps * world / sec, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0, "note": "device-resident batch; no per-step host I/O"}}
     icm.icm_batch_destroy(b)
     for s in sims:
         s.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_served(args, rank, world, dist):
@@ -476,8 +527,16 @@ def run_served(args, rank, world, dist):
     if dist is not None:
         dist.barrier()
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    line = measure_served(args, rank, world, args.jobs)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def measure_served(args, rank, world, njobs):
+    """The served workload's JSON line (njobs Poisson-arriving jobs)."""
+    import paper_1212_6427_gb300 as icm
     icm.use_torch_allocator()
-    jobs = wl.served_jobs(args.jobs, rate=50.0, seed=5 + rank)
+    jobs = wl.served_jobs(njobs, rate=50.0, seed=5 + rank)
     sv = icm.icm_server_create(150 * 10 ** 9, 256)
     ids = {}
     pending = list(jobs)
@@ -522,8 +581,7 @@ def run_served(args, rank, world, dist):
             "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
             "latency_mean_s": float(lat.mean()), "peak_device_bytes": peak_bytes, "wall_s": wall, "clocks": clk,
             "e2e": {"value": cell_steps / wall, "unit": "cell-updates/s", "note": "host submit to host result"}}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def main():

@@ -263,6 +263,14 @@ icm_status icm_fluid_momentum_static(const void* fluid_v_dev, int32_t precision,
  * Errors: ICM_EINVAL (bad kernel, h <= 0 or not finite, NULL volume). */
 icm_status icm_kernel_volume(int32_t kernel, double h, double* volume);
 
+/* Measured FMA throughput of the current device (flop/s, an FMA counts 2) in FP32
+ * (precision 32) or FP64 (64): eight independent FMA chains per thread in eight
+ * 256-thread blocks per SM, timed with CUDA events on cuda_stream (NULL = legacy
+ * stream) over a second launch after a first one; synchronises.  The denominator of
+ * the FP64 path's arithmetic roofline; no counterpart in the paper.
+ * Errors: ICM_EINVAL (bad precision, NULL output), ICM_ECUDA. */
+icm_status icm_peak_fma(int32_t precision, void* cuda_stream, double* flops_per_s);
+
 /* Number of blobs and bytes of device memory the simulation holds. */
 int64_t icm_num_blobs(const icm_sim* sim);
 int64_t icm_device_bytes(const icm_sim* sim);

@@ -75,6 +75,7 @@ SIGNATURES = {
     "icm_fluid_momentum_static": (_c_i32, [_vp, _c_i32, _c_i64, _c_d, _c_d, _vp, _dp]),
     "icm_num_blobs": (_c_i64, [_vp]),
     "icm_kernel_volume": (_c_i32, [_c_i32, _c_d, _dp]),
+    "icm_peak_fma": (_c_i32, [_c_i32, _vp, _dp]),
     "icm_batch_create": (_c_i32, [_vp, ctypes.POINTER(_vp)]),
     "icm_batch_set": (_c_i32, [_vp, _c_i32, ctypes.POINTER(_vp)]),
     "icm_batch_step": (_c_i32, [_vp, _c_i64]),
@@ -285,6 +286,13 @@ def icm_fluid_momentum_static(fluid_v_dev_ptr, precision, ncell, rho, h, cuda_st
     _check(lib().icm_fluid_momentum_static(ctypes.c_void_p(int(fluid_v_dev_ptr)), int(precision), int(ncell),
                                            float(rho), float(h), cuda_stream, op))
     return out
+
+
+def icm_peak_fma(precision=64, cuda_stream=None):
+    """Measured FMA throughput of the current device in flop/s (FP32 or FP64)."""
+    out, op = _out(1)
+    _check(lib().icm_peak_fma(int(precision), cuda_stream, op))
+    return float(out[0])
 
 
 def icm_kernel_volume(kernel, h=1.0):

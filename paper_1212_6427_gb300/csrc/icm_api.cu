@@ -1321,6 +1321,17 @@ icm_status icm_profile_steps(icm_sim* s, int64_t nsteps, int32_t max_stages, int
   return check_device_errors(s);
 }
 
+icm_status icm_peak_fma(int32_t precision, void* cuda_stream, double* flops_per_s) {
+  if (!flops_per_s) return fail(ICM_EINVAL, "flops_per_s must not be NULL");
+  if (precision != 32 && precision != 64) return fail(ICM_EINVAL, "precision must be 32 or 64");
+  // about 40 ms of FMA work at each precision's rate on a GB300
+  const int iters = precision == 64 ? 2048 : 65536;
+  const double r = fma_rate(precision, iters, 8, (cudaStream_t)cuda_stream, nullptr);
+  if (!(r > 0.0)) return fail(ICM_ECUDA, "the FMA-chain kernel failed");
+  *flops_per_s = r;
+  return ICM_OK;
+}
+
 icm_status icm_kernel_volume(int32_t kernel, double h, double* volume) {
   if (volume == nullptr) return fail(ICM_EINVAL, "volume must not be NULL");
   if (kernel != 3 && kernel != 4) return fail(ICM_EINVAL, "kernel must be 3 or 4");

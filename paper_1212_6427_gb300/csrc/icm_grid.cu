@@ -319,6 +319,26 @@ __global__ void k_scal_after(double* scal, int inertial, long long* step_dev, in
   }
 }
 
+// Peak FMA rate: kFmaChains independent dependent chains x = x * a + b per thread,
+// `iters` rounds; a = 1 - 2^-20 and b = 2^-30 keep every value normal and bounded.
+// The sum of the chains is stored only if it equals a value it cannot take, so the
+// work is not removed.
+constexpr int kFmaChains = 8;
+template <typename R>
+__global__ void __launch_bounds__(256) k_fma_chain(R* __restrict__ out, int iters, R a, R b) {
+  R x[kFmaChains];
+#pragma unroll
+  for (int c = 0; c < kFmaChains; ++c) x[c] = R(1) + R(threadIdx.x + c) * R(1e-3);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < kFmaChains; ++c) x[c] = fma(x[c], a, b);
+  }
+  R sum = R(0);
+#pragma unroll
+  for (int c = 0; c < kFmaChains; ++c) sum += x[c];
+  if (out != nullptr && sum == R(-1)) out[blockIdx.x * blockDim.x + threadIdx.x] = sum;
+}
+
 template <typename R>
 size_t rhs_smem() { return sizeof(RhsSmem<R>); }
 
@@ -361,6 +381,32 @@ void convert_to_double(const R* src, double* dst, long long n, cudaStream_t st) 
 template <typename R>
 void convert_from_double(const double* src, R* dst, long long n, cudaStream_t st) {
   k_convert<double, R><<<1024, 256, 0, st>>>(src, dst, n);
+}
+
+double fma_rate(int precision, int iters, int blocks_per_sm, cudaStream_t st, double* seconds) {
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return -1.0;
+  const int blocks = nsm * blocks_per_sm, threads = 256;
+  void* out = nullptr;   // k_fma_chain stores nothing through a null pointer
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -1.0;
+  float ms = 0.0f;
+  for (int rep = 0; rep < 2; ++rep) {   // the first launch warms up
+    cudaEventRecord(e0, st);
+    if (precision == 64)
+      k_fma_chain<double><<<blocks, threads, 0, st>>>((double*)out, iters, 1.0 - 0x1p-20, 0x1p-30);
+    else
+      k_fma_chain<float><<<blocks, threads, 0, st>>>((float*)out, iters, 1.0f - 0x1p-20f, 0x1p-30f);
+    cudaEventRecord(e1, st);
+  }
+  const cudaError_t e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess || cudaGetLastError() != cudaSuccess || ms <= 0.0f) return -1.0;
+  if (seconds) *seconds = ms * 1e-3;
+  return 2.0 * kFmaChains * (double)iters * blocks * threads / (ms * 1e-3);
 }
 
 void grid_prepare() {

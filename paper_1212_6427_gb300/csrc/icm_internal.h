@@ -104,6 +104,11 @@ bool fft_has_group_passes(int nx, int ny, int nz);
 // issued): raises DEV_ERR_TIMEOUT in err after limit_ns.  Tests the failure path only.
 void debug_wait_timeout(int* err, long long limit_ns, cudaStream_t st);
 
+// Peak FMA rate (flop/s, 2 per FMA) of this device in precision 32 or 64: independent
+// FMA chains in every thread of blocks_per_sm 256-thread blocks per SM, `iters` FMAs
+// per chain, the second of two launches timed with CUDA events on st.  -1 on error.
+double fma_rate(int precision, int iters, int blocks_per_sm, cudaStream_t st, double* seconds);
+
 // Raise the dynamic shared-memory limits of the kernels (call once, outside capture).
 void fft_prepare();
 void grid_prepare();
