@@ -132,15 +132,17 @@ icm_status icm_set_blob_trap(icm_sim* sim, double k, const double center[3]);
 icm_status icm_set_blob_wca(icm_sim* sim, double epsilon, double sigma);
 
 /* Execution plan: implementation choices that change the speed of a step but not its
- * result beyond rounding (no counterpart in the paper).  Defaults: every choice on,
- * rhs_kz = 16. */
+ * result beyond rounding (no counterpart in the paper).  Defaults: every choice on
+ * except fused_xy, rhs_kz as below. */
 typedef struct icm_plan {
   int32_t fused_blobs; /* 1: spreading and interpolation inside the x FFT passes through row-block
                           bins (sides 32, 48, 64, 96, 128, 192, 256, 384, 512); 0: separate kernels */
   int32_t tma_z;       /* 1: persistent z pass fed by TMA (z sides <= 256 with register kernels);
                           0: one block per z tile                                                  */
-  int32_t rhs_kz;      /* z planes marched by each block of the right-hand-side kernel, 4..64
-                          (default 8 for Nz <= 48, 32 for Nz >= 256, else 16)                       */
+  int32_t rhs_kz;      /* right-hand-side kernel: 4..64 z planes marched by each block, or 0 for
+                          persistent blocks (as many as the SMs hold) marching even shares of
+                          all tile-planes (default 0 when each of two blocks per SM gets at least
+                          8 tile-planes of 32 x 16 cells, else 8 for Nz <= 48 and 16 otherwise)    */
   int32_t fork;        /* 1: the blob-side prologue runs on a second stream beside the RHS          */
   int32_t fused_xy;    /* 1: forward x and y FFT passes fused on thread-block clusters (FP32,
                           Nx = Ny in 32, 64, 128, 256); 0 (default): two passes                    */
@@ -150,7 +152,7 @@ typedef struct icm_plan {
 icm_status icm_get_plan(const icm_sim* sim, icm_plan* out);
 
 /* Fix the plan (choices the simulation cannot use fall back to the alternative).
- * Errors: ICM_EINVAL (NULL, rhs_kz outside 4..64). */
+ * Errors: ICM_EINVAL (NULL, rhs_kz neither 0 nor in 4..64). */
 icm_status icm_set_plan(icm_sim* sim, const icm_plan* plan);
 
 /* Autotuner: time the candidate plans over nsteps steps each (one choice at a time,

@@ -619,10 +619,17 @@ std::string plan_key(const icm_sim* s) {
   return buf;
 }
 
-// The plan of a simulation nobody tuned: everything on; the RHS blocks march 8 z planes
-// on short z sides, 32 on sides of 256 and more (what the autotuners pick there), else 16.
+// The plan of a simulation nobody tuned: everything on.  The RHS blocks are persistent
+// when every block of a full GPU (two per SM) gets at least 8 tile-planes of 32 x 16
+// cells, which the single-simulation sweeps found fastest from 128^3 up; on smaller
+// grids they march 8 z planes on short z sides, else 16.
 icm_plan default_plan(const icm_sim* s) {
-  const int kz = s->nz <= 48 ? 8 : (s->nz >= 256 ? 32 : 16);
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
+                                                cudaSuccess)
+    nsm = 1;
+  const long long tile_planes = (long long)((s->nx + 31) / 32) * ((s->ny + 15) / 16) * s->nz;
+  const int kz = tile_planes >= 16LL * std::max(nsm, 1) ? 0 : (s->nz <= 48 ? 8 : 16);
   return icm_plan{1, 1, kz, 1, 0};
 }
 
@@ -1119,7 +1126,8 @@ icm_status icm_get_plan(const icm_sim* s, icm_plan* out) {
 
 icm_status icm_set_plan(icm_sim* s, const icm_plan* plan) {
   if (!s || !plan) return fail(ICM_EINVAL, "NULL argument");
-  if (plan->rhs_kz < 4 || plan->rhs_kz > 64) return fail(ICM_EINVAL, "rhs_kz must be in 4..64");
+  if (plan->rhs_kz != 0 && (plan->rhs_kz < 4 || plan->rhs_kz > 64))
+    return fail(ICM_EINVAL, "rhs_kz must be 0 (persistent) or in 4..64");
   s->plan = icm_plan{plan->fused_blobs ? 1 : 0, plan->tma_z ? 1 : 0, plan->rhs_kz, plan->fork ? 1 : 0,
                      plan->fused_xy ? 1 : 0};
   s->plan_src = 2;
@@ -1165,7 +1173,7 @@ icm_status icm_autotune(icm_sim* s, int32_t nsteps, icm_plan* chosen, double* ms
   std::vector<std::pair<int icm_plan::*, std::vector<int>>> knobs;
   if (s->fused) knobs.push_back({&icm_plan::fused_blobs, {1, 0}});
   if (s->has_zmap) knobs.push_back({&icm_plan::tma_z, {1, 0}});
-  knobs.push_back({&icm_plan::rhs_kz, {8, 16, 32}});
+  knobs.push_back({&icm_plan::rhs_kz, {0, 8, 16, 32}});
   knobs.push_back({&icm_plan::fork, {1, 0}});
   if (fft_has_xy_passes(s->prec, s->nx, s->ny)) knobs.push_back({&icm_plan::fused_xy, {0, 1}});
   for (size_t k = 0; st == ICM_OK && k < knobs.size(); ++k)
@@ -1901,7 +1909,7 @@ icm_status icm_batch_autotune(icm_batch* b, int32_t nsteps) {
   double best_ms = 0.0;
   icm_status st = trial(best, best_grouped, best_ms);
   const std::vector<std::pair<int icm_plan::*, std::vector<int>>> knobs = {
-      {&icm_plan::fused_blobs, {1, 0}}, {&icm_plan::tma_z, {1, 0}}, {&icm_plan::rhs_kz, {4, 8, 16, 32}},
+      {&icm_plan::fused_blobs, {1, 0}}, {&icm_plan::tma_z, {1, 0}}, {&icm_plan::rhs_kz, {0, 4, 8, 16, 32}},
       {&icm_plan::fork, {1, 0}}, {&icm_plan::fused_xy, {0, 1}}};
   for (size_t k = 0; st == ICM_OK && k < knobs.size(); ++k)
     for (int val : knobs[k].second) {
@@ -1929,7 +1937,7 @@ icm_status icm_batch_autotune(icm_batch* b, int32_t nsteps) {
       best_ms = ms;
       // the RHS march again: in grouped steps every member's RHS precedes the first
       // group solve, so its latency counts where before it overlapped other members
-      for (int kz : {4, 8, 16, 32}) {
+      for (int kz : {0, 4, 8, 16, 32}) {
         if (kz == best.rhs_kz || st != ICM_OK) continue;
         icm_plan q = best;
         q.rhs_kz = kz;

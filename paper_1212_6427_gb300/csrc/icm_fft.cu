@@ -766,7 +766,12 @@ __global__ void __launch_bounds__(kThreads) k_ypass2(cplx_t<R>* __restrict__ spe
   C* tw = buf + ZB * N * NL;
   const int tid = threadIdx.x;
   load_stage_twiddles<R, R1, R2>(tw, gtw, tid, kThreads);
-  const int kx0 = blockIdx.x * NL, z0 = blockIdx.y * ZB, comp = blockIdx.z % 3;
+  // The forward pass walks the spectrum backwards (last component, last z planes, last
+  // columns first): the x pass before it wrote those last, so the first blocks find
+  // them in L2.  The inverse pass walks forwards.
+  const int bx = INV ? blockIdx.x : gridDim.x - 1 - blockIdx.x;
+  const int by = INV ? blockIdx.y : gridDim.y - 1 - blockIdx.y;
+  const int kx0 = bx * NL, z0 = by * ZB, comp = INV ? blockIdx.z % 3 : 2 - blockIdx.z % 3;
   // plane z0 + zb of the component, columns kx0..
   C* base0 = spec + ((size_t)(comp * nz + z0) * N) * kxp + kx0;
   const C zero = mk(R(0), R(0));
@@ -1062,8 +1067,11 @@ __global__ void __launch_bounds__(kThreads, xi2_lean<R, N, MODE>() ? 4 : 1) k_xi
   C* tw = buf + L * xrow(N);
   const int tid = threadIdx.x;
   load_stage_twiddles<R, R1, R2>(tw, gtw, tid, kThreads);
-  const int comp = blockIdx.y % 3;
-  const long long row0 = (long long)blockIdx.x * (2 * L);
+  // Rows are taken backwards (last component, last row blocks first): the inverse y pass
+  // before this one wrote them last, so the first blocks find them in L2.
+  const int comp = 2 - blockIdx.y % 3;
+  const int bx = gridDim.x - 1 - blockIdx.x;
+  const long long row0 = (long long)bx * (2 * L);
   const C* in = spec + (size_t)comp * nrows * kxp;
   const C zero = mk(R(0), R(0));
   const size_t cb = (size_t)comp * ncell;
@@ -1104,8 +1112,8 @@ __global__ void __launch_bounds__(kThreads, xi2_lean<R, N, MODE>() ? 4 : 1) k_xi
     // the gathers' records: staged by cp.async while the spectrum loads are in flight
     if (GATHER && j0 == 0) {
       StagedTask<R>* stage = reinterpret_cast<StagedTask<R>*>(smem_raw + stage_offset<R, N>());
-      g0 = rb.start[blockIdx.x];
-      ge = rb.start[blockIdx.x + 1];
+      g0 = rb.start[bx];
+      ge = rb.start[bx + 1];
       if (tid < min(ge - g0, NST))
         stage_task<R>(&stage[tid], reinterpret_cast<const BlobStencil<R>*>(rb.geo), rb.list[g0 + tid], comp, nullptr);
       cp_async_commit();

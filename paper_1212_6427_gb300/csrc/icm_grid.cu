@@ -6,6 +6,8 @@
 //     centred conservative (skew-adjoint) form, Adams-Bashforth in time
 //     (Eq. Adams_Bashforth).  A^n overwrites A^{n-1} in place.
 //   * FP64 compensated sums of face fields (momentum bookkeeping, Sec. II).
+#include <algorithm>
+
 #include "icm_internal.h"
 
 namespace icm {
@@ -13,125 +15,144 @@ namespace {
 
 constexpr int TX = 32, TY = 16;     // cells per block in x and y (one thread each)
 constexpr int HX = TX + 2, HY = TY + 2;
-constexpr int HALO = HX * HY;       // cells of one plane with a one-cell halo
 constexpr int NT = TX * TY;         // threads per block
-constexpr int PER = (HALO + NT - 1) / NT;   // halo cells loaded per thread
+constexpr int NHALO = 2 * HX + 2 * TY;   // ring of halo cells around the TX x TY tile
 
 __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+// Periodic index for any i (a tile can be several times wider than a short side).
+__device__ __forceinline__ int wrapm(int i, int n) { return ((i % n) + n) % n; }
 
-// Shared-memory rings of the marching block: velocity planes of the three components
-// and planes of the six stress normals, each with a one-cell halo in x and y.  Plane k
-// reads slots k-1, k, k+1 and writes k+2 (mod 4): with four slots the slot it writes
-// was last read by plane k-2, which every thread has finished when it passes plane
-// k's first barrier, so one barrier per plane suffices.
-constexpr int kRing = 4;
+// Shared memory of the marching block.
+//  * v: a ring of four velocity planes (three components, one-cell halo in x and y).
+//    At plane k the block reads slots of planes k-1, k, k+1 and writes plane k+1's slot
+//    before its barrier; that slot was last read by plane k-3, long finished.
+//  * z: a ring of three planes of the stress normals that neighbours read (Z_xx, Z_yy,
+//    Z_xy, Z_xz, Z_yz; Z_zz is only read by its own cell).  The normals of plane k+1
+//    are written before plane k's barrier and read after plane k+1's; the slot was last
+//    read at plane k-2.  Each thread keeps its own cell's normals in registers.
+constexpr int kRing = 4, kZRing = 3;
 template <typename R>
 struct RhsSmem {
   R v[kRing][3][HY][HX];
-  R z[kRing][6][HY][HX];
+  R z[kZRing][5][HY][HX];
 };
 
-// One plane of stress normals (with halo) into ring slot `slot`.  Each thread first
-// draws the normals of its own cell (no divergence), then the first HALO - NT threads
-// draw the halo cells, computing only what their neighbours read: x-1 needs Z_xx,
-// y-1 Z_yy, x+1 Z_xy and Z_xz, y+1 Z_xy and Z_yz; the corners nothing.
-constexpr int NHALO = 2 * HX + 2 * TY;   // ring of halo cells around the TX x TY tile
+// Halo cell h (0 <= h < NHALO) of the tile as (hx, hy) in the padded plane:
+// bottom row, top row, left column, right column.
+__device__ __forceinline__ void halo_cell(int h, int& hx, int& hy) {
+  if (h < HX) {
+    hx = h;
+    hy = 0;
+  } else if (h < 2 * HX) {
+    hx = h - HX;
+    hy = HY - 1;
+  } else if (h < 2 * HX + TY) {
+    hx = 0;
+    hy = 1 + (h - 2 * HX);
+  } else {
+    hx = HX - 1;
+    hy = 1 + (h - 2 * HX - TY);
+  }
+}
 
+// Which halo cell of the tile, if any, thread (warp, lane) draws the stress normals of:
+// warps are given one kind of halo cell each so that none diverges.  Warp 0 takes the
+// bottom row (whose Z_yy the row above reads) and warp 1 the left column (Z_xx), both
+// from the first Box-Muller pair of call 0; warps 2 and 3 the top row (Z_xy, Z_yz) and
+// warp 4 the right column (Z_xy, Z_xz), from the second pair of call 0 and the first of
+// call 1.  The corners are read by no one.  Returns 0 (none), 1 or 2 (the two kinds).
+__device__ __forceinline__ int halo_noise_cell(int warp, int lane, int& hx, int& hy) {
+  if (warp == 0) {
+    hx = 1 + lane;
+    hy = 0;
+    return 1;
+  }
+  if (warp == 1 && lane < TY) {
+    hx = 0;
+    hy = 1 + lane;
+    return 1;
+  }
+  if ((warp == 2 || warp == 3) && lane < 16) {
+    hx = 1 + (warp - 2) * 16 + lane;
+    hy = HY - 1;
+    return 2;
+  }
+  if (warp == 4 && lane < TY) {
+    hx = HX - 1;
+    hy = 1 + lane;
+    return 2;
+  }
+  return 0;
+}
+
+// The normals of halo cell `cell` (its flat index in plane kk) that neighbours read,
+// into slot `slot` of the z ring at (hx, hy).
 template <typename R>
-__device__ __forceinline__ void gen_plane(RhsSmem<R>& sm, int slot, int i0, int j0, int k, const GridParams& g,
-                                          uint32_t step, int tid) {
-  const int kk = wrapi(k, g.nz);
-  {
-    const int tx = tid % TX, ty = tid / TX;
-    const int gi = wrapi(i0 + tx, g.nx), gj = wrapi(j0 + ty, g.ny);
-    R z[6];
-    cell_normals<R>((uint32_t)(gi + g.nx * (gj + g.ny * kk)), step, g.key0, g.key1, z);
-#pragma unroll
-    for (int c = 0; c < 6; ++c) sm.z[slot][c][ty + 1][tx + 1] = z[c];
-  }
-  for (int h = tid; h < NHALO; h += NT) {
-    int hx, hy;
-    if (h < HX) {                 // bottom row y = -1
-      hx = h;
-      hy = 0;
-    } else if (h < 2 * HX) {      // top row y = TY
-      hx = h - HX;
-      hy = HY - 1;
-    } else if (h < 2 * HX + TY) { // left column x = -1
-      hx = 0;
-      hy = 1 + (h - 2 * HX);
-    } else {                      // right column x = TX
-      hx = HX - 1;
-      hy = 1 + (h - 2 * HX - TY);
-    }
-    const bool xl = hx == 0, xr = hx == HX - 1, yl = hy == 0, yr = hy == HY - 1;
-    if ((xl || xr) && (yl || yr)) continue;
-    const int gi = wrapi(i0 - 1 + hx, g.nx), gj = wrapi(j0 - 1 + hy, g.ny);
-    R z[6];
-    cell_normals_masked<R>((uint32_t)(gi + g.nx * (gj + g.ny * kk)), step, g.key0, g.key1, z, xl || yl, xr || yr,
-                           xr || yr);
-#pragma unroll
-    for (int c = 0; c < 6; ++c) sm.z[slot][c][hy][hx] = z[c];
+__device__ __forceinline__ void gen_halo(RhsSmem<R>& sm, int slot, int kind, uint32_t cell, int hx, int hy,
+                                         const GridParams& g, uint32_t step) {
+  if (kind == 1) {
+    const u32x4 a = philox4x32_10(u32x4{cell, step, 0u, 0u}, g.key0, g.key1);
+    R zxx, zyy;
+    BoxMuller<R>::apply(a.x, a.y, zxx, zyy);
+    sm.z[slot][0][hy][hx] = zxx;
+    sm.z[slot][1][hy][hx] = zyy;
+  } else if (kind == 2) {
+    const u32x4 a = philox4x32_10(u32x4{cell, step, 0u, 0u}, g.key0, g.key1);
+    const u32x4 b = philox4x32_10(u32x4{cell, step, 1u, 0u}, g.key0, g.key1);
+    R zzz, zxy, zxz, zyz;
+    BoxMuller<R>::apply(a.z, a.w, zzz, zxy);
+    BoxMuller<R>::apply(b.x, b.y, zxz, zyz);
+    sm.z[slot][2][hy][hx] = zxy;
+    sm.z[slot][3][hy][hx] = zxz;
+    sm.z[slot][4][hy][hx] = zyz;
   }
 }
 
-// Plane offsets (x + Nx y, wrapped) of the halo cells thread tid loads: cells tid,
-// tid + NT, ... of the (TX+2) x (TY+2) plane; -1 past the plane.
-__device__ __forceinline__ void plane_offsets(int (&off)[PER], int i0, int j0, const GridParams& g, int tid) {
-#pragma unroll
-  for (int t = 0; t < PER; ++t) {
-    const int idx = tid + t * NT;
-    const int hx = idx % HX, hy = idx / HX;
-    off[t] = idx < HALO ? wrapi(i0 - 1 + hx, g.nx) + g.nx * wrapi(j0 - 1 + hy, g.ny) : -1;
-  }
-}
-
-// Global loads of one velocity plane (with halo) into registers.
+// The own cell's normals of plane kk into z[] (registers) and the five that neighbours
+// read into slot `slot` of the z ring.
 template <typename R>
-__device__ __forceinline__ void load_plane(R (&r)[PER][3], const R* __restrict__ v, const int (&off)[PER], int k,
-                                           const GridParams& g) {
-  const long long zo = (long long)g.nx * g.ny * wrapi(k, g.nz);
-#pragma unroll
-  for (int t = 0; t < PER; ++t) {
-    if (off[t] >= 0) {
-      const R* p = v + zo + off[t];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) r[t][c] = p[c * g.ncell];
-    }
-  }
+__device__ __forceinline__ void gen_own(RhsSmem<R>& sm, int slot, R (&z)[6], uint32_t cell, const GridParams& g,
+                                        uint32_t step, int lx, int ly) {
+  cell_normals<R>(cell, step, g.key0, g.key1, z);
+  sm.z[slot][0][ly][lx] = z[0];
+  sm.z[slot][1][ly][lx] = z[1];
+  sm.z[slot][2][ly][lx] = z[3];
+  sm.z[slot][3][ly][lx] = z[4];
+  sm.z[slot][4][ly][lx] = z[5];
 }
 
-// The loaded plane into ring slot `slot` (the plane's cells are stored in load order).
-template <typename R>
-__device__ __forceinline__ void store_plane(RhsSmem<R>& sm, int slot, const R (&r)[PER][3], int tid) {
-#pragma unroll
-  for (int t = 0; t < PER; ++t) {
-    const int idx = tid + t * NT;
-    if (idx < HALO) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) (&sm.v[slot][c][0][0])[idx] = r[t][c];
-    }
-  }
-}
-
-// Marching block: TX x TY cells per plane, g.kz planes (a plan choice).  Per plane: the loads of the
-// plane after next are issued first, the stress normals of the next plane are
-// generated while they are in flight, then the current plane is computed entirely
-// from shared memory.
+// Marching block of TX x TY cells.  A block takes a contiguous range [lo, hi) of
+// tile-planes w = tile * nz + k (tiles x-fastest): with g.kz > 0 the range is the kz
+// planes of one tile (grid = tiles x ceil(nz / kz)); with g.kz == 0 the blocks are
+// persistent, the grid holds two per SM and the ranges split all tile-planes evenly.
+// A range is marched tile by tile; each run starts with a prologue of two planes.  Per
+// plane: the global loads of the plane after next are issued first, the stress normals
+// of the next plane are drawn while they are in flight, then the plane is computed from
+// the thread's registers (its own column) and shared memory (its neighbours).
 template <typename R, bool NOISE>
-__global__ void __launch_bounds__(NT, 2) k_rhs(const R* __restrict__ v, R* __restrict__ adv, R* __restrict__ rhs,
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_rhs(const R* __restrict__ v, R* __restrict__ adv,
+                                                                      R* __restrict__ rhs,
                                             GridParams g, const long long* __restrict__ step_dev,
                                             const int* __restrict__ hist_dev) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RhsSmem<R>& sm = *reinterpret_cast<RhsSmem<R>*>(smem_raw);
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int tid = tx + TX * ty;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * g.kz;
-  const int i = i0 + tx, j = j0 + ty;
-  const bool active = i < g.nx && j < g.ny;
+  const int tid = tx + TX * ty, warp = tid >> 5, lane = tid & 31;
+  const int ntx = (g.nx + TX - 1) / TX, nty = (g.ny + TY - 1) / TY;
+  long long lo, hi;
+  if (g.kz > 0) {
+    const long long tile = blockIdx.x + (long long)ntx * blockIdx.y;
+    lo = tile * g.nz + (long long)blockIdx.z * g.kz;
+    hi = min(lo + g.kz, (tile + 1) * g.nz);
+  } else {
+    const long long total = (long long)ntx * nty * g.nz;
+    lo = total * blockIdx.x / gridDim.x;
+    hi = total * (blockIdx.x + 1) / gridDim.x;
+  }
   const uint32_t step = (uint32_t)(*step_dev);
   const bool hist = *hist_dev != 0;
   const long long nc = g.ncell;
+  const long long plane = (long long)g.nx * g.ny;
   const R rho = (R)g.rho, inv_h = (R)(1.0 / g.h), inv_h2 = (R)(1.0 / (g.h * g.h));
   const R rho_dt = (R)(g.rho / g.dt), half_eta = (R)(0.5 * g.eta);
   const double s_amp = sqrt(g.kT * g.eta / (g.h * g.h * g.h * g.dt));
@@ -140,96 +161,148 @@ __global__ void __launch_bounds__(NT, 2) k_rhs(const R* __restrict__ v, R* __res
   const R h2 = R(0.5);
   const int lx = tx + 1, ly = ty + 1;
 
-  R pre[PER][3];
-  int off[PER];
-  plane_offsets(off, i0, j0, g, tid);
-  load_plane<R>(pre, v, off, k0 - 1, g);
-  store_plane<R>(sm, 0, pre, tid);
-  load_plane<R>(pre, v, off, k0, g);
-  store_plane<R>(sm, 1, pre, tid);
-  load_plane<R>(pre, v, off, k0 + 1, g);
-  if (NOISE) {
-    gen_plane<R>(sm, 0, i0, j0, k0 - 1, g, step, tid);
-    gen_plane<R>(sm, 1, i0, j0, k0, g, step, tid);
-  }
-  const int kend = min(k0 + g.kz, g.nz);
-  for (int k = k0; k < kend; ++k) {
-    const int kk = k - k0;
-    const int sp = kk % kRing, sc = (kk + 1) % kRing, sn = (kk + 2) % kRing;
-    store_plane<R>(sm, sn, pre, tid);                       // plane k+1
-    long long o = 0;
-    R ao[3] = {R(0), R(0), R(0)};
-    if (active) {
-      o = i + (long long)g.nx * (j + (long long)g.ny * k);
-      if (hist) {
-        ao[0] = adv[o];
-        ao[1] = adv[nc + o];
-        ao[2] = adv[2 * nc + o];
-      }
+  for (long long w = lo; w < hi;) {
+    const long long tile = w / g.nz;
+    const int k0 = (int)(w - tile * g.nz);
+    const int kend = (int)min((long long)g.nz, k0 + (hi - w));
+    w += kend - k0;
+    const int i0 = (int)(tile % ntx) * TX, j0 = (int)(tile / ntx) * TY;
+    const int i = i0 + tx, j = j0 + ty;
+    const bool active = i < g.nx && j < g.ny;
+    // threads past a ragged edge hold the periodic images their neighbours read
+    const long long own = wrapm(i, g.nx) + (long long)g.nx * wrapm(j, g.ny);
+    // the halo cell whose velocities this thread loads, if any
+    int hx = 0, hy = 0;
+    long long hoff = -1;
+    if (tid < NHALO) {
+      halo_cell(tid, hx, hy);
+      hoff = wrapm(i0 - 1 + hx, g.nx) + (long long)g.nx * wrapm(j0 - 1 + hy, g.ny);
     }
-    if (k + 1 < kend) load_plane<R>(pre, v, off, k + 2, g);   // in flight during the noise
-    if (NOISE) gen_plane<R>(sm, sn, i0, j0, k + 1, g, step, tid);
+    // the halo cell whose stress normals this thread draws, if any
+    int nhx = 0, nhy = 0;
+    const int nkind = NOISE ? halo_noise_cell(warp, lane, nhx, nhy) : 0;
+    const uint32_t ncell =
+        nkind ? (uint32_t)(wrapm(i0 - 1 + nhx, g.nx) + g.nx * wrapm(j0 - 1 + nhy, g.ny)) : 0u;
+    auto load = [&](R (&o)[3], R (&hv)[3], int k) {
+      const long long zo = plane * wrapi(k, g.nz);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) o[c] = v[c * nc + zo + own];
+      if (hoff >= 0) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) hv[c] = v[c * nc + zo + hoff];
+      }
+    };
+    auto put = [&](int slot, const R (&o)[3], const R (&hv)[3]) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) sm.v[slot][c][ly][lx] = o[c];
+      if (hoff >= 0) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sm.v[slot][c][hy][hx] = hv[c];
+      }
+    };
+    // every thread is past the previous run's last plane before its slots are reused
     __syncthreads();
-    if (active) {
-      const auto P = sm.v[sp];
-      const auto C = sm.v[sc];
-      const auto N = sm.v[sn];
-      // component x
-      const R x_c = C[0][ly][lx], x_xp = C[0][ly][lx + 1], x_xm = C[0][ly][lx - 1];
-      const R x_yp = C[0][ly + 1][lx], x_ym = C[0][ly - 1][lx], x_zp = N[0][ly][lx], x_zm = P[0][ly][lx];
-      const R x_xpym = C[0][ly - 1][lx + 1], x_xpzm = P[0][ly][lx + 1];
-      // component y
-      const R y_c = C[1][ly][lx], y_xp = C[1][ly][lx + 1], y_xm = C[1][ly][lx - 1];
-      const R y_yp = C[1][ly + 1][lx], y_ym = C[1][ly - 1][lx], y_zp = N[1][ly][lx], y_zm = P[1][ly][lx];
-      const R y_ypxm = C[1][ly + 1][lx - 1], y_ypzm = P[1][ly + 1][lx];
-      // component z
-      const R z_c = C[2][ly][lx], z_xp = C[2][ly][lx + 1], z_xm = C[2][ly][lx - 1];
-      const R z_yp = C[2][ly + 1][lx], z_ym = C[2][ly - 1][lx], z_zp = N[2][ly][lx], z_zm = P[2][ly][lx];
-      const R z_zpxm = N[2][ly][lx - 1], z_zpym = N[2][ly - 1][lx];
-
-      // edge products ut_a ut_b at edge index e: ut_a = (v_a[e] + v_a[e-e_b])/2, ut_b = (v_b[e] + v_b[e-e_a])/2
-      const R exy_c = (x_c + x_ym) * h2 * ((y_c + y_xm) * h2);
-      const R exy_yp = (x_yp + x_c) * h2 * ((y_yp + y_ypxm) * h2);
-      const R exy_xp = (x_xp + x_xpym) * h2 * ((y_xp + y_c) * h2);
-      const R exz_c = (x_c + x_zm) * h2 * ((z_c + z_xm) * h2);
-      const R exz_zp = (x_zp + x_c) * h2 * ((z_zp + z_zpxm) * h2);
-      const R exz_xp = (x_xp + x_xpzm) * h2 * ((z_xp + z_c) * h2);
-      const R eyz_c = (y_c + y_zm) * h2 * ((z_c + z_ym) * h2);
-      const R eyz_zp = (y_zp + y_c) * h2 * ((z_zp + z_zpym) * h2);
-      const R eyz_yp = (y_yp + y_ypzm) * h2 * ((z_yp + z_c) * h2);
-      const R ubx_c = (x_xp + x_c) * h2, ubx_m = (x_c + x_xm) * h2;
-      const R uby_c = (y_yp + y_c) * h2, uby_m = (y_c + y_ym) * h2;
-      const R ubz_c = (z_zp + z_c) * h2, ubz_m = (z_c + z_zm) * h2;
-      const R ax = adv_on * rho * inv_h * (ubx_c * ubx_c - ubx_m * ubx_m + exy_yp - exy_c + exz_zp - exz_c);
-      const R ay = adv_on * rho * inv_h * (uby_c * uby_c - uby_m * uby_m + exy_xp - exy_c + eyz_zp - eyz_c);
-      const R az = adv_on * rho * inv_h * (ubz_c * ubz_c - ubz_m * ubz_m + exz_xp - exz_c + eyz_yp - eyz_c);
-      const R lapx = (x_xp + x_xm + x_yp + x_ym + x_zp + x_zm - R(6) * x_c) * inv_h2;
-      const R lapy = (y_xp + y_xm + y_yp + y_ym + y_zp + y_zm - R(6) * y_c) * inv_h2;
-      const R lapz = (z_xp + z_xm + z_yp + z_ym + z_zp + z_zm - R(6) * z_c) * inv_h2;
-      R fx = R(0), fy = R(0), fz = R(0);
+    R vp[3], vc[3], vn[3], vq[3], hq[3];   // own column: planes k-1, k, k+1, k+2; halo k+2
+    R zc[6], zn[6], zzp = R(0);            // own normals: plane k, plane k+1, Z_zz of k-1
+    load(vp, hq, k0 - 1);
+    put(0, vp, hq);
+    load(vc, hq, k0);
+    put(1, vc, hq);
+    load(vn, hq, k0 + 1);
+    if (NOISE) {
+      // plane k0-1: only the own cell's Z_zz is read; plane k0 into slot 1
+      cell_normals<R>((uint32_t)(own + plane * wrapi(k0 - 1, g.nz)), step, g.key0, g.key1, zc);
+      zzp = zc[2];
+      gen_own<R>(sm, 1, zn, (uint32_t)(own + plane * k0), g, step, lx, ly);
+      gen_halo<R>(sm, 1, nkind, ncell + (uint32_t)(plane * k0), nhx, nhy, g, step);
+    }
+    for (int k = k0; k < kend; ++k) {
+      const int kk = k - k0;
+      const int sp = kk % kRing, sc = (kk + 1) % kRing, sn = (kk + 2) % kRing;
+      const int zs = (kk + 1) % kZRing, zsn = (kk + 2) % kZRing;   // normals of planes k, k+1
+      put(sn, vn, hq);                                         // plane k+1
+      long long o = 0;
+      R ao[3] = {R(0), R(0), R(0)};
+      if (active) {
+        o = own + plane * k;
+        if (hist) {
+          ao[0] = adv[o];
+          ao[1] = adv[nc + o];
+          ao[2] = adv[2 * nc + o];
+        }
+      }
+      if (k + 1 < kend) load(vq, hq, k + 2);                  // in flight during the noise
       if (NOISE) {
-        const auto ZC = sm.z[sc];
-        const auto ZP = sm.z[sp];
-        const auto ZN = sm.z[sn];
-        // divergence of the stress at the faces: Sigma_aa at cells, Sigma_ab on edges
-        fx = sd * (ZC[0][ly][lx] - ZC[0][ly][lx - 1]) + so * (ZC[3][ly + 1][lx] - ZC[3][ly][lx]) +
-             so * (ZN[4][ly][lx] - ZC[4][ly][lx]);
-        fy = sd * (ZC[1][ly][lx] - ZC[1][ly - 1][lx]) + so * (ZC[3][ly][lx + 1] - ZC[3][ly][lx]) +
-             so * (ZN[5][ly][lx] - ZC[5][ly][lx]);
-        fz = sd * (ZC[2][ly][lx] - ZP[2][ly][lx]) + so * (ZC[4][ly][lx + 1] - ZC[4][ly][lx]) +
-             so * (ZC[5][ly + 1][lx] - ZC[5][ly][lx]);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) zc[c] = zn[c];
+        const uint32_t pk = (uint32_t)(plane * wrapi(k + 1, g.nz));
+        gen_own<R>(sm, zsn, zn, (uint32_t)own + pk, g, step, lx, ly);
+        gen_halo<R>(sm, zsn, nkind, ncell + pk, nhx, nhy, g, step);
       }
-      if (!hist) {
-        ao[0] = ax;
-        ao[1] = ay;
-        ao[2] = az;
+      __syncthreads();
+      if (active) {
+        const auto P = sm.v[sp];
+        const auto C = sm.v[sc];
+        const auto N = sm.v[sn];
+        // component x
+        const R x_c = vc[0], x_xp = C[0][ly][lx + 1], x_xm = C[0][ly][lx - 1];
+        const R x_yp = C[0][ly + 1][lx], x_ym = C[0][ly - 1][lx], x_zp = vn[0], x_zm = vp[0];
+        const R x_xpym = C[0][ly - 1][lx + 1], x_xpzm = P[0][ly][lx + 1];
+        // component y
+        const R y_c = vc[1], y_xp = C[1][ly][lx + 1], y_xm = C[1][ly][lx - 1];
+        const R y_yp = C[1][ly + 1][lx], y_ym = C[1][ly - 1][lx], y_zp = vn[1], y_zm = vp[1];
+        const R y_ypxm = C[1][ly + 1][lx - 1], y_ypzm = P[1][ly + 1][lx];
+        // component z
+        const R z_c = vc[2], z_xp = C[2][ly][lx + 1], z_xm = C[2][ly][lx - 1];
+        const R z_yp = C[2][ly + 1][lx], z_ym = C[2][ly - 1][lx], z_zp = vn[2], z_zm = vp[2];
+        const R z_zpxm = N[2][ly][lx - 1], z_zpym = N[2][ly - 1][lx];
+
+        // edge products ut_a ut_b at edge index e: ut_a = (v_a[e] + v_a[e-e_b])/2, ut_b = (v_b[e] + v_b[e-e_a])/2
+        const R exy_c = (x_c + x_ym) * h2 * ((y_c + y_xm) * h2);
+        const R exy_yp = (x_yp + x_c) * h2 * ((y_yp + y_ypxm) * h2);
+        const R exy_xp = (x_xp + x_xpym) * h2 * ((y_xp + y_c) * h2);
+        const R exz_c = (x_c + x_zm) * h2 * ((z_c + z_xm) * h2);
+        const R exz_zp = (x_zp + x_c) * h2 * ((z_zp + z_zpxm) * h2);
+        const R exz_xp = (x_xp + x_xpzm) * h2 * ((z_xp + z_c) * h2);
+        const R eyz_c = (y_c + y_zm) * h2 * ((z_c + z_ym) * h2);
+        const R eyz_zp = (y_zp + y_c) * h2 * ((z_zp + z_zpym) * h2);
+        const R eyz_yp = (y_yp + y_ypzm) * h2 * ((z_yp + z_c) * h2);
+        const R ubx_c = (x_xp + x_c) * h2, ubx_m = (x_c + x_xm) * h2;
+        const R uby_c = (y_yp + y_c) * h2, uby_m = (y_c + y_ym) * h2;
+        const R ubz_c = (z_zp + z_c) * h2, ubz_m = (z_c + z_zm) * h2;
+        const R ax = adv_on * rho * inv_h * (ubx_c * ubx_c - ubx_m * ubx_m + exy_yp - exy_c + exz_zp - exz_c);
+        const R ay = adv_on * rho * inv_h * (uby_c * uby_c - uby_m * uby_m + exy_xp - exy_c + eyz_zp - eyz_c);
+        const R az = adv_on * rho * inv_h * (ubz_c * ubz_c - ubz_m * ubz_m + exz_xp - exz_c + eyz_yp - eyz_c);
+        const R lapx = (x_xp + x_xm + x_yp + x_ym + x_zp + x_zm - R(6) * x_c) * inv_h2;
+        const R lapy = (y_xp + y_xm + y_yp + y_ym + y_zp + y_zm - R(6) * y_c) * inv_h2;
+        const R lapz = (z_xp + z_xm + z_yp + z_ym + z_zp + z_zm - R(6) * z_c) * inv_h2;
+        R fx = R(0), fy = R(0), fz = R(0);
+        if (NOISE) {
+          const auto Z = sm.z[zs];   // plane k: [0] xx, [1] yy, [2] xy, [3] xz, [4] yz
+          // divergence of the stress at the faces: Sigma_aa at cells, Sigma_ab on edges
+          fx = sd * (zc[0] - Z[0][ly][lx - 1]) + so * (Z[2][ly + 1][lx] - zc[3]) + so * (zn[4] - zc[4]);
+          fy = sd * (zc[1] - Z[1][ly - 1][lx]) + so * (Z[2][ly][lx + 1] - zc[3]) + so * (zn[5] - zc[5]);
+          fz = sd * (zc[2] - zzp) + so * (Z[3][ly][lx + 1] - zc[4]) + so * (Z[4][ly + 1][lx] - zc[5]);
+        }
+        if (!hist) {
+          ao[0] = ax;
+          ao[1] = ay;
+          ao[2] = az;
+        }
+        adv[o] = ax;
+        adv[nc + o] = ay;
+        adv[2 * nc + o] = az;
+        rhs[o] = rho_dt * x_c + half_eta * lapx + fx - (R(1.5) * ax - R(0.5) * ao[0]);
+        rhs[nc + o] = rho_dt * y_c + half_eta * lapy + fy - (R(1.5) * ay - R(0.5) * ao[1]);
+        rhs[2 * nc + o] = rho_dt * z_c + half_eta * lapz + fz - (R(1.5) * az - R(0.5) * ao[2]);
       }
-      adv[o] = ax;
-      adv[nc + o] = ay;
-      adv[2 * nc + o] = az;
-      rhs[o] = rho_dt * x_c + half_eta * lapx + fx - (R(1.5) * ax - R(0.5) * ao[0]);
-      rhs[nc + o] = rho_dt * y_c + half_eta * lapy + fy - (R(1.5) * ay - R(0.5) * ao[1]);
-      rhs[2 * nc + o] = rho_dt * z_c + half_eta * lapz + fz - (R(1.5) * az - R(0.5) * ao[2]);
+      if (NOISE) zzp = zc[2];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        vp[c] = vc[c];
+        vc[c] = vn[c];
+        vn[c] = vq[c];
+      }
     }
   }
 }
@@ -347,8 +420,27 @@ size_t rhs_smem() { return sizeof(RhsSmem<R>); }
 template <typename R>
 void explicit_rhs(const GridParams& g, const R* v, R* adv, R* rhs, const long long* step_dev, const int* hist_dev,
                   cudaStream_t st) {
-  const dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + g.kz - 1) / g.kz);
   const dim3 block(TX, TY);
+  dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, 1);
+  if (g.kz > 0) {
+    grid.z = (g.nz + g.kz - 1) / g.kz;
+  } else {
+    // persistent: as many blocks as the SMs hold at once, never more than tile-planes
+    static int resident[2] = {0, 0};
+    int& res = resident[sizeof(R) == 4 ? 0 : 1];
+    if (res == 0) {
+      int dev = 0, nsm = 0, per = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      if (g.kT > 0.0)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rhs<R, true>, NT, rhs_smem<R>());
+      else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rhs<R, false>, NT, rhs_smem<R>());
+      res = std::max(1, nsm) * std::max(1, per);
+    }
+    const long long total = (long long)grid.x * grid.y * g.nz;
+    grid = dim3((unsigned)std::min<long long>(res, total), 1, 1);
+  }
   if (g.kT > 0.0)
     k_rhs<R, true><<<grid, block, rhs_smem<R>(), st>>>(v, adv, rhs, g, step_dev, hist_dev);
   else

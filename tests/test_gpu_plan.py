@@ -23,6 +23,7 @@ PLANS = [
     dict(fused_blobs=0, tma_z=1, rhs_kz=16, fork=1, fused_xy=1),     # separate blob kernels on a fused-capable side
     dict(fused_blobs=1, tma_z=0, rhs_kz=8, fork=0, fused_xy=0),      # one block per z tile, short RHS march
     dict(fused_blobs=0, tma_z=0, rhs_kz=32, fork=0, fused_xy=0),
+    dict(fused_blobs=1, tma_z=1, rhs_kz=0, fork=1, fused_xy=0),      # persistent RHS blocks
     dict(fused_blobs=1, tma_z=1, rhs_kz=4, fork=1, fused_xy=0),
 ]
 
@@ -70,7 +71,7 @@ def test_autotune_keeps_the_state_and_shares_its_plan():
     sim.step(2)
     before = sim.read(fluid=True)
     plan, ms = icm.icm_autotune(sim.handle, 2)
-    assert ms > 0 and 4 <= plan["rhs_kz"] <= 64
+    assert ms > 0 and (plan["rhs_kz"] == 0 or 4 <= plan["rhs_kz"] <= 64)
     after = sim.read(fluid=True)
     for k in ("pos", "vel", "fluid", "momentum"):
         np.testing.assert_array_equal(before[k], after[k])
