@@ -357,10 +357,17 @@ icm_status icm_batch_step(icm_batch* batch, int64_t nsteps);
  * member's own stencil and blob kernels run on its stream; members take the separate
  * (unfused) blob path and the plain z pass.  A grid whose sides lack register FFT
  * passes, or that only one member has, runs its step as usual.  Results agree with
- * ungrouped steps to rounding.  Synchronises when the setting changes.
- * Errors: ICM_EINVAL for grouped other than 0 or 1. */
+ * ungrouped steps to rounding.
+ * Batched stages (grouped = 2): the group solves as above, and every other stage of the
+ * step (scalar bookkeeping, predictor, right-hand side, spreads, momentum change,
+ * inertial update, finish) as one launch over all members, whatever their grids and
+ * blob counts, through device tables of the members; about a dozen launches plus the
+ * group solves per step.  Needs one precision for all members, register FFT passes
+ * along every axis of every grid, and no WCA pair forces or thermal drift; otherwise
+ * the batch runs as with grouped = 1.  Synchronises when the setting changes.
+ * Errors: ICM_EINVAL for grouped other than 0, 1 or 2. */
 icm_status icm_batch_set_grouped(icm_batch* batch, int32_t grouped);
-/* The current setting (0 or 1), -1 for a NULL batch. */
+/* The current setting (0, 1 or 2), -1 for a NULL batch. */
 int32_t icm_batch_get_grouped(const icm_batch* batch);
 /* Kernel launches in one batch step of the captured graph (the graph is captured by
  * the first icm_batch_step after a change); -1 before a capture or for NULL. */
@@ -368,7 +375,8 @@ int64_t icm_batch_kernels_per_step(const icm_batch* batch);
 
 /* Autotune the batch as a whole: candidate plans (one choice at a time, as
  * icm_autotune) are applied to every member and timed over nsteps batch steps,
- * then group solves (icm_batch_set_grouped) with that plan; every member's state is
+ * then group solves and batched stages (icm_batch_set_grouped 1, 2) with that plan;
+ * every member's state is
  * restored after each trial and the fastest choice is fixed on the batch and all
  * members.  Synchronises.  Errors: as icm_autotune. */
 icm_status icm_batch_autotune(icm_batch* batch, int32_t nsteps);

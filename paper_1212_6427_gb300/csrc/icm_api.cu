@@ -1549,10 +1549,11 @@ struct icm_batch {
   std::vector<cudaEvent_t> events;  // fork, joins, ..., done (last)
   cudaGraphExec_t gexec = nullptr;
   bool ok = false;
-  int grouped = 0;
+  int grouped = 0;                     // 0 members apart, 1 group solves, 2 group solves + batched stages
   long long kernels = -1;              // kernel nodes of the captured step graph
   std::vector<cudaStream_t> gstreams;  // one per group of the last capture
   void* reps = nullptr;                // device tables of the group solves
+  void* stage_tables = nullptr;        // device member tables of the batched stages
 };
 
 namespace {
@@ -1565,6 +1566,21 @@ void batch_clear_graph(icm_batch* b) {
   b->events.clear();
   if (b->reps) cudaFree(b->reps);
   b->reps = nullptr;
+  if (b->stage_tables) cudaFree(b->stage_tables);
+  b->stage_tables = nullptr;
+}
+
+// Whether every member can run in a batch of batched stages: one precision, register
+// FFT passes along every axis (group solves), no pair forces and no thermal drift (the
+// stages that have no batched form).
+bool stages_possible(const icm_batch* b) {
+  if (b->sims.empty()) return false;
+  for (const icm_sim* s : b->sims) {
+    if (s->prec != b->sims[0]->prec || !fft_has_group_passes(s->nx, s->ny, s->nz)) return false;
+    if ((s->wca_eps > 0.0 && s->nb > 1) || ((s->flags & ICM_FLAG_THERMAL_DRIFT) && s->kT > 0.0 && s->nb > 0))
+      return false;
+  }
+  return true;
 }
 
 struct SolveGroup {
@@ -1614,8 +1630,181 @@ void group_solve(const SolveGroup& g, const RepFft* reps, int rt, cudaStream_t s
                           rt == 2 ? OUT_ADD_AND_STORE2 : OUT_STORE, st);
 }
 
+// The step of every member as batched stages: each stage of the per-member sequence
+// (scalars, predictor, right-hand side, spreads, momentum change, inertial update,
+// finish) is one launch over all members, found through device member tables; the
+// three solves are group solves, one set of launches per grid, the groups side by side
+// on their own streams.  Members with excess mass take part in the second and third
+// solves and the stages between them.
+template <typename R>
+icm_status batch_capture_stages(icm_batch* b) {
+  const size_t n = b->sims.size();
+  // groups: members on the same grid (a group may hold one member)
+  std::vector<SolveGroup> groups;
+  for (icm_sim* s : b->sims) {
+    size_t gi = 0;
+    while (gi < groups.size() && !same_grid(groups[gi].members[0], s)) ++gi;
+    if (gi == groups.size()) groups.emplace_back();
+    groups[gi].members.push_back(s);
+    if (s->any_me) groups[gi].inertial.push_back(s);
+  }
+  std::vector<RepFft> reps_host;
+  for (SolveGroup& g : groups)
+    for (int rt = 0; rt < 3; ++rt) {
+      g.table[rt] = reps_host.size();
+      for (icm_sim* m : rt == 0 ? g.members : g.inertial) reps_host.push_back(rep_entry(m, rt));
+    }
+  // member tables: all members and the inertial ones (blob stages), and the RHS table
+  // (members with noise first, then those without)
+  std::vector<BlobMember> all, inert;
+  std::vector<int> mof_all, mof_in;
+  long long ncell_in = 0;
+  for (icm_sim* s : b->sims) {
+    BlobMember m;
+    m.p = blob_params(s);
+    m.s = blob_state(s);
+    m.v = s->v;
+    m.work = s->work;
+    m.fvec = s->nb == 0 ? nullptr : (s->trap_k != 0.0 ? s->fe : (s->any_force ? s->f : nullptr));
+    m.step_dev = s->step_dev;
+    m.hist_dev = s->hist_dev;
+    m.inertial = s->any_me ? 1 : 0;
+    m.b0 = (long long)mof_all.size();
+    for (long long i = 0; i < s->nb; ++i) mof_all.push_back((int)all.size());
+    all.push_back(m);
+    if (s->any_me) {
+      m.b0 = (long long)mof_in.size();
+      for (long long i = 0; i < s->nb; ++i) mof_in.push_back((int)inert.size());
+      inert.push_back(m);
+      ncell_in = std::max(ncell_in, s->ncell);
+    }
+  }
+  std::vector<RhsMember<R>> rhs_noise, rhs_quiet;
+  long long tot_noise = 0, tot_quiet = 0;
+  for (icm_sim* s : b->sims) {
+    RhsMember<R> r;
+    r.g = grid_params(s);
+    r.g.kz = 0;
+    r.v = (const R*)s->v;
+    r.adv = (R*)s->adv;
+    r.rhs = (R*)s->work;
+    r.step_dev = s->step_dev;
+    r.hist_dev = s->hist_dev;
+    long long& tot = s->kT > 0.0 ? tot_noise : tot_quiet;
+    r.w0 = tot;
+    tot += rhs_tile_planes(s->nx, s->ny, s->nz);
+    (s->kT > 0.0 ? rhs_noise : rhs_quiet).push_back(r);
+  }
+  bool any_force = false;
+  for (const BlobMember& m : all) any_force |= m.fvec != nullptr;
+  // one device allocation for every table, each part 256-byte aligned
+  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  const size_t o_all = 0, o_in = o_all + al(all.size() * sizeof(BlobMember));
+  const size_t o_mall = o_in + al(inert.size() * sizeof(BlobMember));
+  const size_t o_min = o_mall + al(mof_all.size() * sizeof(int));
+  const size_t o_rn = o_min + al(mof_in.size() * sizeof(int));
+  const size_t o_rq = o_rn + al(rhs_noise.size() * sizeof(RhsMember<R>));
+  const size_t o_reps = o_rq + al(rhs_quiet.size() * sizeof(RhsMember<R>));
+  const size_t total_bytes = o_reps + al(reps_host.size() * sizeof(RepFft)) + 256;
+  ICM_CK(cudaMalloc(&b->stage_tables, total_bytes));
+  unsigned char* base = (unsigned char*)b->stage_tables;
+  auto put = [&](size_t off, const void* src, size_t bytes) -> cudaError_t {
+    return bytes ? cudaMemcpy(base + off, src, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
+  };
+  ICM_CK(put(o_all, all.data(), all.size() * sizeof(BlobMember)));
+  ICM_CK(put(o_in, inert.data(), inert.size() * sizeof(BlobMember)));
+  ICM_CK(put(o_mall, mof_all.data(), mof_all.size() * sizeof(int)));
+  ICM_CK(put(o_min, mof_in.data(), mof_in.size() * sizeof(int)));
+  ICM_CK(put(o_rn, rhs_noise.data(), rhs_noise.size() * sizeof(RhsMember<R>)));
+  ICM_CK(put(o_rq, rhs_quiet.data(), rhs_quiet.size() * sizeof(RhsMember<R>)));
+  ICM_CK(put(o_reps, reps_host.data(), reps_host.size() * sizeof(RepFft)));
+  const BlobMember* d_all = (const BlobMember*)(base + o_all);
+  const BlobMember* d_in = (const BlobMember*)(base + o_in);
+  const int* d_mall = (const int*)(base + o_mall);
+  const int* d_min = (const int*)(base + o_min);
+  const RhsMember<R>* d_rn = (const RhsMember<R>*)(base + o_rn);
+  const RhsMember<R>* d_rq = (const RhsMember<R>*)(base + o_rq);
+  const RepFft* d_reps = (const RepFft*)(base + o_reps);
+  while (b->gstreams.size() < groups.size()) {
+    cudaStream_t gs = nullptr;
+    ICM_CK(cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking));
+    b->gstreams.push_back(gs);
+  }
+  // events (created before the capture): into and out of every group solve, and the
+  // one icm_batch_step records after its launches
+  const size_t need = 2 * groups.size() * 3 + 1;
+  b->events.resize(need, nullptr);
+  for (auto& ev : b->events) ICM_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  size_t next_event = 0;
+  auto event = [&]() -> cudaEvent_t { return next_event < need ? b->events[next_event++] : nullptr; };
+  const long long nb_all = (long long)mof_all.size(), nb_in = (long long)mof_in.size();
+  const int n_all = (int)all.size(), n_in = (int)inert.size();
+  cudaStream_t st = b->stream;
+  auto solves = [&](int rt) {
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+      const std::vector<icm_sim*>& m = rt == 0 ? groups[gi].members : groups[gi].inertial;
+      cudaStream_t gs = b->gstreams[gi];
+      cudaEvent_t in = event(), out = event();
+      if (m.empty()) continue;
+      cudaEventRecord(in, st);
+      cudaStreamWaitEvent(gs, in, 0);
+      group_solve<R>(groups[gi], d_reps, rt, gs);
+      cudaEventRecord(out, gs);
+      cudaStreamWaitEvent(st, out, 0);
+    }
+  };
+  cudaGraph_t graph = nullptr;
+  ICM_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  batch_scalars_before(d_all, n_all, st);
+  batch_predict<R>(d_all, d_mall, nb_all, st);
+  batch_rhs<R>(d_rn, (int)rhs_noise.size(), tot_noise, true, st);
+  batch_rhs<R>(d_rq, (int)rhs_quiet.size(), tot_quiet, false, st);
+  if (any_force) batch_spread<R>(d_all, d_mall, nb_all, BV_FORCE, st);
+  solves(0);
+  if (n_in > 0) {
+    batch_dp<R>(d_in, d_min, nb_in, st);
+    batch_zero_work<R>(d_in, n_in, ncell_in, st);
+    batch_spread<R>(d_in, d_min, nb_in, BV_CDP, st);
+  }
+  solves(1);
+  if (n_in > 0) {
+    batch_inertial<R>(d_in, d_min, nb_in, st);
+    batch_zero_work<R>(d_in, n_in, ncell_in, st);
+    batch_spread<R>(d_in, d_min, nb_in, BV_SRC, st);
+  }
+  solves(2);
+  batch_finish<R>(d_all, d_mall, nb_all, st);
+  batch_scalars_after(d_all, n_all, st);
+  event();   // recorded after the launches of icm_batch_step
+  const cudaError_t e = cudaStreamEndCapture(st, &graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ICM_ECUDA, "batch graph capture failed: %s", cudaGetErrorString(e));
+  }
+  (void)n;
+  size_t nn = 0;
+  b->kernels = 0;
+  if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn > 0) {
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
+      for (size_t i = 0; i < nn; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++b->kernels;
+      }
+  }
+  const cudaError_t e2 = cudaGraphInstantiate(&b->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e2 != cudaSuccess) return fail(ICM_ECUDA, "batch graph instantiation failed: %s", cudaGetErrorString(e2));
+  b->versions.clear();
+  for (icm_sim* s : b->sims) b->versions.push_back(s->version);
+  b->ok = true;
+  return ICM_OK;
+}
+
 icm_status batch_capture(icm_batch* b) {
   batch_clear_graph(b);
+  if (b->grouped == 2 && stages_possible(b))
+    return b->sims[0]->prec == 32 ? batch_capture_stages<float>(b) : batch_capture_stages<double>(b);
   const size_t n = b->sims.size();
   // groups of two or more members on a grid with register FFT passes
   std::vector<SolveGroup> groups;
@@ -1848,7 +2037,7 @@ icm_status icm_batch_step(icm_batch* b, int64_t nsteps) {
 }
 
 icm_status icm_batch_set_grouped(icm_batch* b, int32_t grouped) {
-  if (!b || (grouped != 0 && grouped != 1)) return fail(ICM_EINVAL, "bad arguments");
+  if (!b || grouped < 0 || grouped > 2) return fail(ICM_EINVAL, "bad arguments");
   if (b->grouped != grouped) {
     if (b->stream) ICM_CK(cudaStreamSynchronize(b->stream));
     b->grouped = grouped;
@@ -1947,6 +2136,16 @@ icm_status icm_batch_autotune(icm_batch* b, int32_t nsteps) {
           best_ms = mq;
         }
       }
+    }
+  }
+  // batched stages: every per-member stage one launch over all members (the members'
+  // plans do not enter: the stages have their own launch shapes)
+  if (st == ICM_OK && stages_possible(b)) {
+    double ms = 0.0;
+    st = trial(best, 2, ms);
+    if (st == ICM_OK && ms < best_ms) {
+      best_grouped = 2;
+      best_ms = ms;
     }
   }
   cudaEventDestroy(e0);

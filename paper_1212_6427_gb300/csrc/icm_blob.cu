@@ -8,6 +8,8 @@
 //   spreading     (S F)_k = dV_f^-1 sum_i phi(q_i - r_k) F_i    (atomicAdd scatter)
 // Blob state (positions, velocities, masses, lagged slip terms) is FP64 in both
 // precision modes; only the grid values are R.
+#include <algorithm>
+
 #include "icm_internal.h"
 #include "icm_rows.cuh"
 
@@ -201,6 +203,36 @@ __device__ __forceinline__ double pick3(const double v[3], int a) { return a == 
 // With a harmonic trap (Sec. III.D), the force at q^{n+1/2}, F - k d (d to the nearest
 // image of the centre), goes to fe and dt times its trap part to the prescribed grid
 // sum K0 of the first solve (one atomic per block and component).
+// Blob b of the predictor, by one warp; returns (in lanes 0-2) the trap force component.
+template <typename R, int K>
+__device__ __forceinline__ double predict_blob(const BlobParams& p, const BlobState& s, const R* __restrict__ v,
+                                               long long b, int lane, WarpStencil<R, K>& S) {
+  double q[3], w0[3], qh[3], w1[3];
+  load3(s.q, b, q);
+  build_stencil<R, K>(S, q, p, false, lane);
+  gather<R, K>(S, v, p, lane, w0);
+  // every lane needs q^{n+1/2} for the second stencil; lanes 0-2 compute one axis each
+  const int ax = lane < 3 ? lane : 0;
+  const double mine = wrap_pos(fma(0.5 * p.dt, pick3(w0, ax), pick3(q, ax)), p.box[ax], p.inv_box[ax]);
+  for (int a = 0; a < 3; ++a) qh[a] = __shfl_sync(0xffffffffu, mine, a);
+  __syncwarp();
+  build_stencil<R, K>(S, qh, p, false, lane);
+  gather<R, K>(S, v, p, lane, w1);
+  if (lane == 0) {
+    store3(s.w0, b, w0);
+    store3(s.qh, b, qh);
+    store3(s.w1, b, w1);
+  }
+  double ftrap = 0.0;
+  if (p.trap_k != 0.0 && lane < 3) {
+    double d = mine - p.trap_c[lane];
+    d = fma(-p.box[lane], rint(d * p.inv_box[lane]), d);
+    ftrap = -p.trap_k * d;
+    s.fe[3 * b + lane] = s.f[3 * b + lane] + ftrap;
+  }
+  return ftrap;
+}
+
 template <typename R, int K>
 __global__ void __launch_bounds__(32 * kWarps) k_predict(BlobParams p, BlobState s, const R* __restrict__ v) {
   __shared__ WarpStencil<R, K> sten[kWarps];
@@ -208,31 +240,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_predict(BlobParams p, BlobState
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const long long b = (long long)blockIdx.x * kWarps + wid;
   double ftrap = 0.0;
-  if (b < s.nb) {
-    WarpStencil<R, K>& S = sten[wid];
-    double q[3], w0[3], qh[3], w1[3];
-    load3(s.q, b, q);
-    build_stencil<R, K>(S, q, p, false, lane);
-    gather<R, K>(S, v, p, lane, w0);
-    // every lane needs q^{n+1/2} for the second stencil; lanes 0-2 compute one axis each
-    const int ax = lane < 3 ? lane : 0;
-    const double mine = wrap_pos(fma(0.5 * p.dt, pick3(w0, ax), pick3(q, ax)), p.box[ax], p.inv_box[ax]);
-    for (int a = 0; a < 3; ++a) qh[a] = __shfl_sync(0xffffffffu, mine, a);
-    __syncwarp();
-    build_stencil<R, K>(S, qh, p, false, lane);
-    gather<R, K>(S, v, p, lane, w1);
-    if (lane == 0) {
-      store3(s.w0, b, w0);
-      store3(s.qh, b, qh);
-      store3(s.w1, b, w1);
-    }
-    if (p.trap_k != 0.0 && lane < 3) {
-      double d = mine - p.trap_c[lane];
-      d = fma(-p.box[lane], rint(d * p.inv_box[lane]), d);
-      ftrap = -p.trap_k * d;
-      s.fe[3 * b + lane] = s.f[3 * b + lane] + ftrap;
-    }
-  }
+  if (b < s.nb) ftrap = predict_blob<R, K>(p, s, v, b, lane, sten[wid]);
   if (p.trap_k == 0.0) return;   // uniform over the launch
   if (lane < 3) red[wid][lane] = ftrap;
   __syncthreads();
@@ -246,8 +254,8 @@ __global__ void __launch_bounds__(32 * kWarps) k_predict(BlobParams p, BlobState
 // Step 4 (Eq. delta_u_nph[_visc]): slip correction du and momentum change
 // dp = m_e (u^n - J v~ - du); cdp = m~_f / (rho (m~_f + m_e)) dp for step 5.
 template <typename R, int K>
-__global__ void __launch_bounds__(32 * kWarps) k_dp(BlobParams p, BlobState s, const R* __restrict__ vt) {
-  ICM_WARP_SETUP
+__device__ __forceinline__ void dp_blob(const BlobParams& p, const BlobState& s, const R* __restrict__ vt, long long b,
+                                        int lane, WarpStencil<R, K>& S) {
   double qh[3], jvt[3];
   load3(s.qh, b, qh);
   build_stencil<R, K>(S, qh, p, false, lane);
@@ -269,33 +277,44 @@ __global__ void __launch_bounds__(32 * kWarps) k_dp(BlobParams p, BlobState s, c
   }
 }
 
+template <typename R, int K>
+__global__ void __launch_bounds__(32 * kWarps) k_dp(BlobParams p, BlobState s, const R* __restrict__ vt) {
+  ICM_WARP_SETUP
+  dp_blob<R, K>(p, s, vt, b, lane, S);
+}
+
 // Steps 6-8: J dv~, the source dp - m_e J dv~ of the viscous correction, and the
 // momentum-conserving velocity u^{n+1} = J (v~ + dv~) + du (Eq. update_u).  The
 // grid sum of the source feeds the FP64 momentum bookkeeping.
+// Blob b of the steps 6-8 kernel; returns (in lane a < 3) component a of its source.
+template <typename R, int K>
+__device__ __forceinline__ double inertial_blob(const BlobParams& p, const BlobState& s, const R* __restrict__ dvt,
+                                                long long b, int lane, WarpStencil<R, K>& S) {
+  double qh[3], jd[3];
+  load3(s.qh, b, qh);
+  build_stencil<R, K>(S, qh, p, false, lane);
+  gather<R, K>(S, dvt, p, lane, jd);
+  double sr = 0.0;
+  if (lane < 3) {
+    const int a = lane;
+    const long long i = 3 * b + a;
+    const double jv = pick3(jd, a);
+    sr = s.dp[i] - s.me[b] * jv;
+    s.src[i] = sr;
+    s.u[i] = s.jvt[i] + jv + s.du[i];
+  }
+  return sr;
+}
+
 template <typename R, int K>
 __global__ void __launch_bounds__(32 * kWarps) k_inertial(BlobParams p, BlobState s, const R* __restrict__ dvt) {
   __shared__ double red[kWarps][3];
   __shared__ WarpStencil<R, K> sten[kWarps];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const long long b = (long long)blockIdx.x * kWarps + wid;
-  double src[3] = {0.0, 0.0, 0.0};
-  if (b < s.nb) {
-    WarpStencil<R, K>& S = sten[wid];
-    double qh[3], jd[3];
-    load3(s.qh, b, qh);
-    build_stencil<R, K>(S, qh, p, false, lane);
-    gather<R, K>(S, dvt, p, lane, jd);
-    if (lane < 3) {
-      const int a = lane;
-      const long long i = 3 * b + a;
-      const double jv = pick3(jd, a);
-      const double sr = s.dp[i] - s.me[b] * jv;
-      s.src[i] = sr;
-      s.u[i] = s.jvt[i] + jv + s.du[i];
-      src[a] = sr;
-    }
-  }
-  if (lane < 3) red[wid][lane] = src[lane];
+  double src = 0.0;
+  if (b < s.nb) src = inertial_blob<R, K>(p, s, dvt, b, lane, sten[wid]);
+  if (lane < 3) red[wid][lane] = src;
   __syncthreads();
   if (threadIdx.x < 3) {
     double t = 0.0;
@@ -308,9 +327,9 @@ __global__ void __launch_bounds__(32 * kWarps) k_inertial(BlobParams p, BlobStat
 // Inertial path: store the lagged slip term g = J^{n+1/2} L dv.  Neutral path:
 // u^{n+1} = J^{n+1/2} v^{n+1}, g = 0.  Raises CFL / non-finite flags.
 template <typename R, int K>
-__global__ void __launch_bounds__(32 * kWarps) k_finish(BlobParams p, BlobState s, const R* __restrict__ vn,
-                                                        const R* __restrict__ dv, int inertial) {
-  ICM_WARP_SETUP
+__device__ __forceinline__ void finish_blob(const BlobParams& p, const BlobState& s, const R* __restrict__ vn,
+                                            const R* __restrict__ dv, int inertial, long long b, int lane,
+                                            WarpStencil<R, K>& S) {
   double qh[3], jv[3], g[3] = {0.0, 0.0, 0.0};
   load3(s.qh, b, qh);
   build_stencil<R, K>(S, qh, p, false, lane);
@@ -332,6 +351,13 @@ __global__ void __launch_bounds__(32 * kWarps) k_finish(BlobParams p, BlobState 
     if (!isfinite(qn) || !isfinite(u)) atomicOr(s.err, DEV_ERR_NONFINITE);
     if (fabs(u) * p.dt > p.h) atomicOr(s.err, DEV_ERR_CFL);
   }
+}
+
+template <typename R, int K>
+__global__ void __launch_bounds__(32 * kWarps) k_finish(BlobParams p, BlobState s, const R* __restrict__ vn,
+                                                        const R* __restrict__ dv, int inertial) {
+  ICM_WARP_SETUP
+  finish_blob<R, K>(p, s, vn, dv, inertial, b, lane, S);
 }
 
 template <typename R, int K>
@@ -407,6 +433,127 @@ __global__ void __launch_bounds__(32 * kWarps) k_spread_drift(BlobParams p, Blob
 }
 
 inline unsigned nblocks(long long nb) { return (unsigned)((nb + kWarps - 1) / kWarps); }
+
+// ---------------------------------------------------------------------------
+// Stages over every member of a batch: one warp per blob of any member.  The member's
+// kernel width is read at run time (uniform over the warp), the stencil lives in a
+// shared slot large enough for either width, and the block-level sums of the
+// single-simulation kernels become one FP64 atomic per warp and component (a block may
+// hold blobs of several members).
+// ---------------------------------------------------------------------------
+template <typename R>
+struct BatchSlot {
+  __align__(16) unsigned char raw[sizeof(WarpStencil<R, 4>) > sizeof(WarpStencil<R, 3>) ? sizeof(WarpStencil<R, 4>)
+                                                                                         : sizeof(WarpStencil<R, 3>)];
+  template <int K> __device__ WarpStencil<R, K>& as() { return *reinterpret_cast<WarpStencil<R, K>*>(raw); }
+};
+
+#define ICM_BATCH_SETUP                                                 \
+  __shared__ BatchSlot<R> slots[kWarps];                                \
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;            \
+  const long long gb = (long long)blockIdx.x * kWarps + wid;            \
+  if (gb >= nbt) return;                                                \
+  const BlobMember& m = mem[member_of[gb]];                             \
+  const BlobParams p = m.p;                                             \
+  const BlobState s = m.s;                                              \
+  const long long b = gb - m.b0;                                        \
+  BatchSlot<R>& slot = slots[wid];
+
+template <typename R>
+__global__ void __launch_bounds__(32 * kWarps) k_bpredict(const BlobMember* __restrict__ mem,
+                                                          const int* __restrict__ member_of, long long nbt) {
+  ICM_BATCH_SETUP
+  const R* v = (const R*)m.v;
+  const double ft = p.kernel == 3 ? predict_blob<R, 3>(p, s, v, b, lane, slot.template as<3>())
+                                  : predict_blob<R, 4>(p, s, v, b, lane, slot.template as<4>());
+  if (p.trap_k != 0.0 && lane < 3) atomicAdd(&s.scal[SC_K0 + lane], p.dt * ft);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(32 * kWarps) k_bspread(const BlobMember* __restrict__ mem,
+                                                         const int* __restrict__ member_of, long long nbt, int which) {
+  ICM_BATCH_SETUP
+  const double* vec = which == BV_FORCE ? m.fvec : (which == BV_CDP ? s.cdp : s.src);
+  if (vec == nullptr) return;
+  double q[3], f[3];
+  load3(s.qh, b, q);
+  load3(vec, b, f);
+  R* field = (R*)m.work;
+  if (p.kernel == 3) {
+    build_stencil<R, 3>(slot.template as<3>(), q, p, false, lane);
+    scatter<R, 3>(slot.template as<3>(), field, p, lane, f);
+  } else {
+    build_stencil<R, 4>(slot.template as<4>(), q, p, false, lane);
+    scatter<R, 4>(slot.template as<4>(), field, p, lane, f);
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(32 * kWarps) k_bdp(const BlobMember* __restrict__ mem,
+                                                     const int* __restrict__ member_of, long long nbt) {
+  ICM_BATCH_SETUP
+  const R* v = (const R*)m.v;
+  if (p.kernel == 3)
+    dp_blob<R, 3>(p, s, v, b, lane, slot.template as<3>());
+  else
+    dp_blob<R, 4>(p, s, v, b, lane, slot.template as<4>());
+}
+
+template <typename R>
+__global__ void __launch_bounds__(32 * kWarps) k_binertial(const BlobMember* __restrict__ mem,
+                                                           const int* __restrict__ member_of, long long nbt) {
+  ICM_BATCH_SETUP
+  const R* w = (const R*)m.work;
+  const double sr = p.kernel == 3 ? inertial_blob<R, 3>(p, s, w, b, lane, slot.template as<3>())
+                                  : inertial_blob<R, 4>(p, s, w, b, lane, slot.template as<4>());
+  if (lane < 3) atomicAdd(&s.scal[SC_SUMSRC + lane], sr);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(32 * kWarps) k_bfinish(const BlobMember* __restrict__ mem,
+                                                         const int* __restrict__ member_of, long long nbt) {
+  ICM_BATCH_SETUP
+  const R* v = (const R*)m.v;
+  const R* dv = m.inertial ? (const R*)m.work : nullptr;
+  if (p.kernel == 3)
+    finish_blob<R, 3>(p, s, v, dv, m.inertial, b, lane, slot.template as<3>());
+  else
+    finish_blob<R, 4>(p, s, v, dv, m.inertial, b, lane, slot.template as<4>());
+}
+#undef ICM_BATCH_SETUP
+
+// work = 0 over 3 ncell values of member blockIdx.y, in 16-byte stores (register FFT
+// sides are even, so 3 ncell R values are a whole number of 16-byte words).
+template <typename R>
+__global__ void k_bzero(const BlobMember* __restrict__ mem) {
+  const BlobMember& m = mem[blockIdx.y];
+  const long long n16 = 3 * m.p.ncell * (long long)sizeof(R) / 16;
+  float4* w = (float4*)m.work;
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n16; i += (long long)gridDim.x * blockDim.x)
+    w[i] = z;
+}
+
+__global__ void k_bscal_before(const BlobMember* __restrict__ mem) {
+  const BlobMember& m = mem[blockIdx.x];
+  const int a = threadIdx.x;
+  if (a < 3) {
+    double* scal = m.s.scal;
+    scal[SC_K0 + a] = scal[SC_PBAR + a] + m.p.dt * scal[SC_SUMF + a];
+    scal[SC_SUMSRC + a] = 0.0;
+  }
+}
+
+__global__ void k_bscal_after(const BlobMember* __restrict__ mem) {
+  const BlobMember& m = mem[blockIdx.x];
+  const int a = threadIdx.x;
+  double* scal = m.s.scal;
+  if (a < 3) scal[SC_PBAR + a] = scal[SC_K0 + a] + (m.inertial ? scal[SC_SUMSRC + a] : 0.0);
+  if (a == 0) {
+    *m.step_dev += 1;
+    *m.hist_dev = 1;
+  }
+}
 
 // ---------------------------------------------------------------------------
 // Row-block bins (count, scan, fill) and the elementwise updates of the fused step
@@ -652,6 +799,50 @@ void blob_finish_from(const BlobParams& p, BlobState s, const double* base, cons
   } else {                        \
     call4;                        \
   }
+
+template <typename R>
+void batch_predict(const BlobMember* m, const int* member_of, long long nbt, cudaStream_t st) {
+  if (nbt > 0) k_bpredict<R><<<nblocks(nbt), 32 * kWarps, 0, st>>>(m, member_of, nbt);
+}
+template <typename R>
+void batch_spread(const BlobMember* m, const int* member_of, long long nbt, int which, cudaStream_t st) {
+  if (nbt > 0) k_bspread<R><<<nblocks(nbt), 32 * kWarps, 0, st>>>(m, member_of, nbt, which);
+}
+template <typename R>
+void batch_dp(const BlobMember* m, const int* member_of, long long nbt, cudaStream_t st) {
+  if (nbt > 0) k_bdp<R><<<nblocks(nbt), 32 * kWarps, 0, st>>>(m, member_of, nbt);
+}
+template <typename R>
+void batch_inertial(const BlobMember* m, const int* member_of, long long nbt, cudaStream_t st) {
+  if (nbt > 0) k_binertial<R><<<nblocks(nbt), 32 * kWarps, 0, st>>>(m, member_of, nbt);
+}
+template <typename R>
+void batch_finish(const BlobMember* m, const int* member_of, long long nbt, cudaStream_t st) {
+  if (nbt > 0) k_bfinish<R><<<nblocks(nbt), 32 * kWarps, 0, st>>>(m, member_of, nbt);
+}
+template <typename R>
+void batch_zero_work(const BlobMember* m, int nm, long long ncell_max, cudaStream_t st) {
+  if (nm <= 0) return;
+  const long long n16 = 3 * ncell_max * (long long)sizeof(R) / 16;
+  const unsigned gx = (unsigned)std::min<long long>((n16 + 255) / 256, 1024);
+  k_bzero<R><<<dim3(std::max(gx, 1u), nm), 256, 0, st>>>(m);
+}
+void batch_scalars_before(const BlobMember* m, int nm, cudaStream_t st) {
+  if (nm > 0) k_bscal_before<<<nm, 32, 0, st>>>(m);
+}
+void batch_scalars_after(const BlobMember* m, int nm, cudaStream_t st) {
+  if (nm > 0) k_bscal_after<<<nm, 32, 0, st>>>(m);
+}
+#define ICM_BINST(R)                                                                                       \
+  template void batch_predict<R>(const BlobMember*, const int*, long long, cudaStream_t);                \
+  template void batch_spread<R>(const BlobMember*, const int*, long long, int, cudaStream_t);            \
+  template void batch_dp<R>(const BlobMember*, const int*, long long, cudaStream_t);                     \
+  template void batch_inertial<R>(const BlobMember*, const int*, long long, cudaStream_t);               \
+  template void batch_finish<R>(const BlobMember*, const int*, long long, cudaStream_t);                 \
+  template void batch_zero_work<R>(const BlobMember*, int, long long, cudaStream_t);
+ICM_BINST(float)
+ICM_BINST(double)
+#undef ICM_BINST
 
 template <typename R>
 void blob_predict(const BlobParams& p, BlobState s, const R* v, cudaStream_t st) {

@@ -344,10 +344,14 @@ struct SymParams {
 // P^ w / (a + b|d|^2) / ncell on one wave vector: (P^ w)_a = w_a - conj(d_a)(d . w)/|d|^2,
 // identity on the mean mode, whose value is replaced by the FP64 bookkeeping if given
 // (and which is zero when a = 0).
-// 1/x: correctly rounded reciprocal in FP32 (a few roundings more than two divisions
-// per wave vector, far inside the FP32 path's tolerance), exact division in FP64.
+// 1/x: the hardware reciprocal in FP32 (within one ulp: a few roundings more than two
+// divisions per wave vector, far inside the FP32 path's tolerance), exact division in FP64.
 template <typename R> __device__ __forceinline__ R recip(R x);
-template <> __device__ __forceinline__ float recip<float>(float x) { return __frcp_rn(x); }
+template <> __device__ __forceinline__ float recip<float>(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));   // within one ulp; x is never denormal here
+  return r;
+}
 template <> __device__ __forceinline__ double recip<double>(double x) { return 1.0 / x; }
 
 template <typename R>

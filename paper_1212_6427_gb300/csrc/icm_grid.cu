@@ -55,57 +55,50 @@ __device__ __forceinline__ void halo_cell(int h, int& hx, int& hy) {
   }
 }
 
-// Which halo cell of the tile, if any, thread (warp, lane) draws the stress normals of:
-// warps are given one kind of halo cell each so that none diverges.  Warp 0 takes the
-// bottom row (whose Z_yy the row above reads) and warp 1 the left column (Z_xx), both
-// from the first Box-Muller pair of call 0; warps 2 and 3 the top row (Z_xy, Z_yz) and
-// warp 4 the right column (Z_xy, Z_xz), from the second pair of call 0 and the first of
-// call 1.  The corners are read by no one.  Returns 0 (none), 1 or 2 (the two kinds).
-__device__ __forceinline__ int halo_noise_cell(int warp, int lane, int& hx, int& hy) {
-  if (warp == 0) {
-    hx = 1 + lane;
-    hy = 0;
-    return 1;
+// The stress normals the tile's neighbours read from its halo cells, 144 per plane:
+// Z_yy of the bottom row and Z_xx of the left column (the first Box-Muller pair of
+// Philox call 0), Z_xy of the top row and of the right column (the second pair of call
+// 0), Z_yz of the top row and Z_xz of the right column (the first pair of call 1).  Task
+// tau = 32 warp + lane of warps 0-4 draws one of them: one Philox call and one
+// Box-Muller pair per lane, the counter word, word pair and branch chosen per lane, so no
+// warp diverges and none does more than one call.  The corners are read by no one.
+struct HaloTask {
+  int hx, hy;       // position in the padded plane
+  int dst;          // z ring array: 0 xx, 1 yy, 2 xy, 3 xz, 4 yz
+  uint32_t call;    // Philox counter word 2
+  bool hi;          // Box-Muller on words (z, w) rather than (x, y)
+  bool second;      // the sine branch rather than the cosine one
+};
+constexpr int kHaloTasks = 3 * TX + 3 * TY;   // 144
+static_assert(kHaloTasks <= NT, "one halo task per thread at most");
+
+__device__ __forceinline__ bool halo_task(int tau, HaloTask& t) {
+  if (tau < TX) {                       // bottom row: Z_yy
+    t = HaloTask{1 + tau, 0, 1, 0u, false, true};
+  } else if (tau < TX + TY) {           // left column: Z_xx
+    t = HaloTask{0, 1 + (tau - TX), 0, 0u, false, false};
+  } else if (tau < 2 * TX + TY) {       // top row: Z_xy
+    t = HaloTask{1 + (tau - TX - TY), HY - 1, 2, 0u, true, true};
+  } else if (tau < 3 * TX + TY) {       // top row: Z_yz
+    t = HaloTask{1 + (tau - 2 * TX - TY), HY - 1, 4, 1u, false, true};
+  } else if (tau < 3 * TX + 2 * TY) {   // right column: Z_xy
+    t = HaloTask{HX - 1, 1 + (tau - 3 * TX - TY), 2, 0u, true, true};
+  } else if (tau < kHaloTasks) {        // right column: Z_xz
+    t = HaloTask{HX - 1, 1 + (tau - 3 * TX - 2 * TY), 3, 1u, false, false};
+  } else {
+    return false;
   }
-  if (warp == 1 && lane < TY) {
-    hx = 0;
-    hy = 1 + lane;
-    return 1;
-  }
-  if ((warp == 2 || warp == 3) && lane < 16) {
-    hx = 1 + (warp - 2) * 16 + lane;
-    hy = HY - 1;
-    return 2;
-  }
-  if (warp == 4 && lane < TY) {
-    hx = HX - 1;
-    hy = 1 + lane;
-    return 2;
-  }
-  return 0;
+  return true;
 }
 
-// The normals of halo cell `cell` (its flat index in plane kk) that neighbours read,
-// into slot `slot` of the z ring at (hx, hy).
+// Halo task t at flat cell index `cell` of its plane, into slot `slot` of the z ring.
 template <typename R>
-__device__ __forceinline__ void gen_halo(RhsSmem<R>& sm, int slot, int kind, uint32_t cell, int hx, int hy,
+__device__ __forceinline__ void gen_halo(RhsSmem<R>& sm, int slot, const HaloTask& t, uint32_t cell,
                                          const GridParams& g, uint32_t step) {
-  if (kind == 1) {
-    const u32x4 a = philox4x32_10(u32x4{cell, step, 0u, 0u}, g.key0, g.key1);
-    R zxx, zyy;
-    BoxMuller<R>::apply(a.x, a.y, zxx, zyy);
-    sm.z[slot][0][hy][hx] = zxx;
-    sm.z[slot][1][hy][hx] = zyy;
-  } else if (kind == 2) {
-    const u32x4 a = philox4x32_10(u32x4{cell, step, 0u, 0u}, g.key0, g.key1);
-    const u32x4 b = philox4x32_10(u32x4{cell, step, 1u, 0u}, g.key0, g.key1);
-    R zzz, zxy, zxz, zyz;
-    BoxMuller<R>::apply(a.z, a.w, zzz, zxy);
-    BoxMuller<R>::apply(b.x, b.y, zxz, zyz);
-    sm.z[slot][2][hy][hx] = zxy;
-    sm.z[slot][3][hy][hx] = zxz;
-    sm.z[slot][4][hy][hx] = zyz;
-  }
+  const u32x4 r = philox4x32_10(u32x4{cell, step, t.call, 0u}, g.key0, g.key1);
+  R c, sn;
+  BoxMuller<R>::apply(t.hi ? r.z : r.x, t.hi ? r.w : r.y, c, sn);
+  sm.z[slot][t.dst][t.hy][t.hx] = t.second ? sn : c;
 }
 
 // The own cell's normals of plane kk into z[] (registers) and the five that neighbours
@@ -129,28 +122,13 @@ __device__ __forceinline__ void gen_own(RhsSmem<R>& sm, int slot, R (&z)[6], uin
 // plane: the global loads of the plane after next are issued first, the stress normals
 // of the next plane are drawn while they are in flight, then the plane is computed from
 // the thread's registers (its own column) and shared memory (its neighbours).
+// One run of the marching block: planes k0 .. kend-1 of tile `tile` (tiles x-fastest).
 template <typename R, bool NOISE>
-__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_rhs(const R* __restrict__ v, R* __restrict__ adv,
-                                                                      R* __restrict__ rhs,
-                                            GridParams g, const long long* __restrict__ step_dev,
-                                            const int* __restrict__ hist_dev) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  RhsSmem<R>& sm = *reinterpret_cast<RhsSmem<R>*>(smem_raw);
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int tid = tx + TX * ty, warp = tid >> 5, lane = tid & 31;
-  const int ntx = (g.nx + TX - 1) / TX, nty = (g.ny + TY - 1) / TY;
-  long long lo, hi;
-  if (g.kz > 0) {
-    const long long tile = blockIdx.x + (long long)ntx * blockIdx.y;
-    lo = tile * g.nz + (long long)blockIdx.z * g.kz;
-    hi = min(lo + g.kz, (tile + 1) * g.nz);
-  } else {
-    const long long total = (long long)ntx * nty * g.nz;
-    lo = total * blockIdx.x / gridDim.x;
-    hi = total * (blockIdx.x + 1) / gridDim.x;
-  }
-  const uint32_t step = (uint32_t)(*step_dev);
-  const bool hist = *hist_dev != 0;
+__device__ __forceinline__ void rhs_run(RhsSmem<R>& sm, const R* __restrict__ v, R* __restrict__ adv,
+                                        R* __restrict__ rhs, const GridParams& g, uint32_t step, bool hist,
+                                        long long tile, int k0, int kend, int tx, int ty) {
+  const int tid = tx + TX * ty;
+  const int ntx = (g.nx + TX - 1) / TX;
   const long long nc = g.ncell;
   const long long plane = (long long)g.nx * g.ny;
   const R rho = (R)g.rho, inv_h = (R)(1.0 / g.h), inv_h2 = (R)(1.0 / (g.h * g.h));
@@ -160,12 +138,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_rhs(const R* __r
   const R adv_on = g.advection ? R(1) : R(0);
   const R h2 = R(0.5);
   const int lx = tx + 1, ly = ty + 1;
-
-  for (long long w = lo; w < hi;) {
-    const long long tile = w / g.nz;
-    const int k0 = (int)(w - tile * g.nz);
-    const int kend = (int)min((long long)g.nz, k0 + (hi - w));
-    w += kend - k0;
+  {
     const int i0 = (int)(tile % ntx) * TX, j0 = (int)(tile / ntx) * TY;
     const int i = i0 + tx, j = j0 + ty;
     const bool active = i < g.nx && j < g.ny;
@@ -178,11 +151,10 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_rhs(const R* __r
       halo_cell(tid, hx, hy);
       hoff = wrapm(i0 - 1 + hx, g.nx) + (long long)g.nx * wrapm(j0 - 1 + hy, g.ny);
     }
-    // the halo cell whose stress normals this thread draws, if any
-    int nhx = 0, nhy = 0;
-    const int nkind = NOISE ? halo_noise_cell(warp, lane, nhx, nhy) : 0;
-    const uint32_t ncell =
-        nkind ? (uint32_t)(wrapm(i0 - 1 + nhx, g.nx) + g.nx * wrapm(j0 - 1 + nhy, g.ny)) : 0u;
+    // the halo stress normal this thread draws, if any
+    HaloTask ht{0, 0, 0, 0u, false, false};
+    const bool hnoise = NOISE && halo_task(tid, ht);
+    const uint32_t ncell = hnoise ? (uint32_t)(wrapm(i0 - 1 + ht.hx, g.nx) + g.nx * wrapm(j0 - 1 + ht.hy, g.ny)) : 0u;
     auto load = [&](R (&o)[3], R (&hv)[3], int k) {
       const long long zo = plane * wrapi(k, g.nz);
 #pragma unroll
@@ -214,7 +186,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_rhs(const R* __r
       cell_normals<R>((uint32_t)(own + plane * wrapi(k0 - 1, g.nz)), step, g.key0, g.key1, zc);
       zzp = zc[2];
       gen_own<R>(sm, 1, zn, (uint32_t)(own + plane * k0), g, step, lx, ly);
-      gen_halo<R>(sm, 1, nkind, ncell + (uint32_t)(plane * k0), nhx, nhy, g, step);
+      if (hnoise) gen_halo<R>(sm, 1, ht, ncell + (uint32_t)(plane * k0), g, step);
     }
     for (int k = k0; k < kend; ++k) {
       const int kk = k - k0;
@@ -237,7 +209,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_rhs(const R* __r
         for (int c = 0; c < 6; ++c) zc[c] = zn[c];
         const uint32_t pk = (uint32_t)(plane * wrapi(k + 1, g.nz));
         gen_own<R>(sm, zsn, zn, (uint32_t)own + pk, g, step, lx, ly);
-        gen_halo<R>(sm, zsn, nkind, ncell + pk, nhx, nhy, g, step);
+        if (hnoise) gen_halo<R>(sm, zsn, ht, ncell + pk, g, step);
       }
       __syncthreads();
       if (active) {
@@ -304,6 +276,71 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_rhs(const R* __r
         vn[c] = vq[c];
       }
     }
+  }
+}
+
+// A block takes a contiguous range [lo, hi) of tile-planes w = tile * nz + k: with
+// g.kz > 0 the range is the kz planes of one tile (grid = tiles x ceil(nz / kz)); with
+// g.kz == 0 the blocks are persistent, the grid holds as many as the SMs do at once and
+// the ranges split all tile-planes evenly.  A range is marched tile by tile.
+template <typename R, bool NOISE>
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_rhs(const R* __restrict__ v, R* __restrict__ adv,
+                                                                      R* __restrict__ rhs, GridParams g,
+                                                                      const long long* __restrict__ step_dev,
+                                                                      const int* __restrict__ hist_dev) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  RhsSmem<R>& sm = *reinterpret_cast<RhsSmem<R>*>(smem_raw);
+  const int ntx = (g.nx + TX - 1) / TX, nty = (g.ny + TY - 1) / TY;
+  long long lo, hi;
+  if (g.kz > 0) {
+    const long long tile = blockIdx.x + (long long)ntx * blockIdx.y;
+    lo = tile * g.nz + (long long)blockIdx.z * g.kz;
+    hi = min(lo + g.kz, (tile + 1) * g.nz);
+  } else {
+    const long long total = (long long)ntx * nty * g.nz;
+    lo = total * blockIdx.x / gridDim.x;
+    hi = total * (blockIdx.x + 1) / gridDim.x;
+  }
+  const uint32_t step = (uint32_t)(*step_dev);
+  const bool hist = *hist_dev != 0;
+  for (long long w = lo; w < hi;) {
+    const long long tile = w / g.nz;
+    const int k0 = (int)(w - tile * g.nz);
+    const int kend = (int)min((long long)g.nz, k0 + (hi - w));
+    w += kend - k0;
+    rhs_run<R, NOISE>(sm, v, adv, rhs, g, step, hist, tile, k0, kend, threadIdx.x, threadIdx.y);
+  }
+}
+
+// The right-hand side of every member of a batch: persistent blocks split the members'
+// concatenated tile-planes evenly; a run never crosses from one member to the next.
+template <typename R, bool NOISE>
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_rhs_batch(const RhsMember<R>* __restrict__ mem,
+                                                                            int nm, long long total) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  RhsSmem<R>& sm = *reinterpret_cast<RhsSmem<R>*>(smem_raw);
+  const long long lo = total * blockIdx.x / gridDim.x, hi = total * (blockIdx.x + 1) / gridDim.x;
+  int mi = 0;   // the member holding w: the last with w0 <= w
+  {
+    int a = 0, b = nm - 1;
+    while (a < b) {
+      const int c = (a + b + 1) / 2;
+      if (mem[c].w0 <= lo) a = c; else b = c - 1;
+    }
+    mi = a;
+  }
+  for (long long w = lo; w < hi;) {
+    while (mi + 1 < nm && mem[mi + 1].w0 <= w) ++mi;
+    const RhsMember<R>& m = mem[mi];
+    const GridParams g = m.g;
+    const long long end = mi + 1 < nm ? min(hi, mem[mi + 1].w0) : hi;
+    const long long lw = w - m.w0;
+    const long long tile = lw / g.nz;
+    const int k0 = (int)(lw - tile * g.nz);
+    const int kend = (int)min((long long)g.nz, k0 + (end - w));
+    w += kend - k0;
+    rhs_run<R, NOISE>(sm, m.v, m.adv, m.rhs, g, (uint32_t)(*m.step_dev), *m.hist_dev != 0, tile, k0, kend,
+                      threadIdx.x, threadIdx.y);
   }
 }
 
@@ -447,6 +484,29 @@ void explicit_rhs(const GridParams& g, const R* v, R* adv, R* rhs, const long lo
     k_rhs<R, false><<<grid, block, rhs_smem<R>(), st>>>(v, adv, rhs, g, step_dev, hist_dev);
 }
 
+long long rhs_tile_planes(int nx, int ny, int nz) {
+  return (long long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY) * nz;
+}
+
+template <typename R>
+void batch_rhs(const RhsMember<R>* members, int nm, long long total, bool noise, cudaStream_t st) {
+  if (nm <= 0 || total <= 0) return;
+  static int resident[2] = {0, 0};
+  int& res = resident[sizeof(R) == 4 ? 0 : 1];
+  if (res == 0) {
+    int dev = 0, nsm = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rhs_batch<R, true>, NT, rhs_smem<R>());
+    res = std::max(1, nsm) * std::max(1, per);
+  }
+  const dim3 grid((unsigned)std::min<long long>(res, total)), block(TX, TY);
+  if (noise)
+    k_rhs_batch<R, true><<<grid, block, rhs_smem<R>(), st>>>(members, nm, total);
+  else
+    k_rhs_batch<R, false><<<grid, block, rhs_smem<R>(), st>>>(members, nm, total);
+}
+
 template <typename R>
 void stress_normals(const GridParams& g, long long step, R* out, cudaStream_t st) {
   const int bs = 256;
@@ -506,6 +566,11 @@ void grid_prepare() {
   cudaFuncSetAttribute(k_rhs<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_smem<double>());
   cudaFuncSetAttribute(k_rhs<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_smem<float>());
   cudaFuncSetAttribute(k_rhs<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_smem<double>());
+  cudaFuncSetAttribute(k_rhs_batch<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_smem<float>());
+  cudaFuncSetAttribute(k_rhs_batch<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_smem<double>());
+  cudaFuncSetAttribute(k_rhs_batch<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_smem<float>());
+  cudaFuncSetAttribute(k_rhs_batch<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)rhs_smem<double>());
 }
 
 void scalars_before_step(double* scal, double dt, double, double, cudaStream_t st) {
@@ -518,6 +583,7 @@ void scalars_after_step(double* scal, double, double, double, bool inertial, lon
 
 #define ICM_INST(R)                                                                                          \
   template void explicit_rhs<R>(const GridParams&, const R*, R*, R*, const long long*, const int*, cudaStream_t); \
+  template void batch_rhs<R>(const RhsMember<R>*, int, long long, bool, cudaStream_t);                        \
   template void stress_normals<R>(const GridParams&, long long, R*, cudaStream_t);                           \
   template void field_sums<R>(const R*, long long, double*, double*, int, cudaStream_t);                      \
   template void convert_to_double<R>(const R*, double*, long long, cudaStream_t);                             \

@@ -283,6 +283,51 @@ void blob_inertial_from(const BlobParams& p, BlobState s, const double* jdvt, cu
 void blob_finish_from(const BlobParams& p, BlobState s, const double* base, const double* add, const double* g,
                       bool inertial, cudaStream_t st);
 
+// ---------------------------------------------------------------------------
+// Stages launched once over every member of a batch (replica simulations of any grid;
+// one precision per launch).  A device table holds each member's parameters and state;
+// blob work finds its member through member_of[global blob index].
+// ---------------------------------------------------------------------------
+struct BlobMember {
+  BlobParams p;
+  BlobState s;
+  const void* v;          // face velocities (R)
+  void* work;             // work field (R): spread sources, dv~, dv
+  const double* fvec;     // forces spread into the first solve (null: none)
+  long long* step_dev;    // time level
+  int* hist_dev;          // Adams-Bashforth history flag
+  long long b0;           // first global blob index of the member
+  int inertial;           // any excess mass: steps 4-8 run
+};
+enum BatchVec : int { BV_FORCE = 0, BV_CDP = 1, BV_SRC = 2 };
+template <typename R> void batch_predict(const BlobMember* m, const int* member_of, long long nbt, cudaStream_t st);
+template <typename R>
+void batch_spread(const BlobMember* m, const int* member_of, long long nbt, int which, cudaStream_t st);
+template <typename R> void batch_dp(const BlobMember* m, const int* member_of, long long nbt, cudaStream_t st);
+template <typename R> void batch_inertial(const BlobMember* m, const int* member_of, long long nbt, cudaStream_t st);
+template <typename R> void batch_finish(const BlobMember* m, const int* member_of, long long nbt, cudaStream_t st);
+// work[0 .. 3 ncell) = 0 for every member (ncell_max: the largest member's cells)
+template <typename R> void batch_zero_work(const BlobMember* m, int nm, long long ncell_max, cudaStream_t st);
+void batch_scalars_before(const BlobMember* m, int nm, cudaStream_t st);
+void batch_scalars_after(const BlobMember* m, int nm, cudaStream_t st);
+
+// The right-hand side of every member (persistent blocks over all members' tile-planes).
+template <typename R>
+struct RhsMember {
+  GridParams g;
+  const R* v;
+  R* adv;
+  R* rhs;
+  const long long* step_dev;
+  const int* hist_dev;
+  long long w0;           // first global tile-plane of the member
+};
+// members[0 .. nm) in order of w0; total = the last member's w0 + its tile-planes.
+template <typename R>
+void batch_rhs(const RhsMember<R>* members, int nm, long long total, bool noise, cudaStream_t st);
+// Tile-planes (32 x 16 cells per tile) of a grid in the RHS kernel.
+long long rhs_tile_planes(int nx, int ny, int nz);
+
 // Scalar bookkeeping kernels.
 void scalars_before_step(double* scal, double dt, double rho, double dvf, cudaStream_t st);
 void scalars_after_step(double* scal, double dt, double rho, double dvf, bool inertial, long long* step_dev,

@@ -159,7 +159,87 @@ def test_grouped_batch_matches_individual_runs(icm, precision):
         assert rel(got["pos"], want["pos"]) < TOL[precision] * 1e-2
         np.testing.assert_allclose(got["momentum"], want["momentum"], rtol=1e-9, atol=1e-12)
     with pytest.raises(icm.IcmError):
-        icm.icm_batch_set_grouped(b, 2)
+        icm.icm_batch_set_grouped(b, 3)
+    icm.icm_batch_destroy(b)
+    for s in sims:
+        s.close()
+
+
+def _stage_jobs(precision):
+    # (side, h, kernel, blobs, excess mass, kT, trap): register sides only.  Two groups of
+    # 32^3 members (one neutrally buoyant, one without blobs), a group of two 48^3
+    # members (one without noise), a 64^3 member and a 32^3 member with another cell
+    # width (groups of one), one member in a harmonic trap; kernels 3 and 4 mixed.
+    spec = [(32, 1.0, 4, 7, (-0.5, 2.0), 2e-3, None), (32, 1.0, 3, 12, None, 2e-3, None),
+            (32, 1.0, 4, 0, None, 2e-3, None), (48, 1.0, 3, 4, (-0.5, 2.0), 0.0, None),
+            (48, 1.0, 4, 9, (-0.5, 2.0), 2e-3, (0.02, (20.0, 24.0, 30.0))), (64, 1.0, 4, 8, (-0.5, 2.0), 2e-3, None),
+            (32, 0.5, 3, 5, (0.0, 1.0), 2.5e-4, None)]
+    out = []
+    for r, (side, h, kernel, nb, me_range, kT, trap) in enumerate(spec):
+        cfg = dict(grid=(side, side, side), h=h, rho=1.0, eta=1.0, kT=kT, dt=0.05 * h * h, kernel=kernel,
+                   seed=80 + r, precision=precision, steps=5, nblobs=nb, me_range=me_range,
+                   force=(1e-3, 0.0, -2e-3), place_seed=180 + r, min_spacing=2.0)
+        j = wl._materialise(cfg)
+        j["trap"] = trap
+        out.append(j)
+    return out
+
+
+def _make(icm, j, precision):
+    s = icm.Simulation(j["grid"], j["h"], j["rho"], j["eta"], j["kT"], j["dt"], j["kernel"], j["seed"], precision)
+    if len(j["q"]):
+        s.add_blobs(j["q"], j["u"], j["me"])
+        s.set_forces(j["force"])
+    if j.get("trap"):
+        s.set_trap(j["trap"][0], j["trap"][1])
+    return s
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_batched_stages_match_individual_runs(icm, precision):
+    """Batched stages (grouped = 2): every per-member stage is one launch over all members
+    of mixed grids, kernels and blob counts; each member's result equals its run alone."""
+    jobs = _stage_jobs(precision)
+    sims = [_make(icm, j, precision) for j in jobs]
+    b = icm.icm_batch_create()
+    icm.icm_batch_set(b, [s.handle for s in sims])
+    icm.icm_batch_set_grouped(b, 2)
+    assert icm.icm_batch_get_grouped(b) == 2
+    icm.icm_batch_step(b, 2)
+    icm.icm_batch_step(b, 3)   # replays the same graph
+    icm.icm_batch_sync(b)
+    # 13 stage launches at most (two RHS launches: members with and without noise) and
+    # five FFT launches per group and solve (four groups, all with excess mass)
+    assert 0 < icm.icm_batch_kernels_per_step(b) <= 13 + 5 * 3 * 4
+    for j, s in zip(jobs, sims):
+        got = s.read()
+        assert got["step"] == 5
+        alone = _make(icm, j, precision)
+        alone.step(5)
+        want = alone.read()
+        alone.close()
+        if len(j["q"]):
+            assert rel(got["vel"], want["vel"]) < TOL[precision]
+            assert rel(got["pos"], want["pos"]) < TOL[precision] * 1e-2
+        np.testing.assert_allclose(got["momentum"], want["momentum"], rtol=1e-9, atol=1e-12)
+    icm.icm_batch_destroy(b)
+    for s in sims:
+        s.close()
+
+
+def test_batched_stages_fall_back_without_register_sides(icm):
+    """A member whose grid has no register FFT passes (24^3): grouped = 2 steps the batch
+    as grouped = 1 would, with the same results as the members alone."""
+    jobs = _grouped_jobs(64)[5:8]
+    sims = [_make(icm, j, 64) for j in jobs]
+    b = icm.icm_batch_create()
+    icm.icm_batch_set(b, [s.handle for s in sims])
+    icm.icm_batch_set_grouped(b, 2)
+    icm.icm_batch_step(b, 5)
+    icm.icm_batch_sync(b)
+    for j, s in zip(jobs, sims):
+        want = _alone(icm, j)
+        assert rel(s.read()["vel"], want["vel"]) < TOL[64]
     icm.icm_batch_destroy(b)
     for s in sims:
         s.close()
