@@ -53,7 +53,9 @@ typedef enum {
   ICM_ECFL = -4,         /* a blob moved more than one cell in a step: |u| dt / h > 1  */
   ICM_ENONFINITE = -5,   /* a NaN or Inf appeared in the blob state                   */
   ICM_ETIMEOUT = -6,     /* a bounded device-side wait gave up                        */
-  ICM_EBUSY = -7         /* the request cannot be taken now (e.g. batch slots full)   */
+  ICM_EBUSY = -7,        /* the request cannot be taken now (e.g. batch slots full)   */
+  ICM_EINDEX = -8        /* a device-side index check failed (the checked build only,
+                            libicm_checked.so, compiled with -DICM_INDEX_CHECKS=1)     */
 } icm_status;
 
 /* Flags of icm_create. */

@@ -13,11 +13,14 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libicm.so")
+# ICM_CHECKED=1 in the environment loads the checked build (device-side index checks,
+# paper_1212_6427_gb300.build.build_library(checked=True)) instead of the ordinary one.
+LIB_PATH = os.path.join(_PKG, "libicm_checked.so" if os.environ.get("ICM_CHECKED") == "1" else "libicm.so")
 
 ICM_OK, ICM_EINVAL, ICM_ENOMEM, ICM_ECUDA, ICM_ECFL, ICM_ENONFINITE, ICM_ETIMEOUT, ICM_EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
+ICM_EINDEX = -8
 STATUS_NAMES = {0: "ICM_OK", -1: "ICM_EINVAL", -2: "ICM_ENOMEM", -3: "ICM_ECUDA", -4: "ICM_ECFL",
-                -5: "ICM_ENONFINITE", -6: "ICM_ETIMEOUT", -7: "ICM_EBUSY"}
+                -5: "ICM_ENONFINITE", -6: "ICM_ETIMEOUT", -7: "ICM_EBUSY", -8: "ICM_EINDEX"}
 FLAG_NO_ADVECTION, FLAG_SLIP_VISC, FLAG_SLIP_ZERO, FLAG_SLIP_FULL = 0x1, 0x0, 0x2, 0x4
 FLAG_THERMAL_DRIFT = 0x8
 
@@ -116,7 +119,8 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError("libicm.so is not built; run paper_1212_6427_gb300.build.build_library()")
+            raise RuntimeError("%s is not built; run paper_1212_6427_gb300.build.build_library()"
+                               % os.path.basename(LIB_PATH))
         L = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in SIGNATURES.items():
             fn = getattr(L, name)

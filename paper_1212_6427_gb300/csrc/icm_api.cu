@@ -251,6 +251,7 @@ BlobParams blob_params(const icm_sim* s) {
   }
   p.trap_k = s->trap_k;
   p.kT = s->kT;
+  p.err = s->err_dev;
   return p;
 }
 
@@ -779,6 +780,7 @@ icm_status device_error_status(icm_sim* s, int err) {
     ICM_CK(cudaMemsetAsync(s->err_dev, 0, sizeof(int), s->stream));
     ICM_CK(cudaStreamSynchronize(s->stream));
     if (err & DEV_ERR_TIMEOUT) return fail(ICM_ETIMEOUT, "a bounded device-side wait gave up");
+    if (err & DEV_ERR_INDEX) return fail(ICM_EINDEX, "a device-side index check failed (checked build)");
     if (err & DEV_ERR_NONFINITE) return fail(ICM_ENONFINITE, "a non-finite blob position or velocity appeared");
     return fail(ICM_ECFL, "a blob moved more than one cell in a step (|u| dt / h > 1)");
   }

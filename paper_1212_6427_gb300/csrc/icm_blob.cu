@@ -109,7 +109,8 @@ __device__ __forceinline__ void gather(const WarpStencil<R, K>& S, const R* __re
       const int iy = wrap_add(S.first[c][1], b, p.ny);
       const int iz = wrap_add(S.first[c][2], cz, p.nz);
       wgt[j] = S.w[c][0][a] * S.w[c][1][b] * S.w[c][2][cz];
-      val[j] = __ldg(field + c * p.ncell + ix + (long long)p.nx * (iy + (long long)p.ny * iz));
+      const long long off = c * p.ncell + ix + (long long)p.nx * (iy + (long long)p.ny * iz);
+      if (index_ok(off, 3 * p.ncell, p.err)) val[j] = __ldg(field + off);
     }
   }
   R acc[3] = {R(0), R(0), R(0)};
@@ -143,7 +144,8 @@ __device__ __forceinline__ void gather_lap(const WarpStencil<R, K>& S, const R* 
       const int iz = wrap_add(S.first[c][2], cz, p.nz);
       const R wx = S.w[c][0][a], wy = S.w[c][1][b], wz = S.w[c][2][cz];
       const R wgt = S.d2[c][0][a] * wy * wz + wx * S.d2[c][1][b] * wz + wx * wy * S.d2[c][2][cz];
-      const R t = wgt * __ldg(field + c * p.ncell + ix + (long long)p.nx * (iy + (long long)p.ny * iz));
+      const long long off = c * p.ncell + ix + (long long)p.nx * (iy + (long long)p.ny * iz);
+      const R t = index_ok(off, 3 * p.ncell, p.err) ? wgt * __ldg(field + off) : R(0);
       acc[0] += c == 0 ? t : R(0);
       acc[1] += c == 1 ? t : R(0);
       acc[2] += c == 2 ? t : R(0);
@@ -170,7 +172,8 @@ __device__ __forceinline__ void scatter(const WarpStencil<R, K>& S, R* __restric
       const int iy = wrap_add(S.first[c][1], b, p.ny);
       const int iz = wrap_add(S.first[c][2], cz, p.nz);
       const R wgt = S.w[c][0][a] * S.w[c][1][b] * S.w[c][2][cz];
-      atomicAdd(field + c * p.ncell + ix + (long long)p.nx * (iy + (long long)p.ny * iz), wgt * amp[c]);
+      const long long off = c * p.ncell + ix + (long long)p.nx * (iy + (long long)p.ny * iz);
+      if (index_ok(off, 3 * p.ncell, p.err)) atomicAdd(field + off, wgt * amp[c]);
     }
   }
 }
@@ -428,7 +431,8 @@ __global__ void __launch_bounds__(32 * kWarps) k_spread_drift(BlobParams p, Blob
     const R wx = c == 0 ? dw[wid][0][a] : S.w[c][0][a];
     const R wy = c == 1 ? dw[wid][1][bb] : S.w[c][1][bb];
     const R wz = c == 2 ? dw[wid][2][cz] : S.w[c][2][cz];
-    atomicAdd(field + c * p.ncell + ix + (long long)p.nx * (iy + (long long)p.ny * iz), wx * wy * wz * amp);
+    const long long off = c * p.ncell + ix + (long long)p.nx * (iy + (long long)p.ny * iz);
+    if (index_ok(off, 3 * p.ncell, p.err)) atomicAdd(field + off, wx * wy * wz * amp);
   }
 }
 

@@ -172,6 +172,26 @@ template <typename R> struct Peskin<R, 4> {
 };
 
 // Status bits the device raises (read back by icm_sync).
-enum : int { DEV_ERR_CFL = 1, DEV_ERR_NONFINITE = 2, DEV_ERR_TIMEOUT = 4 };
+enum : int { DEV_ERR_CFL = 1, DEV_ERR_NONFINITE = 2, DEV_ERR_TIMEOUT = 4, DEV_ERR_INDEX = 8 };
+
+// Index checks of the checked build (compiled with -DICM_INDEX_CHECKS=1, the library
+// libicm_checked.so): true when 0 <= i < n; otherwise the check raises DEV_ERR_INDEX in
+// *err (if err is set) and returns false, and the caller skips the access.  It never
+// traps.  In the ordinary build it is always true and compiles away.
+#ifndef ICM_INDEX_CHECKS
+#define ICM_INDEX_CHECKS 0
+#endif
+__device__ __forceinline__ bool index_ok(long long i, long long n, int* err) {
+#if ICM_INDEX_CHECKS
+  if (i >= 0 && i < n) return true;
+  if (err != nullptr) atomicOr(err, DEV_ERR_INDEX);
+  return false;
+#else
+  (void)i;
+  (void)n;
+  (void)err;
+  return true;
+#endif
+}
 
 }  // namespace icm

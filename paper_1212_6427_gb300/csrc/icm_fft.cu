@@ -734,8 +734,10 @@ __global__ void __launch_bounds__(zsym2_threads<R, N, R1, R2>(), sizeof(R) == 4 
     __syncthreads();
     if (!s_ok) break;
     const int kx0 = (t % ntx) * NL, py = t / ntx;
-    zsym_tile<R, N, R1, R2, true, NT>(bufs + st * TILE, tw, spec + (size_t)py * kxp + kx0, cs, zs, kx0, py, kx, sp, zdz,
-                                  zddz, tid);
+    // (checked build) the tile's row and its last column lie inside the padded spectrum
+    if (index_ok(py, ny, err) && index_ok(kx0 + NL - 1, kxp, err))
+      zsym_tile<R, N, R1, R2, true, NT>(bufs + st * TILE, tw, spec + (size_t)py * kxp + kx0, cs, zs, kx0, py, kx, sp,
+                                        zdz, zddz, tid);
     __syncthreads();
   }
   if (tid == 0 && !s_ok && t < ntiles) {

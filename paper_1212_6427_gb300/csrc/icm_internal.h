@@ -163,6 +163,7 @@ struct BlobParams {
   double kT;       // thermal energy (the thermal drift's weight)
   double trap_k;   // harmonic trap V = k r^2 / 2 about trap_c (0: none)
   double trap_c[3];
+  int* err;        // device error bits (the checked build's index checks report here)
 };
 
 struct BlobState {

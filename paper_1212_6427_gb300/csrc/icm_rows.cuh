@@ -175,7 +175,10 @@ __device__ __forceinline__ void spread_task(R* rows, int row0, const CompStencil
       if (r < 0 || r >= kRowBlock) continue;
       const R wyz = S.wy[b] * S.wz[c] * amp;
 #pragma unroll
-      for (int a = 0; a < K; ++a) atomicAdd(&rows[lane_of(r, wrap_add1(S.fx, a, N), line)], S.wx[a] * wyz);
+      for (int a = 0; a < K; ++a) {
+        const int x = wrap_add1(S.fx, a, N);
+        if (index_ok(x, N, p.err)) atomicAdd(&rows[lane_of(r, x, line)], S.wx[a] * wyz);
+      }
     }
   }
 }
@@ -195,7 +198,10 @@ __device__ __forceinline__ R gather_task(const R* rows, int row0, const CompSten
       if (r < 0 || r >= kRowBlock) continue;
       R t = R(0);
 #pragma unroll
-      for (int a = 0; a < K; ++a) t += S.wx[a] * rows[lane_of(r, wrap_add1(S.fx, a, N), line)];
+      for (int a = 0; a < K; ++a) {
+        const int x = wrap_add1(S.fx, a, N);
+        if (index_ok(x, N, p.err)) t += S.wx[a] * rows[lane_of(r, x, line)];
+      }
       acc += S.wy[b] * S.wz[c] * t;
     }
   }
@@ -240,7 +246,8 @@ __device__ __forceinline__ R gather_lap_task(const R* rows, int row0, const Comp
       R t0 = R(0), t1 = R(0);   // sum w_x v and sum d2_x v along the row
 #pragma unroll
       for (int a = 0; a < E; ++a) {
-        const R v = rows[lane_of(r, wrap_add1(fx, a, N), line)];
+        const int x = wrap_add1(fx, a, N);
+        const R v = index_ok(x, N, p.err) ? rows[lane_of(r, x, line)] : R(0);
         t0 += wx[a] * v;
         t1 += dx[a] * v;
       }
@@ -273,6 +280,7 @@ __device__ __forceinline__ void spread_plane(R* rows, int z0, int y0, const Comp
   int xo[K];
 #pragma unroll
   for (int a = 0; a < K; ++a) xo[a] = lane_of(0, wrap_add1(S.fx, a, N), line);
+  if (!index_ok(S.fx, N, p.err) || !index_ok(S.fy, p.ny, p.err)) return;
 #pragma unroll
   for (int b = 0; b < K; ++b) {
     const int r = wrap_add1(S.fy, b, p.ny) - y0;
@@ -293,6 +301,7 @@ __device__ __forceinline__ R gather_plane(const R* rows, int z0, int y0, const C
   int xo[K];
 #pragma unroll
   for (int a = 0; a < K; ++a) xo[a] = lane_of(0, wrap_add1(S.fx, a, N), line);
+  if (!index_ok(S.fx, N, p.err) || !index_ok(S.fy, p.ny, p.err)) return R(0);
   R acc = R(0);
 #pragma unroll
   for (int b = 0; b < K; ++b) {
@@ -325,6 +334,7 @@ __device__ __forceinline__ R gather_lap_plane(const R* rows, int z0, int y0, con
   int xo[E];
 #pragma unroll
   for (int a = 0; a < E; ++a) xo[a] = lane_of(0, wrap_add1(fx, a, N), line);
+  if (!index_ok(fx, N, p.err) || !index_ok(fy, p.ny, p.err)) return R(0);
   R acc = R(0);
 #pragma unroll
   for (int b = 0; b < E; ++b) {
