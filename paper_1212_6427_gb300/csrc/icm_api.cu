@@ -1556,6 +1556,7 @@ struct icm_batch {
   std::vector<cudaStream_t> gstreams;  // one per group of the last capture
   void* reps = nullptr;                // device tables of the group solves
   void* stage_tables = nullptr;        // device member tables of the batched stages
+  std::vector<void*> group_specs;      // spectra of the groups with the tensor-map z pass
 };
 
 namespace {
@@ -1570,6 +1571,8 @@ void batch_clear_graph(icm_batch* b) {
   b->reps = nullptr;
   if (b->stage_tables) cudaFree(b->stage_tables);
   b->stage_tables = nullptr;
+  for (void* p : b->group_specs) cudaFree(p);
+  b->group_specs.clear();
 }
 
 // Whether every member can run in a batch of batched stages: one precision, register
@@ -1585,10 +1588,19 @@ bool stages_possible(const icm_batch* b) {
   return true;
 }
 
+struct alignas(64) ZMap {
+  unsigned char bytes[128];
+};
+
 struct SolveGroup {
   std::vector<icm_sim*> members;  // every member: the first solve
   std::vector<icm_sim*> inertial; // members with excess mass: the second and third
   size_t table[3] = {0, 0, 0};    // offsets (in RepFft entries) of the three tables
+  // batched stages: one buffer with every member's spectrum (member i in slot i) and the
+  // tensor map of the z pass over all of them; null where the group has none
+  unsigned char* spec = nullptr;
+  size_t spec_bytes = 0;
+  ZMap zmap;
 };
 
 bool same_grid(const icm_sim* a, const icm_sim* b) {
@@ -1601,6 +1613,7 @@ RepFft rep_entry(const icm_sim* s, int rt) {
   const double k0mul = 1.0 / (s->rho * dvf) / (double)s->ncell;
   r.src = s->work;
   r.spec = s->spec;
+  r.slot = -1;
   r.dst2 = nullptr;
   if (rt == 0) {        // (rho/dt - eta/2 L) v~ = rhs, projected
     r.dst = s->v;
@@ -1629,7 +1642,7 @@ template <typename R>
 void group_solve(const SolveGroup& g, const RepFft* reps, int rt, cudaStream_t st) {
   const std::vector<icm_sim*>& m = rt == 0 ? g.members : g.inertial;
   spectral_solve_group<R>(fft_ctx<R>(m[0]), reps + g.table[rt], (int)m.size(),
-                          rt == 2 ? OUT_ADD_AND_STORE2 : OUT_STORE, st);
+                          rt == 2 ? OUT_ADD_AND_STORE2 : OUT_STORE, st, g.spec ? g.zmap.bytes : nullptr);
 }
 
 // The step of every member as batched stages: each stage of the per-member sequence
@@ -1650,11 +1663,41 @@ icm_status batch_capture_stages(icm_batch* b) {
     groups[gi].members.push_back(s);
     if (s->any_me) groups[gi].inertial.push_back(s);
   }
+  // Groups on a z side of the tensor-map z pass (with the plan's choice of it) put their
+  // members' spectra side by side in one buffer, so that one tensor map covers every
+  // member and the persistent z pass walks all of their tiles; the members' own spectra
+  // stay unused while the batch runs.  Below z side 96 the one-block-per-tile z pass
+  // keeps more blocks per SM and ran faster over a group; without room for the buffer
+  // the group keeps it too.
+  for (SolveGroup& g : groups) {
+    const icm_sim* s0 = g.members[0];
+    if (!s0->plan.tma_z || !s0->has_zmap || s0->nz < 96) continue;
+    g.spec_bytes = 3 * (size_t)s0->nz * s0->ny * s0->kxp * 2 * s0->rsize();
+    void* buf = nullptr;
+    if (cudaMalloc(&buf, g.spec_bytes * g.members.size()) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (!make_zmap(g.zmap.bytes, buf, s0->prec, s0->kx, s0->kxp, s0->ny, s0->nz, 3 * (int)g.members.size())) {
+      cudaFree(buf);
+      continue;
+    }
+    b->group_specs.push_back(buf);
+    g.spec = (unsigned char*)buf;
+  }
   std::vector<RepFft> reps_host;
   for (SolveGroup& g : groups)
     for (int rt = 0; rt < 3; ++rt) {
       g.table[rt] = reps_host.size();
-      for (icm_sim* m : rt == 0 ? g.members : g.inertial) reps_host.push_back(rep_entry(m, rt));
+      for (icm_sim* m : rt == 0 ? g.members : g.inertial) {
+        RepFft r = rep_entry(m, rt);
+        if (g.spec) {
+          const int slot = (int)(std::find(g.members.begin(), g.members.end(), m) - g.members.begin());
+          r.spec = g.spec + (size_t)slot * g.spec_bytes;
+          r.slot = slot;
+        }
+        reps_host.push_back(r);
+      }
     }
   // member tables: all members and the inertial ones (blob stages), and the RHS table
   // (members with noise first, then those without)

@@ -17,6 +17,7 @@
 //   x inverse : Hermitian extension, Nx-point inverse FFT, two real rows out.
 // Each stage of a pass is a radix-2/3/4/8/16 butterfly done in registers with the
 // operands read from and written back to the same shared-memory positions.
+#include <algorithm>
 #include <cstdio>
 
 #include <cooperative_groups.h>
@@ -683,7 +684,8 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
 template <typename R, int N, int R1, int R2>
 __global__ void __launch_bounds__(zsym2_threads<R, N, R1, R2>(), sizeof(R) == 4 ? 2 : 1)
     k_zsym_tma(const __grid_constant__ CUtensorMap zmap, cplx_t<R>* __restrict__ spec,
-               const cplx_t<R>* __restrict__ gtw, int ny, int kx, int kxp, int ntx, SymParams<R> sp, int* err) {
+               const cplx_t<R>* __restrict__ gtw, int ny, int kx, int kxp, int ntx, SymParams<R> sp, int* err,
+               const RepFft* __restrict__ reps, int nrep) {
   using C = cplx_t<R>;
   constexpr int NL = kZLines;
   constexpr int NT = zsym2_threads<R, N, R1, R2>();
@@ -710,15 +712,20 @@ __global__ void __launch_bounds__(zsym2_threads<R, N, R1, R2>(), sizeof(R) == 4 
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  const int ntiles = ntx * ny;
+  // tiles: ntx x ny per spectrum; with reps, replica e = t / (ntx ny) of the table, whose
+  // spectrum is the slot-th of the group buffer the map covers (components 3 slot ..)
+  const int tpm = ntx * ny;
+  const int ntiles = tpm * (reps != nullptr ? nrep : 1);
   const size_t zs = (size_t)ny * kxp, cs = (size_t)N * zs;
   auto issue = [&](int t, int st) {
-    const int kx0 = (t % ntx) * NL, py = t / ntx;
+    const int e = t / tpm, tt = t - e * tpm;
+    const int kx0 = (tt % ntx) * NL, py = tt / ntx;
+    const int c0 = reps != nullptr ? 3 * reps[e].slot : 0;
     // order this block's earlier generic-proxy writes of the buffer before the copy
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(&mbar[st], TILE_BYTES);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) tma_load_4d(bufs + st * TILE + c * N * NL, &zmap, 2 * kx0, py, 0, c, &mbar[st]);
+    for (int c = 0; c < 3; ++c) tma_load_4d(bufs + st * TILE + c * N * NL, &zmap, 2 * kx0, py, 0, c0 + c, &mbar[st]);
   };
   int t = blockIdx.x;
   if (tid == 0 && t < ntiles) issue(t, 0);
@@ -733,11 +740,23 @@ __global__ void __launch_bounds__(zsym2_threads<R, N, R1, R2>(), sizeof(R) == 4 
     }
     __syncthreads();
     if (!s_ok) break;
-    const int kx0 = (t % ntx) * NL, py = t / ntx;
+    const int e = t / tpm, tt = t - e * tpm;
+    const int kx0 = (tt % ntx) * NL, py = tt / ntx;
+    C* sbase = spec;
+    SymParams<R> spt = sp;
+    if (reps != nullptr) {   // the replica's spectrum and symbol
+      const RepFft& rp = reps[e];
+      sbase = reinterpret_cast<C*>(rp.spec);
+      spt.a = (R)rp.a;
+      spt.b = (R)rp.b;
+      spt.mean_scale = rp.a > 0.0 ? (R)((double)sp.inv_ntot / rp.a) : R(0);
+      spt.k0sum = rp.k0sum;
+      spt.k0mul = rp.k0mul;
+    }
     // (checked build) the tile's row and its last column lie inside the padded spectrum
     if (index_ok(py, ny, err) && index_ok(kx0 + NL - 1, kxp, err))
-      zsym_tile<R, N, R1, R2, true, NT>(bufs + st * TILE, tw, spec + (size_t)py * kxp + kx0, cs, zs, kx0, py, kx, sp,
-                                        zdz, zddz, tid);
+      zsym_tile<R, N, R1, R2, true, NT>(bufs + st * TILE, tw, sbase + (size_t)py * kxp + kx0, cs, zs, kx0, py, kx,
+                                        spt, zdz, zddz, tid);
     __syncthreads();
   }
   if (tid == 0 && !s_ok && t < ntiles) {
@@ -1334,6 +1353,18 @@ void set_yz_attributes() {
 #endif
 #define ICM_SHARD(k) (ICM_FFT_SHARD < 0 || ICM_FFT_SHARD == (k))
 
+// SMs of the current device (persistent grids), read once.
+inline int device_sms() {
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    nsm = n > 0 ? n : 1;
+  }
+  return nsm;
+}
+
 template <typename R> void fft_prepare_xf() { set_xf_attributes<R>(); }
 template <typename R> void fft_prepare_xi() { set_xi_attributes<R>(); }
 template <typename R> void fft_prepare_yz() { set_yz_attributes<R>(); }
@@ -1394,13 +1425,7 @@ void fft_z_symbol(const FftCtx<R>& f, double a, double b, const double* k0sum, d
   const cplx_t<R>* tw = (const cplx_t<R>*)f.pz.tw;
   const int kxz = (f.kx + kZLines - 1) / kZLines;
   if (f.zmap != nullptr && f.nz <= 256) {
-    static int nsm = 0;
-    if (nsm == 0) {
-      int dev = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-      if (nsm <= 0) nsm = 1;
-    }
+    const int nsm = device_sms();
     const int ntiles = kxz * f.ny;
     const int grid = ntiles < 2 * nsm ? ntiles : 2 * nsm;
     const CUtensorMap& map = *reinterpret_cast<const CUtensorMap*>(f.zmap);
@@ -1409,7 +1434,7 @@ void fft_z_symbol(const FftCtx<R>& f, double a, double b, const double* k0sum, d
   case N:                                                                                                              \
     if (N <= 256) {                                                                                                    \
       k_zsym_tma<R, N, R1, R2><<<grid, zsym2_threads<R, N, R1, R2>(), smem_ztma<R, N>(), st>>>(map, f.spec, tw, f.ny, \
-                                                                                           f.kx, f.kxp, kxz, sp, f.err); \
+                                                                                           f.kx, f.kxp, kxz, sp, f.err, nullptr, 1); \
       return;                                                                                                          \
     }                                                                                                                  \
     break;
@@ -1581,7 +1606,7 @@ void fft_x_forward_group(const FftCtx<R>& f, const RepFft* reps, int G, cudaStre
 }
 
 template <typename R>
-void fft_yz_group(const FftCtx<R>& f, const RepFft* reps, int G, int which, cudaStream_t st) {
+void fft_yz_group(const FftCtx<R>& f, const RepFft* reps, int G, int which, cudaStream_t st, const void* gzmap) {
   const cplx_t<R>* twy = (const cplx_t<R>*)f.py.tw;
   const cplx_t<R>* twz = (const cplx_t<R>*)f.pz.tw;
   constexpr int NL = seg_lines<R>();
@@ -1598,6 +1623,23 @@ void fft_yz_group(const FftCtx<R>& f, const RepFft* reps, int G, int which, cuda
     sp.dz = f.dz; sp.ddz = f.ddz;
     sp.k0sum = nullptr;
     sp.k0mul = 0.0;
+    if (gzmap != nullptr && f.nz <= 256) {
+      const int grid = std::min(kxz * f.ny * G, 2 * device_sms());
+      const CUtensorMap& map = *reinterpret_cast<const CUtensorMap*>(gzmap);
+      switch (f.nz) {
+#define ICM_CASE(N, R1, R2)                                                                                            \
+  case N:                                                                                                              \
+    if (N <= 256) {                                                                                                    \
+      k_zsym_tma<R, N, R1, R2><<<grid, zsym2_threads<R, N, R1, R2>(), smem_ztma<R, N>(), st>>>(map, nullptr, twz,      \
+                                                                             f.ny, f.kx, f.kxp, kxz, sp, f.err, reps, G); \
+      return;                                                                                                          \
+    }                                                                                                                  \
+    break;
+        ICM_FFT_SIDES(ICM_CASE)
+#undef ICM_CASE
+        default: break;
+      }
+    }
     switch (f.nz) {
 #define ICM_CASE(N, R1, R2) \
   case N: k_zsym2<R, N, R1, R2><<<dim3(kxz, f.ny, G), zplain_threads<R, N, R1, R2>(), smem_z2<R, N>(), st>>>(nullptr, twz, f.ny, f.kx, f.kxp, sp, reps); return;
@@ -1642,11 +1684,12 @@ void fft_x_inverse_group(const FftCtx<R>& f, const RepFft* reps, int G, int mode
 }
 
 template <typename R>
-void spectral_solve_group(const FftCtx<R>& f, const RepFft* reps, int G, int mode, cudaStream_t st) {
+void spectral_solve_group(const FftCtx<R>& f, const RepFft* reps, int G, int mode, cudaStream_t st,
+                          const void* gzmap) {
   fft_x_forward_group<R>(f, reps, G, st);
-  fft_yz_group<R>(f, reps, G, 0, st);
-  fft_yz_group<R>(f, reps, G, 1, st);
-  fft_yz_group<R>(f, reps, G, 2, st);
+  fft_yz_group<R>(f, reps, G, 0, st, nullptr);
+  fft_yz_group<R>(f, reps, G, 1, st, gzmap);
+  fft_yz_group<R>(f, reps, G, 2, st, nullptr);
   fft_x_inverse_group<R>(f, reps, G, mode, st);
 }
 
@@ -1675,7 +1718,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 // The spectrum as a 4-D tensor (floats along kx, y, z, component) and the box one z
 // tile of one component occupies: 2 kZLines floats x 1 x nz x 1.  Wave numbers past
 // kx read as zeros.
-bool make_zmap(void* map, const void* spec, int precision, int kx, int kxp, int ny, int nz) {
+bool make_zmap(void* map, const void* spec, int precision, int kx, int kxp, int ny, int nz, int ncomp) {
   int r1 = 0, r2 = 0;
   if (nz > 256 || !fft_split(nz, r1, r2)) return false;
   static EncodeTiledFn fn = nullptr;
@@ -1690,7 +1733,7 @@ bool make_zmap(void* map, const void* spec, int precision, int kx, int kxp, int 
     fn = (EncodeTiledFn)p;
   }
   const cuuint64_t es = precision == 32 ? 4 : 8;
-  const cuuint64_t dims[4] = {(cuuint64_t)(2 * kx), (cuuint64_t)ny, (cuuint64_t)nz, 3};
+  const cuuint64_t dims[4] = {(cuuint64_t)(2 * kx), (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)ncomp};
   const cuuint64_t strides[3] = {2 * (cuuint64_t)kxp * es, 2 * (cuuint64_t)kxp * es * ny,
                                  2 * (cuuint64_t)kxp * es * ny * nz};
   const cuuint32_t box[4] = {2 * kZLines, 1, (cuuint32_t)nz, 1};
@@ -1719,7 +1762,7 @@ bool make_zmap(void* map, const void* spec, int precision, int kx, int kxp, int 
 #define ICM_INST_YZ(R, KW)                                                                               \
   KW template void fft_y<R>(const FftCtx<R>&, bool, cudaStream_t);                                       \
   KW template void fft_z_symbol<R>(const FftCtx<R>&, double, double, const double*, double, cudaStream_t); \
-  KW template void fft_yz_group<R>(const FftCtx<R>&, const RepFft*, int, int, cudaStream_t);              \
+  KW template void fft_yz_group<R>(const FftCtx<R>&, const RepFft*, int, int, cudaStream_t, const void*); \
   KW template void fft_prepare_yz<R>();
 #define ICM_NONE
 #if ICM_SHARD(0)
@@ -1767,8 +1810,9 @@ template void spectral_solve<float>(const FftCtx<float>&, const float*, float*, 
                                     const double*, double, cudaStream_t);
 template void spectral_solve<double>(const FftCtx<double>&, const double*, double*, double*, int, double, double,
                                      const double*, double, cudaStream_t);
-template void spectral_solve_group<float>(const FftCtx<float>&, const RepFft*, int, int, cudaStream_t);
-template void spectral_solve_group<double>(const FftCtx<double>&, const RepFft*, int, int, cudaStream_t);
+template void spectral_solve_group<float>(const FftCtx<float>&, const RepFft*, int, int, cudaStream_t, const void*);
+template void spectral_solve_group<double>(const FftCtx<double>&, const RepFft*, int, int, cudaStream_t,
+                                           const void*);
 #endif
 #undef ICM_NONE
 #undef ICM_INST_XF

@@ -65,7 +65,7 @@ struct FftCtx {
 
 // Fill `map` (a 128-byte CUtensorMap) with the descriptor the TMA z pass uses for a
 // spectrum buffer; returns false if TMA is unavailable for this shape.
-bool make_zmap(void* map, const void* spec, int precision, int kx, int kxp, int ny, int nz);
+bool make_zmap(void* map, const void* spec, int precision, int kx, int kxp, int ny, int nz, int ncomp = 3);
 
 enum OutMode : int { OUT_STORE = 0, OUT_ADD_AND_STORE2 = 1, OUT_ADD = 2, OUT_NONE = 3 };
 
@@ -93,11 +93,16 @@ struct RepFft {
   void* dst2;           // second output (OUT_ADD_AND_STORE2)
   const double* k0sum;  // prescribed grid sums of the mean mode (or null)
   double a, b, k0mul;   // symbol a + b |d|^2 and k0sum scale (k0scale / ncell)
+  int slot;             // spec = slot-th spectrum of a contiguous group buffer (tensor-map z pass)
 };
-// spectral_solve for G replicas of the grid of f (register sides only, plain z pass):
-// every pass is one launch over all replicas; reps is a device array of G entries.
+// spectral_solve for G replicas of the grid of f (register sides only): every pass is
+// one launch over all replicas; reps is a device array of G entries.  With gzmap (a
+// tensor map of a group buffer that holds every replica's spectrum, from make_zmap with
+// ncomp = 3 x slots) the z pass is the persistent tensor-map one over all replicas'
+// tiles; otherwise one block per z tile.
 template <typename R>
-void spectral_solve_group(const FftCtx<R>& f, const RepFft* reps, int G, int mode, cudaStream_t st);
+void spectral_solve_group(const FftCtx<R>& f, const RepFft* reps, int G, int mode, cudaStream_t st,
+                          const void* gzmap = nullptr);
 bool fft_has_group_passes(int nx, int ny, int nz);
 
 // One-thread kernel whose bounded mbarrier wait runs out (a transaction that is never
