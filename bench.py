@@ -414,7 +414,7 @@ def extras(args, w, prec, sim, line, torch, icm, per_kernel):
     b = measure_batch(args, 0, 1, None, min(args.steps, 20))
     line["batch"] = {"workload": b["config"]["workload"], "ms_per_step": b["ms_per_step"], "value": b["value"],
                      "unit": "cell-updates/s", "blob_steps_per_s": b["blob_steps_per_s"],
-                     "launches_per_step": b["launches_per_step"], "group_solves": b["config"]["group_solves"],
+                     "launches_per_step": b["launches_per_step"], "grouped": b["config"]["grouped"],
                      "step_hbm_frac": b["roofline"]["frac"], "speedup_over_unbatched": b["speedup_over_unbatched"],
                      "steps": b["steps"], "clocks": b["clocks"]}
     log("[bench] extras: served stream")
@@ -500,7 +500,7 @@ def measure_batch(args, rank, world, dist, steps):
             "steps": steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "icm-batch-64-replicas-sides-32-48-64-96-fp32", "replicas": 64 * world,
-                       "plans": plans, "group_solves": bool(grouped),
+                       "plans": plans, "grouped": grouped,
                        "cells_per_replica_set": cells, "blobs": blobs, "parallelism": "replicas only",
                        "l2": "replica set of %.0f MB per field: timed on host clock around whole batch steps"
                              % (3 * cells * 4 / 1e6)},

@@ -366,10 +366,14 @@ icm_status icm_batch_step(icm_batch* batch, int64_t nsteps);
  * blob counts, through device tables of the members; about a dozen launches plus the
  * group solves per step.  Needs one precision for all members, register FFT passes
  * along every axis of every grid, and no WCA pair forces or thermal drift; otherwise
- * the batch runs as with grouped = 1.  Synchronises when the setting changes.
- * Errors: ICM_EINVAL for grouped other than 0, 1 or 2. */
+ * the batch runs as with grouped = 1.  Batched stages with the blob work in the group
+ * x passes (grouped = 3): as 2, but where every member has blobs and a register x side
+ * the spreads and interpolations run inside the x passes of the group solves, as in a
+ * single simulation's fused step (row bins of all members in three launches; no
+ * separate spread, zeroing or interpolation launch); otherwise as 2.  Synchronises when
+ * the setting changes.  Errors: ICM_EINVAL for grouped other than 0 to 3. */
 icm_status icm_batch_set_grouped(icm_batch* batch, int32_t grouped);
-/* The current setting (0, 1 or 2), -1 for a NULL batch. */
+/* The current setting (0 to 3), -1 for a NULL batch. */
 int32_t icm_batch_get_grouped(const icm_batch* batch);
 /* Kernel launches in one batch step of the captured graph (the graph is captured by
  * the first icm_batch_step after a change); -1 before a capture or for NULL. */
@@ -377,7 +381,7 @@ int64_t icm_batch_kernels_per_step(const icm_batch* batch);
 
 /* Autotune the batch as a whole: candidate plans (one choice at a time, as
  * icm_autotune) are applied to every member and timed over nsteps batch steps,
- * then group solves and batched stages (icm_batch_set_grouped 1, 2) with that plan;
+ * then group solves and batched stages (icm_batch_set_grouped 1, 2, 3) with that plan;
  * every member's state is
  * restored after each trial and the fastest choice is fixed on the batch and all
  * members.  Synchronises.  Errors: as icm_autotune. */

@@ -438,6 +438,21 @@ void enqueue_segment(icm_sim* s, int segment, int last) {
   }
 }
 
+// The row-block bins of a simulation's fused x passes (register x sides with blobs).
+RowBins row_bins(const icm_sim* s) {
+  RowBins bins;
+  bins.count = s->bin_idx;
+  bins.start = s->bin_idx ? s->bin_idx + s->nrowblk : nullptr;
+  bins.cursor = s->bin_idx ? s->bin_idx + 2 * s->nrowblk + 1 : nullptr;
+  bins.list = s->bin_list;
+  bins.geo = s->geo;
+  bins.acc = s->acc;
+  bins.nacc = kAccPerBlob;
+  bins.nblocks = s->nrowblk;
+  bins.capacity = (long long)kBinsPerBlob * s->cap;
+  return bins;
+}
+
 // The nine steps of Sec. III.C for one time level, enqueued on s->stream.  With a
 // segment index (batched group solves) only the blob and stencil work between two
 // solves is enqueued: segment 0 ends before the first solve, segments 1 and 2 after
@@ -484,16 +499,7 @@ void enqueue_step(icm_sim* s, Prof* prof, int segment = -1) {
   // thermal drift (Appendix B.2) at q^{n+1/2}, added to the right-hand side of the first solve
   const bool drift = (s->flags & ICM_FLAG_THERMAL_DRIFT) && s->kT > 0.0 && s->nb > 0;
   const bool fused = s->fused && s->plan.fused_blobs && s->nb > 0 && segment < 0;
-  RowBins bins;
-  bins.count = s->bin_idx;
-  bins.start = s->bin_idx + s->nrowblk;
-  bins.cursor = s->bin_idx + 2 * s->nrowblk + 1;
-  bins.list = s->bin_list;
-  bins.geo = s->geo;
-  bins.acc = s->acc;
-  bins.nacc = kAccPerBlob;
-  bins.nblocks = s->nrowblk;
-  bins.capacity = (long long)kBinsPerBlob * s->cap;
+  const RowBins bins = row_bins(s);
   const double geob = (double)(12 * sizeof(int) + 36 * sizeof(R));   // stencil record per blob
 
   // The blob-side prologue (scalars, predictor, pair forces, bins) reads only v and the
@@ -1551,7 +1557,8 @@ struct icm_batch {
   std::vector<cudaEvent_t> events;  // fork, joins, ..., done (last)
   cudaGraphExec_t gexec = nullptr;
   bool ok = false;
-  int grouped = 0;                     // 0 members apart, 1 group solves, 2 group solves + batched stages
+  int grouped = 0;                     // 0 members apart, 1 group solves, 2 group solves + batched stages,
+                                       // 3 the same with the blob work inside the group x passes
   long long kernels = -1;              // kernel nodes of the captured step graph
   std::vector<cudaStream_t> gstreams;  // one per group of the last capture
   void* reps = nullptr;                // device tables of the group solves
@@ -1614,6 +1621,7 @@ RepFft rep_entry(const icm_sim* s, int rt) {
   r.src = s->work;
   r.spec = s->spec;
   r.slot = -1;
+  r.rb = nullptr;
   r.dst2 = nullptr;
   if (rt == 0) {        // (rho/dt - eta/2 L) v~ = rhs, projected
     r.dst = s->v;
@@ -1638,11 +1646,17 @@ RepFft rep_entry(const icm_sim* s, int rt) {
   return r;
 }
 
+// Solve rt (0-2) of a group.  With the blob work in its x passes (blobs): the spread of
+// the table's vectors in the forward pass and the gathers in the inverse pass, which
+// stores v~ (rt 0), nothing (rt 1) or adds dv to v (rt 2).  Without: the spread sources
+// are in the work fields and the inverse pass stores v~, dv~ or v += dv and dv.
 template <typename R>
-void group_solve(const SolveGroup& g, const RepFft* reps, int rt, cudaStream_t st) {
+void group_solve(const SolveGroup& g, const RepFft* reps, int rt, bool blobs, cudaStream_t st) {
   const std::vector<icm_sim*>& m = rt == 0 ? g.members : g.inertial;
-  spectral_solve_group<R>(fft_ctx<R>(m[0]), reps + g.table[rt], (int)m.size(),
-                          rt == 2 ? OUT_ADD_AND_STORE2 : OUT_STORE, st, g.spec ? g.zmap.bytes : nullptr);
+  const int mode = blobs ? (rt == 0 ? OUT_STORE : (rt == 1 ? OUT_NONE : OUT_ADD))
+                         : (rt == 2 ? OUT_ADD_AND_STORE2 : OUT_STORE);
+  spectral_solve_group<R>(fft_ctx<R>(m[0]), reps + g.table[rt], (int)m.size(), mode, st,
+                          g.spec ? g.zmap.bytes : nullptr, blobs);
 }
 
 // The step of every member as batched stages: each stage of the per-member sequence
@@ -1685,16 +1699,49 @@ icm_status batch_capture_stages(icm_batch* b) {
     b->group_specs.push_back(buf);
     g.spec = (unsigned char*)buf;
   }
+  // grouped = 3: the blob work of the solves inside the group x passes, as in a single
+  // simulation's fused step, when every member can (register x side with row bins, and
+  // blobs); otherwise separate spread and gather launches.
+  bool blobs = b->grouped == 3;
+  for (const icm_sim* s : b->sims) blobs = blobs && s->fused && s->nb > 0;
   std::vector<RepFft> reps_host;
+  std::vector<RowBlobs> rbs_host;   // parallel to reps_host (blobs)
   for (SolveGroup& g : groups)
     for (int rt = 0; rt < 3; ++rt) {
       g.table[rt] = reps_host.size();
       for (icm_sim* m : rt == 0 ? g.members : g.inertial) {
         RepFft r = rep_entry(m, rt);
+        r.rb = nullptr;
         if (g.spec) {
           const int slot = (int)(std::find(g.members.begin(), g.members.end(), m) - g.members.begin());
           r.spec = g.spec + (size_t)slot * g.spec_bytes;
           r.slot = slot;
+        }
+        if (blobs) {
+          const RowBins bn = row_bins(m);
+          RowBlobs w;
+          w.start = bn.start;
+          w.list = bn.list;
+          w.geo = bn.geo;
+          w.p = blob_params(m);
+          const long long nb = m->nb;
+          if (rt == 0) {          // forces spread; J v~ gathered
+            w.vec = m->trap_k != 0.0 ? m->fe : (m->any_force ? m->f : nullptr);
+            w.acc = m->acc;
+            w.acc_lap = nullptr;
+          } else if (rt == 1) {   // the weighted momentum change spread; J dv~ gathered
+            r.src = nullptr;
+            w.vec = m->cdp;
+            w.acc = m->acc + 3 * nb;
+            w.acc_lap = nullptr;
+          } else {                // the source of the viscous correction spread; J dv, J L dv
+            r.src = nullptr;
+            r.dst2 = nullptr;
+            w.vec = m->src;
+            w.acc = m->acc + 6 * nb;
+            w.acc_lap = m->acc + 9 * nb;
+          }
+          rbs_host.push_back(w);
         }
         reps_host.push_back(r);
       }
@@ -1714,6 +1761,7 @@ icm_status batch_capture_stages(icm_batch* b) {
     m.step_dev = s->step_dev;
     m.hist_dev = s->hist_dev;
     m.inertial = s->any_me ? 1 : 0;
+    m.bins = row_bins(s);
     m.b0 = (long long)mof_all.size();
     for (long long i = 0; i < s->nb; ++i) mof_all.push_back((int)all.size());
     all.push_back(m);
@@ -1750,9 +1798,11 @@ icm_status batch_capture_stages(icm_batch* b) {
   const size_t o_rn = o_min + al(mof_in.size() * sizeof(int));
   const size_t o_rq = o_rn + al(rhs_noise.size() * sizeof(RhsMember<R>));
   const size_t o_reps = o_rq + al(rhs_quiet.size() * sizeof(RhsMember<R>));
-  const size_t total_bytes = o_reps + al(reps_host.size() * sizeof(RepFft)) + 256;
+  const size_t o_rbs = o_reps + al(reps_host.size() * sizeof(RepFft));
+  const size_t total_bytes = o_rbs + al(rbs_host.size() * sizeof(RowBlobs)) + 256;
   ICM_CK(cudaMalloc(&b->stage_tables, total_bytes));
   unsigned char* base = (unsigned char*)b->stage_tables;
+  for (size_t i = 0; i < rbs_host.size(); ++i) reps_host[i].rb = (const RowBlobs*)(base + o_rbs) + i;
   auto put = [&](size_t off, const void* src, size_t bytes) -> cudaError_t {
     return bytes ? cudaMemcpy(base + off, src, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
   };
@@ -1763,6 +1813,7 @@ icm_status batch_capture_stages(icm_batch* b) {
   ICM_CK(put(o_rn, rhs_noise.data(), rhs_noise.size() * sizeof(RhsMember<R>)));
   ICM_CK(put(o_rq, rhs_quiet.data(), rhs_quiet.size() * sizeof(RhsMember<R>)));
   ICM_CK(put(o_reps, reps_host.data(), reps_host.size() * sizeof(RepFft)));
+  ICM_CK(put(o_rbs, rbs_host.data(), rbs_host.size() * sizeof(RowBlobs)));
   const BlobMember* d_all = (const BlobMember*)(base + o_all);
   const BlobMember* d_in = (const BlobMember*)(base + o_in);
   const int* d_mall = (const int*)(base + o_mall);
@@ -1793,7 +1844,7 @@ icm_status batch_capture_stages(icm_batch* b) {
       if (m.empty()) continue;
       cudaEventRecord(in, st);
       cudaStreamWaitEvent(gs, in, 0);
-      group_solve<R>(groups[gi], d_reps, rt, gs);
+      group_solve<R>(groups[gi], d_reps, rt, blobs, gs);
       cudaEventRecord(out, gs);
       cudaStreamWaitEvent(st, out, 0);
     }
@@ -1802,23 +1853,35 @@ icm_status batch_capture_stages(icm_batch* b) {
   ICM_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   batch_scalars_before(d_all, n_all, st);
   batch_predict<R>(d_all, d_mall, nb_all, st);
+  if (blobs) batch_bins<R>(d_all, d_mall, nb_all, n_all, st);
   batch_rhs<R>(d_rn, (int)rhs_noise.size(), tot_noise, true, st);
   batch_rhs<R>(d_rq, (int)rhs_quiet.size(), tot_quiet, false, st);
-  if (any_force) batch_spread<R>(d_all, d_mall, nb_all, BV_FORCE, st);
+  if (any_force && !blobs) batch_spread<R>(d_all, d_mall, nb_all, BV_FORCE, st);
   solves(0);
   if (n_in > 0) {
-    batch_dp<R>(d_in, d_min, nb_in, st);
-    batch_zero_work<R>(d_in, n_in, ncell_in, st);
-    batch_spread<R>(d_in, d_min, nb_in, BV_CDP, st);
+    if (blobs) {
+      batch_dp_from(d_in, d_min, nb_in, st);
+    } else {
+      batch_dp<R>(d_in, d_min, nb_in, st);
+      batch_zero_work<R>(d_in, n_in, ncell_in, st);
+      batch_spread<R>(d_in, d_min, nb_in, BV_CDP, st);
+    }
   }
   solves(1);
   if (n_in > 0) {
-    batch_inertial<R>(d_in, d_min, nb_in, st);
-    batch_zero_work<R>(d_in, n_in, ncell_in, st);
-    batch_spread<R>(d_in, d_min, nb_in, BV_SRC, st);
+    if (blobs) {
+      batch_inertial_from(d_in, d_min, nb_in, st);
+    } else {
+      batch_inertial<R>(d_in, d_min, nb_in, st);
+      batch_zero_work<R>(d_in, n_in, ncell_in, st);
+      batch_spread<R>(d_in, d_min, nb_in, BV_SRC, st);
+    }
   }
   solves(2);
-  batch_finish<R>(d_all, d_mall, nb_all, st);
+  if (blobs)
+    batch_finish_from(d_all, d_mall, nb_all, st);
+  else
+    batch_finish<R>(d_all, d_mall, nb_all, st);
   batch_scalars_after(d_all, n_all, st);
   event();   // recorded after the launches of icm_batch_step
   const cudaError_t e = cudaStreamEndCapture(st, &graph);
@@ -1848,7 +1911,7 @@ icm_status batch_capture_stages(icm_batch* b) {
 
 icm_status batch_capture(icm_batch* b) {
   batch_clear_graph(b);
-  if (b->grouped == 2 && stages_possible(b))
+  if (b->grouped >= 2 && stages_possible(b))
     return b->sims[0]->prec == 32 ? batch_capture_stages<float>(b) : batch_capture_stages<double>(b);
   const size_t n = b->sims.size();
   // groups of two or more members on a grid with register FFT passes
@@ -1929,9 +1992,9 @@ icm_status batch_capture(icm_batch* b) {
       cudaStream_t gs = b->gstreams[gi];
       for (icm_sim* s : m) edge(s->stream, gs);
       if (m[0]->prec == 32)
-        group_solve<float>(g, reps, rt, gs);
+        group_solve<float>(g, reps, rt, false, gs);
       else
-        group_solve<double>(g, reps, rt, gs);
+        group_solve<double>(g, reps, rt, false, gs);
       cudaEvent_t done = event();
       cudaEventRecord(done, gs);
       for (icm_sim* s : m) {
@@ -2082,7 +2145,7 @@ icm_status icm_batch_step(icm_batch* b, int64_t nsteps) {
 }
 
 icm_status icm_batch_set_grouped(icm_batch* b, int32_t grouped) {
-  if (!b || grouped < 0 || grouped > 2) return fail(ICM_EINVAL, "bad arguments");
+  if (!b || grouped < 0 || grouped > 3) return fail(ICM_EINVAL, "bad arguments");
   if (b->grouped != grouped) {
     if (b->stream) ICM_CK(cudaStreamSynchronize(b->stream));
     b->grouped = grouped;
@@ -2183,16 +2246,24 @@ icm_status icm_batch_autotune(icm_batch* b, int32_t nsteps) {
       }
     }
   }
-  // batched stages: every per-member stage one launch over all members (the members'
-  // plans do not enter: the stages have their own launch shapes)
-  if (st == ICM_OK && stages_possible(b)) {
-    double ms = 0.0;
-    st = trial(best, 2, ms);
-    if (st == ICM_OK && ms < best_ms) {
-      best_grouped = 2;
-      best_ms = ms;
-    }
-  }
+  // batched stages: every per-member stage one launch over all members, the blob work
+  // in separate launches (2) or inside the group x passes (3), with and without the
+  // tensor-map z pass (the members' other plan choices do not enter: the stages have
+  // their own launch shapes)
+  if (stages_possible(b))
+    for (int g : {2, 3})
+      for (int tz : {1, 0}) {
+        if (st != ICM_OK) break;
+        icm_plan p = best;
+        p.tma_z = tz;
+        double ms = 0.0;
+        st = trial(p, g, ms);
+        if (st == ICM_OK && ms < best_ms) {
+          best = p;
+          best_grouped = g;
+          best_ms = ms;
+        }
+      }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != ICM_OK) return st;

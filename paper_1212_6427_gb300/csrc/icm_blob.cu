@@ -562,10 +562,11 @@ __global__ void k_bscal_after(const BlobMember* __restrict__ mem) {
 // ---------------------------------------------------------------------------
 // Row-block bins (count, scan, fill) and the elementwise updates of the fused step
 // ---------------------------------------------------------------------------
+// Blob b of nb: its stencil record, zeroed accumulators, and a count in every row
+// block its stencil reaches.
 template <typename R>
-__global__ void k_bin_count(BlobParams p, long long nb, const double* __restrict__ q, RowBins bins) {
-  const long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (b >= nb) return;
+__device__ __forceinline__ void bin_count_one(const BlobParams& p, long long nb, const double* __restrict__ q,
+                                              const RowBins& bins, long long b) {
   const double qb[3] = {q[3 * b], q[3 * b + 1], q[3 * b + 2]};
   BlobStencil<R> rec;
   const BlobSpan sp = make_stencil<R>(&rec, qb, p);
@@ -574,10 +575,17 @@ __global__ void k_bin_count(BlobParams p, long long nb, const double* __restrict
   for_each_row_block(sp, p, [&](int blk) { atomicAdd(&bins.count[blk], 1); });
 }
 
-// Exclusive scan of the counts (one block); resets the counts for the next build.
-// Each thread sums a contiguous chunk; the 1024 chunk sums are scanned with warp
-// shuffles and one shared array of warp totals (two barriers).
-__global__ void __launch_bounds__(1024) k_bin_scan(RowBins bins) {
+template <typename R>
+__global__ void k_bin_count(BlobParams p, long long nb, const double* __restrict__ q, RowBins bins) {
+  const long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  bin_count_one<R>(p, nb, q, bins, b);
+}
+
+// Exclusive scan of the counts (one block of 1024 threads); resets the counts for the
+// next build.  Each thread sums a contiguous chunk; the 1024 chunk sums are scanned
+// with warp shuffles and one shared array of warp totals (two barriers).
+__device__ __forceinline__ void bin_scan_block(const RowBins& bins) {
   __shared__ int warp_tot[32];
   const int n = bins.nblocks, t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int per = (n + 1023) / 1024;
@@ -613,10 +621,11 @@ __global__ void __launch_bounds__(1024) k_bin_scan(RowBins bins) {
   if (t == 1023) bins.start[n] = warp_tot[31];
 }
 
+__global__ void __launch_bounds__(1024) k_bin_scan(RowBins bins) { bin_scan_block(bins); }
+
 template <typename R>
-__global__ void k_bin_fill(BlobParams p, long long nb, const double* __restrict__ q, RowBins bins) {
-  const long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (b >= nb) return;
+__device__ __forceinline__ void bin_fill_one(const BlobParams& p, const double* __restrict__ q, const RowBins& bins,
+                                             long long b) {
   const double qb[3] = {q[3 * b], q[3 * b + 1], q[3 * b + 2]};
   const BlobSpan sp = make_stencil<R>(nullptr, qb, p);
   for_each_row_block(sp, p, [&](int blk) {
@@ -625,10 +634,17 @@ __global__ void k_bin_fill(BlobParams p, long long nb, const double* __restrict_
   });
 }
 
-// Step 4 from the gathered J v~: slip correction, momentum change, its weighted copy.
-__global__ void k_dp_from(BlobParams p, BlobState s, const double* __restrict__ jvt) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= 3 * s.nb) return;
+template <typename R>
+__global__ void k_bin_fill(BlobParams p, long long nb, const double* __restrict__ q, RowBins bins) {
+  const long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  bin_fill_one<R>(p, q, bins, b);
+}
+
+// Step 4 from the gathered J v~ (element i = 3 b + a): slip correction, momentum
+// change, its weighted copy.
+__device__ __forceinline__ void dp_from_one(const BlobParams& p, const BlobState& s, const double* __restrict__ jvt,
+                                            long long i) {
   const long long b = i / 3;
   const double me = s.me[b];
   const double visc = 0.5 * (p.eta / p.rho) * p.dt;
@@ -643,20 +659,30 @@ __global__ void k_dp_from(BlobParams p, BlobState s, const double* __restrict__ 
   s.cdp[i] = coef * dp;
 }
 
-// Steps 6-8 from the gathered J dv~: source of the viscous correction, u^{n+1}, and
-// the grid sum of the source for the momentum bookkeeping.
+__global__ void k_dp_from(BlobParams p, BlobState s, const double* __restrict__ jvt) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < 3 * s.nb) dp_from_one(p, s, jvt, i);
+}
+
+// Steps 6-8 from the gathered J dv~ (element i): the source of the viscous correction
+// (returned) and u^{n+1}.
+__device__ __forceinline__ double inertial_from_one(const BlobState& s, const double* __restrict__ jdvt, long long i) {
+  const long long b = i / 3;
+  const double jd = jdvt[i];
+  const double sr = s.dp[i] - s.me[b] * jd;
+  s.src[i] = sr;
+  s.u[i] = s.jvt[i] + jd + s.du[i];
+  return sr;
+}
+
+// Steps 6-8 from the gathered J dv~, with the grid sum of the source for the momentum
+// bookkeeping.
 __global__ void __launch_bounds__(256) k_inertial_from(BlobParams p, BlobState s, const double* __restrict__ jdvt) {
   __shared__ double red[3][256];
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int a = (int)(i % 3);
   double sr = 0.0;
-  if (i < 3 * s.nb) {
-    const long long b = i / 3;
-    const double jd = jdvt[i];
-    sr = s.dp[i] - s.me[b] * jd;
-    s.src[i] = sr;
-    s.u[i] = s.jvt[i] + jd + s.du[i];
-  }
+  if (i < 3 * s.nb) sr = inertial_from_one(s, jdvt, i);
   for (int c = 0; c < 3; ++c) red[c][threadIdx.x] = c == a ? sr : 0.0;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
@@ -667,12 +693,11 @@ __global__ void __launch_bounds__(256) k_inertial_from(BlobParams p, BlobState s
   if (threadIdx.x < 3) atomicAdd(&s.scal[SC_SUMSRC + threadIdx.x], red[threadIdx.x][0]);
 }
 
-// Step 9 from the gathered J v^{n+1} (= base + add) and J L dv: positions,
+// Step 9 from the gathered J v^{n+1} (= base + add) and J L dv (element i): positions,
 // velocities, the lagged slip term, checks.
-__global__ void k_finish_from(BlobParams p, BlobState s, const double* __restrict__ base,
-                              const double* __restrict__ add, const double* __restrict__ g, int inertial) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= 3 * s.nb) return;
+__device__ __forceinline__ void finish_from_one(const BlobParams& p, const BlobState& s,
+                                                const double* __restrict__ base, const double* __restrict__ add,
+                                                const double* __restrict__ g, int inertial, long long i) {
   const int a = (int)(i % 3);
   const double jv = base ? base[i] + add[i] : add[i];
   const double u = inertial ? s.u[i] : jv;
@@ -682,6 +707,59 @@ __global__ void k_finish_from(BlobParams p, BlobState s, const double* __restric
   s.g[i] = inertial ? g[i] * (p.inv_h * p.inv_h) : 0.0;
   if (!isfinite(qn) || !isfinite(u)) atomicOr(s.err, DEV_ERR_NONFINITE);
   if (fabs(u) * p.dt > p.h) atomicOr(s.err, DEV_ERR_CFL);
+}
+
+__global__ void k_finish_from(BlobParams p, BlobState s, const double* __restrict__ base,
+                              const double* __restrict__ add, const double* __restrict__ g, int inertial) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < 3 * s.nb) finish_from_one(p, s, base, add, g, inertial, i);
+}
+
+// The same over every member of a batch: one thread per blob (bins) or per blob
+// component (the elementwise steps); the member's accumulators are its bins.acc.
+template <typename R>
+__global__ void k_bbin_count(const BlobMember* __restrict__ mem, const int* __restrict__ member_of, long long nbt) {
+  const long long gb = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gb >= nbt) return;
+  const BlobMember& m = mem[member_of[gb]];
+  bin_count_one<R>(m.p, m.s.nb, m.s.qh, m.bins, gb - m.b0);
+}
+__global__ void __launch_bounds__(1024) k_bbin_scan(const BlobMember* __restrict__ mem) {
+  bin_scan_block(mem[blockIdx.x].bins);
+}
+template <typename R>
+__global__ void k_bbin_fill(const BlobMember* __restrict__ mem, const int* __restrict__ member_of, long long nbt) {
+  const long long gb = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gb >= nbt) return;
+  const BlobMember& m = mem[member_of[gb]];
+  bin_fill_one<R>(m.p, m.s.qh, m.bins, gb - m.b0);
+}
+__global__ void k_bdp_from(const BlobMember* __restrict__ mem, const int* __restrict__ member_of, long long nbt) {
+  const long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gi >= 3 * nbt) return;
+  const BlobMember& m = mem[member_of[gi / 3]];
+  dp_from_one(m.p, m.s, m.bins.acc, gi - 3 * m.b0);
+}
+__global__ void k_binertial_from(const BlobMember* __restrict__ mem, const int* __restrict__ member_of,
+                                 long long nbt) {
+  const long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gi >= 3 * nbt) return;
+  const BlobMember& m = mem[member_of[gi / 3]];
+  const long long i = gi - 3 * m.b0;
+  const double sr = inertial_from_one(m.s, m.bins.acc + 3 * m.s.nb, i);
+  atomicAdd(&m.s.scal[SC_SUMSRC + (int)(i % 3)], sr);
+}
+__global__ void k_bfinish_from(const BlobMember* __restrict__ mem, const int* __restrict__ member_of,
+                               long long nbt) {
+  const long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gi >= 3 * nbt) return;
+  const BlobMember& m = mem[member_of[gi / 3]];
+  const long long i = gi - 3 * m.b0, nb = m.s.nb;
+  const double* acc = m.bins.acc;   // J v~, J dv~, J dv, J L dv
+  if (m.inertial)
+    finish_from_one(m.p, m.s, m.s.jvt, acc + 6 * nb, acc + 9 * nb, 1, i);
+  else
+    finish_from_one(m.p, m.s, nullptr, acc, nullptr, 0, i);
 }
 
 inline unsigned eblocks(long long n) { return (unsigned)((n + 255) / 256); }
@@ -831,6 +909,22 @@ void batch_zero_work(const BlobMember* m, int nm, long long ncell_max, cudaStrea
   const unsigned gx = (unsigned)std::min<long long>((n16 + 255) / 256, 1024);
   k_bzero<R><<<dim3(std::max(gx, 1u), nm), 256, 0, st>>>(m);
 }
+template <typename R>
+void batch_bins(const BlobMember* m, const int* member_of, long long nbt, int nm, cudaStream_t st) {
+  if (nbt <= 0 || nm <= 0) return;
+  k_bbin_count<R><<<eblocks(nbt), 256, 0, st>>>(m, member_of, nbt);
+  k_bbin_scan<<<nm, 1024, 0, st>>>(m);
+  k_bbin_fill<R><<<eblocks(nbt), 256, 0, st>>>(m, member_of, nbt);
+}
+void batch_dp_from(const BlobMember* m, const int* member_of, long long nbt, cudaStream_t st) {
+  if (nbt > 0) k_bdp_from<<<eblocks(3 * nbt), 256, 0, st>>>(m, member_of, nbt);
+}
+void batch_inertial_from(const BlobMember* m, const int* member_of, long long nbt, cudaStream_t st) {
+  if (nbt > 0) k_binertial_from<<<eblocks(3 * nbt), 256, 0, st>>>(m, member_of, nbt);
+}
+void batch_finish_from(const BlobMember* m, const int* member_of, long long nbt, cudaStream_t st) {
+  if (nbt > 0) k_bfinish_from<<<eblocks(3 * nbt), 256, 0, st>>>(m, member_of, nbt);
+}
 void batch_scalars_before(const BlobMember* m, int nm, cudaStream_t st) {
   if (nm > 0) k_bscal_before<<<nm, 32, 0, st>>>(m);
 }
@@ -843,7 +937,8 @@ void batch_scalars_after(const BlobMember* m, int nm, cudaStream_t st) {
   template void batch_dp<R>(const BlobMember*, const int*, long long, cudaStream_t);                     \
   template void batch_inertial<R>(const BlobMember*, const int*, long long, cudaStream_t);               \
   template void batch_finish<R>(const BlobMember*, const int*, long long, cudaStream_t);                 \
-  template void batch_zero_work<R>(const BlobMember*, int, long long, cudaStream_t);
+  template void batch_zero_work<R>(const BlobMember*, int, long long, cudaStream_t);                     \
+  template void batch_bins<R>(const BlobMember*, const int*, long long, int, cudaStream_t);
 ICM_BINST(float)
 ICM_BINST(double)
 #undef ICM_BINST

@@ -858,7 +858,7 @@ __global__ void __launch_bounds__(kThreads) k_ypass2(cplx_t<R>* __restrict__ spe
 // block `bin` spread rb.vec into the rows (in shared memory, where the first stage
 // reads them; NST records staged by cp.async in `stage_mem`), added to src if src is
 // set.  The first-stage twiddles tw are loaded by the caller; ends with a block barrier.
-template <typename R, int N, int R1, int R2, bool BLOBS, int NST, int L = kXLines>
+template <typename R, int N, int R1, int R2, bool BLOBS, int NST, int L = kXLines, bool MAYBE_NO_VEC = false>
 __device__ __forceinline__ void x_forward_rows(cplx_t<R>* __restrict__ buf, const cplx_t<R>* __restrict__ tw,
                                                unsigned char* stage_mem, const R* __restrict__ src, long long row0,
                                                int nrows, long long ncell, int comp, int bin, const RowBlobs& rb,
@@ -867,6 +867,9 @@ __device__ __forceinline__ void x_forward_rows(cplx_t<R>* __restrict__ buf, cons
   static_assert(kRowBlock == 2 * kXLines, "row blocks are the x-pass blocks");
   static_assert(!BLOBS || L == kXLines, "blob work takes one row block per block");
   const bool dense = !BLOBS || src != nullptr;
+  // blob work of this block; with MAYBE_NO_VEC none where the source vector is absent
+  // (a replica of a group solve without forces), uniform over the block
+  const bool blobs = BLOBS && (!MAYBE_NO_VEC || rb.vec != nullptr);
   // one first-stage item (line l, offset n1) per thread; its loads are issued first
   constexpr int ITEMS = L * R2;
   static_assert(ITEMS <= kThreads, "one first-stage item per thread");
@@ -880,7 +883,7 @@ __device__ __forceinline__ void x_forward_rows(cplx_t<R>* __restrict__ buf, cons
     const int x = n1 + R2 * r;
     a[r] = mk(ok0 ? p0[x] : R(0), ok1 ? p0[N + x] : R(0));
   }
-  if (BLOBS) {
+  if (blobs) {
     // this block's tasks: records staged by cp.async while the buffer is zeroed
     StagedTask<R>* stage = reinterpret_cast<StagedTask<R>*>(stage_mem);
     const BlobStencil<R>* rec = reinterpret_cast<const BlobStencil<R>*>(rb.geo);
@@ -908,7 +911,7 @@ __device__ __forceinline__ void x_forward_rows(cplx_t<R>* __restrict__ buf, cons
   }
   __syncthreads();
   if (tid < ITEMS) {
-    if (BLOBS) {
+    if (blobs) {
 #pragma unroll
       for (int r = 0; r < R1; ++r) a[r] = cadd(a[r], buf[xaddr(l, n1 + R2 * r, N)]);
     }
@@ -942,12 +945,13 @@ __device__ __forceinline__ void split_half_spectra(const cplx_t<R>* __restrict__
 }
 
 // x forward pass: x_forward_rows, then the half spectra of the rows to spec.
-template <typename R, int N, int R1, int R2, bool BLOBS>
+// GRP: a group solve whose replicas carry their own blob work (reps[i].rb); otherwise rb.
+template <typename R, int N, int R1, int R2, bool BLOBS, bool GRP = false>
 __global__ void __launch_bounds__(kThreads, xf2_min_blocks<R, N>()) k_xfwd2(const R* __restrict__ src, cplx_t<R>* __restrict__ spec,
                                                     const cplx_t<R>* __restrict__ gtw, int nrows, long long ncell,
                                                     int kx, int kxp, RowBlobs rb, const RepFft* __restrict__ reps) {
   using C = cplx_t<R>;
-  if (!BLOBS && reps != nullptr) {   // replica blockIdx.y / 3 of a group solve
+  if ((!BLOBS || GRP) && reps != nullptr) {   // replica blockIdx.y / 3 of a group solve
     const RepFft& rp = reps[blockIdx.y / 3];
     src = reinterpret_cast<const R*>(rp.src);
     spec = reinterpret_cast<C*>(rp.spec);
@@ -960,8 +964,12 @@ __global__ void __launch_bounds__(kThreads, xf2_min_blocks<R, N>()) k_xfwd2(cons
   load_stage_twiddles<R, R1, R2>(tw, gtw, tid, kThreads);
   const int comp = blockIdx.y % 3;
   const long long row0 = (long long)blockIdx.x * (2 * L);
-  x_forward_rows<R, N, R1, R2, BLOBS, kStageF, L>(buf, tw, smem_raw + stage_offset<R, N>(), src, row0, nrows, ncell,
-                                               comp, blockIdx.x, rb, tid);
+  if constexpr (GRP)
+    x_forward_rows<R, N, R1, R2, BLOBS, kStageF, L, true>(buf, tw, smem_raw + stage_offset<R, N>(), src, row0, nrows,
+                                                       ncell, comp, blockIdx.x, *reps[blockIdx.y / 3].rb, tid);
+  else
+    x_forward_rows<R, N, R1, R2, BLOBS, kStageF, L>(buf, tw, smem_raw + stage_offset<R, N>(), src, row0, nrows,
+                                                 ncell, comp, blockIdx.x, rb, tid);
   C* out = spec + (size_t)comp * nrows * kxp;
   // the two half spectra of line l at wavenumber k (kx = N/2 + 1 of them)
   const auto split = [&](int l, int k) {
@@ -1070,18 +1078,20 @@ __global__ void __launch_bounds__(kThreads, 3) k_xyf(const float* __restrict__ s
 // last stage).  GATHER 1: the blobs of
 // this row block add the part of J x in these rows to rb.acc; GATHER 2: also J L x
 // (without 1/h^2) to rb.acc_lap.  x stays in shared memory for the gathers.
-template <typename R, int N, int R1, int R2, int MODE, int GATHER>
+// GRP: a group solve whose replicas gather into their own accumulators (reps[i].rb).
+template <typename R, int N, int R1, int R2, int MODE, int GATHER, bool GRP = false>
 __global__ void __launch_bounds__(kThreads, xi2_lean<R, N, MODE>() ? 4 : 1) k_xinv2(const cplx_t<R>* __restrict__ spec, R* __restrict__ dst,
                                                     R* __restrict__ dst2, const cplx_t<R>* __restrict__ gtw,
-                                                    int nrows, long long ncell, int kxp, RowBlobs rb,
+                                                    int nrows, long long ncell, int kxp, RowBlobs rb0,
                                                     const RepFft* __restrict__ reps) {
   using C = cplx_t<R>;
-  if (GATHER == 0 && reps != nullptr) {   // replica blockIdx.y / 3 of a group solve
+  if ((GATHER == 0 || GRP) && reps != nullptr) {   // replica blockIdx.y / 3 of a group solve
     const RepFft& rp = reps[blockIdx.y / 3];
     spec = reinterpret_cast<const C*>(rp.spec);
     dst = reinterpret_cast<R*>(rp.dst);
     dst2 = reinterpret_cast<R*>(rp.dst2);
   }
+  const RowBlobs& rb = GRP ? *reps[blockIdx.y / 3].rb : rb0;
   constexpr bool ADDS = MODE == OUT_ADD_AND_STORE2 || MODE == OUT_ADD;
   constexpr bool LEAN = xi2_lean<R, N, MODE>();
   constexpr int NST = xi2_stage<R, N, MODE>();
@@ -1276,7 +1286,8 @@ void set_xf_attributes() {
   const int big = 227 * 1024;
 #define ICM_ATTR(N, R1, R2)                                                                                        \
   cudaFuncSetAttribute(k_xfwd2<R, N, R1, R2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);           \
-  cudaFuncSetAttribute(k_xfwd2<R, N, R1, R2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_xfwd2<R, N, R1, R2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);            \
+  cudaFuncSetAttribute(k_xfwd2<R, N, R1, R2, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   ICM_FFT_SIDES(ICM_ATTR)
 #undef ICM_ATTR
   cudaFuncSetAttribute(k_xfwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
@@ -1320,7 +1331,10 @@ void set_xi_attributes() {
   cudaFuncSetAttribute(k_xinv2<R, N, R1, R2, OUT_ADD_AND_STORE2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big); \
   cudaFuncSetAttribute(k_xinv2<R, N, R1, R2, OUT_STORE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);    \
   cudaFuncSetAttribute(k_xinv2<R, N, R1, R2, OUT_NONE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);     \
-  cudaFuncSetAttribute(k_xinv2<R, N, R1, R2, OUT_ADD, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_xinv2<R, N, R1, R2, OUT_ADD, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);     \
+  cudaFuncSetAttribute(k_xinv2<R, N, R1, R2, OUT_STORE, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big); \
+  cudaFuncSetAttribute(k_xinv2<R, N, R1, R2, OUT_NONE, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);  \
+  cudaFuncSetAttribute(k_xinv2<R, N, R1, R2, OUT_ADD, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   ICM_FFT_SIDES(ICM_ATTR)
 #undef ICM_ATTR
   cudaFuncSetAttribute(k_xinv<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
@@ -1592,12 +1606,18 @@ void spectral_solve(const FftCtx<R>& f, const R* src, R* dst, R* dst2, int mode,
 // is 3 x replica + component, in the y pass blockIdx.z, in the z pass blockIdx.z is
 // the replica; the pointers and symbol constants come from the table.
 template <typename R>
-void fft_x_forward_group(const FftCtx<R>& f, const RepFft* reps, int G, cudaStream_t st) {
+void fft_x_forward_group(const FftCtx<R>& f, const RepFft* reps, int G, cudaStream_t st, bool blobs) {
   const int nrows = f.ny * f.nz;
+  const int xblocks = (nrows + 2 * kXLines - 1) / (2 * kXLines);
   const cplx_t<R>* tw = (const cplx_t<R>*)f.px.tw;
   switch (f.nx) {
 #define ICM_CASE(N, R1, R2) \
-  case N: k_xfwd2<R, N, R1, R2, false><<<dim3(xgrid<R, N, R2>(nrows), 3 * G), kThreads, smem_x2<R, N, x_plain_lines<R, N, R2>()>(), st>>>(nullptr, nullptr, tw, nrows, f.ncell, f.kx, f.kxp, RowBlobs{}, reps); return;
+  case N:                                                                                                              \
+    if (blobs)                                                                                                         \
+      k_xfwd2<R, N, R1, R2, true, true><<<dim3(xblocks, 3 * G), kThreads, smem_x2b<R, N, kStageF>(), st>>>(nullptr, nullptr, tw, nrows, f.ncell, f.kx, f.kxp, RowBlobs{}, reps); \
+    else                                                                                                               \
+      k_xfwd2<R, N, R1, R2, false><<<dim3(xgrid<R, N, R2>(nrows), 3 * G), kThreads, smem_x2<R, N, x_plain_lines<R, N, R2>()>(), st>>>(nullptr, nullptr, tw, nrows, f.ncell, f.kx, f.kxp, RowBlobs{}, reps); \
+    return;
     ICM_FFT_SIDES(ICM_CASE)
 #undef ICM_CASE
     default: break;
@@ -1665,13 +1685,20 @@ void fft_yz_group(const FftCtx<R>& f, const RepFft* reps, int G, int which, cuda
 }
 
 template <typename R>
-void fft_x_inverse_group(const FftCtx<R>& f, const RepFft* reps, int G, int mode, cudaStream_t st) {
+void fft_x_inverse_group(const FftCtx<R>& f, const RepFft* reps, int G, int mode, cudaStream_t st, bool gathers) {
   const int nrows = f.ny * f.nz;
+  const int xblocks = (nrows + 2 * kXLines - 1) / (2 * kXLines);
   const cplx_t<R>* tw = (const cplx_t<R>*)f.px.tw;
   switch (f.nx) {
 #define ICM_CASE(N, R1, R2)                                                                                             \
   case N:                                                                                                               \
-    if (mode == OUT_STORE)                                                                                              \
+    if (gathers && mode == OUT_STORE)                                                                                   \
+      k_xinv2<R, N, R1, R2, OUT_STORE, 1, true><<<dim3(xblocks, 3 * G), kThreads, smem_x2b<R, N, xi2_stage<R, N, OUT_STORE>()>(), st>>>(nullptr, nullptr, nullptr, tw, nrows, f.ncell, f.kxp, RowBlobs{}, reps); \
+    else if (gathers && mode == OUT_NONE)                                                                               \
+      k_xinv2<R, N, R1, R2, OUT_NONE, 1, true><<<dim3(xblocks, 3 * G), kThreads, smem_x2b<R, N, xi2_stage<R, N, OUT_NONE>()>(), st>>>(nullptr, nullptr, nullptr, tw, nrows, f.ncell, f.kxp, RowBlobs{}, reps); \
+    else if (gathers)                                                                                                   \
+      k_xinv2<R, N, R1, R2, OUT_ADD, 2, true><<<dim3(xblocks, 3 * G), kThreads, smem_x2b<R, N, xi2_stage<R, N, OUT_ADD>()>(), st>>>(nullptr, nullptr, nullptr, tw, nrows, f.ncell, f.kxp, RowBlobs{}, reps); \
+    else if (mode == OUT_STORE)                                                                                         \
       k_xinv2<R, N, R1, R2, OUT_STORE, 0><<<dim3(xgrid<R, N, R2>(nrows), 3 * G), kThreads, smem_x2<R, N, x_plain_lines<R, N, R2>()>(), st>>>(nullptr, nullptr, nullptr, tw, nrows, f.ncell, f.kxp, RowBlobs{}, reps); \
     else                                                                                                                \
       k_xinv2<R, N, R1, R2, OUT_ADD_AND_STORE2, 0><<<dim3((nrows + 2 * kXLines - 1) / (2 * kXLines), 3 * G), kThreads, smem_x2<R, N, kXLines>(), st>>>(nullptr, nullptr, nullptr, tw, nrows, f.ncell, f.kxp, RowBlobs{}, reps); \
@@ -1685,12 +1712,12 @@ void fft_x_inverse_group(const FftCtx<R>& f, const RepFft* reps, int G, int mode
 
 template <typename R>
 void spectral_solve_group(const FftCtx<R>& f, const RepFft* reps, int G, int mode, cudaStream_t st,
-                          const void* gzmap) {
-  fft_x_forward_group<R>(f, reps, G, st);
+                          const void* gzmap, bool blobs) {
+  fft_x_forward_group<R>(f, reps, G, st, blobs);
   fft_yz_group<R>(f, reps, G, 0, st, nullptr);
   fft_yz_group<R>(f, reps, G, 1, st, gzmap);
   fft_yz_group<R>(f, reps, G, 2, st, nullptr);
-  fft_x_inverse_group<R>(f, reps, G, mode, st);
+  fft_x_inverse_group<R>(f, reps, G, mode, st, blobs);
 }
 
 #if ICM_SHARD(0)
@@ -1751,13 +1778,13 @@ bool make_zmap(void* map, const void* spec, int precision, int kx, int kxp, int 
 #define ICM_INST_XF(R, KW)                                                                               \
   KW template void fft_x_forward<R>(const FftCtx<R>&, const R*, cudaStream_t);                           \
   KW template void fft_x_forward_blobs<R>(const FftCtx<R>&, const R*, const RowBlobs&, cudaStream_t);    \
-  KW template void fft_x_forward_group<R>(const FftCtx<R>&, const RepFft*, int, cudaStream_t);            \
+  KW template void fft_x_forward_group<R>(const FftCtx<R>&, const RepFft*, int, cudaStream_t, bool);      \
   KW template void fft_xy_forward<R>(const FftCtx<R>&, const R*, const RowBlobs*, cudaStream_t);         \
   KW template void fft_prepare_xf<R>();
 #define ICM_INST_XI(R, KW)                                                                               \
   KW template void fft_x_inverse<R>(const FftCtx<R>&, R*, R*, int, cudaStream_t);                        \
   KW template void fft_x_inverse_blobs<R>(const FftCtx<R>&, R*, int, const RowBlobs&, cudaStream_t);     \
-  KW template void fft_x_inverse_group<R>(const FftCtx<R>&, const RepFft*, int, int, cudaStream_t);       \
+  KW template void fft_x_inverse_group<R>(const FftCtx<R>&, const RepFft*, int, int, cudaStream_t, bool); \
   KW template void fft_prepare_xi<R>();
 #define ICM_INST_YZ(R, KW)                                                                               \
   KW template void fft_y<R>(const FftCtx<R>&, bool, cudaStream_t);                                       \
@@ -1810,9 +1837,10 @@ template void spectral_solve<float>(const FftCtx<float>&, const float*, float*, 
                                     const double*, double, cudaStream_t);
 template void spectral_solve<double>(const FftCtx<double>&, const double*, double*, double*, int, double, double,
                                      const double*, double, cudaStream_t);
-template void spectral_solve_group<float>(const FftCtx<float>&, const RepFft*, int, int, cudaStream_t, const void*);
+template void spectral_solve_group<float>(const FftCtx<float>&, const RepFft*, int, int, cudaStream_t, const void*,
+                                          bool);
 template void spectral_solve_group<double>(const FftCtx<double>&, const RepFft*, int, int, cudaStream_t,
-                                           const void*);
+                                           const void*, bool);
 #endif
 #undef ICM_NONE
 #undef ICM_INST_XF

@@ -85,6 +85,7 @@ template <typename R>
 void fft_z_symbol(const FftCtx<R>& f, double a, double b, const double* k0sum, double k0scale, cudaStream_t st);
 template <typename R> void fft_x_inverse(const FftCtx<R>& f, R* dst, R* dst2, int mode, cudaStream_t st);
 
+struct RowBlobs;
 // One replica of a group solve: the same grid for every replica, launched once for all.
 struct RepFft {
   const void* src;      // real face field (3 ncell)
@@ -94,15 +95,19 @@ struct RepFft {
   const double* k0sum;  // prescribed grid sums of the mean mode (or null)
   double a, b, k0mul;   // symbol a + b |d|^2 and k0sum scale (k0scale / ncell)
   int slot;             // spec = slot-th spectrum of a contiguous group buffer (tensor-map z pass)
+  const RowBlobs* rb;   // the replica's blob work in the x passes (blob solves), or null
 };
 // spectral_solve for G replicas of the grid of f (register sides only): every pass is
 // one launch over all replicas; reps is a device array of G entries.  With gzmap (a
 // tensor map of a group buffer that holds every replica's spectrum, from make_zmap with
 // ncomp = 3 x slots) the z pass is the persistent tensor-map one over all replicas'
-// tiles; otherwise one block per z tile.
+// tiles; otherwise one block per z tile.  With blobs, every replica's x passes carry
+// its blob work as the single-simulation fused passes do (reps[i].rb: the spread of
+// rb->vec in the forward pass, when set, and the gathers of the inverse pass; mode
+// OUT_STORE and OUT_NONE gather J, OUT_ADD also J L; src may be null).
 template <typename R>
 void spectral_solve_group(const FftCtx<R>& f, const RepFft* reps, int G, int mode, cudaStream_t st,
-                          const void* gzmap = nullptr);
+                          const void* gzmap = nullptr, bool blobs = false);
 bool fft_has_group_passes(int nx, int ny, int nz);
 
 // One-thread kernel whose bounded mbarrier wait runs out (a transaction that is never
@@ -304,9 +309,19 @@ struct BlobMember {
   int* hist_dev;          // Adams-Bashforth history flag
   long long b0;           // first global blob index of the member
   int inertial;           // any excess mass: steps 4-8 run
+  RowBins bins;           // row-block bins and accumulators of the fused x passes (batched stages)
 };
 enum BatchVec : int { BV_FORCE = 0, BV_CDP = 1, BV_SRC = 2 };
 template <typename R> void batch_predict(const BlobMember* m, const int* member_of, long long nbt, cudaStream_t st);
+// Batched stages with the blob work inside the group x passes: the row bins of every
+// member at q^{n+1/2} (count, one scan block per member, fill; the accumulators zeroed),
+// and steps 4, 6-8 and 9 from the accumulators the inverse x passes gathered into
+// (bins.acc: J v~, J dv~, J dv, J L dv without 1/h^2, 3 nb each).
+template <typename R>
+void batch_bins(const BlobMember* m, const int* member_of, long long nbt, int nm, cudaStream_t st);
+void batch_dp_from(const BlobMember* m, const int* member_of, long long nbt, cudaStream_t st);
+void batch_inertial_from(const BlobMember* m, const int* member_of, long long nbt, cudaStream_t st);
+void batch_finish_from(const BlobMember* m, const int* member_of, long long nbt, cudaStream_t st);
 template <typename R>
 void batch_spread(const BlobMember* m, const int* member_of, long long nbt, int which, cudaStream_t st);
 template <typename R> void batch_dp(const BlobMember* m, const int* member_of, long long nbt, cudaStream_t st);

@@ -159,7 +159,7 @@ def test_grouped_batch_matches_individual_runs(icm, precision):
         assert rel(got["pos"], want["pos"]) < TOL[precision] * 1e-2
         np.testing.assert_allclose(got["momentum"], want["momentum"], rtol=1e-9, atol=1e-12)
     with pytest.raises(icm.IcmError):
-        icm.icm_batch_set_grouped(b, 3)
+        icm.icm_batch_set_grouped(b, 4)
     icm.icm_batch_destroy(b)
     for s in sims:
         s.close()
@@ -195,16 +195,19 @@ def _make(icm, j, precision):
     return s
 
 
+@pytest.mark.parametrize("grouped", [2, 3])
 @pytest.mark.parametrize("precision", [64, 32])
-def test_batched_stages_match_individual_runs(icm, precision):
+def test_batched_stages_match_individual_runs(icm, precision, grouped):
     """Batched stages (grouped = 2): every per-member stage is one launch over all members
-    of mixed grids, kernels and blob counts; each member's result equals its run alone."""
+    of mixed grids, kernels and blob counts; each member's result equals its run alone.
+    With grouped = 3 the same (one member has no blobs: the blob work stays in separate
+    launches)."""
     jobs = _stage_jobs(precision)
     sims = [_make(icm, j, precision) for j in jobs]
     b = icm.icm_batch_create()
     icm.icm_batch_set(b, [s.handle for s in sims])
-    icm.icm_batch_set_grouped(b, 2)
-    assert icm.icm_batch_get_grouped(b) == 2
+    icm.icm_batch_set_grouped(b, grouped)
+    assert icm.icm_batch_get_grouped(b) == grouped
     icm.icm_batch_step(b, 2)
     icm.icm_batch_step(b, 3)   # replays the same graph
     icm.icm_batch_sync(b)
@@ -221,6 +224,60 @@ def test_batched_stages_match_individual_runs(icm, precision):
         if len(j["q"]):
             assert rel(got["vel"], want["vel"]) < TOL[precision]
             assert rel(got["pos"], want["pos"]) < TOL[precision] * 1e-2
+        np.testing.assert_allclose(got["momentum"], want["momentum"], rtol=1e-9, atol=1e-12)
+    icm.icm_batch_destroy(b)
+    for s in sims:
+        s.close()
+
+
+def _blob_stage_jobs(precision):
+    # every member with blobs: the blob work runs inside the group x passes.  A neutrally
+    # buoyant 32^3 member beside an inertial one, a 48^3 pair (one without noise, one in
+    # a harmonic trap), a 64^3 member without forces, a 32^3 member with another cell width.
+    spec = [(32, 1.0, 4, 7, (-0.5, 2.0), 2e-3, None, (1e-3, 0.0, -2e-3)),
+            (32, 1.0, 3, 12, None, 2e-3, None, (0.0, 2e-3, 0.0)),
+            (48, 1.0, 3, 4, (-0.5, 2.0), 0.0, None, (1e-3, 0.0, -2e-3)),
+            (48, 1.0, 4, 9, (-0.5, 2.0), 2e-3, (0.02, (20.0, 24.0, 30.0)), (1e-3, 0.0, -2e-3)),
+            (64, 1.0, 4, 8, (-0.5, 2.0), 2e-3, None, (0.0, 0.0, 0.0)),
+            (32, 0.5, 3, 5, (0.0, 1.0), 2.5e-4, None, (1e-3, 0.0, -2e-3))]
+    out = []
+    for r, (side, h, kernel, nb, me_range, kT, trap, force) in enumerate(spec):
+        cfg = dict(grid=(side, side, side), h=h, rho=1.0, eta=1.0, kT=kT, dt=0.05 * h * h, kernel=kernel,
+                   seed=90 + r, precision=precision, steps=5, nblobs=nb, me_range=me_range, force=force,
+                   place_seed=190 + r, min_spacing=2.0)
+        j = wl._materialise(cfg)
+        j["trap"] = trap
+        out.append(j)
+    return out
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_batched_stages_with_blob_passes_match_individual_runs(icm, precision):
+    """Batched stages (grouped = 3) whose members all have blobs on register x sides: the
+    spreads and gathers run inside the group x passes (row bins of every member in three
+    launches, no separate spread, zeroing or gather launch); each member's result equals
+    its run alone."""
+    jobs = _blob_stage_jobs(precision)
+    sims = [_make(icm, j, precision) for j in jobs]
+    b = icm.icm_batch_create()
+    icm.icm_batch_set(b, [s.handle for s in sims])
+    icm.icm_batch_set_grouped(b, 3)
+    icm.icm_batch_step(b, 2)
+    icm.icm_batch_step(b, 3)
+    icm.icm_batch_sync(b)
+    # scalars (2), predictor, bins (3), RHS with and without noise (2), steps 4 and 6-8
+    # from the accumulators (2), finish; five FFT launches for each of four groups in
+    # each of the three solves
+    assert icm.icm_batch_kernels_per_step(b) == 11 + 5 * 4 * 3
+    for j, s in zip(jobs, sims):
+        got = s.read()
+        assert got["step"] == 5
+        alone = _make(icm, j, precision)
+        alone.step(5)
+        want = alone.read()
+        alone.close()
+        assert rel(got["vel"], want["vel"]) < TOL[precision]
+        assert rel(got["pos"], want["pos"]) < TOL[precision] * 1e-2
         np.testing.assert_allclose(got["momentum"], want["momentum"], rtol=1e-9, atol=1e-12)
     icm.icm_batch_destroy(b)
     for s in sims:
