@@ -129,45 +129,51 @@ __device__ __forceinline__ void rhs_run(RhsSmem<R>& sm, const R* __restrict__ v,
                                         long long tile, int k0, int kend, int tx, int ty) {
   const int tid = tx + TX * ty;
   const int ntx = (g.nx + TX - 1) / TX;
-  const long long nc = g.ncell;
-  const long long plane = (long long)g.nx * g.ny;
-  const R rho = (R)g.rho, inv_h = (R)(1.0 / g.h), inv_h2 = (R)(1.0 / (g.h * g.h));
-  const R rho_dt = (R)(g.rho / g.dt), half_eta = (R)(0.5 * g.eta);
+  // offsets in 32 bits: 3 ncell <= 3 x 512^3 < 2^32
+  const uint32_t nc = (uint32_t)g.ncell;
+  const uint32_t plane = (uint32_t)g.nx * (uint32_t)g.ny;
+  // r = cc v + ce (sum of the six neighbours) + div Sigma - AB2, with cc = rho/dt - 6 ce,
+  // ce = (eta/2)/h^2; the 1/2 of every face or edge average of the advection is folded
+  // into its factor aq = rho/(4h)
+  const R ce = (R)(0.5 * g.eta / (g.h * g.h));
+  const R cc = (R)(g.rho / g.dt - 3.0 * g.eta / (g.h * g.h));
+  const R aq = g.advection ? (R)(0.25 * g.rho / g.h) : R(0);
   const double s_amp = sqrt(g.kT * g.eta / (g.h * g.h * g.h * g.dt));
   const R sd = (R)(2.0 * s_amp * (1.0 / g.h)), so = (R)(1.4142135623730951 * s_amp * (1.0 / g.h));
-  const R adv_on = g.advection ? R(1) : R(0);
-  const R h2 = R(0.5);
   const int lx = tx + 1, ly = ty + 1;
   {
     const int i0 = (int)(tile % ntx) * TX, j0 = (int)(tile / ntx) * TY;
     const int i = i0 + tx, j = j0 + ty;
     const bool active = i < g.nx && j < g.ny;
     // threads past a ragged edge hold the periodic images their neighbours read
-    const long long own = wrapm(i, g.nx) + (long long)g.nx * wrapm(j, g.ny);
+    const uint32_t own = (uint32_t)wrapm(i, g.nx) + (uint32_t)g.nx * (uint32_t)wrapm(j, g.ny);
     // the halo cell whose velocities this thread loads, if any
     int hx = 0, hy = 0;
-    long long hoff = -1;
-    if (tid < NHALO) {
+    const bool has_halo = tid < NHALO;
+    uint32_t hoff = 0;
+    if (has_halo) {
       halo_cell(tid, hx, hy);
-      hoff = wrapm(i0 - 1 + hx, g.nx) + (long long)g.nx * wrapm(j0 - 1 + hy, g.ny);
+      hoff = (uint32_t)wrapm(i0 - 1 + hx, g.nx) + (uint32_t)g.nx * (uint32_t)wrapm(j0 - 1 + hy, g.ny);
     }
     // the halo stress normal this thread draws, if any
     HaloTask ht{0, 0, 0, 0u, false, false};
     const bool hnoise = NOISE && halo_task(tid, ht);
     const uint32_t ncell = hnoise ? (uint32_t)(wrapm(i0 - 1 + ht.hx, g.nx) + g.nx * wrapm(j0 - 1 + ht.hy, g.ny)) : 0u;
     auto load = [&](R (&o)[3], R (&hv)[3], int k) {
-      const long long zo = plane * wrapi(k, g.nz);
+      const uint32_t zo = plane * (uint32_t)wrapi(k, g.nz);
+      const uint32_t a = zo + own;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) o[c] = v[c * nc + zo + own];
-      if (hoff >= 0) {
+      for (int c = 0; c < 3; ++c) o[c] = v[a + c * nc];
+      if (has_halo) {
+        const uint32_t b = zo + hoff;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) hv[c] = v[c * nc + zo + hoff];
+        for (int c = 0; c < 3; ++c) hv[c] = v[b + c * nc];
       }
     };
     auto put = [&](int slot, const R (&o)[3], const R (&hv)[3]) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) sm.v[slot][c][ly][lx] = o[c];
-      if (hoff >= 0) {
+      if (has_halo) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) sm.v[slot][c][hy][hx] = hv[c];
       }
@@ -183,32 +189,29 @@ __device__ __forceinline__ void rhs_run(RhsSmem<R>& sm, const R* __restrict__ v,
     load(vn, hq, k0 + 1);
     if (NOISE) {
       // plane k0-1: only the own cell's Z_zz is read; plane k0 into slot 1
-      cell_normals<R>((uint32_t)(own + plane * wrapi(k0 - 1, g.nz)), step, g.key0, g.key1, zc);
+      cell_normals<R>(own + plane * (uint32_t)wrapi(k0 - 1, g.nz), step, g.key0, g.key1, zc);
       zzp = zc[2];
-      gen_own<R>(sm, 1, zn, (uint32_t)(own + plane * k0), g, step, lx, ly);
-      if (hnoise) gen_halo<R>(sm, 1, ht, ncell + (uint32_t)(plane * k0), g, step);
+      gen_own<R>(sm, 1, zn, own + plane * (uint32_t)k0, g, step, lx, ly);
+      if (hnoise) gen_halo<R>(sm, 1, ht, ncell + plane * (uint32_t)k0, g, step);
     }
     for (int k = k0; k < kend; ++k) {
       const int kk = k - k0;
       const int sp = kk % kRing, sc = (kk + 1) % kRing, sn = (kk + 2) % kRing;
       const int zs = (kk + 1) % kZRing, zsn = (kk + 2) % kZRing;   // normals of planes k, k+1
       put(sn, vn, hq);                                         // plane k+1
-      long long o = 0;
+      const uint32_t o = own + plane * (uint32_t)k;
       R ao[3] = {R(0), R(0), R(0)};
-      if (active) {
-        o = own + plane * k;
-        if (hist) {
-          ao[0] = adv[o];
-          ao[1] = adv[nc + o];
-          ao[2] = adv[2 * nc + o];
-        }
+      if (active && hist) {
+        ao[0] = adv[o];
+        ao[1] = adv[o + nc];
+        ao[2] = adv[o + 2 * nc];
       }
       if (k + 1 < kend) load(vq, hq, k + 2);                  // in flight during the noise
       if (NOISE) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) zc[c] = zn[c];
-        const uint32_t pk = (uint32_t)(plane * wrapi(k + 1, g.nz));
-        gen_own<R>(sm, zsn, zn, (uint32_t)own + pk, g, step, lx, ly);
+        const uint32_t pk = plane * (uint32_t)wrapi(k + 1, g.nz);
+        gen_own<R>(sm, zsn, zn, own + pk, g, step, lx, ly);
         if (hnoise) gen_halo<R>(sm, zsn, ht, ncell + pk, g, step);
       }
       __syncthreads();
@@ -229,25 +232,27 @@ __device__ __forceinline__ void rhs_run(RhsSmem<R>& sm, const R* __restrict__ v,
         const R z_yp = C[2][ly + 1][lx], z_ym = C[2][ly - 1][lx], z_zp = vn[2], z_zm = vp[2];
         const R z_zpxm = N[2][ly][lx - 1], z_zpym = N[2][ly - 1][lx];
 
-        // edge products ut_a ut_b at edge index e: ut_a = (v_a[e] + v_a[e-e_b])/2, ut_b = (v_b[e] + v_b[e-e_a])/2
-        const R exy_c = (x_c + x_ym) * h2 * ((y_c + y_xm) * h2);
-        const R exy_yp = (x_yp + x_c) * h2 * ((y_yp + y_ypxm) * h2);
-        const R exy_xp = (x_xp + x_xpym) * h2 * ((y_xp + y_c) * h2);
-        const R exz_c = (x_c + x_zm) * h2 * ((z_c + z_xm) * h2);
-        const R exz_zp = (x_zp + x_c) * h2 * ((z_zp + z_zpxm) * h2);
-        const R exz_xp = (x_xp + x_xpzm) * h2 * ((z_xp + z_c) * h2);
-        const R eyz_c = (y_c + y_zm) * h2 * ((z_c + z_ym) * h2);
-        const R eyz_zp = (y_zp + y_c) * h2 * ((z_zp + z_zpym) * h2);
-        const R eyz_yp = (y_yp + y_ypzm) * h2 * ((z_yp + z_c) * h2);
-        const R ubx_c = (x_xp + x_c) * h2, ubx_m = (x_c + x_xm) * h2;
-        const R uby_c = (y_yp + y_c) * h2, uby_m = (y_c + y_ym) * h2;
-        const R ubz_c = (z_zp + z_c) * h2, ubz_m = (z_c + z_zm) * h2;
-        const R ax = adv_on * rho * inv_h * (ubx_c * ubx_c - ubx_m * ubx_m + exy_yp - exy_c + exz_zp - exz_c);
-        const R ay = adv_on * rho * inv_h * (uby_c * uby_c - uby_m * uby_m + exy_xp - exy_c + eyz_zp - eyz_c);
-        const R az = adv_on * rho * inv_h * (ubz_c * ubz_c - ubz_m * ubz_m + exz_xp - exz_c + eyz_yp - eyz_c);
-        const R lapx = (x_xp + x_xm + x_yp + x_ym + x_zp + x_zm - R(6) * x_c) * inv_h2;
-        const R lapy = (y_xp + y_xm + y_yp + y_ym + y_zp + y_zm - R(6) * y_c) * inv_h2;
-        const R lapz = (z_xp + z_xm + z_yp + z_ym + z_zp + z_zm - R(6) * z_c) * inv_h2;
+        // edge products ut_a ut_b at edge index e, ut_a = (v_a[e] + v_a[e-e_b])/2 and
+        // ut_b = (v_b[e] + v_b[e-e_a])/2, and the squared cell-centre averages, each
+        // without its factor 1/4 (in aq)
+        const R exy_c = (x_c + x_ym) * (y_c + y_xm);
+        const R exy_yp = (x_yp + x_c) * (y_yp + y_ypxm);
+        const R exy_xp = (x_xp + x_xpym) * (y_xp + y_c);
+        const R exz_c = (x_c + x_zm) * (z_c + z_xm);
+        const R exz_zp = (x_zp + x_c) * (z_zp + z_zpxm);
+        const R exz_xp = (x_xp + x_xpzm) * (z_xp + z_c);
+        const R eyz_c = (y_c + y_zm) * (z_c + z_ym);
+        const R eyz_zp = (y_zp + y_c) * (z_zp + z_zpym);
+        const R eyz_yp = (y_yp + y_ypzm) * (z_yp + z_c);
+        const R ubx_c = x_xp + x_c, ubx_m = x_c + x_xm;
+        const R uby_c = y_yp + y_c, uby_m = y_c + y_ym;
+        const R ubz_c = z_zp + z_c, ubz_m = z_c + z_zm;
+        const R ax = aq * (ubx_c * ubx_c - ubx_m * ubx_m + exy_yp - exy_c + exz_zp - exz_c);
+        const R ay = aq * (uby_c * uby_c - uby_m * uby_m + exy_xp - exy_c + eyz_zp - eyz_c);
+        const R az = aq * (ubz_c * ubz_c - ubz_m * ubz_m + exz_xp - exz_c + eyz_yp - eyz_c);
+        const R nbx = x_xp + x_xm + x_yp + x_ym + x_zp + x_zm;
+        const R nby = y_xp + y_xm + y_yp + y_ym + y_zp + y_zm;
+        const R nbz = z_xp + z_xm + z_yp + z_ym + z_zp + z_zm;
         R fx = R(0), fy = R(0), fz = R(0);
         if (NOISE) {
           const auto Z = sm.z[zs];   // plane k: [0] xx, [1] yy, [2] xy, [3] xz, [4] yz
@@ -262,11 +267,11 @@ __device__ __forceinline__ void rhs_run(RhsSmem<R>& sm, const R* __restrict__ v,
           ao[2] = az;
         }
         adv[o] = ax;
-        adv[nc + o] = ay;
-        adv[2 * nc + o] = az;
-        rhs[o] = rho_dt * x_c + half_eta * lapx + fx - (R(1.5) * ax - R(0.5) * ao[0]);
-        rhs[nc + o] = rho_dt * y_c + half_eta * lapy + fy - (R(1.5) * ay - R(0.5) * ao[1]);
-        rhs[2 * nc + o] = rho_dt * z_c + half_eta * lapz + fz - (R(1.5) * az - R(0.5) * ao[2]);
+        adv[o + nc] = ay;
+        adv[o + 2 * nc] = az;
+        rhs[o] = cc * x_c + ce * nbx + fx - (R(1.5) * ax - R(0.5) * ao[0]);
+        rhs[o + nc] = cc * y_c + ce * nby + fy - (R(1.5) * ay - R(0.5) * ao[1]);
+        rhs[o + 2 * nc] = cc * z_c + ce * nbz + fz - (R(1.5) * az - R(0.5) * ao[2]);
       }
       if (NOISE) zzp = zc[2];
 #pragma unroll
