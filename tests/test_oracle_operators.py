@@ -192,6 +192,23 @@ def test_stress_normals_moments_and_independence():
     assert not np.allclose(z, philox.stress_normals(seed=78, step=3, ncell=200_000))
 
 
+def test_stress_normals_counter_layout():
+    """The normals are Box-Muller pairs of the Philox words of the counters the layout
+    names, recomputed here for single cells from the generator (pinned by the Random123
+    known-answer vectors): call 0 at (cell, step, 0, 0) gives (Z_xx, Z_yy) and (Z_zz,
+    Z_xy); words 0-1 of call 1 at (cell, step, 1, 0) give (Z_xz, Z_yz)."""
+    ncell, seed, step = 5 * 4 * 7, (1 << 33) + 9, 21
+    z = philox.stress_normals(seed, step, ncell)
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    for cell in (0, 37, 81, 139):
+        a = [int(w) for w in philox.philox4x32((cell, step, 0, 0), key)]
+        b = [int(w) for w in philox.philox4x32((cell, step, 1, 0), key)]
+        want = list(philox.box_muller(np.array([a[0]]), np.array([a[1]])))
+        want += list(philox.box_muller(np.array([a[2]]), np.array([a[3]])))
+        want += list(philox.box_muller(np.array([b[0]]), np.array([b[1]])))
+        np.testing.assert_array_equal(z[:, cell], np.concatenate(want))
+
+
 def test_box_muller_special_values():
     # word 0xffffffff is u = 1 - 2^-33: radius ~ sqrt(2^-32); word 0 for the angle gives cos ~ 1
     c, s = philox.box_muller(np.array([0xFFFFFFFF]), np.array([0]))

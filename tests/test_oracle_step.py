@@ -304,10 +304,12 @@ def test_inertial_blob_velocity_variance_is_kT_over_m_tilde():
     <u_a^2> = kT / m~, m~ = m_e + 3 m_f / 2, for small alpha and beta.  With m_e = m_f
     (m_f = rho dV, dV = 8 h^3 for the 3-point kernel) this is the VACF intercept
     C(0+) = 0.8 kT / m, m = m_e + m_f.  Eight such blobs on 16^3 at h, rho, eta far from 1,
-    beta = nu dt / h^2 = 1/8, no advection, 2900 sampled steps: the measured variance is
-    held to 4% of kT/m~ and to 2.5% of the exact finite-box Gibbs value (about 0.5%
-    below kT/m~), which exercises steps 4-8 of the scheme (slip, dp, the inertial
-    perturbation and the viscous correction)."""
+    beta = nu dt / h^2 = 1/8, no advection, 2900 sampled steps.  The measured variance of
+    one such run scatters by 1.8% (standard deviation of var / exact over eight seeds,
+    mean 0.996): it is held to 5.5% of kT/m~ and to 5% of the exact finite-box Gibbs
+    value (about 0.5% below kT/m~), about three standard deviations, which still
+    separates it from every plausible slip in steps 4-8 of the scheme (the slip, dp, the
+    inertial perturbation and the viscous correction), whose effects are 11% or more."""
     grid = (16, 16, 16)
     h, rho, eta, kT = 0.8, 1.3, 0.7, 1e-3
     dt = 0.125 * rho * h * h / eta
@@ -324,8 +326,8 @@ def test_inertial_blob_velocity_variance_is_kT_over_m_tilde():
             acc.append(np.mean(st.u ** 2))
     var = float(np.mean(acc))
     m_tilde = mf + 1.5 * mf
-    assert var == pytest.approx(kT / m_tilde, rel=0.04)
-    assert var == pytest.approx(0.8 * kT / (2.0 * mf), rel=0.04)
+    assert var == pytest.approx(kT / m_tilde, rel=0.055)
+    assert var == pytest.approx(0.8 * kT / (2.0 * mf), rel=0.055)
     exact = kT * np.trace(_gibbs_blob_covariance(st.q, me, grid, 3, h, rho)) / (3 * nb)
     assert exact == pytest.approx(kT / m_tilde, rel=0.02)
-    assert var == pytest.approx(exact, rel=0.025)
+    assert var == pytest.approx(exact, rel=0.05)
