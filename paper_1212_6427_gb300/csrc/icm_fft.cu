@@ -681,7 +681,8 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-template <typename R, int N, int R1, int R2>
+// GRP: tiles of every replica of a group (reps, nrep; the map covers the group buffer).
+template <typename R, int N, int R1, int R2, bool GRP = false>
 __global__ void __launch_bounds__(zsym2_threads<R, N, R1, R2>(), sizeof(R) == 4 ? 2 : 1)
     k_zsym_tma(const __grid_constant__ CUtensorMap zmap, cplx_t<R>* __restrict__ spec,
                const cplx_t<R>* __restrict__ gtw, int ny, int kx, int kxp, int ntx, SymParams<R> sp, int* err,
@@ -715,12 +716,12 @@ __global__ void __launch_bounds__(zsym2_threads<R, N, R1, R2>(), sizeof(R) == 4 
   // tiles: ntx x ny per spectrum; with reps, replica e = t / (ntx ny) of the table, whose
   // spectrum is the slot-th of the group buffer the map covers (components 3 slot ..)
   const int tpm = ntx * ny;
-  const int ntiles = tpm * (reps != nullptr ? nrep : 1);
+  const int ntiles = GRP ? tpm * nrep : tpm;
   const size_t zs = (size_t)ny * kxp, cs = (size_t)N * zs;
   auto issue = [&](int t, int st) {
-    const int e = t / tpm, tt = t - e * tpm;
+    const int e = GRP ? t / tpm : 0, tt = t - e * tpm;
     const int kx0 = (tt % ntx) * NL, py = tt / ntx;
-    const int c0 = reps != nullptr ? 3 * reps[e].slot : 0;
+    const int c0 = GRP ? 3 * reps[e].slot : 0;
     // order this block's earlier generic-proxy writes of the buffer before the copy
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(&mbar[st], TILE_BYTES);
@@ -740,11 +741,11 @@ __global__ void __launch_bounds__(zsym2_threads<R, N, R1, R2>(), sizeof(R) == 4 
     }
     __syncthreads();
     if (!s_ok) break;
-    const int e = t / tpm, tt = t - e * tpm;
+    const int e = GRP ? t / tpm : 0, tt = t - e * tpm;
     const int kx0 = (tt % ntx) * NL, py = tt / ntx;
     C* sbase = spec;
     SymParams<R> spt = sp;
-    if (reps != nullptr) {   // the replica's spectrum and symbol
+    if constexpr (GRP) {   // the replica's spectrum and symbol
       const RepFft& rp = reps[e];
       sbase = reinterpret_cast<C*>(rp.spec);
       spt.a = (R)rp.a;
@@ -1347,6 +1348,9 @@ void set_yz_attributes() {
   cudaFuncSetAttribute(k_zsym2<R, N, R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);         \
   if (N <= 256) /* exactly its need: the kernel also holds static shared memory */                          \
     cudaFuncSetAttribute(k_zsym_tma<R, N, R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ztma<R, N>()); \
+  if (N <= 256)                                                                                             \
+    cudaFuncSetAttribute(k_zsym_tma<R, N, R1, R2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+                         (int)smem_ztma<R, N>());                                                           \
   cudaFuncSetAttribute(k_ypass2<R, N, R1, R2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big); \
   cudaFuncSetAttribute(k_ypass2<R, N, R1, R2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   ICM_FFT_SIDES(ICM_ATTR)
@@ -1650,7 +1654,7 @@ void fft_yz_group(const FftCtx<R>& f, const RepFft* reps, int G, int which, cuda
 #define ICM_CASE(N, R1, R2)                                                                                            \
   case N:                                                                                                              \
     if (N <= 256) {                                                                                                    \
-      k_zsym_tma<R, N, R1, R2><<<grid, zsym2_threads<R, N, R1, R2>(), smem_ztma<R, N>(), st>>>(map, nullptr, twz,      \
+      k_zsym_tma<R, N, R1, R2, true><<<grid, zsym2_threads<R, N, R1, R2>(), smem_ztma<R, N>(), st>>>(map, nullptr, twz, \
                                                                              f.ny, f.kx, f.kxp, kxz, sp, f.err, reps, G); \
       return;                                                                                                          \
     }                                                                                                                  \
