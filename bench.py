@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64, cuFFT and CPU comparison legs")
     ap.add_argument("--no-autotune", action="store_true", help="time the default plan instead of the tuned one")
+    ap.add_argument("--grouped", type=int, default=None, choices=[0, 1, 2, 3],
+                    help="batch workload: this batch mode (icm_batch_set_grouped) instead of the tuned one")
     ap.add_argument("--cpu-budget", type=float, default=150.0, help="seconds of oracle time for the CPU legs")
     return ap.parse_args()
 
@@ -465,6 +467,8 @@ def measure_batch(args, rank, world, dist, steps):
     if not args.no_autotune:
         icm.icm_batch_autotune(b, 3)
         plans = sorted({str(icm.icm_get_plan(s.handle)) for s in sims})
+    if getattr(args, "grouped", None) is not None:
+        icm.icm_batch_set_grouped(b, args.grouped)
     grouped = icm.icm_batch_get_grouped(b)
     # algorithmic bytes of one step of every member, with the plans the batch runs
     step_bytes = 0.0
