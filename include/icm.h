@@ -112,9 +112,10 @@ icm_status icm_add_blobs(icm_sim* sim, int64_t n, const double* pos, const doubl
 
 /* Set the external force of every blob (Sec. III.C step 1: F^{n+1/2}), held until
  * the next call: force[n_total*3].  The values are copied before the call returns
- * (the caller may reuse the buffer at once); the device upload and the FP64 total
+ * (the caller may reuse the buffer at once); the upload runs on an upload stream of the
+ * simulation beside the steps already queued, and the copy into place and the FP64 total
  * force are queued on the simulation's stream, ordered before the next step.
- * Errors: ICM_EINVAL (NULL, non-finite). */
+ * Errors: ICM_EINVAL (NULL, non-finite), ICM_ENOMEM (device landing buffer). */
 icm_status icm_set_blob_forces(icm_sim* sim, const double* force);
 
 /* Add to every blob the force of the harmonic potential V(r) = k r^2 / 2 about
@@ -198,6 +199,19 @@ icm_status icm_debug_wait_timeout(icm_sim* sim, int64_t limit_ns);
  * wait.  Device errors of earlier steps are returned after the outputs are filled. */
 icm_status icm_read_state(icm_sim* sim, double* pos, double* vel, double* fluid_v,
                           double momentum[3], int64_t* step);
+
+/* Queued reads, for loops that read every step: icm_read_begin gathers icm_read_state's
+ * blob outputs (positions, velocities, total momentum, step; no fluid) into a device
+ * slot behind the work queued so far, copies that slot down to one of two page-locked
+ * staging slots on a download stream of the simulation, and returns at once; the caller
+ * may queue more steps (and forces) while the copy is in flight.  icm_read_finish waits for the oldest queued read and copies it
+ * out (any pointer may be NULL); it returns the device errors raised before that read,
+ * as icm_read_state would have (reporting one clears the device's error bits, including
+ * bits of steps queued after the read).  The blob capacity must not change while reads
+ * are pending.  Errors: icm_read_begin ICM_EINVAL when two reads are pending, ICM_ENOMEM
+ * (staging buffer); icm_read_finish ICM_EINVAL when none is pending. */
+icm_status icm_read_begin(icm_sim* sim);
+icm_status icm_read_finish(icm_sim* sim, double* pos, double* vel, double momentum[3], int64_t* step);
 
 /* Overwrite the full state (checkpoint restore).  pos, vel: n_total*3 (required);
  * fluid_v: 3*N (required); adv_prev: 3*N advective flux div(rho v v^T)^{n-1} of the

@@ -72,6 +72,8 @@ SIGNATURES = {
     "icm_step": (_c_i32, [_vp, _c_i64]),
     "icm_sync": (_c_i32, [_vp]),
     "icm_read_state": (_c_i32, [_vp, _dp, _dp, _dp, _dp, ctypes.POINTER(_c_i64)]),
+    "icm_read_begin": (_c_i32, [_vp]),
+    "icm_read_finish": (_c_i32, [_vp, _dp, _dp, _dp, ctypes.POINTER(_c_i64)]),
     "icm_write_state": (_c_i32, [_vp, _dp, _dp, _dp, _dp, _dp, _c_i64]),
     "icm_read_aux": (_c_i32, [_vp, _dp, _dp, ctypes.POINTER(_c_i32)]),
     "icm_profile_steps": (_c_i32, [_vp, _c_i64, _c_i32, ctypes.POINTER(_c_i32), ctypes.c_char_p, _dp, _dp]),
@@ -331,6 +333,23 @@ def icm_read_state(sim, ncell, fluid=False, check=True):
     return pos.reshape(nb, 3), vel.reshape(nb, 3), fv, mom, int(step.value), st
 
 
+def icm_read_begin(sim):
+    _check(lib().icm_read_begin(sim))
+
+
+def icm_read_finish(sim, check=True):
+    """The oldest queued read: (pos (n,3), vel (n,3), momentum (3,), step, status)."""
+    nb = icm_num_blobs(sim)
+    pos, pp = _out(3 * nb)
+    vel, vp = _out(3 * nb)
+    mom, mp = _out(3)
+    step = _c_i64()
+    st = lib().icm_read_finish(sim, pp, vp, mp, ctypes.byref(step))
+    if check:
+        _check(st)
+    return pos.reshape(nb, 3), vel.reshape(nb, 3), mom, int(step.value), st
+
+
 def icm_write_state(sim, pos, vel, fluid_v, adv_prev=None, slip_g=None, step=0):
     nb = icm_num_blobs(sim)
     _, pp = _f64(pos, 3 * nb)
@@ -552,6 +571,13 @@ class Simulation:
     def read(self, fluid=False):
         pos, vel, fv, mom, step, _ = icm_read_state(self.handle, self.ncell, fluid)
         return dict(pos=pos, vel=vel, fluid=fv, momentum=mom, step=step)
+
+    def read_begin(self):
+        icm_read_begin(self.handle)
+
+    def read_finish(self):
+        pos, vel, mom, step, _ = icm_read_finish(self.handle)
+        return dict(pos=pos, vel=vel, momentum=mom, step=step)
 
     def write(self, pos, vel, fluid_v, adv_prev=None, slip_g=None, step=0):
         icm_write_state(self.handle, pos, vel, fluid_v, adv_prev, slip_g, step)

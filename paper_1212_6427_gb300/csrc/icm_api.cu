@@ -140,6 +140,20 @@ struct icm_sim {
   long long hstage_cap = -1;
   cudaEvent_t ev_hforce = nullptr;
   bool hforce_pending = false;
+  // queued reads (icm_read_begin): two staging slots after the synchronous read's, used
+  // in turn; read_head is the oldest pending, read_pending how many (0-2)
+  static constexpr int kReadSlots = 2;
+  cudaEvent_t ev_read[kReadSlots] = {nullptr, nullptr};
+  int read_head = 0, read_pending = 0;
+  // host <-> device copies of the per-step I/O run on their own streams beside the steps
+  // (one up, one down, so that an upload never queues behind a download that waits for a
+  // step): forces go up into dfstage and are copied into f on the simulation's stream; a
+  // queued read gathers the blob state into a device slot of dsnap and copies that down
+  cudaStream_t copy = nullptr, copy_up = nullptr;
+  cudaEvent_t ev_fup = nullptr, ev_fcons = nullptr, ev_snap[kReadSlots] = {nullptr, nullptr};
+  double* dfstage = nullptr;
+  double* dsnap = nullptr;
+  long long dstage_cap = -1;
   // graph of one step
   cudaGraphExec_t gexec = nullptr;
   bool graph_ok = false;
@@ -801,13 +815,56 @@ icm_status check_device_errors(icm_sim* s) {
 }
 
 // The host staging buffer, sized for the current blob capacity.
+// The device side of the copy stream's I/O, sized for the current blob capacity: the
+// forces' landing buffer [3 cap] and two read slots [6 cap + 8] each; the stream and its
+// events on first use.
+icm_status ensure_dstage(icm_sim* s) {
+  if (!s->copy) {
+    if (cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->copy_up, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      if (s->copy) cudaStreamDestroy(s->copy);
+      s->copy = nullptr;
+      s->copy_up = nullptr;
+      return fail(ICM_ECUDA, "creation of the copy streams failed");
+    }
+    ICM_CK(cudaEventCreateWithFlags(&s->ev_fup, cudaEventDisableTiming));
+    ICM_CK(cudaEventCreateWithFlags(&s->ev_fcons, cudaEventDisableTiming));
+    for (auto& e : s->ev_snap) ICM_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  if (s->dfstage && s->dstage_cap == s->cap) return ICM_OK;
+  if (s->read_pending > 0) return fail(ICM_EINVAL, "blob capacity changed while reads are pending (icm_read_finish them first)");
+  ICM_CK(cudaStreamSynchronize(s->stream));
+  ICM_CK(cudaStreamSynchronize(s->copy));
+  ICM_CK(cudaStreamSynchronize(s->copy_up));
+  if (s->dfstage) dfree(s, s->dfstage);
+  s->dfstage = nullptr;
+  s->dsnap = nullptr;
+  const size_t slot = 6 * (size_t)s->cap + 8;
+  double* p = (double*)dalloc(s, sizeof(double) * (3 * (size_t)s->cap + 2 * slot));
+  if (!p) return fail(ICM_ENOMEM, "no device memory for the copy stream's buffers");
+  s->dfstage = p;
+  s->dsnap = p + 3 * (size_t)s->cap;
+  s->dstage_cap = s->cap;
+  return ICM_OK;
+}
+
+// Layout (doubles): forces [3 cap]; then three read slots (the synchronous read's and the
+// two of icm_read_begin), each positions [3 cap], velocities [3 cap], scalars [8]
+// (momentum [3], step, error bits).
+constexpr size_t kReadScalars = 8;
+size_t read_slot_doubles(long long cap) { return 6 * (size_t)cap + kReadScalars; }
+double* read_slot(icm_sim* s, int slot) { return s->hstage + 3 * (size_t)s->cap + slot * read_slot_doubles(s->cap); }
+
 icm_status ensure_hstage(icm_sim* s) {
   if (s->hstage && s->hstage_cap == s->cap) return ICM_OK;
+  if (s->read_pending > 0) return fail(ICM_EINVAL, "blob capacity changed while reads are pending (icm_read_finish them first)");
   ICM_CK(cudaStreamSynchronize(s->stream));
   if (s->hstage) cudaFreeHost(s->hstage);
   s->hstage = nullptr;
   s->hforce_pending = false;
-  if (cudaMallocHost(&s->hstage, sizeof(double) * (9 * (size_t)s->cap + 16)) != cudaSuccess) {
+  if (cudaMallocHost(&s->hstage, sizeof(double) * (3 * (size_t)s->cap + 3 * read_slot_doubles(s->cap))) !=
+      cudaSuccess) {
     s->hstage = nullptr;
     cudaGetLastError();
     return fail(ICM_ENOMEM, "no page-locked host memory for the staging buffer");
@@ -986,6 +1043,8 @@ icm_status icm_create(const int32_t grid[3], double h, double rho, double eta, d
 void icm_destroy(icm_sim* s) {
   if (!s) return;
   if (s->stream) cudaStreamSynchronize(s->stream);
+  if (s->copy) cudaStreamSynchronize(s->copy);
+  if (s->copy_up) cudaStreamSynchronize(s->copy_up);
   if (s->aux) cudaStreamSynchronize(s->aux);
   invalidate_graph(s);
   while (!s->allocs.empty()) dfree(s, s->allocs.back().first);
@@ -994,6 +1053,14 @@ void icm_destroy(icm_sim* s) {
   if (s->ev_fork) cudaEventDestroy(s->ev_fork);
   if (s->ev_join) cudaEventDestroy(s->ev_join);
   if (s->ev_hforce) cudaEventDestroy(s->ev_hforce);
+  for (cudaEvent_t e : s->ev_read)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : s->ev_snap)
+    if (e) cudaEventDestroy(e);
+  if (s->ev_fup) cudaEventDestroy(s->ev_fup);
+  if (s->ev_fcons) cudaEventDestroy(s->ev_fcons);
+  if (s->copy) cudaStreamDestroy(s->copy);
+  if (s->copy_up) cudaStreamDestroy(s->copy_up);
   if (s->hstage) cudaFreeHost(s->hstage);
   delete s;
 }
@@ -1041,6 +1108,7 @@ icm_status icm_set_blob_forces(icm_sim* s, const double* force) {
   if (!force) return fail(ICM_EINVAL, "force must not be NULL");
   icm_status st = ensure_hstage(s);
   if (st != ICM_OK) return st;
+  if ((st = ensure_dstage(s)) != ICM_OK) return st;
   // the previous copy out of the staging slot must have passed before it is rewritten
   if (s->hforce_pending) ICM_CK(cudaEventSynchronize(s->ev_hforce));
   s->hforce_pending = false;
@@ -1055,9 +1123,16 @@ icm_status icm_set_blob_forces(icm_sim* s, const double* force) {
     fs[i] = x;
   }
   if (!finite) return fail(ICM_EINVAL, "non-finite force");
-  ICM_CK(cudaMemcpyAsync(s->f, fs, sizeof(double) * n3, cudaMemcpyHostToDevice, s->stream));
-  ICM_CK(cudaEventRecord(s->ev_hforce, s->stream));
+  // up on the upload stream (beside the steps still queued), once the previous forces
+  // have left the landing buffer; then into f on the simulation's stream, behind its steps
+  ICM_CK(cudaStreamWaitEvent(s->copy_up, s->ev_fcons, 0));
+  ICM_CK(cudaMemcpyAsync(s->dfstage, fs, sizeof(double) * n3, cudaMemcpyHostToDevice, s->copy_up));
+  ICM_CK(cudaEventRecord(s->ev_hforce, s->copy_up));
+  ICM_CK(cudaEventRecord(s->ev_fup, s->copy_up));
   s->hforce_pending = true;
+  ICM_CK(cudaStreamWaitEvent(s->stream, s->ev_fup, 0));
+  ICM_CK(cudaMemcpyAsync(s->f, s->dfstage, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s->stream));
+  ICM_CK(cudaEventRecord(s->ev_fcons, s->stream));
   // FP64 compensated total force for the momentum bookkeeping
   rows_sum3(s->f, nullptr, s->nb, nullptr, s->scal + SC_SUMF, s->partial, icm_sim::kPartials, s->stream);
   ICM_CK(cudaGetLastError());
@@ -1230,9 +1305,9 @@ icm_status icm_read_state(icm_sim* s, double* pos, double* vel, double* fluid_v,
   icm_status st = ensure_hstage(s);
   if (st != ICM_OK) return st;
   // every read goes into the page-locked staging buffer behind the queued work; one wait
-  double* ps = s->hstage + 3 * s->cap;
-  double* us = s->hstage + 6 * s->cap;
-  double* sc = s->hstage + 9 * s->cap + 3;   // total momentum [3], step, error bits
+  double* ps = read_slot(s, 0);
+  double* us = ps + 3 * s->cap;
+  double* sc = us + 3 * s->cap;   // total momentum [3], step, error bits
   const size_t bb = sizeof(double) * 3 * s->nb;
   if (pos && s->nb) ICM_CK(cudaMemcpyAsync(ps, s->q, bb, cudaMemcpyDeviceToHost, s->stream));
   if (vel && s->nb) ICM_CK(cudaMemcpyAsync(us, s->u, bb, cudaMemcpyDeviceToHost, s->stream));
@@ -1259,6 +1334,56 @@ icm_status icm_read_state(icm_sim* s, double* pos, double* vel, double* fluid_v,
   if (momentum) memcpy(momentum, sc, 3 * sizeof(double));
   if (step) *step = stp;
   return dev;
+}
+
+// Queue the blob-state reads of icm_read_state (without the fluid) into the next free
+// slot behind the queued work, and an event after them; no wait.
+icm_status icm_read_begin(icm_sim* s) {
+  if (!s) return fail(ICM_EINVAL, "NULL simulation");
+  if (s->read_pending >= icm_sim::kReadSlots) return fail(ICM_EINVAL, "two reads are pending already");
+  icm_status st = ensure_hstage(s);
+  if (st != ICM_OK) return st;
+  if ((st = ensure_dstage(s)) != ICM_OK) return st;
+  const int slot = (s->read_head + s->read_pending) % icm_sim::kReadSlots;
+  if (!s->ev_read[slot]) ICM_CK(cudaEventCreateWithFlags(&s->ev_read[slot], cudaEventDisableTiming));
+  // on the simulation's stream: the momentum sum and one gather of the state into the
+  // slot's device block; on the copy stream: that block down to the slot's staging area,
+  // beside the steps queued after this call (the slot was last read by a finished read)
+  double* dslot = s->dsnap + slot * (6 * (size_t)s->cap + 8);
+  rows_sum3(s->u, s->me, s->nb, s->scal + SC_PBAR, s->scal + SC_PTOT, s->partial, icm_sim::kPartials, s->stream);
+  blob_snapshot(s->q, s->u, s->nb, s->scal + SC_PTOT, s->step_dev, s->err_dev, dslot, s->stream);
+  ICM_CK(cudaGetLastError());
+  ICM_CK(cudaEventRecord(s->ev_snap[slot], s->stream));
+  ICM_CK(cudaStreamWaitEvent(s->copy, s->ev_snap[slot], 0));
+  ICM_CK(cudaMemcpyAsync(read_slot(s, 1 + slot), dslot, sizeof(double) * (6 * (size_t)s->nb + 5),
+                         cudaMemcpyDeviceToHost, s->copy));
+  ICM_CK(cudaEventRecord(s->ev_read[slot], s->copy));
+  ++s->read_pending;
+  return ICM_OK;
+}
+
+// Wait for the oldest queued read and copy it out.
+icm_status icm_read_finish(icm_sim* s, double* pos, double* vel, double momentum[3], int64_t* step) {
+  if (!s) return fail(ICM_EINVAL, "NULL simulation");
+  if (s->read_pending == 0) return fail(ICM_EINVAL, "no read is pending (icm_read_begin)");
+  const int slot = s->read_head;
+  ICM_CK(cudaEventSynchronize(s->ev_read[slot]));
+  s->read_head = (s->read_head + 1) % icm_sim::kReadSlots;
+  --s->read_pending;
+  // the slot holds positions [3 nb], velocities [3 nb], momentum [3], step, error bits
+  const double* ps = read_slot(s, 1 + slot);
+  const double* us = ps + 3 * s->nb;
+  const double* sc = us + 3 * s->nb;
+  long long errl = 0, stp = 0;
+  memcpy(&errl, sc + 4, sizeof(long long));
+  memcpy(&stp, sc + 3, sizeof(long long));
+  const int err = (int)errl;
+  const size_t bb = sizeof(double) * 3 * s->nb;
+  if (pos && s->nb) memcpy(pos, ps, bb);
+  if (vel && s->nb) memcpy(vel, us, bb);
+  if (momentum) memcpy(momentum, sc, 3 * sizeof(double));
+  if (step) *step = stp;
+  return device_error_status(s, err);
 }
 
 icm_status icm_write_state(icm_sim* s, const double* pos, const double* vel, const double* fluid_v,

@@ -1006,6 +1006,33 @@ __global__ void __launch_bounds__(256) k_rows_final(const double* __restrict__ p
 }
 }  // namespace
 
+namespace {
+// The blob state a queued read returns, gathered into one contiguous device block:
+// positions [3 nb], velocities [3 nb], then momentum [3], the time level and the error
+// bits (their bit patterns in two doubles).
+__global__ void k_snapshot(const double* __restrict__ q, const double* __restrict__ u, long long nb,
+                           const double* __restrict__ ptot, const long long* __restrict__ step,
+                           const int* __restrict__ err, double* __restrict__ out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long n3 = 3 * nb;
+  if (i < n3) {
+    out[i] = q[i];
+    out[n3 + i] = u[i];
+  }
+  if (i == 0) {
+    for (int a = 0; a < 3; ++a) out[2 * n3 + a] = ptot[a];
+    out[2 * n3 + 3] = __longlong_as_double(*step);
+    out[2 * n3 + 4] = __longlong_as_double((long long)*err);
+  }
+}
+}  // namespace
+
+void blob_snapshot(const double* q, const double* u, long long nb, const double* ptot, const long long* step,
+                   const int* err, double* out, cudaStream_t st) {
+  const long long n = nb > 0 ? 3 * nb : 1;
+  k_snapshot<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(q, u, nb, ptot, step, err, out);
+}
+
 void rows_sum3(const double* x, const double* w, long long n, const double* init, double* out, double* partial,
                int npartial, cudaStream_t st) {
   long long g = (n + 255) / 256;

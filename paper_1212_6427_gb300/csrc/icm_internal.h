@@ -215,6 +215,10 @@ template <typename R> void blob_momentum_change(const BlobParams& p, BlobState s
 // scratch); out may not alias x, w or init.
 void rows_sum3(const double* x, const double* w, long long n, const double* init, double* out, double* partial,
                int npartial, cudaStream_t st);
+// positions and velocities of nb blobs, the momentum ptot [3], the time level and the error
+// bits into out [6 nb + 5] (the last two as bit patterns), one launch.
+void blob_snapshot(const double* q, const double* u, long long nb, const double* ptot, const long long* step,
+                   const int* err, double* out, cudaStream_t st);
 template <typename R> void blob_inertial(const BlobParams& p, BlobState s, const R* dvt, cudaStream_t st);
 template <typename R> void blob_finish(const BlobParams& p, BlobState s, const R* v_new, const R* dv,
                                        bool inertial, cudaStream_t st);

@@ -7,6 +7,8 @@ import os
 import numpy as np
 import pytest
 
+import icm_workloads as wl
+
 from oracle import icm as oracle
 from oracle import philox
 
@@ -171,3 +173,56 @@ def test_host_io_buffers_are_the_callers(icm):
         sim.close()
     for k in ("pos", "vel", "momentum"):
         np.testing.assert_array_equal(out[0][k], out[1][k])
+
+
+def test_queued_reads_match_synchronous_reads(icm):
+    """icm_read_begin / icm_read_finish: a read queued behind a step returns that step's
+    state even when the next step is queued before the host collects it (two slots in
+    turn), the same values a synchronous read gives; the pending count is enforced."""
+    grid = (32, 16, 24)
+    nb = 12
+    q = wl.random_sequential_addition(nb, grid, 1.0, 2.0, 5)
+    rng = np.random.default_rng(5)
+    u0, me = 0.02 * rng.standard_normal((nb, 3)), rng.uniform(-0.5, 2.0, size=nb)
+    sims = []
+    for _ in range(2):
+        s = _sim(icm, grid, 64)
+        s.add_blobs(q, u0, me)
+        sims.append(s)
+    queued, direct = sims
+    f = 1e-3 * rng.standard_normal((nb, 3))
+    want = []
+    for _ in range(5):
+        direct.set_forces(f)
+        direct.step(1)
+        want.append(direct.read())
+    got = []
+    queued.set_forces(f)
+    queued.step(1)
+    queued.read_begin()
+    for _ in range(4):
+        queued.set_forces(f)
+        queued.step(1)
+        queued.read_begin()
+        got.append(queued.read_finish())   # the step before the one just queued
+    got.append(queued.read_finish())
+    for g, w in zip(got, want):
+        assert g["step"] == w["step"]
+        for k in ("pos", "vel", "momentum"):
+            np.testing.assert_allclose(g[k], w[k], rtol=1e-12, atol=1e-15)
+    # a read queued with nothing after it equals a synchronous read bit for bit
+    queued.read_begin()
+    now = queued.read()
+    late = queued.read_finish()
+    for k in ("pos", "vel", "momentum", "step"):
+        np.testing.assert_array_equal(np.asarray(late[k]), np.asarray(now[k]))
+    with pytest.raises(icm.IcmError):
+        queued.read_finish()
+    queued.read_begin()
+    queued.read_begin()
+    with pytest.raises(icm.IcmError):
+        queued.read_begin()
+    queued.read_finish()
+    queued.read_finish()
+    for s in sims:
+        s.close()
