@@ -149,6 +149,10 @@ typedef struct icm_plan {
   int32_t fork;        /* 1: the blob-side prologue runs on a second stream beside the RHS          */
   int32_t fused_xy;    /* 1: forward x and y FFT passes fused on thread-block clusters (FP32,
                           Nx = Ny in 32, 64, 128, 256); 0 (default): two passes                    */
+  int32_t z_split;     /* 1: the z transform with its other two-stage split (Nz = 32: 4 x 8, 48:
+                          12 x 4, 64: 16 x 4, 96: 8 x 12, 128: 8 x 16, 192: 12 x 16, 256: 32 x 8);
+                          0 (default): the axis split (8 x 4, 16 x 3, 8 x 8, 16 x 6, 16 x 8,
+                          16 x 12, 16 x 16)                                                        */
 } icm_plan;
 
 /* The plan the next step will use.  Errors: ICM_EINVAL (NULL). */

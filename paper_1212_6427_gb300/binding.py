@@ -38,7 +38,7 @@ _FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void
 class Plan(ctypes.Structure):
     """icm_plan of include/icm.h."""
     _fields_ = [("fused_blobs", _c_i32), ("tma_z", _c_i32), ("rhs_kz", _c_i32), ("fork", _c_i32),
-                ("fused_xy", _c_i32)]
+                ("fused_xy", _c_i32), ("z_split", _c_i32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -230,8 +230,8 @@ def icm_get_plan(sim):
     return p.as_dict()
 
 
-def icm_set_plan(sim, fused_blobs=1, tma_z=1, rhs_kz=16, fork=1, fused_xy=0):
-    p = Plan(int(fused_blobs), int(tma_z), int(rhs_kz), int(fork), int(fused_xy))
+def icm_set_plan(sim, fused_blobs=1, tma_z=1, rhs_kz=16, fork=1, fused_xy=0, z_split=0):
+    p = Plan(int(fused_blobs), int(tma_z), int(rhs_kz), int(fork), int(fused_xy), int(z_split))
     _check(lib().icm_set_plan(sim, ctypes.byref(p)))
 
 

@@ -103,6 +103,10 @@ struct icm_sim {
   // FFT plans and symbol tables
   AxisPlan px, py, pz;
   void *dx = nullptr, *ddx = nullptr, *dy = nullptr, *ddy = nullptr, *dz = nullptr, *ddz = nullptr;
+  // the other split of the z side (plan z_split), where there is one
+  bool has_zalt = false;
+  AxisPlan pz_alt;
+  void *dz_alt = nullptr, *ddz_alt = nullptr;
   int kx = 0, kxp = 0;
   alignas(64) unsigned char zmap[128];   // TMA descriptor of spec for the z pass
   bool has_zmap = false;
@@ -228,6 +232,13 @@ FftCtx<R> fft_ctx(const icm_sim* s) {
   f.spec = (cplx_t<R>*)s->spec;
   f.zmap = s->has_zmap && s->plan.tma_z ? s->zmap : nullptr;
   f.err = s->err_dev;
+  f.zalt = 0;
+  if (s->plan.z_split && s->has_zalt) {
+    f.zalt = 1;
+    f.pz = s->pz_alt;
+    f.dz = (const cplx_t<R>*)s->dz_alt;
+    f.ddz = (const R*)s->ddz_alt;
+  }
   return f;
 }
 
@@ -304,9 +315,11 @@ WcaParams wca_params(const icm_sim* s) {
 // Build one axis plan: radices, twiddles (long double), digit-reversed order, and
 // the symbol d = (exp(i theta) - 1)/h, |d|^2 = 4 sin^2(theta/2)/h^2 by storage position
 // (x: by natural wavenumber, only nx/2+1 of them).
-icm_status build_axis(icm_sim* s, int n, bool natural, int count, AxisPlan& P, void*& dtab, void*& ddtab) {
+icm_status build_axis(icm_sim* s, int n, bool natural, int count, AxisPlan& P, void*& dtab, void*& ddtab,
+                      bool z_alt = false) {
   int r1 = 0, r2 = 0;
-  const std::vector<int> rad = fft_split(n, r1, r2) ? std::vector<int>{r1, r2} : factor_radices(n);
+  const bool two = z_alt ? fft_split_z_alt(n, r1, r2) : fft_split(n, r1, r2);
+  const std::vector<int> rad = two ? std::vector<int>{r1, r2} : factor_radices(n);
   P.n = n;
   P.nstages = (int)rad.size();
   for (size_t i = 0; i < rad.size(); ++i) P.radix[i] = rad[i];
@@ -640,7 +653,8 @@ std::string plan_key(const icm_sim* s) {
   return buf;
 }
 
-// The plan of a simulation nobody tuned: everything on.  The RHS blocks are persistent
+// The plan of a simulation nobody tuned: everything on (the 32 x 8 z split on FP32 z
+// sides of 256).  The RHS blocks are persistent
 // when every block of a full GPU (two per SM) gets at least 8 tile-planes of 32 x 16
 // cells, which the single-simulation sweeps found fastest from 128^3 up; on smaller
 // grids they march 8 z planes on short z sides, else 16.
@@ -651,7 +665,9 @@ icm_plan default_plan(const icm_sim* s) {
     nsm = 1;
   const long long tile_planes = (long long)((s->nx + 31) / 32) * ((s->ny + 15) / 16) * s->nz;
   const int kz = tile_planes >= 16LL * std::max(nsm, 1) ? 0 : (s->nz <= 48 ? 8 : 16);
-  return icm_plan{1, 1, kz, 1, 0};
+  // the 32 x 8 z split measured 5% faster than 16 x 16 in the FP32 tensor-map z pass at 256
+  const int zs = s->prec == 32 && s->nz == 256 ? 1 : 0;
+  return icm_plan{1, 1, kz, 1, 0, zs};
 }
 
 // Before a capture: simulations without a plan of their own take the tuned plan of
@@ -963,9 +979,9 @@ icm_status icm_create(const int32_t grid[3], double h, double rho, double eta, d
   icm_sim* s = new icm_sim();
   s->nx = grid[0]; s->ny = grid[1]; s->nz = grid[2];
   s->ncell = (long long)s->nx * s->ny * s->nz;
-  s->plan = default_plan(s);
   s->h = h; s->rho = rho; s->eta = eta; s->kT = kT; s->dt = dt;
   s->kernel = kernel; s->seed = seed; s->prec = precision; s->flags = flags;
+  s->plan = default_plan(s);
   s->advection = !(flags & ICM_FLAG_NO_ADVECTION);
   s->slip = (flags & ICM_FLAG_SLIP_ZERO) ? 1 : ((flags & ICM_FLAG_SLIP_FULL) ? 2 : 0);
   s->alloc = g_alloc; s->release = g_free; s->actx = g_actx;
@@ -1009,6 +1025,15 @@ icm_status icm_create(const int32_t grid[3], double h, double rho, double eta, d
   if ((st = build_axis(s, s->nx, true, s->kx, s->px, s->dx, s->ddx)) != ICM_OK ||
       (st = build_axis(s, s->ny, false, s->ny, s->py, s->dy, s->ddy)) != ICM_OK ||
       (st = build_axis(s, s->nz, false, s->nz, s->pz, s->dz, s->ddz)) != ICM_OK) {
+    const std::string msg = g_err;
+    icm_destroy(s);
+    return fail(st, "%s", msg.c_str());
+  }
+  {
+    int r1 = 0, r2 = 0;
+    s->has_zalt = fft_split_z_alt(s->nz, r1, r2);
+  }
+  if (s->has_zalt && (st = build_axis(s, s->nz, false, s->nz, s->pz_alt, s->dz_alt, s->ddz_alt, true)) != ICM_OK) {
     const std::string msg = g_err;
     icm_destroy(s);
     return fail(st, "%s", msg.c_str());
@@ -1212,7 +1237,7 @@ icm_status icm_set_plan(icm_sim* s, const icm_plan* plan) {
   if (plan->rhs_kz != 0 && (plan->rhs_kz < 4 || plan->rhs_kz > 64))
     return fail(ICM_EINVAL, "rhs_kz must be 0 (persistent) or in 4..64");
   s->plan = icm_plan{plan->fused_blobs ? 1 : 0, plan->tma_z ? 1 : 0, plan->rhs_kz, plan->fork ? 1 : 0,
-                     plan->fused_xy ? 1 : 0};
+                     plan->fused_xy ? 1 : 0, plan->z_split ? 1 : 0};
   s->plan_src = 2;
   invalidate_graph(s);
   return ICM_OK;
@@ -1259,6 +1284,7 @@ icm_status icm_autotune(icm_sim* s, int32_t nsteps, icm_plan* chosen, double* ms
   knobs.push_back({&icm_plan::rhs_kz, {0, 8, 16, 32}});
   knobs.push_back({&icm_plan::fork, {1, 0}});
   if (fft_has_xy_passes(s->prec, s->nx, s->ny)) knobs.push_back({&icm_plan::fused_xy, {0, 1}});
+  if (s->has_zalt) knobs.push_back({&icm_plan::z_split, {0, 1}});
   for (size_t k = 0; st == ICM_OK && k < knobs.size(); ++k)
     for (int val : knobs[k].second) {
       if (best.*(knobs[k].first) == val) continue;
@@ -2326,13 +2352,13 @@ icm_status icm_batch_autotune(icm_batch* b, int32_t nsteps) {
     }
     return ICM_OK;
   };
-  icm_plan best = icm_plan{1, 1, 16, 1, 0};
+  icm_plan best = icm_plan{1, 1, 16, 1, 0, 0};
   int best_grouped = 0;
   double best_ms = 0.0;
   icm_status st = trial(best, best_grouped, best_ms);
   const std::vector<std::pair<int icm_plan::*, std::vector<int>>> knobs = {
       {&icm_plan::fused_blobs, {1, 0}}, {&icm_plan::tma_z, {1, 0}}, {&icm_plan::rhs_kz, {0, 4, 8, 16, 32}},
-      {&icm_plan::fork, {1, 0}}, {&icm_plan::fused_xy, {0, 1}}};
+      {&icm_plan::fork, {1, 0}}, {&icm_plan::fused_xy, {0, 1}}, {&icm_plan::z_split, {0, 1}}};
   for (size_t k = 0; st == ICM_OK && k < knobs.size(); ++k)
     for (int val : knobs[k].second) {
       if (best.*(knobs[k].first) == val) continue;

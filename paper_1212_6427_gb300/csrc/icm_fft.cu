@@ -773,6 +773,13 @@ __global__ void __launch_bounds__(zsym2_threads<R, N, R1, R2>(), sizeof(R) == 4 
   }
 }
 
+// First-stage radix of the z split a plan selects (fft_split_z_alt; the axis split
+// where there is no other).
+template <int N, int R1>
+constexpr int zalt_r1() {
+  return N == 32 ? 4 : N == 48 ? 12 : N == 64 ? 16 : N == 96 ? 8 : N == 128 ? 8 : N == 192 ? 12 : N == 256 ? 32 : R1;
+}
+
 // z planes per block of the y pass: short FP32 sides take several, so that the first
 // stage (R2 items per line and plane) finds work for most of the block's threads.
 template <typename R, int N, int R2>
@@ -1256,6 +1263,20 @@ template <typename R, int N> size_t smem_z2() { return 3 * (size_t)N * kZLines *
 template <typename R, int N, int R2> size_t smem_y2() {
   return (size_t)y_planes<R, N, R2>() * N * seg_lines<R>() * sizeof(cplx_t<R>) + N * sizeof(cplx_t<R>);
 }
+template <typename R, int N, int R1, int R2, bool GRP>
+void launch_ztma(int grid, const CUtensorMap& map, cplx_t<R>* spec, const cplx_t<R>* tw, const FftCtx<R>& f, int kxz,
+                 const SymParams<R>& sp, const RepFft* reps, int G, cudaStream_t st) {
+  k_zsym_tma<R, N, R1, R2, GRP><<<grid, zsym2_threads<R, N, R1, R2>(), smem_ztma<R, N>(), st>>>(
+      map, spec, tw, f.ny, f.kx, f.kxp, kxz, sp, f.err, reps, G);
+}
+
+template <typename R, int N, int R1, int R2>
+void launch_zplain(dim3 grid, cplx_t<R>* spec, const cplx_t<R>* tw, const FftCtx<R>& f, const SymParams<R>& sp,
+                   const RepFft* reps, cudaStream_t st) {
+  k_zsym2<R, N, R1, R2><<<grid, zplain_threads<R, N, R1, R2>(), smem_z2<R, N>(), st>>>(spec, tw, f.ny, f.kx, f.kxp,
+                                                                                    sp, reps);
+}
+
 template <typename R, int N, int L> size_t smem_x2() { return (size_t)L * xrow(N) * sizeof(cplx_t<R>) + N * sizeof(cplx_t<R>); }
 // Blocks of a plain x pass over nrows rows (2 x_plain_lines rows per block).
 template <typename R, int N, int R2> int xgrid(int nrows) {
@@ -1346,6 +1367,14 @@ void set_yz_attributes() {
   const int big = 227 * 1024;
 #define ICM_ATTR(N, R1, R2)                                                                               \
   cudaFuncSetAttribute(k_zsym2<R, N, R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);         \
+  cudaFuncSetAttribute(k_zsym2<R, N, zalt_r1<N, R1>(), N / zalt_r1<N, R1>()>,                              \
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, big);                                   \
+  if (N <= 256) {                                                                                           \
+    cudaFuncSetAttribute(k_zsym_tma<R, N, zalt_r1<N, R1>(), N / zalt_r1<N, R1>()>,                         \
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ztma<R, N>());              \
+    cudaFuncSetAttribute(k_zsym_tma<R, N, zalt_r1<N, R1>(), N / zalt_r1<N, R1>(), true>,                   \
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ztma<R, N>());              \
+  }                                                                                                         \
   if (N <= 256) /* exactly its need: the kernel also holds static shared memory */                          \
     cudaFuncSetAttribute(k_zsym_tma<R, N, R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ztma<R, N>()); \
   if (N <= 256)                                                                                             \
@@ -1451,8 +1480,10 @@ void fft_z_symbol(const FftCtx<R>& f, double a, double b, const double* k0sum, d
 #define ICM_CASE(N, R1, R2)                                                                                            \
   case N:                                                                                                              \
     if (N <= 256) {                                                                                                    \
-      k_zsym_tma<R, N, R1, R2><<<grid, zsym2_threads<R, N, R1, R2>(), smem_ztma<R, N>(), st>>>(map, f.spec, tw, f.ny, \
-                                                                                           f.kx, f.kxp, kxz, sp, f.err, nullptr, 1); \
+      if (f.zalt)                                                                                                      \
+        launch_ztma<R, N, zalt_r1<N, R1>(), N / zalt_r1<N, R1>(), false>(grid, map, f.spec, tw, f, kxz, sp, nullptr, 1, st); \
+      else                                                                                                             \
+        launch_ztma<R, N, R1, R2, false>(grid, map, f.spec, tw, f, kxz, sp, nullptr, 1, st);                         \
       return;                                                                                                          \
     }                                                                                                                  \
     break;
@@ -1462,8 +1493,13 @@ void fft_z_symbol(const FftCtx<R>& f, double a, double b, const double* k0sum, d
     }
   }
   switch (f.nz) {
-#define ICM_CASE(N, R1, R2) \
-  case N: k_zsym2<R, N, R1, R2><<<dim3(kxz, f.ny), zplain_threads<R, N, R1, R2>(), smem_z2<R, N>(), st>>>(f.spec, tw, f.ny, f.kx, f.kxp, sp, nullptr); return;
+#define ICM_CASE(N, R1, R2)                                                                                     \
+  case N:                                                                                                       \
+    if (f.zalt)                                                                                                 \
+      launch_zplain<R, N, zalt_r1<N, R1>(), N / zalt_r1<N, R1>()>(dim3(kxz, f.ny), f.spec, tw, f, sp, nullptr, st); \
+    else                                                                                                        \
+      launch_zplain<R, N, R1, R2>(dim3(kxz, f.ny), f.spec, tw, f, sp, nullptr, st);                            \
+    return;
     ICM_FFT_SIDES(ICM_CASE)
 #undef ICM_CASE
     default: break;
@@ -1654,8 +1690,10 @@ void fft_yz_group(const FftCtx<R>& f, const RepFft* reps, int G, int which, cuda
 #define ICM_CASE(N, R1, R2)                                                                                            \
   case N:                                                                                                              \
     if (N <= 256) {                                                                                                    \
-      k_zsym_tma<R, N, R1, R2, true><<<grid, zsym2_threads<R, N, R1, R2>(), smem_ztma<R, N>(), st>>>(map, nullptr, twz, \
-                                                                             f.ny, f.kx, f.kxp, kxz, sp, f.err, reps, G); \
+      if (f.zalt)                                                                                                      \
+        launch_ztma<R, N, zalt_r1<N, R1>(), N / zalt_r1<N, R1>(), true>(grid, map, nullptr, twz, f, kxz, sp, reps, G, st); \
+      else                                                                                                             \
+        launch_ztma<R, N, R1, R2, true>(grid, map, nullptr, twz, f, kxz, sp, reps, G, st);                           \
       return;                                                                                                          \
     }                                                                                                                  \
     break;
@@ -1665,8 +1703,13 @@ void fft_yz_group(const FftCtx<R>& f, const RepFft* reps, int G, int which, cuda
       }
     }
     switch (f.nz) {
-#define ICM_CASE(N, R1, R2) \
-  case N: k_zsym2<R, N, R1, R2><<<dim3(kxz, f.ny, G), zplain_threads<R, N, R1, R2>(), smem_z2<R, N>(), st>>>(nullptr, twz, f.ny, f.kx, f.kxp, sp, reps); return;
+#define ICM_CASE(N, R1, R2)                                                                                     \
+  case N:                                                                                                       \
+    if (f.zalt)                                                                                                 \
+      launch_zplain<R, N, zalt_r1<N, R1>(), N / zalt_r1<N, R1>()>(dim3(kxz, f.ny, G), nullptr, twz, f, sp, reps, st); \
+    else                                                                                                        \
+      launch_zplain<R, N, R1, R2>(dim3(kxz, f.ny, G), nullptr, twz, f, sp, reps, st);                          \
+    return;
       ICM_FFT_SIDES(ICM_CASE)
 #undef ICM_CASE
       default: break;

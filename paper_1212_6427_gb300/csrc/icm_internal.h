@@ -33,6 +33,22 @@ inline bool fft_split(int n, int& r1, int& r2) {
   }
 }
 
+// The other two-stage split of a z side a plan may choose (plan z_split).  The z
+// transform is internal to the z pass, so its split changes only the kernel and the
+// storage order the z symbol tables follow.
+inline bool fft_split_z_alt(int n, int& r1, int& r2) {
+  switch (n) {
+    case 32: r1 = 4; r2 = 8; return true;
+    case 48: r1 = 12; r2 = 4; return true;
+    case 64: r1 = 16; r2 = 4; return true;
+    case 96: r1 = 8; r2 = 12; return true;
+    case 128: r1 = 8; r2 = 16; return true;
+    case 192: r1 = 12; r2 = 16; return true;
+    case 256: r1 = 32; r2 = 8; return true;
+    default: return false;
+  }
+}
+
 // One axis of the 3D FFT: a mixed-radix factorisation N = prod radix[s] with
 // in-place decimation-in-frequency stages.  The forward pass leaves frequency k
 // at storage position pos_of_freq[k]; the inverse pass takes that order back to
@@ -61,6 +77,7 @@ struct FftCtx {
   cplx_t<R>* spec;   // 3 * nz * ny * kxp complex scratch
   const void* zmap;  // host copy of the TMA descriptor of spec for the z pass (or null)
   int* err;          // device error bits (bounded waits report here)
+  int zalt;          // 1: the z pass uses the other split of fft_split_z_alt (pz, dz, ddz follow it)
 };
 
 // Fill `map` (a 128-byte CUtensorMap) with the descriptor the TMA z pass uses for a

@@ -19,12 +19,14 @@ def built():
 
 
 PLANS = [
-    dict(fused_blobs=1, tma_z=1, rhs_kz=16, fork=1, fused_xy=1),
-    dict(fused_blobs=0, tma_z=1, rhs_kz=16, fork=1, fused_xy=1),     # separate blob kernels on a fused-capable side
-    dict(fused_blobs=1, tma_z=0, rhs_kz=8, fork=0, fused_xy=0),      # one block per z tile, short RHS march
-    dict(fused_blobs=0, tma_z=0, rhs_kz=32, fork=0, fused_xy=0),
-    dict(fused_blobs=1, tma_z=1, rhs_kz=0, fork=1, fused_xy=0),      # persistent RHS blocks
-    dict(fused_blobs=1, tma_z=1, rhs_kz=4, fork=1, fused_xy=0),
+    dict(fused_blobs=1, tma_z=1, rhs_kz=16, fork=1, fused_xy=1, z_split=0),
+    dict(fused_blobs=0, tma_z=1, rhs_kz=16, fork=1, fused_xy=1, z_split=0),   # separate blob kernels, fused-capable side
+    dict(fused_blobs=1, tma_z=0, rhs_kz=8, fork=0, fused_xy=0, z_split=0),    # one block per z tile, short RHS march
+    dict(fused_blobs=0, tma_z=0, rhs_kz=32, fork=0, fused_xy=0, z_split=0),
+    dict(fused_blobs=1, tma_z=1, rhs_kz=0, fork=1, fused_xy=0, z_split=0),    # persistent RHS blocks
+    dict(fused_blobs=1, tma_z=1, rhs_kz=4, fork=1, fused_xy=0, z_split=0),
+    dict(fused_blobs=1, tma_z=1, rhs_kz=0, fork=1, fused_xy=0, z_split=1),    # the other z split, TMA z pass
+    dict(fused_blobs=1, tma_z=0, rhs_kz=16, fork=1, fused_xy=0, z_split=1),   # the other z split, plain z pass
 ]
 
 
@@ -39,7 +41,7 @@ def _case(grid, nb, seed):
 
 @pytest.mark.parametrize("precision", [64, 32])
 @pytest.mark.parametrize("plan", PLANS, ids=[str(i) for i in range(len(PLANS))])
-@pytest.mark.parametrize("grid", [(32, 32, 48), (24, 16, 64)])
+@pytest.mark.parametrize("grid", [(32, 32, 48), (24, 16, 64), (16, 24, 96), (16, 8, 256)])
 def test_every_plan_matches_the_oracle(precision, plan, grid):
     import paper_1212_6427_gb300 as icm
     prm, st = _case(grid, 10, 91)
