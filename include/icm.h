@@ -106,7 +106,8 @@ const char* icm_last_error(void);
  *                 (8 h^3 for the 3-point kernel), so that m~ = m_e + m~_f > 0
  *                 (Appendix A, Eq. rho_eff_inv_incomp).
  * New blobs get F = 0 and a zero lagged slip term (q^{-1/2} = q^0).
- * Errors: ICM_EINVAL (n < 0, NULL pos, non-finite input, excess mass out of range). */
+ * Errors: ICM_EINVAL (n < 0, NULL pos, non-finite input, excess mass out of range),
+ * ICM_EBUSY (queued reads pending: icm_read_finish them first). */
 icm_status icm_add_blobs(icm_sim* sim, int64_t n, const double* pos, const double* vel,
                          const double* excess_mass);
 
@@ -211,9 +212,9 @@ icm_status icm_read_state(icm_sim* sim, double* pos, double* vel, double* fluid_
  * may queue more steps (and forces) while the copy is in flight.  icm_read_finish waits for the oldest queued read and copies it
  * out (any pointer may be NULL); it returns the device errors raised before that read,
  * as icm_read_state would have (reporting one clears the device's error bits, including
- * bits of steps queued after the read).  The blob capacity must not change while reads
- * are pending.  Errors: icm_read_begin ICM_EINVAL when two reads are pending, ICM_ENOMEM
- * (staging buffer); icm_read_finish ICM_EINVAL when none is pending. */
+ * bits of steps queued after the read).  Blobs cannot be added while reads are pending.
+ * Errors: icm_read_begin ICM_EBUSY when two reads are pending, ICM_ENOMEM (staging
+ * buffers); icm_read_finish ICM_EINVAL when none is pending. */
 icm_status icm_read_begin(icm_sim* sim);
 icm_status icm_read_finish(icm_sim* sim, double* pos, double* vel, double momentum[3], int64_t* step);
 

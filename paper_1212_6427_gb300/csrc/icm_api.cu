@@ -849,7 +849,6 @@ icm_status ensure_dstage(icm_sim* s) {
     for (auto& e : s->ev_snap) ICM_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
   if (s->dfstage && s->dstage_cap == s->cap) return ICM_OK;
-  if (s->read_pending > 0) return fail(ICM_EINVAL, "blob capacity changed while reads are pending (icm_read_finish them first)");
   ICM_CK(cudaStreamSynchronize(s->stream));
   ICM_CK(cudaStreamSynchronize(s->copy));
   ICM_CK(cudaStreamSynchronize(s->copy_up));
@@ -874,7 +873,6 @@ double* read_slot(icm_sim* s, int slot) { return s->hstage + 3 * (size_t)s->cap 
 
 icm_status ensure_hstage(icm_sim* s) {
   if (s->hstage && s->hstage_cap == s->cap) return ICM_OK;
-  if (s->read_pending > 0) return fail(ICM_EINVAL, "blob capacity changed while reads are pending (icm_read_finish them first)");
   ICM_CK(cudaStreamSynchronize(s->stream));
   if (s->hstage) cudaFreeHost(s->hstage);
   s->hstage = nullptr;
@@ -1094,6 +1092,8 @@ icm_status icm_add_blobs(icm_sim* s, int64_t n, const double* pos, const double*
   if (!s) return fail(ICM_EINVAL, "NULL simulation");
   if (n < 0) return fail(ICM_EINVAL, "n must be >= 0");
   if (n == 0) return ICM_OK;
+  // a queued read returns the blobs that existed when it was queued
+  if (s->read_pending > 0) return fail(ICM_EBUSY, "reads are pending (icm_read_finish them first)");
   if (!pos || !excess_mass) return fail(ICM_EINVAL, "pos and excess_mass are required");
   if (!finite_all(pos, 3 * n) || !finite_all(excess_mass, n) || (vel && !finite_all(vel, 3 * n)))
     return fail(ICM_EINVAL, "non-finite blob input");
@@ -1366,7 +1366,7 @@ icm_status icm_read_state(icm_sim* s, double* pos, double* vel, double* fluid_v,
 // slot behind the queued work, and an event after them; no wait.
 icm_status icm_read_begin(icm_sim* s) {
   if (!s) return fail(ICM_EINVAL, "NULL simulation");
-  if (s->read_pending >= icm_sim::kReadSlots) return fail(ICM_EINVAL, "two reads are pending already");
+  if (s->read_pending >= icm_sim::kReadSlots) return fail(ICM_EBUSY, "two reads are pending already");
   icm_status st = ensure_hstage(s);
   if (st != ICM_OK) return st;
   if ((st = ensure_dstage(s)) != ICM_OK) return st;

@@ -220,9 +220,20 @@ def test_queued_reads_match_synchronous_reads(icm):
         queued.read_finish()
     queued.read_begin()
     queued.read_begin()
-    with pytest.raises(icm.IcmError):
+    with pytest.raises(icm.IcmError) as ei:
         queued.read_begin()
+    assert ei.value.status == icm.ICM_EBUSY
     queued.read_finish()
     queued.read_finish()
+    # no blobs are added while a read is pending (it returns the blobs it was queued with)
+    queued.read_begin()
+    extra = wl.random_sequential_addition(200, grid, 1.0, 0.5, 9)
+    with pytest.raises(icm.IcmError) as ei:
+        queued.add_blobs(extra, np.zeros((200, 3)), np.zeros(200))
+    assert ei.value.status == icm.ICM_EBUSY
+    assert queued.read_finish()["pos"].shape == (nb, 3)
+    queued.add_blobs(extra, np.zeros((200, 3)), np.zeros(200))   # staging grows at the next read
+    queued.read_begin()
+    assert queued.read_finish()["pos"].shape == (nb + 200, 3)
     for s in sims:
         s.close()
