@@ -385,7 +385,11 @@ icm_status icm_batch_step(icm_batch* batch, int64_t nsteps);
  * blob counts, through device tables of the members; about a dozen launches plus the
  * group solves per step.  Needs one precision for all members, register FFT passes
  * along every axis of every grid, and no WCA pair forces or thermal drift; otherwise
- * the batch runs as with grouped = 1.  Batched stages with the blob work in the group
+ * the batch runs as with grouped = 1.  Groups on z sides from 96 whose plan takes the
+ * tensor-map z pass put their members' spectra in one buffer of the batch (the members'
+ * own spectra stay unused meanwhile).  The batch's device tables and these buffers come
+ * from cudaMalloc, not from the members' allocator, and are freed at the next capture
+ * or by icm_batch_destroy.  Batched stages with the blob work in the group
  * x passes (grouped = 3): as 2, but where every member has blobs and a register x side
  * the spreads and interpolations run inside the x passes of the group solves, as in a
  * single simulation's fused step (row bins of all members in three launches; no
