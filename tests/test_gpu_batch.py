@@ -300,3 +300,42 @@ def test_batched_stages_fall_back_without_register_sides(icm):
     icm.icm_batch_destroy(b)
     for s in sims:
         s.close()
+
+
+@pytest.mark.parametrize("z_split", [0, 1])
+def test_batched_stages_tensor_map_group_matches_individual_runs(icm, z_split):
+    """Batched stages with a group on z side 96 (its members' spectra in one buffer, the
+    tensor-map z pass over all of them) beside a side-64 group, with either z split: each
+    member's result equals its run alone with the same plan."""
+    spec = [(96, 4, 9, 201), (96, 3, 5, 202), (64, 4, 7, 203), (64, 3, 4, 204)]
+    jobs = []
+    for side, kernel, nb, seed in spec:
+        cfg = dict(grid=(side, side, side), h=1.0, rho=1.0, eta=1.0, kT=1e-3, dt=0.05, kernel=kernel, seed=seed,
+                   precision=32, steps=4, nblobs=nb, me_range=(-0.5, 2.0), force=(1e-3, 0.0, -2e-3),
+                   place_seed=seed + 100, min_spacing=2.0)
+        j = wl._materialise(cfg)
+        j["trap"] = None
+        jobs.append(j)
+    plan = dict(fused_blobs=1, tma_z=1, rhs_kz=0, fork=1, fused_xy=0, z_split=z_split)
+    sims = [_make(icm, j, 32) for j in jobs]
+    for s in sims:
+        icm.icm_set_plan(s.handle, **plan)
+    b = icm.icm_batch_create()
+    icm.icm_batch_set(b, [s.handle for s in sims])
+    icm.icm_batch_set_grouped(b, 2)
+    icm.icm_batch_step(b, 4)
+    icm.icm_batch_sync(b)
+    for j, s in zip(jobs, sims):
+        got = s.read()
+        alone = _make(icm, j, 32)
+        icm.icm_set_plan(alone.handle, **plan)
+        alone.step(4)
+        want = alone.read()
+        alone.close()
+        assert got["step"] == 4
+        assert rel(got["vel"], want["vel"]) < TOL[32]
+        assert rel(got["pos"], want["pos"]) < TOL[32] * 1e-2
+        np.testing.assert_allclose(got["momentum"], want["momentum"], rtol=1e-9, atol=1e-12)
+    icm.icm_batch_destroy(b)
+    for s in sims:
+        s.close()
