@@ -1901,7 +1901,7 @@ icm_status batch_capture_stages(icm_batch* b) {
   // (members with noise first, then those without)
   std::vector<BlobMember> all, inert;
   std::vector<int> mof_all, mof_in;
-  long long ncell_in = 0;
+  std::vector<long long> zero_prefix{0};   // running 16-byte words of the inertial members' work
   for (icm_sim* s : b->sims) {
     BlobMember m;
     m.p = blob_params(s);
@@ -1920,7 +1920,7 @@ icm_status batch_capture_stages(icm_batch* b) {
       m.b0 = (long long)mof_in.size();
       for (long long i = 0; i < s->nb; ++i) mof_in.push_back((int)inert.size());
       inert.push_back(m);
-      ncell_in = std::max(ncell_in, s->ncell);
+      zero_prefix.push_back(zero_prefix.back() + 3 * s->ncell * (long long)sizeof(R) / 16);
     }
   }
   std::vector<RhsMember<R>> rhs_noise, rhs_quiet;
@@ -1950,7 +1950,8 @@ icm_status batch_capture_stages(icm_batch* b) {
   const size_t o_rq = o_rn + al(rhs_noise.size() * sizeof(RhsMember<R>));
   const size_t o_reps = o_rq + al(rhs_quiet.size() * sizeof(RhsMember<R>));
   const size_t o_rbs = o_reps + al(reps_host.size() * sizeof(RepFft));
-  const size_t total_bytes = o_rbs + al(rbs_host.size() * sizeof(RowBlobs)) + 256;
+  const size_t o_zp = o_rbs + al(rbs_host.size() * sizeof(RowBlobs));
+  const size_t total_bytes = o_zp + al(zero_prefix.size() * sizeof(long long)) + 256;
   ICM_CK(cudaMalloc(&b->stage_tables, total_bytes));
   unsigned char* base = (unsigned char*)b->stage_tables;
   for (size_t i = 0; i < rbs_host.size(); ++i) reps_host[i].rb = (const RowBlobs*)(base + o_rbs) + i;
@@ -1965,6 +1966,8 @@ icm_status batch_capture_stages(icm_batch* b) {
   ICM_CK(put(o_rq, rhs_quiet.data(), rhs_quiet.size() * sizeof(RhsMember<R>)));
   ICM_CK(put(o_reps, reps_host.data(), reps_host.size() * sizeof(RepFft)));
   ICM_CK(put(o_rbs, rbs_host.data(), rbs_host.size() * sizeof(RowBlobs)));
+  ICM_CK(put(o_zp, zero_prefix.data(), zero_prefix.size() * sizeof(long long)));
+  const long long* d_zp = (const long long*)(base + o_zp);
   const BlobMember* d_all = (const BlobMember*)(base + o_all);
   const BlobMember* d_in = (const BlobMember*)(base + o_in);
   const int* d_mall = (const int*)(base + o_mall);
@@ -2014,7 +2017,7 @@ icm_status batch_capture_stages(icm_batch* b) {
       batch_dp_from(d_in, d_min, nb_in, st);
     } else {
       batch_dp<R>(d_in, d_min, nb_in, st);
-      batch_zero_work<R>(d_in, n_in, ncell_in, st);
+      batch_zero_work(d_in, d_zp, n_in, zero_prefix.back(), st);
       batch_spread<R>(d_in, d_min, nb_in, BV_CDP, st);
     }
   }
@@ -2024,7 +2027,7 @@ icm_status batch_capture_stages(icm_batch* b) {
       batch_inertial_from(d_in, d_min, nb_in, st);
     } else {
       batch_inertial<R>(d_in, d_min, nb_in, st);
-      batch_zero_work<R>(d_in, n_in, ncell_in, st);
+      batch_zero_work(d_in, d_zp, n_in, zero_prefix.back(), st);
       batch_spread<R>(d_in, d_min, nb_in, BV_SRC, st);
     }
   }

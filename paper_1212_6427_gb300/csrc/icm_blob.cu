@@ -526,16 +526,21 @@ __global__ void __launch_bounds__(32 * kWarps) k_bfinish(const BlobMember* __res
 }
 #undef ICM_BATCH_SETUP
 
-// work = 0 over 3 ncell values of member blockIdx.y, in 16-byte stores (register FFT
-// sides are even, so 3 ncell R values are a whole number of 16-byte words).
-template <typename R>
-__global__ void k_bzero(const BlobMember* __restrict__ mem) {
-  const BlobMember& m = mem[blockIdx.y];
-  const long long n16 = 3 * m.p.ncell * (long long)sizeof(R) / 16;
-  float4* w = (float4*)m.work;
+// work = 0 for every member, in 16-byte stores over the members' concatenated work
+// fields (register FFT sides are even, so 3 ncell R values are a whole number of 16-byte
+// words): word i belongs to the member m with prefix[m] <= i < prefix[m + 1].
+__global__ void k_bzero(const BlobMember* __restrict__ mem, const long long* __restrict__ prefix, int nm,
+                        long long total) {
   const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n16; i += (long long)gridDim.x * blockDim.x)
-    w[i] = z;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    int a = 0, b = nm - 1;
+    while (a < b) {
+      const int c = (a + b + 1) / 2;
+      if (prefix[c] <= i) a = c; else b = c - 1;
+    }
+    reinterpret_cast<float4*>(mem[a].work)[i - prefix[a]] = z;
+  }
 }
 
 __global__ void k_bscal_before(const BlobMember* __restrict__ mem) {
@@ -902,12 +907,10 @@ template <typename R>
 void batch_finish(const BlobMember* m, const int* member_of, long long nbt, cudaStream_t st) {
   if (nbt > 0) k_bfinish<R><<<nblocks(nbt), 32 * kWarps, 0, st>>>(m, member_of, nbt);
 }
-template <typename R>
-void batch_zero_work(const BlobMember* m, int nm, long long ncell_max, cudaStream_t st) {
-  if (nm <= 0) return;
-  const long long n16 = 3 * ncell_max * (long long)sizeof(R) / 16;
-  const unsigned gx = (unsigned)std::min<long long>((n16 + 255) / 256, 1024);
-  k_bzero<R><<<dim3(std::max(gx, 1u), nm), 256, 0, st>>>(m);
+void batch_zero_work(const BlobMember* m, const long long* prefix16, int nm, long long total16, cudaStream_t st) {
+  if (nm <= 0 || total16 <= 0) return;
+  const unsigned g = (unsigned)std::min<long long>((total16 + 255) / 256, 4096);
+  k_bzero<<<g, 256, 0, st>>>(m, prefix16, nm, total16);
 }
 template <typename R>
 void batch_bins(const BlobMember* m, const int* member_of, long long nbt, int nm, cudaStream_t st) {
@@ -937,7 +940,6 @@ void batch_scalars_after(const BlobMember* m, int nm, cudaStream_t st) {
   template void batch_dp<R>(const BlobMember*, const int*, long long, cudaStream_t);                     \
   template void batch_inertial<R>(const BlobMember*, const int*, long long, cudaStream_t);               \
   template void batch_finish<R>(const BlobMember*, const int*, long long, cudaStream_t);                 \
-  template void batch_zero_work<R>(const BlobMember*, int, long long, cudaStream_t);                     \
   template void batch_bins<R>(const BlobMember*, const int*, long long, int, cudaStream_t);
 ICM_BINST(float)
 ICM_BINST(double)

@@ -349,7 +349,9 @@ template <typename R> void batch_dp(const BlobMember* m, const int* member_of, l
 template <typename R> void batch_inertial(const BlobMember* m, const int* member_of, long long nbt, cudaStream_t st);
 template <typename R> void batch_finish(const BlobMember* m, const int* member_of, long long nbt, cudaStream_t st);
 // work[0 .. 3 ncell) = 0 for every member (ncell_max: the largest member's cells)
-template <typename R> void batch_zero_work(const BlobMember* m, int nm, long long ncell_max, cudaStream_t st);
+// work = 0 for every member of m; prefix16 (device, nm + 1 entries) holds the running
+// sums of the members' work sizes in 16-byte words, total16 their sum.
+void batch_zero_work(const BlobMember* m, const long long* prefix16, int nm, long long total16, cudaStream_t st);
 void batch_scalars_before(const BlobMember* m, int nm, cudaStream_t st);
 void batch_scalars_after(const BlobMember* m, int nm, cudaStream_t st);
 
