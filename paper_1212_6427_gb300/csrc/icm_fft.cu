@@ -798,7 +798,6 @@ __global__ void __launch_bounds__(kThreads) k_ypass2(cplx_t<R>* __restrict__ spe
   C* buf = reinterpret_cast<C*>(smem_raw);   // [ZB][N][NL]
   C* tw = buf + ZB * N * NL;
   const int tid = threadIdx.x;
-  load_stage_twiddles<R, R1, R2>(tw, gtw, tid, kThreads);
   // The forward pass walks the spectrum backwards (last component, last z planes, last
   // columns first): the x pass before it wrote those last, so the first blocks find
   // them in L2.  The inverse pass walks forwards.
@@ -808,15 +807,23 @@ __global__ void __launch_bounds__(kThreads) k_ypass2(cplx_t<R>* __restrict__ spe
   // plane z0 + zb of the component, columns kx0..
   C* base0 = spec + ((size_t)(comp * nz + z0) * N) * kxp + kx0;
   const C zero = mk(R(0), R(0));
-  __syncthreads();
   if (!INV) {
-    for (int it = tid; it < ZB * R2 * NL; it += kThreads) {
+    // the loads of this thread's first item go out before the twiddle table is staged
+    // (whose barrier they would otherwise wait behind)
+    const auto load_item = [&](int it, C (&a)[R1]) {
       const int line = it % NL, rest = it / NL, n1 = rest % R2, zb = rest / R2;
       const bool ok = kx0 + line < kx && z0 + zb < nz;
       const C* base = base0 + (size_t)zb * N * kxp;
-      C a[R1];
 #pragma unroll
       for (int r = 0; r < R1; ++r) a[r] = ok ? base[(size_t)(n1 + R2 * r) * kxp + line] : zero;
+    };
+    C a[R1];
+    if (tid < ZB * R2 * NL) load_item(tid, a);
+    load_stage_twiddles<R, R1, R2>(tw, gtw, tid, kThreads);
+    __syncthreads();
+    for (int it = tid; it < ZB * R2 * NL; it += kThreads) {
+      const int line = it % NL, rest = it / NL, n1 = rest % R2, zb = rest / R2;
+      if (it != tid) load_item(it, a);
       stage_a_fwd<R, R1, R2>(a, tw + n1);
 #pragma unroll
       for (int k2 = 0; k2 < R1; ++k2) buf[(zb * N + n1 + R2 * k2) * NL + line] = a[k2];
@@ -834,6 +841,8 @@ __global__ void __launch_bounds__(kThreads) k_ypass2(cplx_t<R>* __restrict__ spe
       for (int k1 = 0; k1 < R2; ++k1) base[(size_t)(R2 * blk + k1) * kxp + line] = b[k1];
     }
   } else {
+    // the second stage comes first and needs no twiddles: its loads go out first, the
+    // table is staged after it, before the barrier the first stage waits at anyway
     for (int it = tid; it < ZB * R1 * NL; it += kThreads) {
       const int line = it % NL, rest = it / NL, blk = rest % R1, zb = rest / R1;
       const bool ok = kx0 + line < kx && z0 + zb < nz;
@@ -845,6 +854,7 @@ __global__ void __launch_bounds__(kThreads) k_ypass2(cplx_t<R>* __restrict__ spe
 #pragma unroll
       for (int n = 0; n < R2; ++n) buf[(zb * N + R2 * blk + n) * NL + line] = b[n];
     }
+    load_stage_twiddles<R, R1, R2>(tw, gtw, tid, kThreads);
     __syncthreads();
     for (int it = tid; it < ZB * R2 * NL; it += kThreads) {
       const int line = it % NL, rest = it / NL, n1 = rest % R2, zb = rest / R2;
