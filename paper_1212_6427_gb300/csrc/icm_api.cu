@@ -249,6 +249,7 @@ GridParams grid_params(const icm_sim* s) {
   g.h = s->h; g.rho = s->rho; g.eta = s->eta; g.kT = s->kT; g.dt = s->dt;
   g.key0 = (uint32_t)(s->seed & 0xffffffffu);
   g.key1 = (uint32_t)(s->seed >> 32);
+  g.rk = philox_round_keys(g.key0, g.key1);
   g.advection = s->advection ? 1 : 0;
   g.kz = s->plan.rhs_kz;
   return g;

@@ -50,6 +50,32 @@ __host__ __device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, uint32_t k0, ui
   return c;
 }
 
+// The ten round keys of one key (round r uses the key bumped r times), formed once so
+// that a kernel drawing many numbers reads them as constants instead of bumping the
+// key in every call.
+struct PhiloxRoundKeys { uint32_t k0[10], k1[10]; };
+inline PhiloxRoundKeys philox_round_keys(uint32_t k0, uint32_t k1) {
+  PhiloxRoundKeys rk;
+  for (int r = 0; r < 10; ++r) {
+    rk.k0[r] = k0;
+    rk.k1[r] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return rk;
+}
+__device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, const PhiloxRoundKeys& rk) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)M0 * c.x, p1 = (uint64_t)M1 * c.z;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    c = u32x4{hi1 ^ c.y ^ rk.k0[r], lo1, hi0 ^ c.w ^ rk.k1[r], lo0};
+  }
+  return c;
+}
+
 // Box-Muller: two 32-bit words -> two unit normals (cos branch, sin branch).
 // u = (x + 1/2) 2^-32 in (0, 1).
 template <typename R> struct BoxMuller;
@@ -89,6 +115,14 @@ template <typename R>
 __device__ __forceinline__ void cell_normals(uint32_t cell, uint32_t step, uint32_t k0, uint32_t k1, R z[6]) {
   const u32x4 a = philox4x32_10(u32x4{cell, step, 0u, 0u}, k0, k1);
   const u32x4 b = philox4x32_10(u32x4{cell, step, 1u, 0u}, k0, k1);
+  BoxMuller<R>::apply(a.x, a.y, z[0], z[1]);
+  BoxMuller<R>::apply(a.z, a.w, z[2], z[3]);
+  BoxMuller<R>::apply(b.x, b.y, z[4], z[5]);
+}
+template <typename R>
+__device__ __forceinline__ void cell_normals(uint32_t cell, uint32_t step, const PhiloxRoundKeys& rk, R z[6]) {
+  const u32x4 a = philox4x32_10(u32x4{cell, step, 0u, 0u}, rk);
+  const u32x4 b = philox4x32_10(u32x4{cell, step, 1u, 0u}, rk);
   BoxMuller<R>::apply(a.x, a.y, z[0], z[1]);
   BoxMuller<R>::apply(a.z, a.w, z[2], z[3]);
   BoxMuller<R>::apply(b.x, b.y, z[4], z[5]);

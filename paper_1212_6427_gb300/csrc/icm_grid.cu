@@ -91,11 +91,21 @@ __device__ __forceinline__ bool halo_task(int tau, HaloTask& t) {
   return true;
 }
 
+// Philox of the RHS: with RK the round keys of the kernel parameters (read as
+// constants), otherwise the key bumped in every call (parameters copied from memory).
+template <bool RK>
+__device__ __forceinline__ u32x4 rhs_philox(u32x4 c, const GridParams& g) {
+  if constexpr (RK)
+    return philox4x32_10(c, g.rk);
+  else
+    return philox4x32_10(c, g.key0, g.key1);
+}
+
 // Halo task t at flat cell index `cell` of its plane, into slot `slot` of the z ring.
-template <typename R>
+template <typename R, bool RK>
 __device__ __forceinline__ void gen_halo(RhsSmem<R>& sm, int slot, const HaloTask& t, uint32_t cell,
                                          const GridParams& g, uint32_t step) {
-  const u32x4 r = philox4x32_10(u32x4{cell, step, t.call, 0u}, g.key0, g.key1);
+  const u32x4 r = rhs_philox<RK>(u32x4{cell, step, t.call, 0u}, g);
   R c, sn;
   BoxMuller<R>::apply(t.hi ? r.z : r.x, t.hi ? r.w : r.y, c, sn);
   sm.z[slot][t.dst][t.hy][t.hx] = t.second ? sn : c;
@@ -103,10 +113,13 @@ __device__ __forceinline__ void gen_halo(RhsSmem<R>& sm, int slot, const HaloTas
 
 // The own cell's normals of plane kk into z[] (registers) and the five that neighbours
 // read into slot `slot` of the z ring.
-template <typename R>
+template <typename R, bool RK>
 __device__ __forceinline__ void gen_own(RhsSmem<R>& sm, int slot, R (&z)[6], uint32_t cell, const GridParams& g,
                                         uint32_t step, int lx, int ly) {
-  cell_normals<R>(cell, step, g.key0, g.key1, z);
+  if constexpr (RK)
+    cell_normals<R>(cell, step, g.rk, z);
+  else
+    cell_normals<R>(cell, step, g.key0, g.key1, z);
   sm.z[slot][0][ly][lx] = z[0];
   sm.z[slot][1][ly][lx] = z[1];
   sm.z[slot][2][ly][lx] = z[3];
@@ -114,16 +127,16 @@ __device__ __forceinline__ void gen_own(RhsSmem<R>& sm, int slot, R (&z)[6], uin
   sm.z[slot][4][ly][lx] = z[5];
 }
 
-// Marching block of TX x TY cells.  A block takes a contiguous range [lo, hi) of
-// tile-planes w = tile * nz + k (tiles x-fastest): with g.kz > 0 the range is the kz
-// planes of one tile (grid = tiles x ceil(nz / kz)); with g.kz == 0 the blocks are
-// persistent, the grid holds two per SM and the ranges split all tile-planes evenly.
-// A range is marched tile by tile; each run starts with a prologue of two planes.  Per
+// Marching block of TX x TY cells.  A block takes a contiguous range of planes: with
+// g.kz > 0 the kz planes of one tile (grid = tiles x ceil(nz / kz)); with g.kz == 0 the
+// blocks are persistent (about two per SM) in groups of one block per tile of a tile
+// row, and the groups split all tile-row planes evenly.  A range is marched tile by
+// tile; each run starts with a prologue of two planes.  Per
 // plane: the global loads of the plane after next are issued first, the stress normals
 // of the next plane are drawn while they are in flight, then the plane is computed from
 // the thread's registers (its own column) and shared memory (its neighbours).
 // One run of the marching block: planes k0 .. kend-1 of tile `tile` (tiles x-fastest).
-template <typename R, bool NOISE>
+template <typename R, bool NOISE, bool RK>
 __device__ __forceinline__ void rhs_run(RhsSmem<R>& sm, const R* __restrict__ v, R* __restrict__ adv,
                                         R* __restrict__ rhs, const GridParams& g, uint32_t step, bool hist,
                                         long long tile, int k0, int kend, int tx, int ty) {
@@ -189,10 +202,13 @@ __device__ __forceinline__ void rhs_run(RhsSmem<R>& sm, const R* __restrict__ v,
     load(vn, hq, k0 + 1);
     if (NOISE) {
       // plane k0-1: only the own cell's Z_zz is read; plane k0 into slot 1
-      cell_normals<R>(own + plane * (uint32_t)wrapi(k0 - 1, g.nz), step, g.key0, g.key1, zc);
+      if constexpr (RK)
+        cell_normals<R>(own + plane * (uint32_t)wrapi(k0 - 1, g.nz), step, g.rk, zc);
+      else
+        cell_normals<R>(own + plane * (uint32_t)wrapi(k0 - 1, g.nz), step, g.key0, g.key1, zc);
       zzp = zc[2];
-      gen_own<R>(sm, 1, zn, own + plane * (uint32_t)k0, g, step, lx, ly);
-      if (hnoise) gen_halo<R>(sm, 1, ht, ncell + plane * (uint32_t)k0, g, step);
+      gen_own<R, RK>(sm, 1, zn, own + plane * (uint32_t)k0, g, step, lx, ly);
+      if (hnoise) gen_halo<R, RK>(sm, 1, ht, ncell + plane * (uint32_t)k0, g, step);
     }
     for (int k = k0; k < kend; ++k) {
       const int kk = k - k0;
@@ -211,8 +227,8 @@ __device__ __forceinline__ void rhs_run(RhsSmem<R>& sm, const R* __restrict__ v,
 #pragma unroll
         for (int c = 0; c < 6; ++c) zc[c] = zn[c];
         const uint32_t pk = plane * (uint32_t)wrapi(k + 1, g.nz);
-        gen_own<R>(sm, zsn, zn, own + pk, g, step, lx, ly);
-        if (hnoise) gen_halo<R>(sm, zsn, ht, ncell + pk, g, step);
+        gen_own<R, RK>(sm, zsn, zn, own + pk, g, step, lx, ly);
+        if (hnoise) gen_halo<R, RK>(sm, zsn, ht, ncell + pk, g, step);
       }
       __syncthreads();
       if (active) {
@@ -284,10 +300,11 @@ __device__ __forceinline__ void rhs_run(RhsSmem<R>& sm, const R* __restrict__ v,
   }
 }
 
-// A block takes a contiguous range [lo, hi) of tile-planes w = tile * nz + k: with
-// g.kz > 0 the range is the kz planes of one tile (grid = tiles x ceil(nz / kz)); with
-// g.kz == 0 the blocks are persistent, the grid holds as many as the SMs do at once and
-// the ranges split all tile-planes evenly.  A range is marched tile by tile.
+// A block takes a contiguous range [lo, hi) of planes: with g.kz > 0 the kz planes
+// w = tile * nz + k of one tile (grid = tiles x ceil(nz / kz)); with g.kz == 0 the
+// blocks are persistent (whole groups of one block per tile of a tile row, as many as
+// the SMs hold at once) and a group's range is of tile-row planes u = row * nz + k, its
+// block xt marching tile xt of each row.  A range is marched tile by tile.
 template <typename R, bool NOISE>
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_rhs(const R* __restrict__ v, R* __restrict__ adv,
                                                                       R* __restrict__ rhs, GridParams g,
@@ -297,23 +314,31 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_rhs(const R* __r
   RhsSmem<R>& sm = *reinterpret_cast<RhsSmem<R>*>(smem_raw);
   const int ntx = (g.nx + TX - 1) / TX, nty = (g.ny + TY - 1) / TY;
   long long lo, hi;
+  int xt = 0;
   if (g.kz > 0) {
     const long long tile = blockIdx.x + (long long)ntx * blockIdx.y;
     lo = tile * g.nz + (long long)blockIdx.z * g.kz;
     hi = min(lo + g.kz, (tile + 1) * g.nz);
   } else {
-    const long long total = (long long)ntx * nty * g.nz;
-    lo = total * blockIdx.x / gridDim.x;
-    hi = total * (blockIdx.x + 1) / gridDim.x;
+    // Persistent blocks in groups of ntx, one block per tile of a tile row: the groups
+    // split the tile-row planes u = (tile row) nz + k evenly, and the blocks of a group
+    // march the same planes side by side, so the halo columns a block reads are rows its
+    // neighbours load at about the same time (found in L2, not fetched again).
+    const int ngrp = gridDim.x / ntx, grp = blockIdx.x / ntx;
+    xt = blockIdx.x - grp * ntx;
+    const long long total = (long long)nty * g.nz;
+    lo = total * grp / ngrp;
+    hi = total * (grp + 1) / ngrp;
   }
   const uint32_t step = (uint32_t)(*step_dev);
   const bool hist = *hist_dev != 0;
   for (long long w = lo; w < hi;) {
-    const long long tile = w / g.nz;
-    const int k0 = (int)(w - tile * g.nz);
+    const long long q = w / g.nz;   // the tile (fixed marches) or the tile row (groups)
+    const int k0 = (int)(w - q * g.nz);
     const int kend = (int)min((long long)g.nz, k0 + (hi - w));
     w += kend - k0;
-    rhs_run<R, NOISE>(sm, v, adv, rhs, g, step, hist, tile, k0, kend, threadIdx.x, threadIdx.y);
+    const long long tile = g.kz > 0 ? q : q * ntx + xt;
+    rhs_run<R, NOISE, true>(sm, v, adv, rhs, g, step, hist, tile, k0, kend, threadIdx.x, threadIdx.y);
   }
 }
 
@@ -344,7 +369,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_rhs_batch(const 
     const int k0 = (int)(lw - tile * g.nz);
     const int kend = (int)min((long long)g.nz, k0 + (end - w));
     w += kend - k0;
-    rhs_run<R, NOISE>(sm, m.v, m.adv, m.rhs, g, (uint32_t)(*m.step_dev), *m.hist_dev != 0, tile, k0, kend,
+    rhs_run<R, NOISE, false>(sm, m.v, m.adv, m.rhs, g, (uint32_t)(*m.step_dev), *m.hist_dev != 0, tile, k0, kend,
                       threadIdx.x, threadIdx.y);
   }
 }
@@ -480,8 +505,11 @@ void explicit_rhs(const GridParams& g, const R* v, R* adv, R* rhs, const long lo
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rhs<R, false>, NT, rhs_smem<R>());
       res = std::max(1, nsm) * std::max(1, per);
     }
-    const long long total = (long long)grid.x * grid.y * g.nz;
-    grid = dim3((unsigned)std::min<long long>(res, total), 1, 1);
+    // whole groups of grid.x blocks (one per tile of a tile row), never more groups
+    // than tile-row planes
+    const long long rows = (long long)grid.y * g.nz;
+    const long long ngrp = std::max<long long>(1, std::min<long long>(res / grid.x, rows));
+    grid = dim3((unsigned)(ngrp * grid.x), 1, 1);
   }
   if (g.kT > 0.0)
     k_rhs<R, true><<<grid, block, rhs_smem<R>(), st>>>(v, adv, rhs, g, step_dev, hist_dev);

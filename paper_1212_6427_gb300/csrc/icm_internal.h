@@ -148,6 +148,7 @@ struct GridParams {
   long long ncell;
   double h, rho, eta, kT, dt;
   uint32_t key0, key1;
+  PhiloxRoundKeys rk;   // the round keys of (key0, key1)
   int advection;
   int kz;           // z planes marched per block of the RHS kernel (>= 1)
 };
