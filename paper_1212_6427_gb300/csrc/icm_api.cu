@@ -607,12 +607,13 @@ void enqueue_step(icm_sim* s, Prof* prof, int segment = -1) {
       ICM_STAGE("inertial", nb * 168, blob_inertial_from(bp, bs, acc2, st));
       // step 6: (rho - dt/2 eta L) dv + dt grad dpi = S (dp - m_e J dv~); step 7: v = v~ + dv
       passes("rt3", nullptr, s->src, s->rho, 0.5 * s->dt * s->eta, s->scal + SC_SUMSRC, v, OUT_ADD, acc3, acc3l);
-      // step 9 and the lagged slip term: J v^{n+1} = J v~ + J dv
-      ICM_STAGE("finish", nb * 216, blob_finish_from(bp, bs, s->jvt, acc3, acc3l, true, st));
+      // step 9 and the lagged slip term: J v^{n+1} = J v~ + J dv; with the end-of-step
+      // scalars (the bookkeeping of scalars_after_step) in the same launch
+      ICM_STAGE("finish", nb * 216, blob_finish_from(bp, bs, s->jvt, acc3, acc3l, true, st, s->step_dev, s->hist_dev));
     } else {
-      ICM_STAGE("finish", nb * 144, blob_finish_from(bp, bs, nullptr, acc1, nullptr, false, st));
+      ICM_STAGE("finish", nb * 144,
+                blob_finish_from(bp, bs, nullptr, acc1, nullptr, false, st, s->step_dev, s->hist_dev));
     }
-    ICM_STAGE("scalars", 0, scalars_after_step(s->scal, s->dt, s->rho, dvf, s->any_me, s->step_dev, s->hist_dev, st));
     return;
   }
   if (fvec) ICM_STAGE("spread", 2 * gath + nb * 48, blob_spread<R>(bp, s->nb, s->qh, fvec, work, st));

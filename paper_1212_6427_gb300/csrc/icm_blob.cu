@@ -714,10 +714,22 @@ __device__ __forceinline__ void finish_from_one(const BlobParams& p, const BlobS
   if (fabs(u) * p.dt > p.h) atomicOr(s.err, DEV_ERR_CFL);
 }
 
+// With step_dev set, block 0 also closes the step's FP64 bookkeeping (the momentum
+// target P^{n+1} = K0 + the viscous correction's source sum, the time level and the
+// history flag), which reads nothing this kernel writes.
 __global__ void k_finish_from(BlobParams p, BlobState s, const double* __restrict__ base,
-                              const double* __restrict__ add, const double* __restrict__ g, int inertial) {
+                              const double* __restrict__ add, const double* __restrict__ g, int inertial,
+                              long long* __restrict__ step_dev, int* __restrict__ hist_dev) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i < 3 * s.nb) finish_from_one(p, s, base, add, g, inertial, i);
+  if (step_dev != nullptr && blockIdx.x == 0) {
+    const int a = threadIdx.x;
+    if (a < 3) s.scal[SC_PBAR + a] = s.scal[SC_K0 + a] + (inertial ? s.scal[SC_SUMSRC + a] : 0.0);
+    if (a == 0) {
+      *step_dev += 1;
+      *hist_dev = 1;
+    }
+  }
 }
 
 // The same over every member of a batch: one thread per blob (bins) or per blob
@@ -876,8 +888,9 @@ void blob_inertial_from(const BlobParams& p, BlobState s, const double* jdvt, cu
   if (s.nb > 0) k_inertial_from<<<eblocks(3 * s.nb), 256, 0, st>>>(p, s, jdvt);
 }
 void blob_finish_from(const BlobParams& p, BlobState s, const double* base, const double* add, const double* g,
-                      bool inertial, cudaStream_t st) {
-  if (s.nb > 0) k_finish_from<<<eblocks(3 * s.nb), 256, 0, st>>>(p, s, base, add, g, inertial ? 1 : 0);
+                      bool inertial, cudaStream_t st, long long* step_dev, int* hist_dev) {
+  if (s.nb > 0)
+    k_finish_from<<<eblocks(3 * s.nb), 256, 0, st>>>(p, s, base, add, g, inertial ? 1 : 0, step_dev, hist_dev);
 }
 
 #define ICM_KSWITCH(call3, call4) \

@@ -313,8 +313,10 @@ void blob_wca_forces(const BlobParams& p, BlobState s, const WcaParams& w, bool 
 void blob_dp_from(const BlobParams& p, BlobState s, const double* jvt, cudaStream_t st);
 void blob_inertial_from(const BlobParams& p, BlobState s, const double* jdvt, cudaStream_t st);
 // jv = base + add (base may be null): J^{n+1/2} v^{n+1}; g: J L dv without 1/h^2.
+// With step_dev (and hist_dev) the same launch also does the end-of-step bookkeeping of
+// scalars_after_step (inertial: the viscous correction's source sum enters P^{n+1}).
 void blob_finish_from(const BlobParams& p, BlobState s, const double* base, const double* add, const double* g,
-                      bool inertial, cudaStream_t st);
+                      bool inertial, cudaStream_t st, long long* step_dev = nullptr, int* hist_dev = nullptr);
 
 // ---------------------------------------------------------------------------
 // Stages launched once over every member of a batch (replica simulations of any grid;
