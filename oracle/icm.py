@@ -477,7 +477,8 @@ def explicit_rhs(v, adv_prev, step, prm):
     r = (prm.rho / prm.dt) * v + 0.5 * prm.eta * vector_laplacian(v, h)
     if prm.kT > 0.0:
         s = np.sqrt(prm.kT * prm.eta / (h ** 3 * prm.dt))
-        z = stress_normals(prm.seed, step, ncell)
+        nx, ny, _ = prm.grid
+        z = stress_normals(prm.seed, step, ncell, nx * ny)
         r = r + stochastic_flux_divergence(z, s, h, prm.shape)
     r = r - (1.5 * adv_n - 0.5 * adv_old)
     return r, adv_n

@@ -68,19 +68,29 @@ def box_muller(x1, x2):
     return rad * np.cos(ang), rad * np.sin(ang)
 
 
-def stress_normals(seed, step, ncell):
+def stress_normals(seed, step, ncell, plane):
     """The 6 unit normals of every cell for one step.
 
     Returns an array (6, ncell) ordered (Z_xx, Z_yy, Z_zz, Z_xy, Z_xz, Z_yz),
-    cell index = i + Nx (j + Ny k).
+    cell index = i + Nx (j + Ny k); plane = Nx Ny cells per z plane.
+
+    Counter layout (key = the seed's two 32-bit halves, counter word 1 = the step):
+    call 0 at (cell, step, 0, 0) gives (Z_xx, Z_yy) from words 0-1 and (Z_zz, Z_xy)
+    from words 2-3.  Call 1 at (cell of plane 2m, step, 1, 0) serves the two planes
+    2m and 2m + 1: words 0-1 give (Z_xz, Z_yz) of the cell in plane 2m, words 2-3 those
+    of the cell above it.  Every normal comes from its own pair of words, so all of
+    them are independent (Sec. III.B: W holds independent unit normals per cell and
+    step; which counter draws which entry is a free choice).
     """
     seed = int(seed)
     key = (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
-    lin = np.arange(ncell, dtype=np.uint64)
+    lin = np.arange(ncell, dtype=np.int64)
+    odd = (lin // int(plane)) % 2 == 1
+    below = (lin - np.where(odd, int(plane), 0)).astype(np.uint64)
     n = np.uint64(int(step) & 0xFFFFFFFF)
-    a0, a1, a2, a3 = philox4x32((lin, n, np.uint64(0), np.uint64(0)), key)
-    b0, b1, _, _ = philox4x32((lin, n, np.uint64(1), np.uint64(0)), key)
+    a0, a1, a2, a3 = philox4x32((lin.astype(np.uint64), n, np.uint64(0), np.uint64(0)), key)
+    b0, b1, b2, b3 = philox4x32((below, n, np.uint64(1), np.uint64(0)), key)
     zxx, zyy = box_muller(a0, a1)
     zzz, zxy = box_muller(a2, a3)
-    zxz, zyz = box_muller(b0, b1)
+    zxz, zyz = box_muller(np.where(odd, b2, b0), np.where(odd, b3, b1))
     return np.stack([zxx, zyy, zzz, zxy, zxz, zyz])

@@ -108,40 +108,24 @@ template <> struct BoxMuller<float> {
   }
 };
 
-// The 6 stress normals of one cell and step: (xx, yy, zz, xy, xz, yz).
-// Counter (cell, step, call, 0), key (seed_lo, seed_hi); call 0 gives xx,yy,zz,xy,
-// words 0-1 of call 1 give xz,yz.
-template <typename R>
-__device__ __forceinline__ void cell_normals(uint32_t cell, uint32_t step, uint32_t k0, uint32_t k1, R z[6]) {
-  const u32x4 a = philox4x32_10(u32x4{cell, step, 0u, 0u}, k0, k1);
-  const u32x4 b = philox4x32_10(u32x4{cell, step, 1u, 0u}, k0, k1);
-  BoxMuller<R>::apply(a.x, a.y, z[0], z[1]);
-  BoxMuller<R>::apply(a.z, a.w, z[2], z[3]);
-  BoxMuller<R>::apply(b.x, b.y, z[4], z[5]);
-}
-template <typename R>
-__device__ __forceinline__ void cell_normals(uint32_t cell, uint32_t step, const PhiloxRoundKeys& rk, R z[6]) {
-  const u32x4 a = philox4x32_10(u32x4{cell, step, 0u, 0u}, rk);
-  const u32x4 b = philox4x32_10(u32x4{cell, step, 1u, 0u}, rk);
-  BoxMuller<R>::apply(a.x, a.y, z[0], z[1]);
-  BoxMuller<R>::apply(a.z, a.w, z[2], z[3]);
-  BoxMuller<R>::apply(b.x, b.y, z[4], z[5]);
-}
+// The key as two words (the round keys formed in every call).
+struct PhiloxKey { uint32_t k0, k1; };
+__device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, PhiloxKey k) { return philox4x32_10(c, k.k0, k.k1); }
 
-// The same normals, computing only the Box-Muller pairs flagged: p00 -> (xx, yy),
-// p01 -> (zz, xy), p10 -> (xz, yz).  Entries of pairs not flagged are left unset.
-template <typename R>
-__device__ __forceinline__ void cell_normals_masked(uint32_t cell, uint32_t step, uint32_t k0, uint32_t k1, R z[6],
-                                                    bool p00, bool p01, bool p10) {
-  if (p00 || p01) {
-    const u32x4 a = philox4x32_10(u32x4{cell, step, 0u, 0u}, k0, k1);
-    if (p00) BoxMuller<R>::apply(a.x, a.y, z[0], z[1]);
-    if (p01) BoxMuller<R>::apply(a.z, a.w, z[2], z[3]);
-  }
-  if (p10) {
-    const u32x4 b = philox4x32_10(u32x4{cell, step, 1u, 0u}, k0, k1);
-    BoxMuller<R>::apply(b.x, b.y, z[4], z[5]);
-  }
+// The 6 stress normals of one cell and step: (xx, yy, zz, xy, xz, yz).  Counters
+// (cell, step, call, 0), key (seed_lo, seed_hi): call 0 of the cell gives xx, yy, zz,
+// xy; call 1 serves two z planes: at the cell of plane 2m its words 0-1 give xz, yz of
+// that cell, words 2-3 those of the cell above it (plane 2m + 1).  `odd`: the cell's
+// plane is odd (its call 1 is the one at cell - plane).  KEYS: PhiloxKey or
+// PhiloxRoundKeys.
+template <typename R, typename KEYS>
+__device__ __forceinline__ void cell_normals(uint32_t cell, uint32_t plane, bool odd, uint32_t step, const KEYS& key,
+                                             R z[6]) {
+  const u32x4 a = philox4x32_10(u32x4{cell, step, 0u, 0u}, key);
+  const u32x4 b = philox4x32_10(u32x4{odd ? cell - plane : cell, step, 1u, 0u}, key);
+  BoxMuller<R>::apply(a.x, a.y, z[0], z[1]);
+  BoxMuller<R>::apply(a.z, a.w, z[2], z[3]);
+  BoxMuller<R>::apply(odd ? b.z : b.x, odd ? b.w : b.y, z[4], z[5]);
 }
 
 // ---------------------------------------------------------------------------

@@ -101,25 +101,50 @@ __device__ __forceinline__ u32x4 rhs_philox(u32x4 c, const GridParams& g) {
     return philox4x32_10(c, g.key0, g.key1);
 }
 
-// Halo task t at flat cell index `cell` of its plane, into slot `slot` of the z ring.
+// Halo task t at flat cell index `cell` (plane `odd` or even) into slot `slot` of the z
+// ring.  Its call-1 normals (Z_xz, Z_yz) on an odd plane are words 2-3 of the call at
+// the cell one plane down (`plane` cells per plane).
 template <typename R, bool RK>
-__device__ __forceinline__ void gen_halo(RhsSmem<R>& sm, int slot, const HaloTask& t, uint32_t cell,
-                                         const GridParams& g, uint32_t step) {
-  const u32x4 r = rhs_philox<RK>(u32x4{cell, step, t.call, 0u}, g);
+__device__ __forceinline__ void gen_halo(RhsSmem<R>& sm, int slot, const HaloTask& t, uint32_t cell, uint32_t plane,
+                                         bool odd, const GridParams& g, uint32_t step) {
+  const bool up = t.call == 1u && odd;
+  const u32x4 r = rhs_philox<RK>(u32x4{up ? cell - plane : cell, step, t.call, 0u}, g);
+  const bool hi = t.hi || up;
   R c, sn;
-  BoxMuller<R>::apply(t.hi ? r.z : r.x, t.hi ? r.w : r.y, c, sn);
+  BoxMuller<R>::apply(hi ? r.z : r.x, hi ? r.w : r.y, c, sn);
   sm.z[slot][t.dst][t.hy][t.hx] = t.second ? sn : c;
 }
 
-// The own cell's normals of plane kk into z[] (registers) and the five that neighbours
-// read into slot `slot` of the z ring.
+// The own cell's normals of plane p (flat index `cell`) into z[] (registers) and the
+// five that neighbours read into slot `slot` of the z ring.  The call-1 words of an
+// even plane also hold the next plane's (Z_xz, Z_yz): kept in `next` (valid set) for
+// the odd plane that follows in the march; an odd plane without them draws that call
+// again at the cell below.
 template <typename R, bool RK>
-__device__ __forceinline__ void gen_own(RhsSmem<R>& sm, int slot, R (&z)[6], uint32_t cell, const GridParams& g,
-                                        uint32_t step, int lx, int ly) {
-  if constexpr (RK)
-    cell_normals<R>(cell, step, g.rk, z);
-  else
-    cell_normals<R>(cell, step, g.key0, g.key1, z);
+__device__ __forceinline__ void gen_own(RhsSmem<R>& sm, int slot, R (&z)[6], uint32_t cell, int p, uint32_t plane,
+                                        const GridParams& g, uint32_t step, int lx, int ly, uint32_t (&next)[2],
+                                        bool& valid) {
+  const u32x4 a = rhs_philox<RK>(u32x4{cell, step, 0u, 0u}, g);
+  BoxMuller<R>::apply(a.x, a.y, z[0], z[1]);
+  BoxMuller<R>::apply(a.z, a.w, z[2], z[3]);
+  uint32_t w0, w1;
+  if ((p & 1) == 0) {
+    const u32x4 b = rhs_philox<RK>(u32x4{cell, step, 1u, 0u}, g);
+    w0 = b.x;
+    w1 = b.y;
+    next[0] = b.z;
+    next[1] = b.w;
+    valid = true;
+  } else if (valid) {
+    w0 = next[0];
+    w1 = next[1];
+    valid = false;
+  } else {
+    const u32x4 b = rhs_philox<RK>(u32x4{cell - plane, step, 1u, 0u}, g);
+    w0 = b.z;
+    w1 = b.w;
+  }
+  BoxMuller<R>::apply(w0, w1, z[4], z[5]);
   sm.z[slot][0][ly][lx] = z[0];
   sm.z[slot][1][ly][lx] = z[1];
   sm.z[slot][2][ly][lx] = z[3];
@@ -200,15 +225,17 @@ __device__ __forceinline__ void rhs_run(RhsSmem<R>& sm, const R* __restrict__ v,
     load(vc, hq, k0);
     put(1, vc, hq);
     load(vn, hq, k0 + 1);
+    uint32_t next[2] = {0u, 0u};   // call-1 words of the plane after an even one
+    bool nvalid = false;
     if (NOISE) {
-      // plane k0-1: only the own cell's Z_zz is read; plane k0 into slot 1
-      if constexpr (RK)
-        cell_normals<R>(own + plane * (uint32_t)wrapi(k0 - 1, g.nz), step, g.rk, zc);
-      else
-        cell_normals<R>(own + plane * (uint32_t)wrapi(k0 - 1, g.nz), step, g.key0, g.key1, zc);
-      zzp = zc[2];
-      gen_own<R, RK>(sm, 1, zn, own + plane * (uint32_t)k0, g, step, lx, ly);
-      if (hnoise) gen_halo<R, RK>(sm, 1, ht, ncell + plane * (uint32_t)k0, g, step);
+      // plane k0-1: only the own cell's Z_zz is read (call 0); plane k0 into slot 1
+      {
+        const u32x4 a = rhs_philox<RK>(u32x4{own + plane * (uint32_t)wrapi(k0 - 1, g.nz), step, 0u, 0u}, g);
+        R zxy;
+        BoxMuller<R>::apply(a.z, a.w, zzp, zxy);
+      }
+      gen_own<R, RK>(sm, 1, zn, own + plane * (uint32_t)k0, k0, plane, g, step, lx, ly, next, nvalid);
+      if (hnoise) gen_halo<R, RK>(sm, 1, ht, ncell + plane * (uint32_t)k0, plane, (k0 & 1) != 0, g, step);
     }
     for (int k = k0; k < kend; ++k) {
       const int kk = k - k0;
@@ -226,9 +253,10 @@ __device__ __forceinline__ void rhs_run(RhsSmem<R>& sm, const R* __restrict__ v,
       if (NOISE) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) zc[c] = zn[c];
-        const uint32_t pk = plane * (uint32_t)wrapi(k + 1, g.nz);
-        gen_own<R, RK>(sm, zsn, zn, own + pk, g, step, lx, ly);
-        if (hnoise) gen_halo<R, RK>(sm, zsn, ht, ncell + pk, g, step);
+        const int p1 = wrapi(k + 1, g.nz);
+        const uint32_t pk = plane * (uint32_t)p1;
+        gen_own<R, RK>(sm, zsn, zn, own + pk, p1, plane, g, step, lx, ly, next, nvalid);
+        if (hnoise) gen_halo<R, RK>(sm, zsn, ht, ncell + pk, plane, (p1 & 1) != 0, g, step);
       }
       __syncthreads();
       if (active) {
@@ -379,7 +407,8 @@ __global__ void k_normals(GridParams g, uint32_t step, R* __restrict__ out) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= g.ncell) return;
   R z[6];
-  cell_normals<R>((uint32_t)c, step, g.key0, g.key1, z);
+  const uint32_t plane = (uint32_t)g.nx * (uint32_t)g.ny;
+  cell_normals<R>((uint32_t)c, plane, ((uint32_t)c / plane) & 1u, step, PhiloxKey{g.key0, g.key1}, z);
 #pragma unroll
   for (int a = 0; a < 6; ++a) out[a * g.ncell + c] = z[a];
 }

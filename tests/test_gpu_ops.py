@@ -52,7 +52,7 @@ def test_stress_normals(icm, precision):
     sim = _sim(icm, grid, precision, seed=(1 << 40) + 3)
     n = int(np.prod(grid))
     got = icm.icm_op_stress_normals(sim.handle, n, 11)
-    want = philox.stress_normals((1 << 40) + 3, 11, n)
+    want = philox.stress_normals((1 << 40) + 3, 11, n, grid[0] * grid[1])
     tol = 1e-14 if precision == 64 else 2e-6
     assert rel(got, want) < tol
     sim.close()

@@ -179,7 +179,8 @@ def test_philox_known_answers():
 
 
 def test_stress_normals_moments_and_independence():
-    z = philox.stress_normals(seed=77, step=3, ncell=200_000)
+    plane = 500   # 400 planes of 500 cells
+    z = philox.stress_normals(seed=77, step=3, ncell=200_000, plane=plane)
     assert z.shape == (6, 200_000)
     np.testing.assert_allclose(z.mean(axis=1), 0.0, atol=0.01)
     np.testing.assert_allclose(z.var(axis=1), 1.0, atol=0.01)
@@ -187,26 +188,39 @@ def test_stress_normals_moments_and_independence():
     assert np.abs(c - np.eye(6)).max() < 0.01
     # fourth moment of a unit normal is 3
     np.testing.assert_allclose((z ** 4).mean(axis=1), 3.0, atol=0.06)
+    # the off-diagonal normals of planes 2m and 2m + 1 (one Philox call) are uncorrelated
+    zz = z.reshape(6, 400, plane)
+    for a in (4, 5):
+        for b in (4, 5):
+            r = np.corrcoef(zz[a, 0::2].ravel(), zz[b, 1::2].ravel())[0, 1]
+            assert abs(r) < 0.01, (a, b, r)
     # a new step or seed gives new numbers
-    assert not np.allclose(z, philox.stress_normals(seed=77, step=4, ncell=200_000))
-    assert not np.allclose(z, philox.stress_normals(seed=78, step=3, ncell=200_000))
+    assert not np.allclose(z, philox.stress_normals(seed=77, step=4, ncell=200_000, plane=plane))
+    assert not np.allclose(z, philox.stress_normals(seed=78, step=3, ncell=200_000, plane=plane))
 
 
 def test_stress_normals_counter_layout():
     """The normals are Box-Muller pairs of the Philox words of the counters the layout
     names, recomputed here for single cells from the generator (pinned by the Random123
     known-answer vectors): call 0 at (cell, step, 0, 0) gives (Z_xx, Z_yy) and (Z_zz,
-    Z_xy); words 0-1 of call 1 at (cell, step, 1, 0) give (Z_xz, Z_yz)."""
-    ncell, seed, step = 5 * 4 * 7, (1 << 33) + 9, 21
-    z = philox.stress_normals(seed, step, ncell)
+    Z_xy); call 1 at (cell of plane 2m, step, 1, 0) gives (Z_xz, Z_yz) of that cell from
+    words 0-1 and of the cell above it (plane 2m + 1) from words 2-3.  Five planes of
+    4 x 5 cells: cells on even and odd planes and on the last, unpaired, plane."""
+    nx, ny, nz = 4, 5, 5
+    plane, ncell, seed, step = nx * ny, nx * ny * nz, (1 << 33) + 9, 21
+    z = philox.stress_normals(seed, step, ncell, plane)
     key = (seed & 0xFFFFFFFF, seed >> 32)
-    for cell in (0, 37, 81, 139):
+    for cell in (0, 3, 27, 39, 45, 61, 99):
+        k = cell // plane
         a = [int(w) for w in philox.philox4x32((cell, step, 0, 0), key)]
-        b = [int(w) for w in philox.philox4x32((cell, step, 1, 0), key)]
+        b = [int(w) for w in philox.philox4x32((cell - (k % 2) * plane, step, 1, 0), key)]
+        pair = b[2:4] if k % 2 else b[0:2]
         want = list(philox.box_muller(np.array([a[0]]), np.array([a[1]])))
         want += list(philox.box_muller(np.array([a[2]]), np.array([a[3]])))
-        want += list(philox.box_muller(np.array([b[0]]), np.array([b[1]])))
+        want += list(philox.box_muller(np.array([pair[0]]), np.array([pair[1]])))
         np.testing.assert_array_equal(z[:, cell], np.concatenate(want))
+    # the pairs of a call: plane 1's off-diagonal normals are not plane 0's
+    assert not np.allclose(z[4:, plane:2 * plane], z[4:, :plane])
 
 
 def test_box_muller_special_values():
@@ -218,6 +232,6 @@ def test_box_muller_special_values():
 
 def test_stochastic_flux_is_divergence_of_symmetric_stress():
     """Discrete Gauss theorem: the flux divergence sums to zero over the box."""
-    z = philox.stress_normals(seed=5, step=0, ncell=6 * 7 * 8)
+    z = philox.stress_normals(seed=5, step=0, ncell=6 * 7 * 8, plane=7 * 8)
     f = icm.stochastic_flux_divergence(z, 0.7, 0.5, (6, 7, 8))
     np.testing.assert_allclose(f.reshape(3, -1).sum(axis=1), 0.0, atol=1e-11)
