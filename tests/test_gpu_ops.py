@@ -110,13 +110,17 @@ def test_interpolate_spread_and_laplacian_gather(icm, precision, kernel, grid):
 
 
 @pytest.mark.parametrize("precision", [64, 32])
-@pytest.mark.parametrize("grid", [(16, 16, 16), (48, 24, 36), (9, 18, 8), (6, 8, 12), (96, 36, 12)])
+@pytest.mark.parametrize("grid", [(16, 16, 16), (48, 24, 36), (9, 18, 8), (6, 8, 12), (96, 36, 12), (24, 12, 9),
+                                  (72, 16, 27)])
 @pytest.mark.parametrize("kT,hist,adv", [(1e-3, True, True), (0.0, False, True), (2e-3, True, False)])
 def test_explicit_rhs(icm, precision, grid, kT, hist, adv):
     """The right-hand side against the oracle with fixed z marches (4 and 16 planes per
     block) and persistent blocks (rhs_kz = 0); the three launch shapes run the same
     arithmetic, so their results agree bit for bit.  Tiles of 32 x 16 cells are wider
-    than the short sides here (several periodic wraps per tile) and ragged on the others."""
+    than the short sides here (several periodic wraps per tile) and ragged on the others.
+    Odd Nz: the last plane's off-diagonal normals come from an unpaired Philox call and
+    the march wraps from it to plane 0; marches start on odd planes (whose call is the
+    one of the plane below)."""
     sim = _sim(icm, grid, precision, kernel=3, kT=kT, flags=0 if adv else 0x1, seed=99)
     nx, ny, nz = grid
     rng = np.random.default_rng(3)
