@@ -344,7 +344,11 @@ icm_status icm_op_explicit_rhs(icm_sim* sim, const double* fluid_v, const double
                                int64_t step, double* out_rhs, double* out_adv);
 
 /* The 6 unit normals per cell of step `step` (Sec. III.B.2: W^n), ordered
- * (xx, yy, zz, xy, xz, yz), out[6*N]. */
+ * (xx, yy, zz, xy, xz, yz), out[6*N] (component-major, cell i + Nx (j + Ny k)).
+ * Philox4x32-10, key = the seed's two 32-bit halves, counter (cell, step, call, 0):
+ * call 0 of a cell gives xx, yy (words 0-1) and zz, xy (words 2-3); call 1 at the
+ * cell of plane k = 2m gives its xz, yz (words 0-1) and those of the cell above it,
+ * plane 2m + 1 (words 2-3); unit normals by Box-Muller from u = (word + 1/2) 2^-32. */
 icm_status icm_op_stress_normals(icm_sim* sim, int64_t step, double* out);
 
 /* Raw Philox4x32-10 words: for i < n, counter (ctr0 + i, ctr1, ctr2, ctr3) and
